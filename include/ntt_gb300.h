@@ -1,0 +1,152 @@
+/*
+ * ntt_gb300.h -- C ABI of the batched negacyclic NTT library (sm_103a).
+ *
+ * What the library computes (arxiv 2410.05934, Sec. II-D, Eq. 1): for
+ * polynomials of R_q = Z_q[x]/(x^N + 1) held in RNS form (one row of N
+ * uint64 coefficients per (polynomial, modulus) pair),
+ *
+ *   forward  NTT_{no->bo}^{CT,psi}:  A[j] = sum_i a[i] psi^(i (2 brv(j) + 1))  mod q
+ *   inverse  INTT_{bo->no}^{GS,psi^-1}: a[i] = N^-1 sum_j A[j] psi^(-i (2 brv(j) + 1))  mod q
+ *   pointwise (the (.) of Eq. 1):    c[j] = a[j] b[j] mod q
+ *
+ * so that INTT(NTT(a) (.) NTT(b)) = a b mod (x^N + 1, q).  psi is the
+ * primitive 2N-th root of unity required by Eq. 1; the library fixes it as
+ * psi = g^((q-1)/2N) with g the least quadratic non-residue mod q (the paper
+ * leaves the choice open; any fixed choice permutes nothing else).
+ * Forward outputs are in bit-reversed order (the CT no->bo form of Eq. 1),
+ * inverse outputs in natural order.  All results are canonical in [0, q)
+ * and bit-exact: there is no approximation anywhere.
+ *
+ * Conventions shared by every entry point:
+ *  - Return 0 on success or a negative NTT_ERR_* code; ntt_strerror() names it.
+ *  - Device pointers are caller-owned CUDA device memory, 16-byte aligned.
+ *    Calls are asynchronous on the given stream (a cudaStream_t passed as
+ *    void*, NULL = legacy default stream).  Launch errors are returned at
+ *    once; errors detected inside kernels are read with ntt_status().
+ *  - Inputs must be canonical (< q of their row); with NTT_FLAG_CHECK the
+ *    kernels verify this and report NTT_ERR_RANGE through ntt_status().
+ *  - Data layout: [batch][n_moduli][N] uint64, row r = b * n_moduli + l uses
+ *    modulus l.  in == out is allowed (in-place); other overlap is not.
+ *  - A plan owns its twiddle tables (device memory) and is immutable after
+ *    creation except for its schedule and status word; do not destroy a plan
+ *    while work using it is in flight or while another thread uses it.
+ */
+#ifndef NTT_GB300_H
+#define NTT_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ---- */
+#define NTT_OK                    0
+#define NTT_ERR_ARG              -1  /* bad size, null pointer, bad flag, bad index   */
+#define NTT_ERR_NOT_PRIME        -2  /* a modulus failed the primality test           */
+#define NTT_ERR_NOT_NTT_FRIENDLY -3  /* a modulus is not 1 mod 2N                     */
+#define NTT_ERR_MODULUS_TOO_LARGE -4 /* a modulus is >= 2^62                          */
+#define NTT_ERR_ALIGN            -5  /* a device pointer is not 16-byte aligned       */
+#define NTT_ERR_CUDA             -6  /* a CUDA runtime call failed                    */
+#define NTT_ERR_TIMEOUT          -7  /* a bounded device-side wait ran out            */
+#define NTT_ERR_RANGE            -8  /* NTT_FLAG_CHECK found an input >= q            */
+#define NTT_ERR_NOMEM            -9  /* host or device allocation failed              */
+#define NTT_ERR_UNSUPPORTED      -10 /* schedule not available for this shape         */
+
+/* ---- plan flags ---- */
+#define NTT_FLAG_HOST_ONLY  1u  /* build and validate on the host only: no device
+                                   memory, compute entry points return NTT_ERR_ARG */
+#define NTT_FLAG_CHECK      2u  /* kernels check inputs < q (status word)          */
+
+#define NTT_MIN_LOG2N 1
+#define NTT_MAX_LOG2N 16
+#define NTT_MAX_MODULUS_BITS 62
+
+typedef struct ntt_plan_s* ntt_plan_t;
+
+/*
+ * ntt_plan -- validate (N = 2^log2n, moduli[0..n_moduli), batch) and build
+ * the twiddle tables of Sec. II-D (powers of psi in bit-reversed order, in
+ * Shoup form w' = floor(w 2^64 / q)), then copy them to the current device.
+ *   log2n     in [NTT_MIN_LOG2N, NTT_MAX_LOG2N]
+ *   moduli    host array, each a prime q < 2^62 with q = 1 mod 2N
+ *   n_moduli  >= 1;  batch >= 1;  batch * n_moduli * N < 2^40
+ *   flags     NTT_FLAG_*
+ * On success *out receives a plan the caller releases with ntt_plan_destroy.
+ * Errors: ARG, NOT_PRIME, NOT_NTT_FRIENDLY, MODULUS_TOO_LARGE, NOMEM, CUDA.
+ */
+int ntt_plan(ntt_plan_t* out, uint32_t log2n, const uint64_t* moduli, uint32_t n_moduli,
+             uint32_t batch, uint32_t flags);
+int ntt_plan_destroy(ntt_plan_t plan);
+
+/* psi of modulus `limb` (the root every transform of this plan uses). */
+int ntt_plan_root(ntt_plan_t plan, uint32_t limb, uint64_t* psi);
+
+/* Shape queries: N, n_moduli, batch, and rows = batch * n_moduli. */
+int ntt_plan_shape(ntt_plan_t plan, uint32_t* log2n, uint32_t* n_moduli, uint32_t* batch,
+                   uint64_t* rows);
+
+/*
+ * Forward NTT (CT, natural -> bit-reversed, Sec. II-D Eq. 1) of all
+ * batch * n_moduli rows: d_in -> d_out (may alias).  The inverse is the GS
+ * bit-reversed -> natural transform with psi^-1, scaled by N^-1, so that
+ * ntt_inverse(ntt_forward(a)) = a.
+ */
+int ntt_forward(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, void* cuda_stream);
+int ntt_inverse(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, void* cuda_stream);
+
+/*
+ * Row-range variants: transform rows [row_begin, row_begin + n_rows) of the
+ * plan's layout; d_in / d_out point at the FIRST ROW OF THE PLAN (row 0), so
+ * a multi-device caller can give each device a disjoint range of one buffer
+ * layout.  Errors: ARG when the range leaves [0, rows).
+ */
+int ntt_forward_rows(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, uint64_t row_begin,
+                     uint64_t n_rows, void* cuda_stream);
+int ntt_inverse_rows(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, uint64_t row_begin,
+                     uint64_t n_rows, void* cuda_stream);
+
+/*
+ * Pointwise product (the (.) of Eq. 1): d_c[r][j] = d_a[r][j] * d_b[r][j]
+ * mod q_l(r) over n_polys * n_moduli rows (n_polys = 0 means the plan's
+ * batch).  Row r uses modulus r mod n_moduli.  d_c may alias d_a or d_b.
+ */
+int poly_mul_pointwise(ntt_plan_t plan, const uint64_t* d_a, const uint64_t* d_b, uint64_t* d_c,
+                       uint32_t n_polys, void* cuda_stream);
+
+/*
+ * Schedules (Sec. V-D: the split of the log2 N stages into fused groups and
+ * kernel passes, threads per polynomial, polynomials per CTA).  Each N has a
+ * small fixed list of candidate schedules; ntt_plan picks a default, an
+ * autotuner or cost model may override it.  Bit-exact results do not depend
+ * on the schedule.
+ *   ntt_schedule_count(log2n)              -> number of candidates (>= 1)
+ *   ntt_schedule_name(log2n, id, buf, len) -> human-readable description
+ *   ntt_plan_set_schedule / get_schedule   -> choose / read the plan's choice
+ */
+int ntt_schedule_count(uint32_t log2n);
+int ntt_schedule_name(uint32_t log2n, uint32_t id, char* buf, size_t len);
+int ntt_plan_set_schedule(ntt_plan_t plan, uint32_t id);
+int ntt_plan_get_schedule(ntt_plan_t plan, uint32_t* id);
+
+/*
+ * Device status word of the plan: 0 or the first NTT_ERR_* a kernel recorded
+ * (RANGE under NTT_FLAG_CHECK, TIMEOUT from a bounded wait).  Synchronises
+ * `cuda_stream`, returns the status and clears it.
+ */
+int ntt_status(ntt_plan_t plan, void* cuda_stream);
+
+/* Number of kernel launches the most recent call on this plan issued. */
+int ntt_plan_last_launches(ntt_plan_t plan, uint32_t* launches);
+
+const char* ntt_strerror(int code);
+
+/* Library version string ("ntt_gb300 <major>.<minor> sm_103a"). */
+const char* ntt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NTT_GB300_H */

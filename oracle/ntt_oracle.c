@@ -177,6 +177,21 @@ void oracle_negacyclic_schoolbook(const uint64_t* a, const uint64_t* b, uint64_t
     }
 }
 
+/* Selected coefficients c_k (k in idx) of a * b mod (x^N + 1, q), each from
+ * its O(N) defining sum: c_k = sum_{i<=k} a_i b_{k-i} - sum_{i>k} a_i b_{N+k-i}. */
+void oracle_negacyclic_schoolbook_at(const uint64_t* a, const uint64_t* b, uint32_t log2n, uint64_t q,
+                                     const uint32_t* idx, uint32_t n_idx, uint64_t* out) {
+    uint64_t n = (uint64_t)1 << log2n;
+    for (uint32_t t = 0; t < n_idx; t++) {
+        uint64_t k = idx[t], acc = 0;
+        for (uint64_t i = 0; i < n; i++) {
+            if (i <= k) acc = oracle_addmod(acc, oracle_mulmod(a[i] % q, b[k - i] % q, q), q);
+            else        acc = oracle_submod(acc, oracle_mulmod(a[i] % q, b[n + k - i] % q, q), q);
+        }
+        out[t] = acc;
+    }
+}
+
 /* ---- many rows over host threads (rows are independent) ---- */
 
 typedef struct {

@@ -45,6 +45,8 @@ def bind(path):
     L.oracle_pointwise.argtypes = [U64P, U64P, U64P, u64, u64]
     L.oracle_negacyclic_schoolbook.restype = None
     L.oracle_negacyclic_schoolbook.argtypes = [U64P, U64P, U64P, u32, u64]
+    L.oracle_negacyclic_schoolbook_at.restype = None
+    L.oracle_negacyclic_schoolbook_at.argtypes = [U64P, U64P, u32, u64, U32P, u32, U64P]
     L.oracle_transform_rows.restype = i32
     L.oracle_transform_rows.argtypes = [i32, U64P, U64P, u32, u32, U64P, U64P, U32P, u32, i32]
     L.oracle_transform_rows_split.restype = i32
@@ -141,6 +143,17 @@ def schoolbook(a, b, q):
     c = np.zeros(a.size, dtype=np.uint64)
     lib().oracle_negacyclic_schoolbook(ap, bp, c.ctypes.data_as(U64P), log2n, q)
     return c
+
+
+def schoolbook_at(a, b, q, idx):
+    """Coefficients idx of a*b mod (x^N + 1, q), each by its O(N) sum."""
+    a, ap = _u64(a)
+    b, bp = _u64(b)
+    idx, ip = _u32(idx)
+    log2n = int(a.size).bit_length() - 1
+    out = np.zeros(idx.size, dtype=np.uint64)
+    lib().oracle_negacyclic_schoolbook_at(ap, bp, log2n, q, ip, idx.size, out.ctypes.data_as(U64P))
+    return out
 
 
 # ---- many rows -------------------------------------------------------------

@@ -1,0 +1,297 @@
+// C ABI of the NTT library (declared in include/ntt_gb300.h): argument
+// checks, plan lifetime, schedule table and dispatch to the kernel launchers.
+// Host code only; the kernels live in kernels_*.cu.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "ntt_gb300.h"
+#include "ntt_internal.h"
+#include "ntt_launch.h"
+#include "ntt_schedules.h"
+
+namespace nttgb {
+
+// ---- schedule table (order = NTT_SCHEDULES_ALL) ----
+struct SchedParams {
+    int kind;       // 1 = single kernel, 2 = column + row kernels
+    int v[9];
+};
+
+#define NTT_ENTRY_S1(LOGN, LOGT, LOGRP, TPC) \
+    {LOGN, 1, nullptr, &launch_s1<LOGN, LOGT, LOGRP, TPC, false>, &launch_s1<LOGN, LOGT, LOGRP, TPC, true>},
+#define NTT_ENTRY_S2(LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB)             \
+    {LOGN, 2, nullptr,                                                                       \
+     &launch_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, false>,          \
+     &launch_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, true>},
+static const SchedEntry g_table[] = {NTT_SCHEDULES_ALL(NTT_ENTRY_S1, NTT_ENTRY_S2)};
+
+#define NTT_PARAM_S1(LOGN, LOGT, LOGRP, TPC) {1, {LOGN, LOGT, LOGRP, TPC, 0, 0, 0, 0, 0}},
+#define NTT_PARAM_S2(LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB) \
+    {2, {LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB}},
+static const SchedParams g_params[] = {NTT_SCHEDULES_ALL(NTT_PARAM_S1, NTT_PARAM_S2)};
+
+static const int g_count = (int)(sizeof(g_table) / sizeof(g_table[0]));
+
+const SchedEntry* sched_table(int* count) {
+    if (count) *count = g_count;
+    return g_table;
+}
+
+static int sched_index(uint32_t log2n, uint32_t id) {
+    uint32_t seen = 0;
+    for (int i = 0; i < g_count; ++i) {
+        if (g_table[i].log2n != log2n) continue;
+        if (seen == id) return i;
+        ++seen;
+    }
+    return -1;
+}
+
+int schedule_count(uint32_t log2n) {
+    int c = 0;
+    for (int i = 0; i < g_count; ++i) c += g_table[i].log2n == log2n;
+    return c;
+}
+
+static void sched_describe(int i, char* buf, size_t len) {
+    const SchedParams& s = g_params[i];
+    const int* v = s.v;
+    if (s.kind == 1) {
+        int r = v[0] - v[1];
+        snprintf(buf, len, "1k: %d thr/row x %d coef, <=%d fused stages/pass, %d rows/CTA",
+                 1 << v[1], 1 << r, v[2], v[3]);
+    } else {
+        int ra = v[1] + v[2] - v[3], rb = (v[0] - v[1]) - v[6];
+        snprintf(buf, len,
+                 "2k split %d+%d: col tile 2^%dx%d (%d thr x %d coef, <=%d/pass, %d/CTA); "
+                 "row tile 2^%d (%d thr x %d coef, <=%d/pass, %d/CTA)",
+                 v[1], v[0] - v[1], v[1], 1 << v[2], 1 << v[3], 1 << ra, v[4], v[5], v[0] - v[1],
+                 1 << v[6], 1 << rb, v[7], v[8]);
+    }
+}
+
+// Default choice before any tuning: the first candidate of each N (the
+// lists put the widest-radix register layout first).
+uint32_t default_schedule(uint32_t log2n, uint64_t rows) {
+    (void)log2n;
+    (void)rows;
+    return 0;
+}
+
+static PlanDev plan_dev(const ntt_plan_s* p) {
+    PlanDev d;
+    d.fwd = p->d_fwd;
+    d.inv = p->d_inv;
+    d.lc = p->d_consts;
+    d.status = p->d_status;
+    d.n_moduli = p->h.n_moduli;
+    d.check = (p->h.flags & NTT_FLAG_CHECK) ? 1u : 0u;
+    return d;
+}
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+static int check_device(const ntt_plan_s* p) {
+    if (p->h.flags & NTT_FLAG_HOST_ONLY) return NTT_ERR_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return NTT_ERR_CUDA;
+    return dev == p->device ? NTT_OK : NTT_ERR_ARG;
+}
+
+static int transform(ntt_plan_t plan, bool inverse, const uint64_t* in, uint64_t* out,
+                     uint64_t row_begin, uint64_t n_rows, void* stream) {
+    if (!plan || !in || !out) return NTT_ERR_ARG;
+    if (!aligned16(in) || !aligned16(out)) return NTT_ERR_ALIGN;
+    if (row_begin > plan->h.rows || n_rows > plan->h.rows - row_begin) return NTT_ERR_ARG;
+    int rc = check_device(plan);
+    if (rc) return rc;
+    int idx = sched_index(plan->h.log2n, plan->schedule);
+    if (idx < 0) return NTT_ERR_UNSUPPORTED;
+    plan->last_launches = 0;
+    if (n_rows == 0) return NTT_OK;
+    PlanDev d = plan_dev(plan);
+    const SchedEntry& e = g_table[idx];
+    return (inverse ? e.inv : e.fwd)(d, in, out, row_begin, n_rows, stream, &plan->last_launches);
+}
+
+static void free_device(ntt_plan_s* p) {
+    if (p->d_fwd) cudaFree(p->d_fwd);
+    if (p->d_inv) cudaFree(p->d_inv);
+    if (p->d_consts) cudaFree(p->d_consts);
+    if (p->d_status) cudaFree(p->d_status);
+    p->d_fwd = p->d_inv = nullptr;
+    p->d_consts = nullptr;
+    p->d_status = nullptr;
+}
+
+}  // namespace nttgb
+
+using namespace nttgb;
+
+extern "C" {
+
+int ntt_plan(ntt_plan_t* out, uint32_t log2n, const uint64_t* moduli, uint32_t n_moduli,
+             uint32_t batch, uint32_t flags) {
+    if (!out) return NTT_ERR_ARG;
+    *out = nullptr;
+    ntt_plan_s* p = new (std::nothrow) ntt_plan_s();
+    if (!p) return NTT_ERR_NOMEM;
+    int rc;
+    try {
+        rc = build_plan_host(p->h, log2n, moduli, n_moduli, batch, flags);
+    } catch (const std::bad_alloc&) {
+        rc = NTT_ERR_NOMEM;
+    }
+    if (rc) {
+        delete p;
+        return rc;
+    }
+    p->schedule = default_schedule(log2n, p->h.rows);
+    if (!(flags & NTT_FLAG_HOST_ONLY)) {
+        const size_t tw_bytes = p->h.fwd.size() * sizeof(TwPair);
+        const size_t lc_bytes = p->h.consts.size() * sizeof(LimbConst);
+        bool ok = cudaGetDevice(&p->device) == cudaSuccess &&
+                  cudaMalloc(&p->d_fwd, tw_bytes) == cudaSuccess &&
+                  cudaMalloc(&p->d_inv, tw_bytes) == cudaSuccess &&
+                  cudaMalloc(&p->d_consts, lc_bytes) == cudaSuccess &&
+                  cudaMalloc(&p->d_status, sizeof(int)) == cudaSuccess &&
+                  cudaMemcpy(p->d_fwd, p->h.fwd.data(), tw_bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(p->d_inv, p->h.inv.data(), tw_bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(p->d_consts, p->h.consts.data(), lc_bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemset(p->d_status, 0, sizeof(int)) == cudaSuccess;
+        if (!ok) {
+            free_device(p);
+            delete p;
+            cudaGetLastError();
+            return NTT_ERR_CUDA;
+        }
+        // the device copies are authoritative; drop the host tables
+        std::vector<TwPair>().swap(p->h.fwd);
+        std::vector<TwPair>().swap(p->h.inv);
+    }
+    *out = p;
+    return NTT_OK;
+}
+
+int ntt_plan_destroy(ntt_plan_t plan) {
+    if (!plan) return NTT_ERR_ARG;
+    free_device(plan);
+    delete plan;
+    return NTT_OK;
+}
+
+int ntt_plan_root(ntt_plan_t plan, uint32_t limb, uint64_t* psi) {
+    if (!plan || !psi || limb >= plan->h.n_moduli) return NTT_ERR_ARG;
+    *psi = plan->h.psi[limb];
+    return NTT_OK;
+}
+
+int ntt_plan_shape(ntt_plan_t plan, uint32_t* log2n, uint32_t* n_moduli, uint32_t* batch,
+                   uint64_t* rows) {
+    if (!plan) return NTT_ERR_ARG;
+    if (log2n) *log2n = plan->h.log2n;
+    if (n_moduli) *n_moduli = plan->h.n_moduli;
+    if (batch) *batch = plan->h.batch;
+    if (rows) *rows = plan->h.rows;
+    return NTT_OK;
+}
+
+int ntt_forward(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, void* cuda_stream) {
+    return transform(plan, false, d_in, d_out, 0, plan ? plan->h.rows : 0, cuda_stream);
+}
+
+int ntt_inverse(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, void* cuda_stream) {
+    return transform(plan, true, d_in, d_out, 0, plan ? plan->h.rows : 0, cuda_stream);
+}
+
+int ntt_forward_rows(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, uint64_t row_begin,
+                     uint64_t n_rows, void* cuda_stream) {
+    return transform(plan, false, d_in, d_out, row_begin, n_rows, cuda_stream);
+}
+
+int ntt_inverse_rows(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, uint64_t row_begin,
+                     uint64_t n_rows, void* cuda_stream) {
+    return transform(plan, true, d_in, d_out, row_begin, n_rows, cuda_stream);
+}
+
+int poly_mul_pointwise(ntt_plan_t plan, const uint64_t* d_a, const uint64_t* d_b, uint64_t* d_c,
+                       uint32_t n_polys, void* cuda_stream) {
+    if (!plan || !d_a || !d_b || !d_c) return NTT_ERR_ARG;
+    if (!aligned16(d_a) || !aligned16(d_b) || !aligned16(d_c)) return NTT_ERR_ALIGN;
+    if (n_polys == 0) n_polys = plan->h.batch;
+    if (n_polys > plan->h.batch) return NTT_ERR_ARG;
+    int rc = check_device(plan);
+    if (rc) return rc;
+    plan->last_launches = 0;
+    PlanDev d = plan_dev(plan);
+    return launch_pointwise(d, plan->h.log2n, d_a, d_b, d_c, 0,
+                            (uint64_t)n_polys * plan->h.n_moduli, cuda_stream,
+                            &plan->last_launches);
+}
+
+int ntt_schedule_count(uint32_t log2n) {
+    if (log2n < NTT_MIN_LOG2N || log2n > NTT_MAX_LOG2N) return NTT_ERR_ARG;
+    return schedule_count(log2n);
+}
+
+int ntt_schedule_name(uint32_t log2n, uint32_t id, char* buf, size_t len) {
+    int i = sched_index(log2n, id);
+    if (i < 0 || !buf || len == 0) return NTT_ERR_ARG;
+    sched_describe(i, buf, len);
+    return NTT_OK;
+}
+
+int ntt_plan_set_schedule(ntt_plan_t plan, uint32_t id) {
+    if (!plan) return NTT_ERR_ARG;
+    if (sched_index(plan->h.log2n, id) < 0) return NTT_ERR_ARG;
+    plan->schedule = id;
+    return NTT_OK;
+}
+
+int ntt_plan_get_schedule(ntt_plan_t plan, uint32_t* id) {
+    if (!plan || !id) return NTT_ERR_ARG;
+    *id = plan->schedule;
+    return NTT_OK;
+}
+
+int ntt_status(ntt_plan_t plan, void* cuda_stream) {
+    if (!plan) return NTT_ERR_ARG;
+    int rc = check_device(plan);
+    if (rc) return rc;
+    int host = 0;
+    if (cudaStreamSynchronize((cudaStream_t)cuda_stream) != cudaSuccess) return NTT_ERR_CUDA;
+    if (cudaMemcpy(&host, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return NTT_ERR_CUDA;
+    if (host && cudaMemset(plan->d_status, 0, sizeof(int)) != cudaSuccess) return NTT_ERR_CUDA;
+    return host;
+}
+
+int ntt_plan_last_launches(ntt_plan_t plan, uint32_t* launches) {
+    if (!plan || !launches) return NTT_ERR_ARG;
+    *launches = plan->last_launches;
+    return NTT_OK;
+}
+
+const char* ntt_strerror(int code) {
+    switch (code) {
+        case NTT_OK: return "ok";
+        case NTT_ERR_ARG: return "invalid argument";
+        case NTT_ERR_NOT_PRIME: return "modulus is not prime";
+        case NTT_ERR_NOT_NTT_FRIENDLY: return "modulus is not 1 mod 2N";
+        case NTT_ERR_MODULUS_TOO_LARGE: return "modulus is not below 2^62";
+        case NTT_ERR_ALIGN: return "device pointer not 16-byte aligned";
+        case NTT_ERR_CUDA: return "CUDA runtime error";
+        case NTT_ERR_TIMEOUT: return "bounded device wait timed out";
+        case NTT_ERR_RANGE: return "input coefficient not below its modulus";
+        case NTT_ERR_NOMEM: return "out of memory";
+        case NTT_ERR_UNSUPPORTED: return "schedule unsupported for this shape";
+        default: return "unknown error";
+    }
+}
+
+const char* ntt_version(void) { return "ntt_gb300 0.1 sm_103a"; }
+
+}  // extern "C"

@@ -1,0 +1,216 @@
+// Host emulation of the tile NTT kernels, built as a separate library
+// (libntt_gb300_emu.so) that the CPU test suite loads.  It runs the very
+// same phase functions as the CUDA kernels (ntt_tile.cuh), CTA by CTA and
+// thread by thread, with every shared- and global-memory index checked, so
+// index arithmetic and pass layouts can be verified without a GPU.  It is
+// never used by the product library.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ntt_internal.h"
+#include "ntt_launch.h"
+#include "ntt_schedules.h"
+
+namespace nttgb {
+
+template <class C, int I>
+static void emu_passes(const TileArgs& a, const std::vector<TileLoc>& L, std::vector<uint64_t>& sm) {
+    if constexpr (I < C::NPASS) {
+        constexpr int P = C::INV ? (C::NPASS - 1 - I) : I;
+        for (int tid = 0; tid < C::THREADS; ++tid)
+            phase_pass<C, P>(a, L[tid >> C::LOGT], tid & (C::T - 1), sm.data() + (size_t)(tid >> C::LOGT) * C::E);
+        emu_passes<C, I + 1>(a, L, sm);
+    }
+}
+
+// Structural checks of a config: every pass, the load/store phases and the
+// swizzle touch each tile element exactly once (no races between threads of
+// one phase), and the tiles of a row partition it.
+template <class C>
+static bool verify_cfg() {
+    std::vector<int> seen(C::E);
+    for (int e = 0; e < C::E; ++e) {
+        uint32_t s = swz((uint32_t)e);
+        if (s >= (uint32_t)C::E || seen[s]++) return false;
+    }
+    for (int p = 0; p < C::NPASS; ++p) {
+        int s_lo, r;
+        pass_range<C>(p, s_lo, r);
+        const int pe = C::LOGP + C::S1 - s_lo - r;
+        std::fill(seen.begin(), seen.end(), 0);
+        for (int t = 0; t < C::T; ++t)
+            for (int j = 0; j < C::R; ++j) {
+                uint32_t e = pass_elem<C>(t, j, pe, r);
+                if (e >= (uint32_t)C::E || seen[e]++) return false;
+            }
+    }
+    std::fill(seen.begin(), seen.end(), 0);
+    for (int t = 0; t < C::T; ++t)
+        for (int i = 0; i < C::R / 2; ++i) {
+            uint32_t e = 2 * ((uint32_t)t + (uint32_t)i * C::T);
+            if (e + 1 >= (uint32_t)C::E || seen[e]++ || seen[e + 1]++) return false;
+        }
+    std::vector<int> row(1u << C::LOGN);
+    TileArgs a{};
+    a.n_tiles = 1ull << C::LOGTPR;
+    a.n_moduli = 1;
+    for (uint64_t tile = 0; tile < a.n_tiles; ++tile) {
+        TileLoc L = locate<C>(a, tile);
+        for (int e = 0; e < C::E; ++e) {
+            uint32_t g = gidx<C>(L, (uint32_t)e);
+            if (g >= (1u << C::LOGN) || row[g]++) return false;
+        }
+    }
+    return true;
+}
+
+template <class C>
+static int emu_kernel(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t row_begin,
+                      uint64_t n_rows) {
+    if (!verify_cfg<C>()) return NTT_ERR_UNSUPPORTED;
+    TileArgs a;
+    a.in = in;
+    a.out = out;
+    a.tw = C::INV ? p.inv : p.fwd;
+    a.lc = p.lc;
+    a.status = p.status;
+    a.row_begin = row_begin;
+    a.n_tiles = n_rows << C::LOGTPR;
+    a.n_moduli = p.n_moduli;
+    a.check = p.check;
+    const uint64_t ctas = (a.n_tiles + C::TPC - 1) / C::TPC;
+    std::vector<uint64_t> sm((size_t)C::E * C::TPC, 0xdeadbeefdeadbeefull);
+    std::vector<TileLoc> L(C::TPC);
+    for (uint64_t cta = 0; cta < ctas; ++cta) {
+        for (int tin = 0; tin < C::TPC; ++tin) L[tin] = locate<C>(a, cta * C::TPC + tin);
+        for (int tid = 0; tid < C::THREADS; ++tid)
+            phase_load<C>(a, L[tid >> C::LOGT], tid & (C::T - 1), sm.data() + (size_t)(tid >> C::LOGT) * C::E);
+        emu_passes<C, 0>(a, L, sm);
+        for (int tid = 0; tid < C::THREADS; ++tid)
+            phase_store<C>(a, L[tid >> C::LOGT], tid & (C::T - 1), sm.data() + (size_t)(tid >> C::LOGT) * C::E);
+    }
+    return NTT_OK;
+}
+
+template <int LOGN, int LOGT, int LOGRP, int TPC, bool INV>
+static int emu_s1(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t rb, uint64_t nr) {
+    return emu_kernel<TileCfg<LOGN, 0, LOGN, 0, LOGT, LOGRP, TPC, INV>>(p, in, out, rb, nr);
+}
+
+template <int LOGN, int SPLIT, int LOGP, int LOGTA, int LOGRPA, int TPCA, int LOGTB, int LOGRPB,
+          int TPCB, bool INV>
+static int emu_s2(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t rb, uint64_t nr) {
+    using CA = TileCfg<LOGN, 0, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, INV>;
+    using CB = TileCfg<LOGN, SPLIT, LOGN, 0, LOGTB, LOGRPB, TPCB, INV>;
+    int rc;
+    if (!INV) {
+        rc = emu_kernel<CA>(p, in, out, rb, nr);
+        if (!rc) rc = emu_kernel<CB>(p, in, out, rb, nr);
+    } else {
+        rc = emu_kernel<CB>(p, in, out, rb, nr);
+        if (!rc) rc = emu_kernel<CA>(p, in, out, rb, nr);
+    }
+    return rc;
+}
+
+typedef int (*EmuFn)(const PlanDev&, const uint64_t*, uint64_t*, uint64_t, uint64_t);
+struct EmuEntry {
+    uint32_t log2n;
+    EmuFn fwd, inv;
+};
+#define NTT_EMU_S1(LOGN, LOGT, LOGRP, TPC) \
+    {LOGN, &emu_s1<LOGN, LOGT, LOGRP, TPC, false>, &emu_s1<LOGN, LOGT, LOGRP, TPC, true>},
+#define NTT_EMU_S2(LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB)          \
+    {LOGN, &emu_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, false>,   \
+     &emu_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, true>},
+static const EmuEntry g_emu[] = {NTT_SCHEDULES_ALL(NTT_EMU_S1, NTT_EMU_S2)};
+static const int g_emu_count = (int)(sizeof(g_emu) / sizeof(g_emu[0]));
+
+static const EmuEntry* emu_find(uint32_t log2n, uint32_t id) {
+    uint32_t seen = 0;
+    for (int i = 0; i < g_emu_count; ++i) {
+        if (g_emu[i].log2n != log2n) continue;
+        if (seen == id) return &g_emu[i];
+        ++seen;
+    }
+    return nullptr;
+}
+
+struct EmuPlan {
+    PlanHost h;
+    int status = 0;
+};
+
+}  // namespace nttgb
+
+using namespace nttgb;
+
+extern "C" {
+
+// Host-only plan for the emulation (same validation and tables as ntt_plan).
+int nttemu_plan(void** out, uint32_t log2n, const uint64_t* moduli, uint32_t n_moduli,
+                uint32_t batch, uint32_t flags) {
+    if (!out) return NTT_ERR_ARG;
+    EmuPlan* p = new (std::nothrow) EmuPlan();
+    if (!p) return NTT_ERR_NOMEM;
+    int rc = build_plan_host(p->h, log2n, moduli, n_moduli, batch, flags);
+    if (rc) {
+        delete p;
+        return rc;
+    }
+    *out = p;
+    return NTT_OK;
+}
+
+int nttemu_plan_destroy(void* plan) {
+    delete static_cast<EmuPlan*>(plan);
+    return NTT_OK;
+}
+
+int nttemu_schedule_count(uint32_t log2n) {
+    int c = 0;
+    for (int i = 0; i < g_emu_count; ++i) c += g_emu[i].log2n == log2n;
+    return c;
+}
+
+// Runs schedule `sched` of the plan's N over rows [row_begin, row_begin + n_rows).
+int nttemu_transform(void* plan, uint32_t sched, int inverse, const uint64_t* in, uint64_t* out,
+                     uint64_t row_begin, uint64_t n_rows) {
+    EmuPlan* p = static_cast<EmuPlan*>(plan);
+    if (!p || !in || !out) return NTT_ERR_ARG;
+    if (row_begin > p->h.rows || n_rows > p->h.rows - row_begin) return NTT_ERR_ARG;
+    const EmuEntry* e = emu_find(p->h.log2n, sched);
+    if (!e) return NTT_ERR_ARG;
+    PlanDev d;
+    d.fwd = p->h.fwd.data();
+    d.inv = p->h.inv.data();
+    d.lc = p->h.consts.data();
+    d.status = &p->status;
+    d.n_moduli = p->h.n_moduli;
+    d.check = (p->h.flags & NTT_FLAG_CHECK) ? 1u : 0u;
+    return (inverse ? e->inv : e->fwd)(d, in, out, row_begin, n_rows);
+}
+
+// Pointwise product with the kernel's arithmetic (Barrett).
+int nttemu_pointwise(void* plan, const uint64_t* a, const uint64_t* b, uint64_t* c, uint64_t n_rows) {
+    EmuPlan* p = static_cast<EmuPlan*>(plan);
+    if (!p || n_rows > p->h.rows) return NTT_ERR_ARG;
+    const uint64_t n = 1ull << p->h.log2n;
+    for (uint64_t r = 0; r < n_rows; ++r) {
+        const LimbConst& m = p->h.consts[r % p->h.n_moduli];
+        for (uint64_t j = 0; j < n; ++j)
+            c[r * n + j] = barrett_mulmod(a[r * n + j], b[r * n + j], m.q, m.mu, m.bits);
+    }
+    return NTT_OK;
+}
+
+int nttemu_status(void* plan) {
+    EmuPlan* p = static_cast<EmuPlan*>(plan);
+    int s = p->status;
+    p->status = 0;
+    return s;
+}
+
+}  // extern "C"

@@ -1,0 +1,92 @@
+// Modular arithmetic of the NTT kernels (arxiv 2410.05934, Sec. II-D).
+//
+// Words are uint64, moduli q < 2^62.  Twiddles are multiplied in Shoup form:
+// for a fixed w < q the plan stores w' = floor(w 2^64 / q); then for ANY
+// y < 2^64,  Q = floor(y w' / 2^64)  and  r = y w - Q q  satisfy
+// r = y w mod q  or  r = y w mod q + q, i.e. r in [0, 2q).  (y w/q - y w'/2^64
+// lies in [0, 1), so Q is floor(y w / q) or one less.)  Only the low 64 bits
+// of y w and Q q are needed because r < 2q < 2^64.
+//
+// Butterflies keep values lazily reduced (Harvey's bounds), which q < 2^62
+// makes safe in 64-bit words:
+//   CT (forward, Eq. 1's NTT^{CT}):  X, Y in [0, 4q) -> X + wY, X - wY in [0, 4q)
+//   GS (inverse, Eq. 1's INTT^{GS}): X, Y in [0, 2q) -> X + Y, (X - Y) w in [0, 2q)
+//
+// Every function here is __host__ __device__ so the kernels' phase functions
+// can also run on the CPU (the host emulation used by the CPU test suite).
+#pragma once
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define NTT_HD __host__ __device__ __forceinline__
+#else
+#define NTT_HD inline
+#endif
+
+namespace nttgb {
+
+NTT_HD uint64_t mulhi64(uint64_t a, uint64_t b) {
+#if defined(__CUDA_ARCH__)
+    return __umul64hi(a, b);
+#else
+    return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+// y * w mod q lazily: result in [0, 2q) for any y < 2^64 (w < q, wp its Shoup form).
+NTT_HD uint64_t shoup_mul(uint64_t y, uint64_t w, uint64_t wp, uint64_t q) {
+    uint64_t Q = mulhi64(y, wp);
+    return y * w - Q * q;
+}
+
+// x in [0, 2m) -> [0, m)
+NTT_HD uint64_t csub(uint64_t x, uint64_t m) { return x >= m ? x - m : x; }
+
+// Cooley-Tukey butterfly, Harvey-lazy.  In/out in [0, 4q).
+NTT_HD void ct_butterfly(uint64_t& X, uint64_t& Y, uint64_t w, uint64_t wp, uint64_t q,
+                         uint64_t two_q) {
+    uint64_t x = csub(X, two_q);
+    uint64_t t = shoup_mul(Y, w, wp, q);
+    X = x + t;
+    Y = x - t + two_q;
+}
+
+// Gentleman-Sande butterfly, Harvey-lazy.  In/out in [0, 2q).
+NTT_HD void gs_butterfly(uint64_t& X, uint64_t& Y, uint64_t w, uint64_t wp, uint64_t q,
+                         uint64_t two_q) {
+    uint64_t s = csub(X + Y, two_q);
+    uint64_t d = X - Y + two_q;
+    Y = shoup_mul(d, w, wp, q);
+    X = s;
+}
+
+// Last GS stage with the N^-1 scaling folded in:
+//   X' = (X + Y) N^-1,  Y' = (X - Y) w N^-1;   in [0, 2q) -> out [0, 2q).
+NTT_HD void gs_butterfly_scaled(uint64_t& X, uint64_t& Y, uint64_t ninv, uint64_t ninv_p,
+                                uint64_t wn, uint64_t wn_p, uint64_t q, uint64_t two_q) {
+    uint64_t s = X + Y;                 // [0, 4q)
+    uint64_t d = X - Y + two_q;         // [0, 4q)
+    X = shoup_mul(s, ninv, ninv_p, q);
+    Y = shoup_mul(d, wn, wn_p, q);
+}
+
+// Exact a * b mod q for a, b < q by Barrett reduction with k = bitlen(q) and
+// mu = floor(2^(2k) / q) < 2^63:  x = a b < 2^(2k);  q3 = ((x >> (k-1)) mu) >> (k+1)
+// underestimates floor(x / q) by at most 2, so r = x - q3 q < 3q (Handbook of
+// Applied Cryptography, Alg. 14.42).
+NTT_HD uint64_t barrett_mulmod(uint64_t a, uint64_t b, uint64_t q, uint64_t mu, uint32_t k) {
+    uint64_t lo = a * b;
+    uint64_t hi = mulhi64(a, b);
+    // x >> (k - 1), with 1 <= k <= 62: fits in 64 bits since x < 2^(2k)
+    uint32_t sh = k - 1;
+    uint64_t q1 = sh == 0 ? lo : ((lo >> sh) | (hi << (64 - sh)));
+    uint64_t plo = q1 * mu;
+    uint64_t phi = mulhi64(q1, mu);
+    uint32_t sh2 = k + 1;  // 2..63
+    uint64_t q3 = (plo >> sh2) | (phi << (64 - sh2));
+    uint64_t r = lo - q3 * q;
+    r = csub(r, q);  // [0, 3q) -> [0, 2q)
+    return csub(r, q);
+}
+
+}  // namespace nttgb

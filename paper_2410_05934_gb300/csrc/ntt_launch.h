@@ -1,0 +1,48 @@
+// Launcher interface between the C ABI and the kernel translation units.
+#pragma once
+#include <stdint.h>
+
+#include "ntt_tile.cuh"
+
+namespace nttgb {
+
+// Device-side view of a plan (host pointers when used by the emulation).
+struct PlanDev {
+    const TwPair* fwd;
+    const TwPair* inv;
+    const LimbConst* lc;
+    int* status;
+    uint32_t n_moduli;
+    uint32_t check;
+};
+
+// Transforms rows [row_begin, row_begin + n_rows) of the layout that starts
+// at in/out.  Returns NTT_OK or NTT_ERR_CUDA; adds its launch count.
+typedef int (*LaunchFn)(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t row_begin,
+                        uint64_t n_rows, void* stream, uint32_t* launches);
+
+template <int LOGN, int LOGT, int LOGRP, int TPC, bool INV>
+int launch_s1(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t row_begin,
+              uint64_t n_rows, void* stream, uint32_t* launches);
+
+template <int LOGN, int SPLIT, int LOGP, int LOGTA, int LOGRPA, int TPCA, int LOGTB, int LOGRPB,
+          int TPCB, bool INV>
+int launch_s2(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t row_begin,
+              uint64_t n_rows, void* stream, uint32_t* launches);
+
+// c = a (.) b over n_rows rows of 2^log2n, row r using modulus (row_begin + r) mod n_moduli
+int launch_pointwise(const PlanDev& p, uint32_t log2n, const uint64_t* a, const uint64_t* b,
+                     uint64_t* c, uint64_t row_begin, uint64_t n_rows, void* stream,
+                     uint32_t* launches);
+
+struct SchedEntry {
+    uint32_t log2n;
+    uint32_t kernels;
+    const char* name;
+    LaunchFn fwd, inv;
+};
+
+// the table of NTT_SCHEDULES_ALL, in order
+const SchedEntry* sched_table(int* count);
+
+}  // namespace nttgb

@@ -1,0 +1,158 @@
+// Host side of ntt_plan: argument validation, the number theory that fixes
+// psi (arxiv 2410.05934, Sec. II-D: psi is a primitive 2N-th root of unity
+// mod q, which needs q prime and q = 1 mod 2N) and the twiddle tables.
+//
+// Twiddles follow the merged-psi negacyclic layout of Eq. 1: forward entry
+// k = psi^{brv(k)}, inverse entry k = psi^{-brv(k)} (brv over log2 N bits),
+// each with its Shoup companion w' = floor(w 2^64 / q).
+#include <cstring>
+
+#include "ntt_internal.h"
+
+namespace nttgb {
+
+typedef unsigned __int128 u128;
+
+uint64_t mul_mod(uint64_t a, uint64_t b, uint64_t q) { return (uint64_t)((u128)a * b % q); }
+
+uint64_t pow_mod(uint64_t a, uint64_t e, uint64_t q) {
+    uint64_t acc = 1 % q;
+    a %= q;
+    for (; e; e >>= 1) {
+        if (e & 1) acc = mul_mod(acc, a, q);
+        a = mul_mod(a, a, q);
+    }
+    return acc;
+}
+
+// Deterministic Miller-Rabin for 64-bit n with the seven bases found by
+// J. Sinclair (2, 325, 9375, 28178, 450775, 9780504, 1795265022), which
+// admit no strong pseudoprime below 2^64.
+bool is_prime_u64(uint64_t n) {
+    if (n < 2) return false;
+    static const uint64_t small[] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+    for (uint64_t p : small) {
+        if (n == p) return true;
+        if (n % p == 0) return false;
+    }
+    uint64_t d = n - 1;
+    unsigned s = __builtin_ctzll(d);
+    d >>= s;
+    static const uint64_t bases[] = {2, 325, 9375, 28178, 450775, 9780504, 1795265022};
+    for (uint64_t b : bases) {
+        uint64_t a = b % n;
+        if (a == 0) continue;
+        uint64_t x = pow_mod(a, d, n);
+        if (x == 1 || x == n - 1) continue;
+        bool witness = true;
+        for (unsigned i = 1; i < s && witness; ++i) {
+            x = mul_mod(x, x, n);
+            if (x == n - 1) witness = false;
+        }
+        if (witness) return false;
+    }
+    return true;
+}
+
+// Jacobi symbol (a/n) for odd n > 0 by quadratic reciprocity (binary form).
+int jacobi(uint64_t a, uint64_t n) {
+    a %= n;
+    int t = 1;
+    while (a != 0) {
+        while ((a & 1) == 0) {
+            a >>= 1;
+            uint64_t r = n & 7;
+            if (r == 3 || r == 5) t = -t;
+        }
+        uint64_t tmp = a;
+        a = n;
+        n = tmp;
+        if ((a & 3) == 3 && (n & 3) == 3) t = -t;
+        a %= n;
+    }
+    return n == 1 ? t : 0;
+}
+
+// psi = g^((q-1)/2N) with g the least quadratic non-residue (Jacobi = -1).
+// Returns 0 if q is not a prime = 1 mod 2N.
+uint64_t root_2n(uint64_t q, uint32_t log2n) {
+    uint64_t two_n = 2ull << log2n;
+    if (!is_prime_u64(q) || q < 3 || (q - 1) % two_n) return 0;
+    uint64_t g = 2;
+    while (jacobi(g, q) != -1) ++g;
+    uint64_t psi = pow_mod(g, (q - 1) / two_n, q);
+    // psi^N must be -1: then the order of psi is exactly 2N
+    if (pow_mod(psi, two_n / 2, q) != q - 1) return 0;
+    return psi;
+}
+
+uint64_t shoup_of(uint64_t w, uint64_t q) { return (uint64_t)(((u128)w << 64) / q); }
+
+static uint32_t brv(uint32_t x, uint32_t bits) {
+    uint32_t r = 0;
+    for (uint32_t i = 0; i < bits; ++i, x >>= 1) r = (r << 1) | (x & 1);
+    return r;
+}
+
+static uint32_t bit_length(uint64_t x) { return x ? 64u - (uint32_t)__builtin_clzll(x) : 0u; }
+
+int build_plan_host(PlanHost& h, uint32_t log2n, const uint64_t* moduli, uint32_t n_moduli,
+                    uint32_t batch, uint32_t flags) {
+    if (log2n < NTT_MIN_LOG2N || log2n > NTT_MAX_LOG2N) return NTT_ERR_ARG;
+    if (!moduli || n_moduli == 0 || batch == 0) return NTT_ERR_ARG;
+    if (flags & ~(NTT_FLAG_HOST_ONLY | NTT_FLAG_CHECK)) return NTT_ERR_ARG;
+    const uint64_t n = 1ull << log2n;
+    const u128 total = (u128)batch * n_moduli * n;
+    if (total >= ((u128)1 << 40)) return NTT_ERR_ARG;
+    for (uint32_t l = 0; l < n_moduli; ++l) {
+        uint64_t q = moduli[l];
+        if (q >= (1ull << NTT_MAX_MODULUS_BITS)) return NTT_ERR_MODULUS_TOO_LARGE;
+        if (!is_prime_u64(q)) return NTT_ERR_NOT_PRIME;
+        if ((q - 1) % (2 * n)) return NTT_ERR_NOT_NTT_FRIENDLY;
+    }
+    h.log2n = log2n;
+    h.n_moduli = n_moduli;
+    h.batch = batch;
+    h.flags = flags;
+    h.rows = (uint64_t)batch * n_moduli;
+    h.moduli.assign(moduli, moduli + n_moduli);
+    h.psi.resize(n_moduli);
+    h.fwd.resize((size_t)n_moduli * n);
+    h.inv.resize((size_t)n_moduli * n);
+    h.consts.resize(n_moduli);
+    std::vector<uint64_t> pw(n), pwi(n);
+    for (uint32_t l = 0; l < n_moduli; ++l) {
+        const uint64_t q = moduli[l];
+        const uint64_t psi = root_2n(q, log2n);
+        if (!psi) return NTT_ERR_NOT_NTT_FRIENDLY;
+        const uint64_t psi_inv = pow_mod(psi, 2 * n - 1, q);
+        h.psi[l] = psi;
+        pw[0] = pwi[0] = 1;
+        for (uint64_t i = 1; i < n; ++i) {
+            pw[i] = mul_mod(pw[i - 1], psi, q);
+            pwi[i] = mul_mod(pwi[i - 1], psi_inv, q);
+        }
+        TwPair* f = &h.fwd[(size_t)l * n];
+        TwPair* v = &h.inv[(size_t)l * n];
+        for (uint64_t k = 0; k < n; ++k) {
+            uint32_t b = brv((uint32_t)k, log2n);
+            f[k].w = pw[b];
+            f[k].wp = shoup_of(pw[b], q);
+            v[k].w = pwi[b];
+            v[k].wp = shoup_of(pwi[b], q);
+        }
+        LimbConst& c = h.consts[l];
+        std::memset(&c, 0, sizeof(c));
+        c.q = q;
+        c.two_q = 2 * q;
+        c.ninv = pow_mod(n % q, q - 2, q);
+        c.ninv_p = shoup_of(c.ninv, q);
+        c.w1ninv = mul_mod(v[1].w, c.ninv, q);
+        c.w1ninv_p = shoup_of(c.w1ninv, q);
+        c.bits = bit_length(q);
+        c.mu = (uint64_t)(((u128)1 << (2 * c.bits)) / q);
+    }
+    return NTT_OK;
+}
+
+}  // namespace nttgb

@@ -1,0 +1,169 @@
+"""Python binding of the batched negacyclic NTT library (C ABI: ntt_gb300.h).
+
+The names follow the C ABI: ``Plan`` wraps ``ntt_plan`` and its methods call
+``ntt_forward``, ``ntt_inverse`` and ``poly_mul_pointwise``.  Data are CUDA
+tensors of 64-bit integers (int64 or uint64 holding the uint64 coefficient
+bits), laid out [batch][n_moduli][N] and contiguous; torch provides only the
+memory and the stream.  Raw device pointers (ints) are accepted as well.
+"""
+import ctypes
+
+from . import _native
+from ._native import U32P, U64P, check, load
+
+NTT_FLAG_HOST_ONLY = 1
+NTT_FLAG_CHECK = 2
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return ctypes.c_void_p(0)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(x, min_elems=None, what="tensor"):
+    if isinstance(x, int):
+        return ctypes.c_void_p(x)
+    if not x.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % what)
+    if x.element_size() != 8 or x.is_floating_point():
+        raise ValueError("%s must hold 64-bit integers" % what)
+    if not x.is_contiguous():
+        raise ValueError("%s must be contiguous" % what)
+    if min_elems is not None and x.numel() < min_elems:
+        raise ValueError("%s has %d elements, needs %d" % (what, x.numel(), min_elems))
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def schedule_count(log2n):
+    return load().ntt_schedule_count(log2n)
+
+
+def schedule_name(log2n, sched_id):
+    buf = ctypes.create_string_buffer(256)
+    check(load().ntt_schedule_name(log2n, sched_id, buf, 256), "ntt_schedule_name")
+    return buf.value.decode()
+
+
+class Plan:
+    """ntt_plan(log2n, moduli, batch, flags): tables on the current device."""
+
+    def __init__(self, log2n, moduli, batch=1, flags=0, schedule=None):
+        L = load()
+        moduli = [int(q) for q in moduli]
+        arr = (ctypes.c_uint64 * len(moduli))(*moduli)
+        h = ctypes.c_void_p()
+        check(L.ntt_plan(ctypes.byref(h), log2n, arr, len(moduli), batch, flags), "ntt_plan")
+        self._h = h
+        self.log2n, self.n, self.moduli, self.batch = log2n, 1 << log2n, moduli, batch
+        self.n_moduli = len(moduli)
+        self.rows = batch * len(moduli)
+        if schedule is not None:
+            self.schedule = schedule
+
+    # -- lifetime --
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().ntt_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- queries --
+    def root(self, limb=0):
+        v = ctypes.c_uint64()
+        check(load().ntt_plan_root(self._h, limb, ctypes.byref(v)), "ntt_plan_root")
+        return v.value
+
+    @property
+    def schedule(self):
+        v = ctypes.c_uint32()
+        check(load().ntt_plan_get_schedule(self._h, ctypes.byref(v)), "ntt_plan_get_schedule")
+        return v.value
+
+    @schedule.setter
+    def schedule(self, sched_id):
+        check(load().ntt_plan_set_schedule(self._h, int(sched_id)), "ntt_plan_set_schedule")
+
+    def last_launches(self):
+        v = ctypes.c_uint32()
+        check(load().ntt_plan_last_launches(self._h, ctypes.byref(v)), "ntt_plan_last_launches")
+        return v.value
+
+    def status(self, stream=None):
+        """Synchronises the stream; returns and clears the device status word."""
+        return load().ntt_status(self._h, _stream_handle(stream))
+
+    # -- compute --
+    def forward(self, x, out=None, stream=None):
+        out = x if out is None else out
+        need = self.rows * self.n
+        check(load().ntt_forward(self._h, _ptr(x, need, "in"), _ptr(out, need, "out"),
+                                 _stream_handle(stream)), "ntt_forward")
+        return out
+
+    def inverse(self, x, out=None, stream=None):
+        out = x if out is None else out
+        need = self.rows * self.n
+        check(load().ntt_inverse(self._h, _ptr(x, need, "in"), _ptr(out, need, "out"),
+                                 _stream_handle(stream)), "ntt_inverse")
+        return out
+
+    def forward_rows(self, x, out, row_begin, n_rows, stream=None):
+        need = (row_begin + n_rows) * self.n
+        check(load().ntt_forward_rows(self._h, _ptr(x, need, "in"), _ptr(out, need, "out"),
+                                      row_begin, n_rows, _stream_handle(stream)), "ntt_forward_rows")
+        return out
+
+    def inverse_rows(self, x, out, row_begin, n_rows, stream=None):
+        need = (row_begin + n_rows) * self.n
+        check(load().ntt_inverse_rows(self._h, _ptr(x, need, "in"), _ptr(out, need, "out"),
+                                      row_begin, n_rows, _stream_handle(stream)), "ntt_inverse_rows")
+        return out
+
+    def pointwise(self, a, b, out=None, n_polys=0, stream=None):
+        out = a if out is None else out
+        need = (n_polys or self.batch) * self.n_moduli * self.n
+        check(load().poly_mul_pointwise(self._h, _ptr(a, need, "a"), _ptr(b, need, "b"),
+                                        _ptr(out, need, "c"), n_polys, _stream_handle(stream)),
+              "poly_mul_pointwise")
+        return out
+
+
+# C-ABI names as plain functions
+def ntt_plan(log2n, moduli, batch=1, flags=0):
+    return Plan(log2n, moduli, batch, flags)
+
+
+def ntt_forward(plan, d_in, d_out=None, stream=None):
+    return plan.forward(d_in, d_out, stream)
+
+
+def ntt_inverse(plan, d_in, d_out=None, stream=None):
+    return plan.inverse(d_in, d_out, stream)
+
+
+def poly_mul_pointwise(plan, d_a, d_b, d_c=None, n_polys=0, stream=None):
+    return plan.pointwise(d_a, d_b, d_c, n_polys, stream)

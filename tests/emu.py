@@ -1,0 +1,67 @@
+"""ctypes binding of the host emulation library (tests only)."""
+import ctypes
+
+import numpy as np
+
+from paper_2410_05934_gb300 import build as B
+
+U64P = ctypes.POINTER(ctypes.c_uint64)
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(B.build_emulation())
+        u32, u64, i32, vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p
+        L.nttemu_plan.argtypes = [ctypes.POINTER(vp), u32, U64P, u32, u32, u32]
+        L.nttemu_plan.restype = i32
+        L.nttemu_plan_destroy.argtypes = [vp]
+        L.nttemu_schedule_count.argtypes = [u32]
+        L.nttemu_transform.argtypes = [vp, u32, i32, U64P, U64P, u64, u64]
+        L.nttemu_transform.restype = i32
+        L.nttemu_pointwise.argtypes = [vp, U64P, U64P, U64P, u64]
+        L.nttemu_status.argtypes = [vp]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(U64P)
+
+
+class EmuPlan:
+    def __init__(self, log2n, moduli, batch=1, flags=0):
+        arr = np.ascontiguousarray(np.array(moduli, dtype=np.uint64))
+        self.h = ctypes.c_void_p()
+        rc = lib().nttemu_plan(ctypes.byref(self.h), log2n, _p(arr), arr.size, batch, flags)
+        if rc:
+            raise ValueError("nttemu_plan failed: %d" % rc)
+        self.log2n, self.n, self.rows = log2n, 1 << log2n, batch * arr.size
+
+    def __del__(self):
+        if self.h:
+            lib().nttemu_plan_destroy(self.h)
+
+    def transform(self, x, sched, inverse=False, out=None, row_begin=0, n_rows=None):
+        x = np.ascontiguousarray(x, dtype=np.uint64)
+        out = np.zeros_like(x) if out is None else out
+        n_rows = self.rows - row_begin if n_rows is None else n_rows
+        rc = lib().nttemu_transform(self.h, sched, int(inverse), _p(x), _p(out), row_begin, n_rows)
+        if rc:
+            raise ValueError("nttemu_transform failed: %d" % rc)
+        return out
+
+    def pointwise(self, a, b, n_rows=None):
+        a = np.ascontiguousarray(a, dtype=np.uint64)
+        b = np.ascontiguousarray(b, dtype=np.uint64)
+        c = np.zeros_like(a)
+        lib().nttemu_pointwise(self.h, _p(a), _p(b), _p(c), self.rows if n_rows is None else n_rows)
+        return c
+
+    def status(self):
+        return lib().nttemu_status(self.h)
+
+
+def schedule_count(log2n):
+    return lib().nttemu_schedule_count(log2n)

@@ -1,0 +1,100 @@
+"""The CUDA kernels' phase functions run on the host (libntt_gb300_emu.so,
+same source as the kernels, every memory index bounds-checked) and must be
+bit-exact against the oracle for every schedule of every N."""
+import numpy as np
+import pytest
+
+from paper_2410_05934_gb300 import workloads as W
+import emu
+
+
+def _moduli(log2n):
+    if log2n <= 10:
+        return [W.Q62_N1024, W.Q59_N1024]
+    return [W.POOL50[0], W.POOL50[7]]
+
+
+@pytest.mark.parametrize("log2n", range(1, 17))
+def test_every_schedule_matches_oracle(oracle, log2n):
+    n = 1 << log2n
+    mods = _moduli(log2n)
+    batch = 2
+    plan = emu.EmuPlan(log2n, mods, batch)
+    per_row = [mods[r % len(mods)] for r in range(batch * len(mods))]
+    x = W.rows_uniform(31, log2n, per_row, n)
+    if log2n <= 11:
+        ref = oracle.transform_rows(x, per_row)
+        idx = None
+    else:
+        rng = np.random.default_rng(log2n)
+        idx = np.stack([np.concatenate([[0, 1, n // 2, n - 1], rng.integers(0, n, 12)])
+                        for _ in per_row]).astype(np.uint32)
+        ref = oracle.transform_rows(x, per_row, idx=idx)
+    rows = np.arange(len(per_row))[:, None]
+    for s in range(emu.schedule_count(log2n)):
+        out = plan.transform(x, s)
+        got = out if idx is None else out[rows, idx]
+        assert np.array_equal(got, ref), "schedule %d" % s
+        back = plan.transform(out, s, inverse=True)
+        assert np.array_equal(back, x), "round trip, schedule %d" % s
+        # inverse of arbitrary canonical data against the oracle inverse
+        if idx is None:
+            inv = plan.transform(x, s, inverse=True)
+            assert np.array_equal(inv, oracle.transform_rows(x, per_row, inverse=True))
+
+
+@pytest.mark.parametrize("log2n", [1, 5, 10, 16])
+def test_in_place_and_row_ranges(oracle, log2n):
+    n = 1 << log2n
+    mods = _moduli(log2n)
+    plan = emu.EmuPlan(log2n, mods, 3)
+    per_row = [mods[r % 2] for r in range(6)]
+    x = W.rows_uniform(5, 3, per_row, n)
+    full = plan.transform(x, 0)
+    y = x.copy()
+    plan.transform(y, 0, out=y)            # in place
+    assert np.array_equal(y, full)
+    z = x.copy()
+    plan.transform(z, 0, out=z, row_begin=2, n_rows=3)
+    assert np.array_equal(z[2:5], full[2:5])
+    assert np.array_equal(z[:2], x[:2]) and np.array_equal(z[5:], x[5:])
+
+
+def test_extreme_values(oracle):
+    log2n, q = 10, W.Q62_N1024
+    n = 1 << log2n
+    plan = emu.EmuPlan(log2n, [q], 3)
+    x = np.zeros((3, n), dtype=np.uint64)
+    x[1, :] = q - 1
+    x[2, 0] = 1
+    for s in range(emu.schedule_count(log2n)):
+        out = plan.transform(x, s)
+        assert not out[0].any()
+        assert np.array_equal(out[1], oracle.ntt_forward(x[1], q))
+        assert np.all(out[2] == 1)
+        assert np.array_equal(plan.transform(out, s, inverse=True), x)
+
+
+def test_range_check_flag_reports_non_canonical_input():
+    q = W.Q59_N1024
+    plan = emu.EmuPlan(10, [q], 1, flags=2)
+    x = np.zeros((1, 1024), dtype=np.uint64)
+    plan.transform(x, 0)
+    assert plan.status() == 0
+    x[0, 77] = q
+    plan.transform(x, 0)
+    assert plan.status() == -8
+
+
+def test_pointwise_barrett_matches_oracle(oracle):
+    for q in [W.Q62_N1024, W.Q59_N1024, W.POOL50[0], 12289, 257]:
+        log2n = 4 if q == 257 else 6
+        n = 1 << log2n
+        plan = emu.EmuPlan(log2n, [q], 4)
+        a = W.rows_uniform(1, 1, [q] * 4, n)
+        b = W.rows_uniform(1, 2, [q] * 4, n)
+        a[0, :] = q - 1
+        b[0, :] = q - 1
+        c = plan.pointwise(a, b)
+        for r in range(4):
+            assert np.array_equal(c[r], oracle.pointwise(a[r], b[r], q))

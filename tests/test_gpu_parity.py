@@ -1,0 +1,245 @@
+"""Parity of the sm_103a kernels (through the C ABI) with the CPU oracle:
+bit-exact on every schedule of every N, on the three fixed workloads at their
+full sizes (sampled outputs where the O(N^2) oracle is too slow), and on the
+edge cases (in-place, row ranges, empty launches, extreme values, maximum
+sizes, range checking)."""
+import numpy as np
+import pytest
+
+from paper_2410_05934_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2410_05934_gb300 as ntt  # noqa: E402
+from gpu_util import to_dev, to_host  # noqa: E402
+
+
+def _moduli(log2n):
+    if log2n <= 10:
+        return [W.Q62_N1024, W.Q59_N1024]
+    return [W.POOL50[0], W.POOL50[7]]
+
+
+def _sample_idx(n, rows, k, seed):
+    rng = np.random.default_rng(seed)
+    base = np.array([0, 1, n // 2, n - 1], dtype=np.int64)
+    return np.stack([np.concatenate([base, rng.integers(0, n, k)]) for _ in range(rows)]).astype(np.uint32)
+
+
+@pytest.mark.parametrize("log2n", range(1, 17))
+def test_every_schedule_bit_exact(oracle, log2n):
+    n = 1 << log2n
+    mods = _moduli(log2n)
+    batch = 3 if log2n > 12 else 5            # ragged: not a multiple of rows per CTA
+    per_row = [mods[r % 2] for r in range(batch * 2)]
+    x = W.rows_uniform(101, log2n, per_row, n)
+    if log2n <= 11:
+        idx = None
+        ref = oracle.transform_rows(x, per_row)
+        ref_inv = oracle.transform_rows(x, per_row, inverse=True)
+    else:
+        idx = _sample_idx(n, len(per_row), 28, log2n)
+        ref = oracle.transform_rows(x, per_row, idx=idx)
+        ref_inv = oracle.transform_rows(x, per_row, inverse=True, idx=idx)
+    rows = np.arange(len(per_row))[:, None]
+    plan = ntt.Plan(log2n, mods, batch)
+    dx = to_dev(x)
+    for s in range(ntt.schedule_count(log2n)):
+        plan.schedule = s
+        out = torch.empty_like(dx)
+        plan.forward(dx, out)
+        got = to_host(out)
+        got = got if idx is None else got[rows, idx]
+        assert np.array_equal(got, ref), "forward, schedule %d" % s
+        back = torch.empty_like(dx)
+        plan.inverse(out, back)
+        assert np.array_equal(to_host(back), x), "round trip, schedule %d" % s
+        inv = torch.empty_like(dx)
+        plan.inverse(dx, inv)
+        got = to_host(inv)
+        got = got if idx is None else got[rows, idx]
+        assert np.array_equal(got, ref_inv), "inverse, schedule %d" % s
+        assert plan.status() == 0
+
+
+def test_plain_n1024_workload(oracle):
+    """64 rows at N=1024 (59-bit prime); 32 product pairs vs schoolbook."""
+    w = W.plain_n1024()
+    q, x = w["moduli"][0], w["x"]
+    plan = ntt.Plan(10, [q], 64)
+    dx = to_dev(x)
+    A = torch.empty_like(dx)
+    plan.forward(dx, A)
+    assert np.array_equal(to_host(A), oracle.transform_rows(x, [q] * 64))
+    pairs = ntt.Plan(10, [q], 32)
+    C = torch.empty_like(A[:32])
+    pairs.pointwise(A[:32].contiguous(), A[32:].contiguous(), C)
+    pairs.inverse(C, C)
+    c = to_host(C)
+    for i in range(32):
+        if i < 6:
+            assert np.array_equal(c[i], oracle.schoolbook(x[i], x[32 + i], q)), i
+        else:
+            k = np.array([0, 1, 511, 1023, 3 * i], dtype=np.uint32)
+            assert np.array_equal(c[i][k], oracle.schoolbook_at(x[i], x[32 + i], q, k)), i
+    back = torch.empty_like(dx)
+    plan.inverse(A, back)
+    assert np.array_equal(to_host(back), x)
+
+
+def test_ckks_hmul_n65536_workload(oracle):
+    """The full CKKS-HMUL-shaped batch: 4 polys x 24 limbs at N=2^16, forward,
+    the 4 cross products, inverse; sampled outputs on every row, one full
+    O(N^2) row, the convolution identity at sampled coefficients."""
+    w = W.ckks_hmul_n65536()
+    mods, x = w["moduli"], w["x"]
+    L, n = len(mods), 1 << 16
+    per_row = [mods[r % L] for r in range(4 * L)]
+    xr = x.reshape(4 * L, n)
+    plan = ntt.Plan(16, mods, 4)
+    dx = to_dev(xr)
+    A = torch.empty_like(dx)
+    plan.forward(dx, A)
+    a_host = to_host(A)
+    idx = _sample_idx(n, 4 * L, 12, 2)
+    ref = oracle.transform_rows(xr, per_row, idx=idx)
+    assert np.array_equal(a_host[np.arange(4 * L)[:, None], idx], ref)
+    # one whole row by the O(N^2) definition
+    full = oracle.transform_rows(xr[37:38], [per_row[37]], split=True, chunk=512)
+    assert np.array_equal(a_host[37], full[0])
+    # cross products a_i (.) b_j, i, j in {0, 1}, then the inverse
+    limb_plan = ntt.Plan(16, mods, 1)
+    Ap = A.view(4, L, n)
+    prods = torch.empty((4, L, n), dtype=A.dtype, device=A.device)
+    for k, (i, j) in enumerate([(0, 0), (0, 1), (1, 0), (1, 1)]):
+        limb_plan.pointwise(Ap[i].contiguous(), Ap[2 + j].contiguous(), prods[k])
+    plan.inverse(prods.view(4 * L, n), prods.view(4 * L, n))
+    c = to_host(prods)
+    for k, (i, j) in enumerate([(0, 0), (0, 1), (1, 0), (1, 1)]):
+        for l in (0, 11, 23):
+            kk = np.array([0, 1, 4097, n - 1], dtype=np.uint32)
+            assert np.array_equal(c[k, l][kk], oracle.schoolbook_at(x[i, l], x[2 + j, l], mods[l], kk))
+    back = torch.empty_like(dx)
+    plan.inverse(A, back)
+    assert torch.equal(back, dx)
+
+
+def test_tfhe_blind_rotation_workload(oracle):
+    """3780 forward NTTs of signed digits + 1260 inverse NTTs (62-bit prime)."""
+    w = W.tfhe_blind_rotation()
+    q = w["moduli"][0]
+    fwd, inv = w["fwd"], w["inv"]
+    pf = ntt.Plan(10, [q], fwd.shape[0])
+    pi = ntt.Plan(10, [q], inv.shape[0])
+    df, di = to_dev(fwd), to_dev(inv)
+    of, oi = torch.empty_like(df), torch.empty_like(di)
+    pf.forward(df, of)
+    pi.inverse(di, oi)
+    gf, gi = to_host(of), to_host(oi)
+    rows_f = np.arange(0, fwd.shape[0], 59)
+    rows_i = np.arange(0, inv.shape[0], 41)
+    assert np.array_equal(gf[rows_f], oracle.transform_rows(fwd[rows_f], [q] * len(rows_f)))
+    assert np.array_equal(gi[rows_i], oracle.transform_rows(inv[rows_i], [q] * len(rows_i), inverse=True))
+    idx = _sample_idx(1024, fwd.shape[0], 4, 3)
+    assert np.array_equal(gf[np.arange(fwd.shape[0])[:, None], idx],
+                          oracle.transform_rows(fwd, [q] * fwd.shape[0], idx=idx))
+
+
+@pytest.mark.parametrize("log2n", [1, 4, 10, 14, 16])
+def test_in_place_row_ranges_and_empty(oracle, log2n):
+    n = 1 << log2n
+    mods = _moduli(log2n)
+    plan = ntt.Plan(log2n, mods, 3)
+    per_row = [mods[r % 2] for r in range(6)]
+    x = W.rows_uniform(9, 4, per_row, n)
+    dx = to_dev(x)
+    full = torch.empty_like(dx)
+    plan.forward(dx, full)
+    y = dx.clone()
+    plan.forward(y)                                   # in place
+    assert torch.equal(y, full)
+    z = dx.clone()
+    plan.forward_rows(z, z, 2, 3)
+    assert torch.equal(z[2:5], full[2:5]) and torch.equal(z[:2], dx[:2]) and torch.equal(z[5:], dx[5:])
+    plan.forward_rows(z, z, 6, 0)                     # empty range: no launch
+    assert plan.last_launches() == 0
+    from paper_2410_05934_gb300 import _native
+    L = _native.load()
+    assert L.ntt_forward_rows(plan.handle, z.data_ptr(), z.data_ptr(), 5, 2, None) == -1
+    assert L.ntt_forward(plan.handle, z.data_ptr() + 8, z.data_ptr(), None) == -5
+
+
+def test_extreme_values(oracle):
+    q = W.Q62_N1024
+    plan = ntt.Plan(10, [q], 4)
+    x = np.zeros((4, 1024), dtype=np.uint64)
+    x[1, :] = q - 1
+    x[2, 0] = 1
+    x[3, 1] = 1
+    for s in range(ntt.schedule_count(10)):
+        plan.schedule = s
+        out = plan.forward(to_dev(x), torch.empty((4, 1024), dtype=torch.int64, device="cuda"))
+        h = to_host(out)
+        assert not h[0].any()
+        assert np.array_equal(h[1], oracle.ntt_forward(x[1], q))
+        assert np.all(h[2] == 1)
+        assert np.array_equal(h[3], oracle.ntt_forward(x[3], q))
+
+
+def test_range_check_reports_status():
+    q = W.Q59_N1024
+    plan = ntt.Plan(10, [q], 2, flags=ntt.NTT_FLAG_CHECK)
+    x = np.zeros((2, 1024), dtype=np.uint64)
+    d = to_dev(x)
+    plan.forward(d, torch.empty_like(d))
+    assert plan.status() == 0
+    x[1, 500] = q
+    d = to_dev(x)
+    plan.forward(d, torch.empty_like(d))
+    assert plan.status() == -8
+    assert plan.status() == 0                        # cleared on read
+
+
+def test_pointwise_against_oracle(oracle):
+    for q, log2n in [(W.Q62_N1024, 10), (W.POOL50[0], 16), (W.Q59_N1024, 1)]:
+        n = 1 << log2n
+        plan = ntt.Plan(log2n, [q], 3)
+        a = W.rows_uniform(3, 1, [q] * 3, n)
+        b = W.rows_uniform(3, 2, [q] * 3, n)
+        a[0, : min(n, 64)] = q - 1
+        b[0, : min(n, 64)] = q - 1
+        c = to_host(plan.pointwise(to_dev(a), to_dev(b), torch.empty((3, n), dtype=torch.int64, device="cuda")))
+        for r in range(3):
+            assert np.array_equal(c[r], oracle.pointwise(a[r], b[r], q))
+
+
+def test_maximum_size_row_index_beyond_2_32(oracle):
+    """2^16 rows of N = 2^16: 2^32 coefficients, so element offsets need 64 bits."""
+    log2n, rows = 16, 1 << 16
+    n = 1 << log2n
+    q = W.POOL50[0]
+    free, _ = torch.cuda.mem_get_info()
+    if free < 40 * 2**30:
+        pytest.skip("needs 40 GiB free")
+    plan = ntt.Plan(log2n, [q], rows)
+    d = torch.zeros((rows, n), dtype=torch.int64, device="cuda")
+    pick = [0, 1, rows // 2 + 3, rows - 1]
+    x = W.rows_uniform(77, 8, [q] * len(pick), n)
+    for i, r in enumerate(pick):
+        d[r] = to_dev(x[i])
+    for s in range(ntt.schedule_count(log2n)):
+        plan.schedule = s
+        e = d.clone() if s == 0 else e.copy_(d)
+        plan.forward(e)
+        idx = _sample_idx(n, len(pick), 12, s)
+        ref = oracle.transform_rows(x, [q] * len(pick), idx=idx)
+        got = to_host(e[pick])
+        assert np.array_equal(got[np.arange(len(pick))[:, None], idx], ref), s
+        zero_rows = to_host(e[[2, rows // 2, rows - 2]])
+        assert not zero_rows.any()
+    del d, e
+    torch.cuda.empty_cache()

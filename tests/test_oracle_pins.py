@@ -203,3 +203,15 @@ def test_sampled_and_threaded_paths_agree(oracle):
     inv = np.stack([oracle.ntt_inverse(r, q) for r in full])
     assert np.array_equal(oracle.transform_rows(full, [q] * 6, inverse=True, nthreads=3), inv)
     assert np.array_equal(inv, x)
+
+
+@pytest.mark.parametrize("q,log2n", [(257, 5), (W.Q62_N1024, 10), (W.POOL50[3], 8)])
+def test_sampled_schoolbook_matches_numpy(oracle, q, log2n):
+    n = 1 << log2n
+    rng = random.Random(q + 17)
+    a = [rng.randrange(q) for _ in range(n)]
+    b = [rng.randrange(q) for _ in range(n)]
+    ref = _numpy_negacyclic(a, b, q)
+    idx = [0, 1, n // 2, n - 1, rng.randrange(n)]
+    got = oracle.schoolbook_at(a, b, q, idx)
+    assert [int(v) for v in got] == [ref[k] for k in idx]
