@@ -1,0 +1,427 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched negacyclic NTT path on GB300.
+
+Workload (one "step"): the CKKS-HMUL-shaped batch -- N = 65536, 24 RNS
+limbs (the 24 largest 50-bit primes = 1 mod 2^17), 2 ciphertexts x 2
+components = 96 rows -- forward NTT of all 96 rows, the 4 cross products
+a_i (.) b_j per limb (96 product rows), inverse NTT of the 96 products
+(Sec. II-D, Eq. 1).  Metric: coefficients pushed through the transforms per
+second, counting both the forward and the inverse pass
+(2 x 96 x 65536 = 12.58 M coefficient-transforms per step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs its own independent batch (weak
+scaling, no data-path collective); time is the max over ranks.
+`--impl reference` times the CPU oracle (O(N^2) definitions) on a bounded
+sample of the same workload on the host cores.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "ckks_hmul_n65536"
+LOG2N, LIMBS, POLYS = 16, 24, 4
+METRIC = "NTT coeffs/s (forward+inverse coefficient-transforms per second)"
+UNIT = "coeffs/s"
+L2_FLUSH_BYTES = 512 << 20     # > 2x the 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--schedule", type=int, default=None)
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------- clocks --
+
+class ClockSampler:
+    """Samples nvidia-smi every 200 ms while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------- CPU baseline --
+
+def oracle_sample(seconds_target, nthreads=None):
+    """Times the C oracle (O(N^2) definitions) on a bounded sample of the
+    workload: forward outputs and inverse outputs of rows of the same batch.
+    Returns (coefficient-transforms/s, threads, description)."""
+    from oracle import oracle as O
+    from paper_2410_05934_gb300 import workloads as W
+    n = 1 << LOG2N
+    nthreads = nthreads or (os.cpu_count() or 1)
+    w = W.ckks_hmul_n65536()
+    x = w["x"].reshape(-1, n)
+    mods = w["moduli"]
+    # calibration: 1 row, 2*nthreads outputs each way
+    def run(k):
+        idx = np.arange(k, dtype=np.uint32)[None, :] * 7 % n
+        t0 = time.perf_counter()
+        O.transform_rows(x[:1], [mods[0]], idx=idx.astype(np.uint32), nthreads=1)
+        return time.perf_counter() - t0
+    t1 = run(4) / 4                      # seconds per output, one thread
+    per_dir = max(2 * nthreads, int(seconds_target * nthreads / t1 / 2))
+    rows = 2
+    per_row = max(1, per_dir // rows)
+    idx = np.stack([(np.arange(per_row, dtype=np.uint64) * 2654435761 + r) % n
+                    for r in range(rows)]).astype(np.uint32)
+    # split each row's outputs over threads: one "row" per chunk of outputs
+    chunks = max(1, nthreads)
+    sub = np.array_split(np.arange(per_row), chunks)
+    xs, qs, ids = [], [], []
+    for r in range(rows):
+        for s in sub:
+            if len(s) == 0:
+                continue
+            xs.append(x[r])
+            qs.append(mods[r % LIMBS])
+            ids.append(idx[r][s])
+    m = min(len(i) for i in ids)
+    ids = np.stack([i[:m] for i in ids])
+    xs = np.stack(xs)
+    t0 = time.perf_counter()
+    O.transform_rows(xs, qs, idx=ids, nthreads=nthreads)
+    O.transform_rows(xs, qs, idx=ids, inverse=True, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    count = 2 * ids.size
+    desc = ("O(N^2) oracle (forward + inverse definitions, 128-bit products) at N=65536: "
+            "%d output coefficients (%d forward + %d inverse, %d rows of the batch), %d threads"
+            % (count, ids.size, ids.size, rows, nthreads))
+    return count / dt, nthreads, desc, dt
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    from paper_2410_05934_gb300 import workloads as W
+    n = 1 << LOG2N
+    nthreads = os.cpu_count() or 1
+    w = W.ckks_hmul_n65536()
+    x = w["x"].reshape(-1, n)
+    mods = w["moduli"]
+    k = 32 * nthreads                    # outputs per direction per step
+    per_thread = max(1, k // nthreads)
+
+    def step(i):
+        rows = [(i * nthreads + t) % (4 * LIMBS) for t in range(nthreads)]
+        idx = np.stack([(np.arange(per_thread, dtype=np.uint64) * 40503 + 977 * i + t) % n
+                        for t in range(nthreads)]).astype(np.uint32)
+        xs = x[rows]
+        qs = [mods[r % LIMBS] for r in rows]
+        O.transform_rows(xs, qs, idx=idx, nthreads=nthreads)
+        O.transform_rows(xs, qs, idx=idx, inverse=True, nthreads=nthreads)
+        return 2 * idx.size
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    count = 0
+    for i in range(args.steps):
+        count += step(args.warmup + i)
+    dt = time.perf_counter() - t0
+    value = count / dt
+    sample = ("per step: %d forward + %d inverse output coefficients of the O(N^2) definitions "
+              "at N=65536 over %d rows of the CKKS-HMUL-shaped batch" % (count // args.steps // 2,
+                                                                          count // args.steps // 2,
+                                                                          nthreads))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "log2n": LOG2N, "limbs": LIMBS, "polys": POLYS},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------- GPU arm --
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device for --impl ours")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2410_05934_gb300 import build as B
+    B.build_product()
+    import paper_2410_05934_gb300 as ntt
+    from paper_2410_05934_gb300 import _native, shard
+    from paper_2410_05934_gb300 import workloads as W
+
+    n = 1 << LOG2N
+    rows = POLYS * LIMBS
+    w = W.ckks_hmul_n65536(seed=W.DEFAULT_SEED + rank)
+    mods = w["moduli"]
+    x_host = w["x"].reshape(rows, n)
+    stream = torch.cuda.current_stream()
+
+    plan = ntt.Plan(LOG2N, mods, POLYS)
+    limb_plan = ntt.Plan(LOG2N, mods, 1)
+    if args.schedule is not None:
+        plan.schedule = args.schedule
+    x = torch.from_numpy(x_host.view(np.int64)).to(dev)
+    A = torch.empty_like(x)
+    P = torch.empty_like(x)
+    Av, Pv = A.view(POLYS, LIMBS, n), P.view(POLYS, LIMBS, n)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    pairs = [(0, 0), (0, 1), (1, 0), (1, 1)]
+
+    fwd_ev = []
+
+    def step(x_in, record=False):
+        launches = 0
+        if record:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        plan.forward(x_in, A)
+        launches += plan.last_launches()
+        if record:
+            e1.record(stream)
+            fwd_ev.append((e0, e1))
+        for k, (i, j) in enumerate(pairs):
+            limb_plan.pointwise(Av[i], Av[2 + j], Pv[k])
+            launches += limb_plan.last_launches()
+        plan.inverse(P, P)
+        launches += plan.last_launches()
+        return launches
+
+    # ---- integer-pipe probe: the "alu" roofline denominator ----
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sink = torch.empty(sms * 8 * 256, dtype=torch.int64, device=dev)
+    L = _native.load()
+    probe_iters = 4000
+    probe_best = 0.0
+    for _ in range(4):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc = L.ntt_bench_butterflies(mods[0], 0, sms * 8, 256, probe_iters, sink.data_ptr(),
+                                     stream.cuda_stream)
+        assert rc == 0, rc
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bfly = sms * 8 * 256 * probe_iters * 8
+        probe_best = max(probe_best, bfly / (e0.elapsed_time(e1) * 1e-3))
+
+    # ---- warm-up ----
+    for _ in range(max(3, args.warmup)):
+        step(x)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, L2 flushed before each, events per step ----
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    shard.barrier()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches = 0
+    wall0 = time.perf_counter()
+    for s in range(args.steps):
+        flush.fill_(s)
+        starts[s].record(stream)
+        launches += step(x, record=True)
+        ends[s].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    shard.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    fwd_ms = [a.elapsed_time(b) for a, b in fwd_ev]
+    t_total = shard.max_over_ranks(sum(step_ms) * 1e-3)
+    coeffs_step = 2 * rows * n
+    value = world * args.steps * coeffs_step / t_total
+    ms_per_step = 1e3 * t_total / args.steps
+
+    # correctness guard on the measured output: INTT(NTT(a)) spot check via the oracle-free identity
+    back = torch.empty_like(x)
+    plan.forward(x, A)
+    plan.inverse(A, back)
+    torch.cuda.synchronize()
+    if not torch.equal(back, x):
+        raise SystemExit("round trip failed: results are wrong, refusing to report a number")
+
+    # ---- e2e: host buffers, copies inside the timed region ----
+    h_in = torch.from_numpy(x_host.view(np.int64)).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    x_dev = torch.empty_like(x)
+    for _ in range(2):
+        x_dev.copy_(h_in, non_blocking=True)
+        step(x_dev)
+        h_out.copy_(P, non_blocking=True)
+    torch.cuda.synchronize()
+    shard.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        x_dev.copy_(h_in, non_blocking=True)
+        step(x_dev)
+        h_out.copy_(P, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_e2e = shard.max_over_ranks(e0.elapsed_time(e1) * 1e-3)
+    e2e_value = world * args.steps * coeffs_step / t_e2e
+
+    # ---- roofline of the dominant kernel: the forward transform ----
+    fwd_s = statistics.mean(fwd_ms) * 1e-3
+    bfly_fwd = rows * (n // 2) * LOG2N                       # N/2 log2 N per row
+    bytes_fwd = rows * n * 16 + LIMBS * n * 16               # data in+out + one twiddle table pass
+    achieved_bfly = bfly_fwd / fwd_s
+    hbm_peak = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            hbm_peak = json.load(f).get("hbm_gbs")
+    except (OSError, ValueError):
+        pass
+    hbm_src = "measured"
+    if not hbm_peak:
+        hbm_peak, hbm_src = 6800.0, "fallback"
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(tpath) as f:
+            t = json.load(f)
+        if t.get("build_stamp") == open(B.LIB + ".stamp").read().strip() and t.get("schedule") == plan.schedule:
+            traffic = t.get("fwd_bytes_per_transform")
+    except (OSError, ValueError):
+        pass
+    clock_mhz = (clk or {}).get("sm_mhz")
+    roofline = {
+        "bound": "alu",
+        "kernel": "ntt_forward (%s)" % ntt.schedule_name(LOG2N, plan.schedule),
+        "achieved": achieved_bfly / 1e9, "peak": probe_best / 1e9, "unit": "Gbutterfly/s",
+        "frac": achieved_bfly / probe_best,
+        "peak_source": "in-run probe: %d SMs x 8 CTAs x 256 thr x 8 independent Harvey CT butterflies "
+                       "(same arithmetic as the kernels)" % sms,
+        "imad_slots_per_butterfly": (sms * 64 * (clock_mhz or 2070.0) * 1e6) / probe_best,
+        "traffic": traffic,
+        "hbm": {"achieved": bytes_fwd / fwd_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                "frac": bytes_fwd / fwd_s / 1e9 / hbm_peak, "peak_source": hbm_src,
+                "algorithmic_bytes": bytes_fwd},
+        "fwd_ms": statistics.mean(fwd_ms),
+    }
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "log2n": LOG2N, "limbs": LIMBS, "polys": POLYS,
+                   "rows": rows, "moduli": "24 largest primes < 2^50, = 1 mod 2^17",
+                   "step": "NTT(96 rows) -> 4 cross products x 24 limbs -> INTT(96 rows)",
+                   "schedule": plan.schedule,
+                   "l2": "flushed before every timed step (512 MiB write, outside the step events)",
+                   "timing": "CUDA events per step on the launching stream, summed; max over ranks",
+                   "wall_s_timed_loop": wall},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x.numel() * 8),
+                "d2h_bytes_per_step": int(P.numel() * 8),
+                "how": "pinned host -> device copy, the step, device -> host copy of the products, "
+                       "all on one stream inside one event pair"},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "roofline": roofline,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, desc, dt = oracle_sample(args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": desc, "seconds": dt}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

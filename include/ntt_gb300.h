@@ -140,6 +140,19 @@ int ntt_status(ntt_plan_t plan, void* cuda_stream);
 /* Number of kernel launches the most recent call on this plan issued. */
 int ntt_plan_last_launches(ntt_plan_t plan, uint32_t* launches);
 
+/*
+ * Integer-pipe peak probe (the denominator of the "alu" roofline): launches
+ * blocks x threads threads, each running `iters` rounds of 8 independent
+ * butterflies in registers with the exact arithmetic of the transform
+ * kernels (kind 0: Harvey CT forward butterfly, kind 1: Harvey GS inverse
+ * butterfly) under modulus q < 2^62.  Total butterflies =
+ * blocks * threads * iters * 8; time it with events on `cuda_stream`.
+ * d_sink (blocks * threads uint64, caller-owned) only defeats dead-code
+ * elimination.  Not part of the paper: a measurement aid.
+ */
+int ntt_bench_butterflies(uint64_t q, uint32_t kind, uint32_t blocks, uint32_t threads,
+                          uint32_t iters, uint64_t* d_sink, void* cuda_stream);
+
 const char* ntt_strerror(int code);
 
 /* Library version string ("ntt_gb300 <major>.<minor> sm_103a"). */

@@ -31,6 +31,7 @@ SIGNATURES = [
     ("ntt_plan_get_schedule", i32, [vp, U32P]),
     ("ntt_status", i32, [vp, vp]),
     ("ntt_plan_last_launches", i32, [vp, U32P]),
+    ("ntt_bench_butterflies", i32, [u64, u32, u32, u32, u32, vp, vp]),
     ("ntt_strerror", ctypes.c_char_p, [i32]),
     ("ntt_version", ctypes.c_char_p, []),
 ]

@@ -48,4 +48,45 @@ int launch_pointwise(const PlanDev& p, uint32_t log2n, const uint64_t* a, const 
     return NTT_OK;
 }
 
+// Throughput probe: independent butterflies per thread, same arithmetic as
+// the transform kernels, so butterflies/s measures the integer-pipe ceiling
+// of the NTT itself.
+template <int KIND>
+__global__ void __launch_bounds__(256) k_bench_bfly(uint64_t q, uint64_t w0, uint64_t wp0,
+                                                    uint32_t iters, uint64_t* sink) {
+    constexpr int P = 8;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t two_q = 2 * q;
+    uint64_t X[P], Y[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        X[i] = (tid * 7919u + (uint64_t)i * 104729u) % q;
+        Y[i] = (tid * 31u + (uint64_t)i * 17u) % q;
+    }
+    const uint64_t w = w0, wp = wp0;
+    for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            if (KIND == 0) ct_butterfly(X[i], Y[i], w, wp, q, two_q);
+            else gs_butterfly(X[i], Y[i], w, wp, q, two_q);
+        }
+    }
+    uint64_t acc = 0;
+#pragma unroll
+    for (int i = 0; i < P; ++i) acc ^= X[i] ^ Y[i];
+    if (acc == 0x5eed5eed5eedull) sink[tid] = acc;   // practically never taken
+}
+
+int launch_bench_bfly(uint64_t q, uint32_t kind, uint32_t blocks, uint32_t threads, uint32_t iters,
+                      uint64_t* sink, void* stream) {
+    // a fixed twiddle in Shoup form: w = q/3 rounded, w' = floor(w 2^64 / q)
+    const uint64_t w = q / 3;
+    const uint64_t wp = (uint64_t)(((unsigned __int128)w << 64) / q);
+    if (kind == 0)
+        k_bench_bfly<0><<<blocks, threads, 0, (cudaStream_t)stream>>>(q, w, wp, iters, sink);
+    else
+        k_bench_bfly<1><<<blocks, threads, 0, (cudaStream_t)stream>>>(q, w, wp, iters, sink);
+    return cudaPeekAtLastError() == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
+}
+
 }  // namespace nttgb

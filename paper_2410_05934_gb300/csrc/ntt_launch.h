@@ -35,6 +35,9 @@ int launch_pointwise(const PlanDev& p, uint32_t log2n, const uint64_t* a, const 
                      uint64_t* c, uint64_t row_begin, uint64_t n_rows, void* stream,
                      uint32_t* launches);
 
+int launch_bench_bfly(uint64_t q, uint32_t kind, uint32_t blocks, uint32_t threads, uint32_t iters,
+                      uint64_t* sink, void* stream);
+
 struct SchedEntry {
     uint32_t log2n;
     uint32_t kernels;
