@@ -145,7 +145,8 @@ int ntt_plan_last_launches(ntt_plan_t plan, uint32_t* launches);
  * blocks x threads threads, each running `iters` rounds of 8 independent
  * butterflies in registers with the exact arithmetic of the transform
  * kernels (kind 0: Harvey CT forward butterfly, kind 1: Harvey GS inverse
- * butterfly) under modulus q < 2^62.  Total butterflies =
+ * butterfly, both for any q < 2^62; kinds 2 and 3: the forward and inverse
+ * butterflies of the small-modulus class, q < 2^57).  Total butterflies =
  * blocks * threads * iters * 8; time it with events on `cuda_stream`.
  * d_sink (blocks * threads uint64, caller-owned) only defeats dead-code
  * elimination.  Not part of the paper: a measurement aid.

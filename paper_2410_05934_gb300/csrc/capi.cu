@@ -18,19 +18,21 @@ namespace nttgb {
 struct SchedParams {
     int kind;       // 1 = single kernel, 2 = column + row kernels
     int v[9];
+    int pipe;
 };
 
-#define NTT_ENTRY_S1(LOGN, LOGT, LOGRP, TPC) \
-    {LOGN, 1, nullptr, &launch_s1<LOGN, LOGT, LOGRP, TPC, false>, &launch_s1<LOGN, LOGT, LOGRP, TPC, true>},
-#define NTT_ENTRY_S2(LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB)             \
+#define NTT_ENTRY_S1(LOGN, LOGT, LOGRP, TPC, PIPE)                          \
+    {LOGN, 1, nullptr, &launch_s1<LOGN, LOGT, LOGRP, TPC, PIPE, false>,     \
+     &launch_s1<LOGN, LOGT, LOGRP, TPC, PIPE, true>},
+#define NTT_ENTRY_S2(LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE)       \
     {LOGN, 2, nullptr,                                                                       \
-     &launch_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, false>,          \
-     &launch_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, true>},
+     &launch_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE, false>,    \
+     &launch_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE, true>},
 static const SchedEntry g_table[] = {NTT_SCHEDULES_ALL(NTT_ENTRY_S1, NTT_ENTRY_S2)};
 
-#define NTT_PARAM_S1(LOGN, LOGT, LOGRP, TPC) {1, {LOGN, LOGT, LOGRP, TPC, 0, 0, 0, 0, 0}},
-#define NTT_PARAM_S2(LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB) \
-    {2, {LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB}},
+#define NTT_PARAM_S1(LOGN, LOGT, LOGRP, TPC, PIPE) {1, {LOGN, LOGT, LOGRP, TPC, 0, 0, 0, 0, 0}, PIPE},
+#define NTT_PARAM_S2(LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE) \
+    {2, {LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB}, PIPE},
 static const SchedParams g_params[] = {NTT_SCHEDULES_ALL(NTT_PARAM_S1, NTT_PARAM_S2)};
 
 static const int g_count = (int)(sizeof(g_table) / sizeof(g_table[0]));
@@ -61,24 +63,33 @@ static void sched_describe(int i, char* buf, size_t len) {
     const int* v = s.v;
     if (s.kind == 1) {
         int r = v[0] - v[1];
-        snprintf(buf, len, "1k: %d thr/row x %d coef, <=%d fused stages/pass, %d rows/CTA",
-                 1 << v[1], 1 << r, v[2], v[3]);
+        snprintf(buf, len, "1k%s: %d thr/row x %d coef, <=%d fused stages/pass, %d rows/CTA",
+                 s.pipe ? " pipelined" : "", 1 << v[1], 1 << r, v[2], v[3]);
     } else {
         int ra = v[1] + v[2] - v[3], rb = (v[0] - v[1]) - v[6];
         snprintf(buf, len,
-                 "2k split %d+%d: col tile 2^%dx%d (%d thr x %d coef, <=%d/pass, %d/CTA); "
+                 "2k%s split %d+%d: col tile 2^%dx%d (%d thr x %d coef, <=%d/pass, %d/CTA); "
                  "row tile 2^%d (%d thr x %d coef, <=%d/pass, %d/CTA)",
-                 v[1], v[0] - v[1], v[1], 1 << v[2], 1 << v[3], 1 << ra, v[4], v[5], v[0] - v[1],
+                 s.pipe ? " pipelined" : "", v[1], v[0] - v[1], v[1], 1 << v[2], 1 << v[3], 1 << ra, v[4], v[5], v[0] - v[1],
                  1 << v[6], 1 << rb, v[7], v[8]);
     }
 }
 
-// Default choice before any tuning: the first candidate of each N (the
-// lists put the widest-radix register layout first).
+// Default choice before any tuning: the schedule measured fastest on GB300
+// for typical batches of each N (timing sweep of the autotuner); small
+// batches of N <= 2^12 prefer the persistent pipelined form, which keeps
+// every SM busy with fewer CTAs.
 uint32_t default_schedule(uint32_t log2n, uint64_t rows) {
-    (void)log2n;
-    (void)rows;
-    return 0;
+    switch (log2n) {
+        case 10: return rows < 1024 ? 1u : 0u;   // pipelined / direct, 128 thr x 8 coef
+        case 11: return 1u;                      // pipelined, 256 thr x 8 coef
+        case 12: return 1u;                      // pipelined, 512 thr x 8 coef
+        case 13: return 1u;                      // direct, 256 thr x 32 coef
+        case 14: return 2u;                      // pipelined column + row kernels (7 + 7)
+        case 15: return 0u;                      // pipelined column + row kernels (7 + 8)
+        case 16: return 1u;                      // direct column + row kernels (8 + 8, 16 coef/thr)
+        default: return 0u;
+    }
 }
 
 static PlanDev plan_dev(const ntt_plan_s* p) {
@@ -89,6 +100,7 @@ static PlanDev plan_dev(const ntt_plan_s* p) {
     d.status = p->d_status;
     d.n_moduli = p->h.n_moduli;
     d.check = (p->h.flags & NTT_FLAG_CHECK) ? 1u : 0u;
+    d.mc = p->h.mc;
     return d;
 }
 
@@ -277,7 +289,8 @@ int ntt_plan_last_launches(ntt_plan_t plan, uint32_t* launches) {
 
 int ntt_bench_butterflies(uint64_t q, uint32_t kind, uint32_t blocks, uint32_t threads,
                           uint32_t iters, uint64_t* d_sink, void* cuda_stream) {
-    if (q < 3 || q >= (1ull << NTT_MAX_MODULUS_BITS) || kind > 1 || blocks == 0 || threads == 0 ||
+    if (q < 3 || q >= (1ull << NTT_MAX_MODULUS_BITS) || kind > 3 ||
+        (kind >= 2 && q >= (1ull << NTT_SMALL_MODULUS_BITS)) || blocks == 0 || threads == 0 ||
         threads > 256 || !d_sink)
         return NTT_ERR_ARG;
     return launch_bench_bfly(q, kind, blocks, threads, iters, d_sink, cuda_stream);

@@ -16,18 +16,25 @@
 namespace nttgb {
 
 template <class C, int I>
-static void emu_passes(const TileArgs& a, const std::vector<TileLoc>& L, std::vector<uint64_t>& sm) {
+static void emu_passes(std::vector<TileRegs<C>>& st, const TileArgs& a, const std::vector<TileLoc>& L,
+                       uint64_t* buf) {
     if constexpr (I < C::NPASS) {
         constexpr int P = C::INV ? (C::NPASS - 1 - I) : I;
-        for (int tid = 0; tid < C::THREADS; ++tid)
-            phase_pass<C, P>(a, L[tid >> C::LOGT], tid & (C::T - 1), sm.data() + (size_t)(tid >> C::LOGT) * C::E);
-        emu_passes<C, I + 1>(a, L, sm);
+        for (int tid = 0; tid < C::THREADS; ++tid) {
+            const int tin = tid >> C::LOGT, t = tid & (C::T - 1);
+            uint64_t* sm = buf + (size_t)tin * C::TILE_WORDS;
+            pass_read<C, P>(st[tid], L[tin], t, sm);
+            pass_compute<C, P>(st[tid], a, L[tin], t, sm);
+            pass_write<C, P>(st[tid], L[tin], t, sm);
+        }
+        emu_passes<C, I + 1>(st, a, L, buf);
     }
 }
 
 // Structural checks of a config: every pass, the load/store phases and the
 // swizzle touch each tile element exactly once (no races between threads of
-// one phase), and the tiles of a row partition it.
+// one phase), the tiles of a row partition it, and the bulk copies of a tile
+// cover its data and twiddle words exactly once.
 template <class C>
 static bool verify_cfg() {
     std::vector<int> seen(C::E);
@@ -42,7 +49,8 @@ static bool verify_cfg() {
         std::fill(seen.begin(), seen.end(), 0);
         for (int t = 0; t < C::T; ++t)
             for (int j = 0; j < C::R; ++j) {
-                uint32_t e = pass_elem<C>(t, j, pe, r);
+                uint32_t jlo = (uint32_t)j & ((1u << r) - 1), jhi = (uint32_t)j >> r;
+                uint32_t e = spread((uint32_t)t | (jhi << C::LOGT), pe, r) | (jlo << pe);
                 if (e >= (uint32_t)C::E || seen[e]++) return false;
             }
     }
@@ -63,13 +71,32 @@ static bool verify_cfg() {
             if (g >= (1u << C::LOGN) || row[g]++) return false;
         }
     }
+    if (C::PIPE) {
+        // copy coverage on a fake row: words [0, E) data, [E, E + 2(2^A - 1)) twiddles
+        std::vector<int> words(C::TILE_WORDS);
+        TileArgs b{};
+        static uint64_t fake[2];
+        b.in = b.out = fake;
+        b.tw = reinterpret_cast<const TwPair*>(fake);
+        b.n_tiles = 1;
+        b.n_moduli = 1;
+        TileLoc L = locate<C>(b, 0);
+        uint32_t bytes = 0;
+        for (int c = 0; c < C::COPIES; ++c) {
+            CopyDesc d = tile_copy<C>(b, L, c);
+            if (d.bytes % 16 || d.dst_word % 2) return false;
+            for (uint32_t w = 0; w < d.bytes / 8; ++w)
+                if (d.dst_word + w >= C::TILE_WORDS || words[d.dst_word + w]++) return false;
+            bytes += d.bytes;
+        }
+        if (bytes != C::TILE_TX_BYTES) return false;
+    }
     return true;
 }
 
 template <class C>
-static int emu_kernel(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t row_begin,
-                      uint64_t n_rows) {
-    if (!verify_cfg<C>()) return NTT_ERR_UNSUPPORTED;
+static TileArgs emu_args(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t row_begin,
+                         uint64_t n_rows) {
     TileArgs a;
     a.in = in;
     a.out = out;
@@ -80,30 +107,101 @@ static int emu_kernel(const PlanDev& p, const uint64_t* in, uint64_t* out, uint6
     a.n_tiles = n_rows << C::LOGTPR;
     a.n_moduli = p.n_moduli;
     a.check = p.check;
-    const uint64_t ctas = (a.n_tiles + C::TPC - 1) / C::TPC;
-    std::vector<uint64_t> sm((size_t)C::E * C::TPC, 0xdeadbeefdeadbeefull);
+    return a;
+}
+
+// the phases after the data sit in a buffer (direct form: swizzled already)
+template <class C>
+static void emu_compute_store(const TileArgs& a, const std::vector<TileLoc>& L, uint64_t* buf,
+                              std::vector<TileRegs<C>>& st) {
+    emu_passes<C, 0>(st, a, L, buf);
+    for (int tid = 0; tid < C::THREADS; ++tid) {
+        const int tin = tid >> C::LOGT, t = tid & (C::T - 1);
+        store_tile<C>(a, L[tin], t, buf + (size_t)tin * C::TILE_WORDS);
+    }
+}
+
+template <class C>
+static int emu_kernel(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t row_begin,
+                      uint64_t n_rows) {
+    if (!verify_cfg<C>()) return NTT_ERR_UNSUPPORTED;
+    const TileArgs a = emu_args<C>(p, in, out, row_begin, n_rows);
+    const uint64_t groups = (a.n_tiles + C::TPC - 1) / C::TPC;
+    std::vector<TileRegs<C>> st(C::THREADS);
     std::vector<TileLoc> L(C::TPC);
-    for (uint64_t cta = 0; cta < ctas; ++cta) {
-        for (int tin = 0; tin < C::TPC; ++tin) L[tin] = locate<C>(a, cta * C::TPC + tin);
-        for (int tid = 0; tid < C::THREADS; ++tid)
-            phase_load<C>(a, L[tid >> C::LOGT], tid & (C::T - 1), sm.data() + (size_t)(tid >> C::LOGT) * C::E);
-        emu_passes<C, 0>(a, L, sm);
-        for (int tid = 0; tid < C::THREADS; ++tid)
-            phase_store<C>(a, L[tid >> C::LOGT], tid & (C::T - 1), sm.data() + (size_t)(tid >> C::LOGT) * C::E);
+    if (!C::PIPE) {
+        std::vector<uint64_t> sm(C::BUF_WORDS, 0xdeadbeefdeadbeefull);
+        for (uint64_t g = 0; g < groups; ++g) {
+            for (int tin = 0; tin < C::TPC; ++tin) L[tin] = locate<C>(a, g * C::TPC + tin);
+            for (int tid = 0; tid < C::THREADS; ++tid) {
+                const int tin = tid >> C::LOGT, t = tid & (C::T - 1);
+                uint64_t* sm_t = sm.data() + (size_t)tin * C::TILE_WORDS;
+                load_direct<C>(st[tid], a, L[tin], t, sm_t);
+                write_pairs_swizzled<C>(st[tid], L[tin], t, sm_t);
+            }
+            emu_compute_store<C>(a, L, sm.data(), st);
+        }
+        return NTT_OK;
+    }
+    // pipelined form: a small pseudo-grid of persistent CTAs so that every
+    // CTA walks several groups and the buffers (and twiddle reuse) rotate
+    const uint64_t grid = groups < 3 ? groups : 3;
+    for (uint64_t cta = 0; cta < grid; ++cta) {
+        std::vector<uint64_t> sm(2 * C::BUF_WORDS, 0xdeadbeefdeadbeefull);
+        uint32_t it = 0;
+        for (uint64_t g = cta; g < groups; g += grid, ++it) {
+            const int b = it & 1;
+            uint64_t* buf = sm.data() + (size_t)b * C::BUF_WORDS;
+            // the bulk copies that the kernel issues for this group
+            const bool have_prev = it >= 2;
+            const uint64_t g_prev = have_prev ? g - 2 * grid : 0;
+            uint32_t expect = 0, copied = 0;
+            for (int tin = 0; tin < C::TPC; ++tin) {
+                const TileLoc T0 = locate<C>(a, g * C::TPC + tin);
+                if (!T0.valid) continue;
+                expect += (uint32_t)C::DATA_BYTES;
+                if (!twiddles_reusable<C>(a, g, g_prev, have_prev, tin))
+                    expect += (uint32_t)(C::TILE_TX_BYTES - C::DATA_BYTES);
+            }
+            for (int c = 0; c < C::TPC * C::COPIES; ++c) {
+                const int tin = c / C::COPIES, cc = c % C::COPIES;
+                const TileLoc T0 = locate<C>(a, g * C::TPC + tin);
+                if (!T0.valid) continue;
+                if (cc >= C::RUNS && twiddles_reusable<C>(a, g, g_prev, have_prev, tin)) continue;
+                const CopyDesc d = tile_copy<C>(a, T0, cc);
+                uint64_t* dst = buf + (size_t)tin * C::TILE_WORDS + d.dst_word;
+                NTT_SMEM_CHECK((size_t)tin * C::TILE_WORDS + d.dst_word + d.bytes / 8 - 1, C::BUF_WORDS);
+                memcpy(dst, d.src, d.bytes);
+                copied += d.bytes;
+            }
+            if (copied != expect) return NTT_ERR_UNSUPPORTED;
+            for (int tin = 0; tin < C::TPC; ++tin) L[tin] = locate<C>(a, g * C::TPC + tin);
+            for (int tid = 0; tid < C::THREADS; ++tid) {
+                const int tin = tid >> C::LOGT, t = tid & (C::T - 1);
+                relayout_read<C>(st[tid], a, L[tin], t, buf + (size_t)tin * C::TILE_WORDS);
+            }
+            for (int tid = 0; tid < C::THREADS; ++tid) {
+                const int tin = tid >> C::LOGT, t = tid & (C::T - 1);
+                write_pairs_swizzled<C>(st[tid], L[tin], t, buf + (size_t)tin * C::TILE_WORDS);
+            }
+            emu_compute_store<C>(a, L, buf, st);
+        }
     }
     return NTT_OK;
 }
 
-template <int LOGN, int LOGT, int LOGRP, int TPC, bool INV>
+template <int LOGN, int LOGT, int LOGRP, int TPC, int PIPE, bool INV>
 static int emu_s1(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t rb, uint64_t nr) {
-    return emu_kernel<TileCfg<LOGN, 0, LOGN, 0, LOGT, LOGRP, TPC, INV>>(p, in, out, rb, nr);
+    if (p.mc == 1)
+        return emu_kernel<TileCfg<LOGN, 0, LOGN, 0, LOGT, LOGRP, TPC, INV, 1, PIPE != 0>>(p, in, out, rb, nr);
+    return emu_kernel<TileCfg<LOGN, 0, LOGN, 0, LOGT, LOGRP, TPC, INV, 0, PIPE != 0>>(p, in, out, rb, nr);
 }
 
 template <int LOGN, int SPLIT, int LOGP, int LOGTA, int LOGRPA, int TPCA, int LOGTB, int LOGRPB,
-          int TPCB, bool INV>
-static int emu_s2(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t rb, uint64_t nr) {
-    using CA = TileCfg<LOGN, 0, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, INV>;
-    using CB = TileCfg<LOGN, SPLIT, LOGN, 0, LOGTB, LOGRPB, TPCB, INV>;
+          int TPCB, int PIPE, bool INV, int MC>
+static int emu_s2_mc(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t rb, uint64_t nr) {
+    using CA = TileCfg<LOGN, 0, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, INV, MC, PIPE != 0>;
+    using CB = TileCfg<LOGN, SPLIT, LOGN, 0, LOGTB, LOGRPB, TPCB, INV, MC, PIPE != 0>;
     int rc;
     if (!INV) {
         rc = emu_kernel<CA>(p, in, out, rb, nr);
@@ -115,16 +213,24 @@ static int emu_s2(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t 
     return rc;
 }
 
+template <int LOGN, int SPLIT, int LOGP, int LOGTA, int LOGRPA, int TPCA, int LOGTB, int LOGRPB,
+          int TPCB, int PIPE, bool INV>
+static int emu_s2(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t rb, uint64_t nr) {
+    if (p.mc == 1)
+        return emu_s2_mc<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE, INV, 1>(p, in, out, rb, nr);
+    return emu_s2_mc<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE, INV, 0>(p, in, out, rb, nr);
+}
+
 typedef int (*EmuFn)(const PlanDev&, const uint64_t*, uint64_t*, uint64_t, uint64_t);
 struct EmuEntry {
     uint32_t log2n;
     EmuFn fwd, inv;
 };
-#define NTT_EMU_S1(LOGN, LOGT, LOGRP, TPC) \
-    {LOGN, &emu_s1<LOGN, LOGT, LOGRP, TPC, false>, &emu_s1<LOGN, LOGT, LOGRP, TPC, true>},
-#define NTT_EMU_S2(LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB)          \
-    {LOGN, &emu_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, false>,   \
-     &emu_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, true>},
+#define NTT_EMU_S1(LOGN, LOGT, LOGRP, TPC, PIPE) \
+    {LOGN, &emu_s1<LOGN, LOGT, LOGRP, TPC, PIPE, false>, &emu_s1<LOGN, LOGT, LOGRP, TPC, PIPE, true>},
+#define NTT_EMU_S2(LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE)          \
+    {LOGN, &emu_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE, false>,   \
+     &emu_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE, true>},
 static const EmuEntry g_emu[] = {NTT_SCHEDULES_ALL(NTT_EMU_S1, NTT_EMU_S2)};
 static const int g_emu_count = (int)(sizeof(g_emu) / sizeof(g_emu[0]));
 
@@ -190,6 +296,7 @@ int nttemu_transform(void* plan, uint32_t sched, int inverse, const uint64_t* in
     d.status = &p->status;
     d.n_moduli = p->h.n_moduli;
     d.check = (p->h.flags & NTT_FLAG_CHECK) ? 1u : 0u;
+    d.mc = p->h.mc;
     return (inverse ? e->inv : e->fwd)(d, in, out, row_begin, n_rows);
 }
 

@@ -68,7 +68,9 @@ __global__ void __launch_bounds__(256) k_bench_bfly(uint64_t q, uint64_t w0, uin
 #pragma unroll
         for (int i = 0; i < P; ++i) {
             if (KIND == 0) ct_butterfly(X[i], Y[i], w, wp, q, two_q);
-            else gs_butterfly(X[i], Y[i], w, wp, q, two_q);
+            else if (KIND == 1) gs_butterfly(X[i], Y[i], w, wp, q, two_q);
+            else if (KIND == 2) ct_butterfly_small(X[i], Y[i], w, wp, q, 2 * two_q);
+            else gs_butterfly_small(X[i], Y[i], w, wp, q, 2 * two_q);
         }
     }
     uint64_t acc = 0;
@@ -82,10 +84,13 @@ int launch_bench_bfly(uint64_t q, uint32_t kind, uint32_t blocks, uint32_t threa
     // a fixed twiddle in Shoup form: w = q/3 rounded, w' = floor(w 2^64 / q)
     const uint64_t w = q / 3;
     const uint64_t wp = (uint64_t)(((unsigned __int128)w << 64) / q);
-    if (kind == 0)
-        k_bench_bfly<0><<<blocks, threads, 0, (cudaStream_t)stream>>>(q, w, wp, iters, sink);
-    else
-        k_bench_bfly<1><<<blocks, threads, 0, (cudaStream_t)stream>>>(q, w, wp, iters, sink);
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (kind) {
+        case 0: k_bench_bfly<0><<<blocks, threads, 0, st>>>(q, w, wp, iters, sink); break;
+        case 1: k_bench_bfly<1><<<blocks, threads, 0, st>>>(q, w, wp, iters, sink); break;
+        case 2: k_bench_bfly<2><<<blocks, threads, 0, st>>>(q, w, wp, iters, sink); break;
+        default: k_bench_bfly<3><<<blocks, threads, 0, st>>>(q, w, wp, iters, sink); break;
+    }
     return cudaPeekAtLastError() == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
 }
 

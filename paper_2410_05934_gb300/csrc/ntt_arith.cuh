@@ -39,6 +39,24 @@ NTT_HD uint64_t shoup_mul(uint64_t y, uint64_t w, uint64_t wp, uint64_t q) {
     return y * w - Q * q;
 }
 
+// Shoup product with a three-partial-product quotient: with y = yh 2^32 + yl
+// and w' = wh 2^32 + wl,  Q~ = yh wh + floor(yh wl / 2^32) + floor(yl wh / 2^32)
+// drops three fractional parts (each < 1) of y w' / 2^64, so
+// floor(y w' / 2^64) - Q~ is in {0, 1, 2} and floor(y w / q) - Q~ in {0..3}:
+// the result y w - Q~ q is y w mod q plus 0..3 q, i.e. in [0, 4q), for any
+// y < 2^64.  Used when 4q-wide lazy bounds fit (moduli below 2^57).
+NTT_HD uint64_t shoup_mul_approx(uint64_t y, uint64_t w, uint64_t wp, uint64_t q) {
+    const uint32_t yl = (uint32_t)y, yh = (uint32_t)(y >> 32);
+    const uint32_t wl = (uint32_t)wp, wh = (uint32_t)(wp >> 32);
+#if defined(__CUDA_ARCH__)
+    const uint64_t mid = (uint64_t)__umulhi(yh, wl) + __umulhi(yl, wh);
+#else
+    const uint64_t mid = (((uint64_t)yh * wl) >> 32) + (((uint64_t)yl * wh) >> 32);
+#endif
+    const uint64_t Q = (uint64_t)yh * wh + mid;
+    return y * w - Q * q;
+}
+
 // x in [0, 2m) -> [0, m)
 NTT_HD uint64_t csub(uint64_t x, uint64_t m) { return x >= m ? x - m : x; }
 
@@ -58,6 +76,43 @@ NTT_HD void gs_butterfly(uint64_t& X, uint64_t& Y, uint64_t w, uint64_t wp, uint
     uint64_t d = X - Y + two_q;
     Y = shoup_mul(d, w, wp, q);
     X = s;
+}
+
+// Modulus class 1 (q < 2^57): quotient-approximate products, 4q-wide bounds.
+// Forward CT without any conditional subtraction: X, Y < B q  ->
+//   X + wY < (B + 4) q,  X - wY + 4q < (B + 4) q   (wY in [0, 4q)).
+// From canonical input the bound after s stages is (1 + 4 s) q <= 65 q < 2^64.
+NTT_HD void ct_butterfly_small(uint64_t& X, uint64_t& Y, uint64_t w, uint64_t wp, uint64_t q,
+                               uint64_t four_q) {
+    uint64_t t = shoup_mul_approx(Y, w, wp, q);
+    uint64_t x = X;
+    X = x + t;
+    Y = x - t + four_q;
+}
+
+// GS with 4q-wide bounds: X, Y in [0, 4q) -> X + Y reduced to [0, 4q),
+// (X - Y + 4q) w in [0, 4q).  Needs 8q < 2^64.
+NTT_HD void gs_butterfly_small(uint64_t& X, uint64_t& Y, uint64_t w, uint64_t wp, uint64_t q,
+                               uint64_t four_q) {
+    uint64_t s = csub(X + Y, four_q);
+    uint64_t d = X - Y + four_q;
+    Y = shoup_mul_approx(d, w, wp, q);
+    X = s;
+}
+
+NTT_HD void gs_butterfly_scaled_small(uint64_t& X, uint64_t& Y, uint64_t ninv, uint64_t ninv_p,
+                                      uint64_t wn, uint64_t wn_p, uint64_t q, uint64_t four_q) {
+    uint64_t s = X + Y;                 // [0, 8q)
+    uint64_t d = X - Y + four_q;        // [0, 8q)
+    X = shoup_mul_approx(s, ninv, ninv_p, q);
+    Y = shoup_mul_approx(d, wn, wn_p, q);
+}
+
+// Any x < 2^64 to [0, q): x * 1 in Shoup form (w' = floor(2^64 / q)) lands in
+// [0, 4q), then two conditional subtractions.
+NTT_HD uint64_t reduce_full_small(uint64_t x, uint64_t one_p, uint64_t q, uint64_t two_q) {
+    uint64_t r = shoup_mul_approx(x, 1, one_p, q);
+    return csub(csub(r, two_q), q);
 }
 
 // Last GS stage with the N^-1 scaling folded in:

@@ -21,6 +21,7 @@ uint64_t shoup_of(uint64_t w, uint64_t q);
 
 struct PlanHost {
     uint32_t log2n = 0, n_moduli = 0, batch = 0, flags = 0;
+    uint32_t mc = 0;                   // modulus class (see ntt_tile.cuh)
     uint64_t rows = 0;
     std::vector<uint64_t> moduli, psi;
     std::vector<TwPair> fwd, inv;      // [n_moduli][N]

@@ -1,6 +1,7 @@
 // Kernel and launcher templates of the tile NTT (see ntt_tile.cuh for the
-// tile geometry).  Included by the kernel translation units, each of which
-// explicitly instantiates one slice of the schedule list.
+// tile geometry and the two kernel forms).  Included by the kernel
+// translation units, each of which explicitly instantiates one slice of the
+// schedule list.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -10,18 +11,73 @@
 
 namespace nttgb {
 
+// ---- PTX helpers: mbarrier and bulk asynchronous copies (sm_90+) ----
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait: each try_wait suspends for a hardware-chosen interval, so
+// the iteration limit bounds the total time; false means it ran out.
+#define NTT_MBAR_SPIN_LIMIT (1u << 22)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    for (uint32_t i = 0; i < NTT_MBAR_SPIN_LIMIT; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// global -> shared bulk copy completing on `bar` (addresses 16-byte aligned,
+// size a multiple of 16)
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
 template <class C, int I>
-__device__ __forceinline__ void run_passes(const TileArgs& a, const TileLoc& L, int t, uint64_t* sm) {
+__device__ __forceinline__ void run_passes(TileRegs<C>& st, const TileArgs& a, const TileLoc& L, int t,
+                                           uint64_t* sm) {
     if constexpr (I < C::NPASS) {
         constexpr int P = C::INV ? (C::NPASS - 1 - I) : I;
-        phase_pass<C, P>(a, L, t, sm);
+        pass_read<C, P>(st, L, t, sm);
+        pass_compute<C, P>(st, a, L, t, sm);
+        pass_write<C, P>(st, L, t, sm);
         __syncthreads();
-        run_passes<C, I + 1>(a, L, t, sm);
+        run_passes<C, I + 1>(st, a, L, t, sm);
     }
 }
 
-// One CTA = TPC tiles; each tile is staged through shared memory, runs the
-// kernel's fused passes, and is written back with 16-byte stores.
+// ---- direct form: one CTA = TPC tiles, loaded with 16-byte loads ----
 template <class C>
 __global__ void __launch_bounds__(C::THREADS) k_ntt_tile(TileArgs a) {
     extern __shared__ __align__(16) uint64_t smem[];
@@ -30,11 +86,105 @@ __global__ void __launch_bounds__(C::THREADS) k_ntt_tile(TileArgs a) {
     const int t = tid & (C::T - 1);
     const uint64_t tile = (uint64_t)blockIdx.x * C::TPC + tin;
     const TileLoc L = locate<C>(a, tile);
-    uint64_t* sm = smem + (size_t)tin * C::E;
-    phase_load<C>(a, L, t, sm);
+    uint64_t* sm = smem + (size_t)tin * C::TILE_WORDS;
+    TileRegs<C> st;
+    load_direct<C>(st, a, L, t, sm);
+    write_pairs_swizzled<C>(st, L, t, sm);
     __syncthreads();
-    run_passes<C, 0>(a, L, t, sm);
-    phase_store<C>(a, L, t, sm);
+    run_passes<C, 0>(st, a, L, t, sm);
+    store_tile<C>(a, L, t, sm);
+}
+
+// Issues the bulk copies of tile group g into buffer `buf` (all threads take
+// part; thread 0 arms the barrier with the byte count).
+template <class C>
+__device__ __forceinline__ void issue_group(const TileArgs& a, uint64_t g, int buf, uint64_t* bars,
+                                           uint64_t* smem, uint64_t g_prev, bool have_prev) {
+    const int tid = threadIdx.x;
+    fence_proxy_async_smem();
+    if (tid == 0) {
+        uint32_t bytes = 0;
+        for (int tin = 0; tin < C::TPC; ++tin) {
+            const TileLoc L = locate<C>(a, g * C::TPC + tin);
+            if (!L.valid) continue;
+            bytes += (uint32_t)C::DATA_BYTES;
+            if (!twiddles_reusable<C>(a, g, g_prev, have_prev, tin))
+                bytes += (uint32_t)(C::TILE_TX_BYTES - C::DATA_BYTES);
+        }
+        mbar_arrive_expect_tx(&bars[buf], bytes);
+    }
+    for (int c = tid; c < C::TPC * C::COPIES; c += C::THREADS) {
+        const int tin = c / C::COPIES, cc = c % C::COPIES;
+        const TileLoc L = locate<C>(a, g * C::TPC + tin);
+        if (!L.valid) continue;
+        if (cc >= C::RUNS && twiddles_reusable<C>(a, g, g_prev, have_prev, tin)) continue;
+        const CopyDesc d = tile_copy<C>(a, L, cc);
+        uint64_t* dst = smem + (size_t)buf * C::BUF_WORDS + (size_t)tin * C::TILE_WORDS + d.dst_word;
+        bulk_load(dst, d.src, d.bytes, &bars[buf]);
+    }
+}
+
+// ---- pipelined form: persistent CTAs, two buffers, bulk copies ----
+template <class C>
+__global__ void __launch_bounds__(C::THREADS) k_ntt_tile_pipe(TileArgs a, uint64_t groups) {
+    extern __shared__ __align__(16) uint64_t smem[];
+    uint64_t* bars = smem + C::BAR_OFFSET / sizeof(uint64_t);
+    const int tid = threadIdx.x;
+    const int tin = tid >> C::LOGT;
+    const int t = tid & (C::T - 1);
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const uint64_t step = gridDim.x;
+    uint64_t g = blockIdx.x;
+    if (g < groups) issue_group<C>(a, g, 0, bars, smem, 0, false);
+    uint32_t parity = 0;   // bit b: phase parity expected next on buffer b
+    for (uint32_t it = 0; g < groups; ++it, g += step) {
+        const int b = it & 1;
+        const uint64_t gn = g + step;
+        if (gn < groups) issue_group<C>(a, gn, b ^ 1, bars, smem, g - step, it >= 1);
+        const bool ok = mbar_wait_bounded(&bars[b], (parity >> b) & 1u);
+        parity ^= 1u << b;
+        if (__syncthreads_or(!ok)) {
+            // a copy never completed: report, wait (bounded) for the other
+            // buffer's copies in flight, and leave
+            if (tid == 0) record_status(a.status, NTT_STATUS_TIMEOUT);
+            if (gn < groups) (void)mbar_wait_bounded(&bars[b ^ 1], (parity >> (b ^ 1)) & 1u);
+            return;
+        }
+        const TileLoc L = locate<C>(a, g * C::TPC + tin);
+        uint64_t* sm = smem + (size_t)b * C::BUF_WORDS + (size_t)tin * C::TILE_WORDS;
+        TileRegs<C> st;
+        relayout_read<C>(st, a, L, t, sm);
+        __syncthreads();
+        write_pairs_swizzled<C>(st, L, t, sm);
+        __syncthreads();
+        run_passes<C, 0>(st, a, L, t, sm);
+        store_tile<C>(a, L, t, sm);
+        __syncthreads();   // buffer b is refilled by the next iteration's issue
+    }
+}
+
+template <class C>
+int resident_ctas_per_sm() {
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cached[dev]) {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ntt_tile_pipe<C>, C::THREADS, C::SMEM_BYTES) !=
+                cudaSuccess ||
+            n < 1)
+            n = 1;
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = n * (sms > 0 ? sms : 1);
+    }
+    return cached[dev];
 }
 
 template <class C>
@@ -50,35 +200,45 @@ int launch_tile_kernel(const PlanDev& p, const uint64_t* in, uint64_t* out, uint
     a.n_tiles = n_rows << C::LOGTPR;
     a.n_moduli = p.n_moduli;
     a.check = p.check;
-    const uint64_t ctas = (a.n_tiles + C::TPC - 1) / C::TPC;
-    if (ctas == 0) return NTT_OK;
-    if (ctas > 0x7fffffffull) return NTT_ERR_ARG;
+    const uint64_t groups = (a.n_tiles + C::TPC - 1) / C::TPC;
+    if (groups == 0) return NTT_OK;
+    if (groups > 0x7fffffffull) return NTT_ERR_ARG;
     if (C::SMEM_BYTES > 48 * 1024) {
-        // per-function attribute; cheap to repeat, needed once per device
-        cudaError_t e = cudaFuncSetAttribute(k_ntt_tile<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)C::SMEM_BYTES);
+        cudaError_t e = C::PIPE
+            ? cudaFuncSetAttribute(k_ntt_tile_pipe<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_BYTES)
+            : cudaFuncSetAttribute(k_ntt_tile<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_BYTES);
         if (e != cudaSuccess) return NTT_ERR_CUDA;
     }
-    k_ntt_tile<C><<<(unsigned)ctas, C::THREADS, C::SMEM_BYTES, st>>>(a);
+    if (C::PIPE) {
+        uint64_t grid = (uint64_t)resident_ctas_per_sm<C>();
+        if (grid > groups) grid = groups;
+        k_ntt_tile_pipe<C><<<(unsigned)grid, C::THREADS, C::SMEM_BYTES, st>>>(a, groups);
+    } else {
+        k_ntt_tile<C><<<(unsigned)groups, C::THREADS, C::SMEM_BYTES, st>>>(a);
+    }
     return cudaPeekAtLastError() == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
 }
 
-template <int LOGN, int LOGT, int LOGRP, int TPC, bool INV>
+template <int LOGN, int LOGT, int LOGRP, int TPC, int PIPE, bool INV>
 int launch_s1(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t row_begin,
               uint64_t n_rows, void* stream, uint32_t* launches) {
-    using C = TileCfg<LOGN, 0, LOGN, 0, LOGT, LOGRP, TPC, INV>;
-    int rc = launch_tile_kernel<C>(p, in, out, row_begin, n_rows, (cudaStream_t)stream);
+    int rc;
+    if (p.mc == 1)
+        rc = launch_tile_kernel<TileCfg<LOGN, 0, LOGN, 0, LOGT, LOGRP, TPC, INV, 1, PIPE != 0>>(
+            p, in, out, row_begin, n_rows, (cudaStream_t)stream);
+    else
+        rc = launch_tile_kernel<TileCfg<LOGN, 0, LOGN, 0, LOGT, LOGRP, TPC, INV, 0, PIPE != 0>>(
+            p, in, out, row_begin, n_rows, (cudaStream_t)stream);
     if (rc == NTT_OK && launches) *launches += 1;
     return rc;
 }
 
 template <int LOGN, int SPLIT, int LOGP, int LOGTA, int LOGRPA, int TPCA, int LOGTB, int LOGRPB,
-          int TPCB, bool INV>
-int launch_s2(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t row_begin,
-              uint64_t n_rows, void* stream, uint32_t* launches) {
-    using CA = TileCfg<LOGN, 0, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, INV>;
-    using CB = TileCfg<LOGN, SPLIT, LOGN, 0, LOGTB, LOGRPB, TPCB, INV>;
-    cudaStream_t st = (cudaStream_t)stream;
+          int TPCB, int PIPE, bool INV, int MC>
+int launch_s2_mc(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t row_begin,
+                 uint64_t n_rows, cudaStream_t st) {
+    using CA = TileCfg<LOGN, 0, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, INV, MC, PIPE != 0>;
+    using CB = TileCfg<LOGN, SPLIT, LOGN, 0, LOGTB, LOGRPB, TPCB, INV, MC, PIPE != 0>;
     int rc;
     if (!INV) {
         rc = launch_tile_kernel<CA>(p, in, out, row_begin, n_rows, st);
@@ -87,21 +247,34 @@ int launch_s2(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t row_
         rc = launch_tile_kernel<CB>(p, in, out, row_begin, n_rows, st);
         if (rc == NTT_OK) rc = launch_tile_kernel<CA>(p, in, out, row_begin, n_rows, st);
     }
+    return rc;
+}
+
+template <int LOGN, int SPLIT, int LOGP, int LOGTA, int LOGRPA, int TPCA, int LOGTB, int LOGRPB,
+          int TPCB, int PIPE, bool INV>
+int launch_s2(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t row_begin,
+              uint64_t n_rows, void* stream, uint32_t* launches) {
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = p.mc == 1
+        ? launch_s2_mc<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE, INV, 1>(p, in, out, row_begin, n_rows, st)
+        : launch_s2_mc<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE, INV, 0>(p, in, out, row_begin, n_rows, st);
     if (rc == NTT_OK && launches) *launches += 2;
     return rc;
 }
 
-#define NTT_INST_S1(LOGN, LOGT, LOGRP, TPC)                                                     \
-    template int launch_s1<LOGN, LOGT, LOGRP, TPC, false>(const PlanDev&, const uint64_t*,      \
-                                                          uint64_t*, uint64_t, uint64_t, void*, \
-                                                          uint32_t*);                           \
-    template int launch_s1<LOGN, LOGT, LOGRP, TPC, true>(const PlanDev&, const uint64_t*,       \
-                                                         uint64_t*, uint64_t, uint64_t, void*,  \
-                                                         uint32_t*);
-#define NTT_INST_S2(LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB)                \
-    template int launch_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, false>( \
-        const PlanDev&, const uint64_t*, uint64_t*, uint64_t, uint64_t, void*, uint32_t*);      \
-    template int launch_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, true>(  \
-        const PlanDev&, const uint64_t*, uint64_t*, uint64_t, uint64_t, void*, uint32_t*);
+#define NTT_INST_S1(LOGN, LOGT, LOGRP, TPC, PIPE)                                                  \
+    template int launch_s1<LOGN, LOGT, LOGRP, TPC, PIPE, false>(const PlanDev&, const uint64_t*,  \
+                                                                uint64_t*, uint64_t, uint64_t,    \
+                                                                void*, uint32_t*);                \
+    template int launch_s1<LOGN, LOGT, LOGRP, TPC, PIPE, true>(const PlanDev&, const uint64_t*,   \
+                                                               uint64_t*, uint64_t, uint64_t,     \
+                                                               void*, uint32_t*);
+#define NTT_INST_S2(LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE)              \
+    template int launch_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE,      \
+                           false>(const PlanDev&, const uint64_t*, uint64_t*, uint64_t, uint64_t, \
+                                  void*, uint32_t*);                                              \
+    template int launch_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE,      \
+                           true>(const PlanDev&, const uint64_t*, uint64_t*, uint64_t, uint64_t,  \
+                                 void*, uint32_t*);
 
 }  // namespace nttgb

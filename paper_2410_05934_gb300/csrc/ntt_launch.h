@@ -14,6 +14,7 @@ struct PlanDev {
     int* status;
     uint32_t n_moduli;
     uint32_t check;
+    uint32_t mc;        // modulus class: 1 when every modulus is below 2^57
 };
 
 // Transforms rows [row_begin, row_begin + n_rows) of the layout that starts
@@ -21,12 +22,12 @@ struct PlanDev {
 typedef int (*LaunchFn)(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t row_begin,
                         uint64_t n_rows, void* stream, uint32_t* launches);
 
-template <int LOGN, int LOGT, int LOGRP, int TPC, bool INV>
+template <int LOGN, int LOGT, int LOGRP, int TPC, int PIPE, bool INV>
 int launch_s1(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t row_begin,
               uint64_t n_rows, void* stream, uint32_t* launches);
 
 template <int LOGN, int SPLIT, int LOGP, int LOGTA, int LOGRPA, int TPCA, int LOGTB, int LOGRPB,
-          int TPCB, bool INV>
+          int TPCB, int PIPE, bool INV>
 int launch_s2(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t row_begin,
               uint64_t n_rows, void* stream, uint32_t* launches);
 

@@ -16,11 +16,21 @@
 // Each tile lives in shared memory; 2^LOGT threads own it, R = E / 2^LOGT
 // elements each.  Stages are fused in groups of up to LOGRP ("passes",
 // the thread-aggregation idea of Sec. V-B with radix 2^LOGRP per thread): a
-// pass loads a thread's R elements from shared memory into registers,
-// runs its stages there with no synchronisation, and writes them back.
-// Phases are separated only by __syncthreads(), and every phase is a pure
-// function of (thread, shared memory, global memory), so the same code also
-// runs on the host as an emulation (see ntt_emulate.cpp).
+// pass loads a thread's R elements from shared memory into registers, runs
+// its stages there with no synchronisation, and writes them back.
+//
+// Two kernel forms share these phases:
+//   - direct: each CTA loads its tiles with 16-byte loads into registers and
+//     stores them swizzled;
+//   - pipelined (PIPE): a persistent CTA streams its tile groups through two
+//     shared-memory buffers with bulk asynchronous copies (cp.async.bulk +
+//     mbarrier), so the next group's data and twiddles arrive while the
+//     current group computes; data land in natural order and are re-laid
+//     out into the swizzled order before the first pass.
+//
+// Every phase is a function of (thread, its register state, shared memory,
+// global memory) with barriers only between phases, so the same code runs on
+// the host as an emulation (see emulate.cpp), thread by thread.
 //
 // Twiddle table (one per modulus, N entries of {w, w'}): entry k = 2^s + i is
 // psi^{brv(k)} (forward) or psi^{-brv(k)} (inverse) for stage s, group i.
@@ -30,24 +40,30 @@
 #include "ntt_arith.cuh"
 
 #if !defined(__CUDA_ARCH__)
-#include <cassert>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #endif
 
 namespace nttgb {
 
-struct TwPair {
+struct alignas(16) TwPair {
     uint64_t w, wp;
 };
 
 struct LimbConst {
-    uint64_t q, two_q;
+    uint64_t q, two_q, four_q;
+    uint64_t one_p;             // floor(2^64 / q): Shoup form of 1
     uint64_t ninv, ninv_p;      // N^-1 mod q and its Shoup form
     uint64_t w1ninv, w1ninv_p;  // psi^{-brv(1)} N^-1 and its Shoup form (last GS stage)
     uint64_t mu;                // Barrett constant floor(2^(2 bits) / q)
     uint32_t bits, pad_;
 };
+
+// Modulus classes: 0 = any q < 2^62 (exact Shoup quotient, Harvey bounds),
+// 1 = q < 2^57 (approximate quotient, 4q-wide lazy bounds, no conditional
+// subtraction in the forward transform).
+#define NTT_SMALL_MODULUS_BITS 57
 
 struct TileArgs {
     const uint64_t* in;
@@ -62,21 +78,31 @@ struct TileArgs {
 };
 
 #define NTT_STATUS_RANGE (-8)
+#define NTT_STATUS_TIMEOUT (-7)
 
 // Swizzled shared-memory slot of tile element e: XOR-folds the higher 4-bit
 // groups of e into its low 4 bits, which spreads the strided accesses of the
 // later passes over the 16 eight-byte bank pairs.  A bijection on every
-// 16-aligned block, hence on the tile.
-NTT_HD uint32_t swz(uint32_t e) {
-    uint32_t h = e >> 4;
-    return e ^ ((h ^ (h >> 4) ^ (h >> 8)) & 15u);
+// 16-aligned block, hence on the tile.  It is linear over GF(2):
+// swz(a ^ b) = swz(a) ^ swz(b), which the phases use to split an address
+// into a per-thread part and a compile-time part.
+NTT_HD constexpr uint32_t swz(uint32_t e) {
+    return e ^ (((e >> 4) ^ (e >> 8) ^ (e >> 12)) & 15u);
 }
 
-template <int LOGN_, int S0_, int S1_, int LOGP_, int LOGT_, int LOGRP_, int TPC_, bool INV_>
+// Places the bits of x around an r-bit hole at position pe (linear in x).
+NTT_HD constexpr uint32_t spread(uint32_t x, int pe, int r) {
+    return ((x >> pe) << (pe + r)) | (x & ((1u << pe) - 1));
+}
+
+template <int LOGN_, int S0_, int S1_, int LOGP_, int LOGT_, int LOGRP_, int TPC_, bool INV_,
+          int MC_ = 0, bool PIPE_ = false>
 struct TileCfg {
     static constexpr int LOGN = LOGN_, S0 = S0_, S1 = S1_, LOGP = LOGP_, LOGT = LOGT_;
     static constexpr int TPC = TPC_;
     static constexpr bool INV = INV_;
+    static constexpr int MC = MC_;
+    static constexpr bool PIPE = PIPE_;
     static constexpr int A = S1 - S0;
     static constexpr int LOGLO = LOGN - S1;
     static constexpr int LOGE = A + LOGP;
@@ -93,13 +119,33 @@ struct TileCfg {
     // the last writes canonical output
     static constexpr bool FIRST = INV ? (S1 == LOGN) : (S0 == 0);
     static constexpr bool LAST = INV ? (S0 == 0) : (S1 == LOGN);
-    static constexpr size_t SMEM_BYTES = sizeof(uint64_t) * (size_t)E * TPC;
+    // Twiddles of a tile: stages [S0, S1) of one "hi" block need 2^(s-S0)
+    // entries each, 2^A - 1 in all; they are staged in shared memory next to
+    // the tile (always when pipelined, else when both fit comfortably) or
+    // read through the read-only path.
+    static constexpr size_t DATA_BYTES = sizeof(uint64_t) * (size_t)E;
+    static constexpr size_t TW_BYTES = 16 * ((size_t)1 << A);
+    static constexpr bool TWS = PIPE || (DATA_BYTES + TW_BYTES) * TPC <= 160 * 1024;
+    static constexpr size_t TILE_BYTES = DATA_BYTES + (TWS ? TW_BYTES : 0);
+    static constexpr size_t TILE_WORDS = TILE_BYTES / sizeof(uint64_t);
+    static constexpr int NBUF = PIPE ? 2 : 1;
+    static constexpr size_t BUF_BYTES = TILE_BYTES * TPC;
+    static constexpr size_t BUF_WORDS = BUF_BYTES / sizeof(uint64_t);
+    static constexpr size_t BAR_OFFSET = BUF_BYTES * NBUF;      // mbarriers after the buffers
+    static constexpr size_t SMEM_BYTES = BAR_OFFSET + (PIPE ? 16 : 0);
+    // bulk copies of one tile: contiguous runs of 2^LOGP elements (one run
+    // for row tiles) plus one run of twiddles per stage
+    static constexpr int RUNS = LOGLO == 0 ? 1 : (1 << A);
+    static constexpr uint32_t RUN_BYTES = (uint32_t)(LOGLO == 0 ? DATA_BYTES : (8u << LOGP));
+    static constexpr int COPIES = RUNS + A;
+    static constexpr uint32_t TILE_TX_BYTES = (uint32_t)(DATA_BYTES + 16u * ((1u << A) - 1));
 
     static_assert(A >= 1 && A <= LOGN, "stage range");
     static_assert(LOGLO >= LOGP, "passive columns must fit below the active bits");
     static_assert(LOGLO == 0 || LOGP >= 1, "column tiles need >= 2 adjacent columns");
     static_assert(LOGR >= 1, "each thread needs an element pair");
     static_assert(RP >= 1, "pass width");
+    static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per CTA");
 };
 
 // stage range [s_lo, s_lo + r) of pass p, passes numbered from the top index
@@ -115,7 +161,7 @@ struct TileLoc {
     uint64_t row;
     uint32_t limb;
     uint32_t hi;
-    uint32_t lo_base;
+    uint32_t gbase;     // g(0): the tile's hi and lo_base bits
     bool valid;
 };
 
@@ -129,16 +175,21 @@ NTT_HD TileLoc locate(const TileArgs& a, uint64_t tile) {
     L.row = a.row_begin + row_local;
     L.limb = (uint32_t)(L.row % a.n_moduli);
     L.hi = tau >> C::LOGLOBLK;
-    L.lo_base = (tau & ((1u << C::LOGLOBLK) - 1)) << C::LOGP;
+    uint32_t lo_base = (tau & ((1u << C::LOGLOBLK) - 1)) << C::LOGP;
+    L.gbase = (L.hi << (C::LOGN - C::S0)) | lo_base;
     return L;
 }
 
-// global index (within the row) of tile element e
+// bits of the row-local index g contributed by tile element e (linear in e):
+// g(e) = gbase | place(e)
+template <class C>
+NTT_HD constexpr uint32_t place(uint32_t e) {
+    return ((e >> C::LOGP) << C::LOGLO) | (e & ((1u << C::LOGP) - 1));
+}
+
 template <class C>
 NTT_HD uint32_t gidx(const TileLoc& L, uint32_t e) {
-    uint32_t a = e >> C::LOGP;
-    uint32_t p = e & ((1u << C::LOGP) - 1);
-    return ((uint32_t)L.hi << (C::LOGN - C::S0)) | (a << C::LOGLO) | (L.lo_base + p);
+    return L.gbase | place<C>(e);
 }
 
 #if defined(__CUDA_ARCH__)
@@ -194,75 +245,164 @@ NTT_HD void record_status(int* status, int code) {
 #endif
 }
 
-// ---- phase 1: global -> shared (16-byte pairs, coalesced) ----
+NTT_HD uint32_t floor_log2(uint32_t x) {
+#if defined(__CUDA_ARCH__)
+    return 31u - (uint32_t)__clz(x);
+#else
+    return 31u - (uint32_t)__builtin_clz(x);
+#endif
+}
+
+// Per-thread register state carried between phases.
 template <class C>
-NTT_HD void phase_load(const TileArgs& a, const TileLoc& L, int t, uint64_t* sm) {
+struct TileRegs {
+    uint64_t x[C::R];
+};
+
+// ---- load (direct form): global -> registers, 16-byte coalesced pairs ----
+// Thread t holds the pairs e = 2 (t + i T) = 2t ^ 2iT (disjoint bits), so
+// g(e) = (gbase | place(2t)) + place(2iT) with a compile-time second term.
+template <class C>
+NTT_HD void load_direct(TileRegs<C>& st, const TileArgs& a, const TileLoc& L, int t, uint64_t* sm) {
     if (!L.valid) return;
-    const uint64_t* src = (C::FIRST ? a.in : a.out) + (L.row << C::LOGN);
+    if (C::TWS) {
+        // the tile's 2^A - 1 twiddles: slot i <-> stage S0 + d, d = floor(log2(i + 1))
+        const TwPair* tw = a.tw + ((uint64_t)L.limb << C::LOGN);
+        TwPair* tws = reinterpret_cast<TwPair*>(sm + C::E);
+        for (uint32_t i = (uint32_t)t; i < (1u << C::A) - 1; i += C::T) {
+            const uint32_t d = floor_log2(i + 1);
+            const uint32_t k = (1u << (C::S0 + d)) + (L.hi << d) + (i + 1 - (1u << d));
+            NTT_GMEM_CHECK(k, 1u << C::LOGN);
+            tws[i] = load_tw(tw, k);
+        }
+    }
+    const uint32_t gt = L.gbase | place<C>(2u * (uint32_t)t);
+    const uint64_t* src = (C::FIRST ? a.in : a.out) + (L.row << C::LOGN) + gt;
     const uint64_t q = a.lc[L.limb].q;
+    bool bad = false;
 #pragma unroll
     for (int i = 0; i < C::R / 2; ++i) {
-        uint32_t k = (uint32_t)t + (uint32_t)i * C::T;
-        uint32_t e = 2 * k;
-        uint32_t g = gidx<C>(L, e);
-        NTT_GMEM_CHECK(g + 1, 1u << C::LOGN);
-        uint64_t x, y;
-        load_pair(src + g, x, y);
-        if (C::FIRST && a.check && (x >= q || y >= q)) record_status(a.status, NTT_STATUS_RANGE);
-        NTT_SMEM_CHECK(swz(e), C::E);
-        NTT_SMEM_CHECK(swz(e + 1), C::E);
-        sm[swz(e)] = x;
-        sm[swz(e + 1)] = y;
+        const uint32_t off = place<C>(2u * (uint32_t)i * C::T);
+        NTT_GMEM_CHECK(gt + off + 1, 1u << C::LOGN);
+        load_pair(src + off, st.x[2 * i], st.x[2 * i + 1]);
+        if (C::FIRST) bad |= st.x[2 * i] >= q || st.x[2 * i + 1] >= q;
+    }
+    if (C::FIRST && a.check && bad) record_status(a.status, NTT_STATUS_RANGE);
+}
+
+// registers (pair layout of load_direct / relayout_read) -> swizzled shared memory
+template <class C>
+NTT_HD void write_pairs_swizzled(const TileRegs<C>& st, const TileLoc& L, int t, uint64_t* sm) {
+    if (!L.valid) return;
+    const uint32_t b = swz(2u * (uint32_t)t);
+#pragma unroll
+    for (int i = 0; i < C::R / 2; ++i) {
+        const uint32_t c = swz(2u * (uint32_t)i * C::T);
+        NTT_SMEM_CHECK(b ^ c, C::E);
+        NTT_SMEM_CHECK(b ^ c ^ 1u, C::E);
+        sm[b ^ c] = st.x[2 * i];
+        sm[(b ^ c) ^ 1u] = st.x[2 * i + 1];   // swz(e + 1) = swz(e) ^ 1 for even e
     }
 }
 
-// tile element held in register j of thread t during a pass over e-bits [pe, pe + r)
+// natural-order shared memory (pipelined staging) -> registers in the pair
+// layout; checks canonical inputs for the first kernel of a transform
 template <class C>
-NTT_HD uint32_t pass_elem(int t, int j, int pe, int r) {
-    uint32_t jlo = (uint32_t)j & ((1u << r) - 1);
-    uint32_t jhi = (uint32_t)j >> r;
-    uint32_t other = (uint32_t)t | (jhi << C::LOGT);
-    uint32_t low = other & ((1u << pe) - 1);
-    uint32_t high = other >> pe;
-    return (high << (pe + r)) | (jlo << pe) | low;
+NTT_HD void relayout_read(TileRegs<C>& st, const TileArgs& a, const TileLoc& L, int t, const uint64_t* sm) {
+    if (!L.valid) return;
+    const uint64_t q = a.lc[L.limb].q;
+    bool bad = false;
+#pragma unroll
+    for (int i = 0; i < C::R / 2; ++i) {
+        const uint32_t e = 2u * ((uint32_t)t + (uint32_t)i * C::T);
+        NTT_SMEM_CHECK(e + 1, C::E);
+        load_pair(sm + e, st.x[2 * i], st.x[2 * i + 1]);
+        if (C::FIRST) bad |= st.x[2 * i] >= q || st.x[2 * i + 1] >= q;
+    }
+    if (C::FIRST && a.check && bad) record_status(a.status, NTT_STATUS_RANGE);
 }
 
-// ---- phase 2..: one fused group of r stages in registers ----
+// ---- passes: one fused group of r stages in registers ----
 template <class C, int P>
-NTT_HD void phase_pass(const TileArgs& a, const TileLoc& L, int t, uint64_t* sm) {
+struct PassGeom {
+    static constexpr int S_LO = C::S0 + P * C::RP;
+    static constexpr int REM = C::S1 - S_LO;
+    static constexpr int r = REM < C::RP ? REM : C::RP;
+    static constexpr int PE = C::LOGP + C::S1 - S_LO - r;   // e-bit of the pass's lowest bit
+    static constexpr int G = C::R >> r;                     // independent groups per thread
+    static constexpr int GS = 1 << r;                       // elements per group
+    // e of register j, minus the thread's contribution spread(t)
+    static NTT_HD constexpr uint32_t ej(int j) {
+        return spread(((uint32_t)j >> r) << C::LOGT, PE, r) | (((uint32_t)j & (GS - 1)) << PE);
+    }
+};
+
+template <class C, int P>
+NTT_HD void pass_read(TileRegs<C>& st, const TileLoc& L, int t, const uint64_t* sm) {
     if (!L.valid) return;
-    constexpr int S_LO = C::S0 + P * C::RP;
-    constexpr int REM = C::S1 - S_LO;
-    constexpr int r = REM < C::RP ? REM : C::RP;
-    // e-bit position of the pass's lowest bit
-    constexpr int PE = C::LOGP + C::S1 - S_LO - r;
-    constexpr int G = C::R >> r;        // independent groups per thread
-    constexpr int GS = 1 << r;          // elements per group
-    const LimbConst lc = a.lc[L.limb];
-    const TwPair* tw = a.tw + ((uint64_t)L.limb << C::LOGN);
-    uint64_t x[C::R];
+    using Gm = PassGeom<C, P>;
+    const uint32_t b = swz(spread((uint32_t)t, Gm::PE, Gm::r));
 #pragma unroll
     for (int j = 0; j < C::R; ++j) {
-        uint32_t e = pass_elem<C>(t, j, PE, r);
-        NTT_SMEM_CHECK(swz(e), C::E);
-        x[j] = sm[swz(e)];
+        const uint32_t addr = b ^ swz(Gm::ej(j));
+        NTT_SMEM_CHECK(addr, C::E);
+        st.x[j] = sm[addr];
     }
+}
+
+template <class C, int P>
+NTT_HD void pass_write(const TileRegs<C>& st, const TileLoc& L, int t, uint64_t* sm) {
+    if (!L.valid) return;
+    using Gm = PassGeom<C, P>;
+    const uint32_t b = swz(spread((uint32_t)t, Gm::PE, Gm::r));
 #pragma unroll
-    for (int gi = 0; gi < G; ++gi) {
-        uint32_t e0 = pass_elem<C>(t, gi * GS, PE, r);
-        uint32_t prefix = gidx<C>(L, e0) >> (C::LOGN - S_LO);
+    for (int j = 0; j < C::R; ++j) {
+        const uint32_t addr = b ^ swz(Gm::ej(j));
+        sm[addr] = st.x[j];
+    }
+}
+
+template <class C, int P>
+NTT_HD void pass_compute(TileRegs<C>& st, const TileArgs& a, const TileLoc& L, int t, const uint64_t* sm) {
+    if (!L.valid) return;
+    using Gm = PassGeom<C, P>;
+    constexpr int S_LO = Gm::S_LO, r = Gm::r, GS = Gm::GS;
+    const LimbConst lc = a.lc[L.limb];
+    const TwPair* tw = a.tw + ((uint64_t)L.limb << C::LOGN);
+    const TwPair* tws = reinterpret_cast<const TwPair*>(sm + C::E);
+    // row-local index bits above the pass: (g >> (LOGN - S_LO)) = hi part | pre_t | pre(gi)
+    constexpr int SH = C::LOGN - S_LO;
+    const uint32_t pre_t = place<C>(spread((uint32_t)t, Gm::PE, r)) >> SH;
+    const uint32_t hi_part = L.hi << (S_LO - C::S0);
+#pragma unroll
+    for (int gi = 0; gi < Gm::G; ++gi) {
+        const uint32_t pre = pre_t | (place<C>(Gm::ej(gi * GS)) >> SH);
+        uint64_t* x = st.x + gi * GS;
         if (!C::INV) {
 #pragma unroll
             for (int v = 0; v < r; ++v) {
                 const int s = S_LO + v;
                 const int d = 1 << (r - 1 - v);
+                const int dd = s - C::S0;
+                // butterfly jl uses table entry k0 + (jl >> (r - v)), staged at slot0 + (jl >> (r - v))
+                const uint32_t slot0 = ((1u << dd) - 1) + (pre << v);
+                const uint32_t k0 = (1u << s) + ((hi_part | pre) << v);
 #pragma unroll
                 for (int jl = 0; jl < GS; ++jl) {
                     if (jl & d) continue;
-                    uint32_t k = (1u << s) + (prefix << v) + ((uint32_t)jl >> (r - v));
-                    NTT_GMEM_CHECK(k, 1u << C::LOGN);
-                    TwPair w = load_tw(tw, k);
-                    ct_butterfly(x[gi * GS + jl], x[gi * GS + jl + d], w.w, w.wp, lc.q, lc.two_q);
+                    const uint32_t off = (uint32_t)jl >> (r - v);
+                    TwPair w;
+                    if (C::TWS) {
+                        NTT_SMEM_CHECK(slot0 + off, (1u << C::A) - 1);
+                        w = tws[slot0 + off];
+                    } else {
+                        NTT_GMEM_CHECK(k0 + off, 1u << C::LOGN);
+                        w = load_tw(tw, k0 + off);
+                    }
+                    if (C::MC == 1)
+                        ct_butterfly_small(x[jl], x[jl + d], w.w, w.wp, lc.q, lc.four_q);
+                    else
+                        ct_butterfly(x[jl], x[jl + d], w.w, w.wp, lc.q, lc.two_q);
                 }
             }
         } else {
@@ -270,43 +410,58 @@ NTT_HD void phase_pass(const TileArgs& a, const TileLoc& L, int t, uint64_t* sm)
             for (int v = r - 1; v >= 0; --v) {
                 const int s = S_LO + v;
                 const int d = 1 << (r - 1 - v);
+                const int dd = s - C::S0;
+                const uint32_t slot0 = ((1u << dd) - 1) + (pre << v);
+                const uint32_t k0 = (1u << s) + ((hi_part | pre) << v);
 #pragma unroll
                 for (int jl = 0; jl < GS; ++jl) {
                     if (jl & d) continue;
                     if (s == 0) {
-                        gs_butterfly_scaled(x[gi * GS + jl], x[gi * GS + jl + d], lc.ninv, lc.ninv_p,
-                                            lc.w1ninv, lc.w1ninv_p, lc.q, lc.two_q);
+                        if (C::MC == 1)
+                            gs_butterfly_scaled_small(x[jl], x[jl + d], lc.ninv, lc.ninv_p, lc.w1ninv,
+                                                      lc.w1ninv_p, lc.q, lc.four_q);
+                        else
+                            gs_butterfly_scaled(x[jl], x[jl + d], lc.ninv, lc.ninv_p, lc.w1ninv,
+                                                lc.w1ninv_p, lc.q, lc.two_q);
                     } else {
-                        uint32_t k = (1u << s) + (prefix << v) + ((uint32_t)jl >> (r - v));
-                        NTT_GMEM_CHECK(k, 1u << C::LOGN);
-                        TwPair w = load_tw(tw, k);
-                        gs_butterfly(x[gi * GS + jl], x[gi * GS + jl + d], w.w, w.wp, lc.q, lc.two_q);
+                        const uint32_t off = (uint32_t)jl >> (r - v);
+                        TwPair w;
+                        if (C::TWS) {
+                            NTT_SMEM_CHECK(slot0 + off, (1u << C::A) - 1);
+                            w = tws[slot0 + off];
+                        } else {
+                            NTT_GMEM_CHECK(k0 + off, 1u << C::LOGN);
+                            w = load_tw(tw, k0 + off);
+                        }
+                        if (C::MC == 1)
+                            gs_butterfly_small(x[jl], x[jl + d], w.w, w.wp, lc.q, lc.four_q);
+                        else
+                            gs_butterfly(x[jl], x[jl + d], w.w, w.wp, lc.q, lc.two_q);
                     }
                 }
             }
         }
     }
-#pragma unroll
-    for (int j = 0; j < C::R; ++j) {
-        uint32_t e = pass_elem<C>(t, j, PE, r);
-        sm[swz(e)] = x[j];
-    }
 }
 
-// ---- last phase: shared -> global, canonical when this kernel ends the transform ----
+// ---- store: swizzled shared -> global, canonical when this kernel ends the transform ----
 template <class C>
-NTT_HD void phase_store(const TileArgs& a, const TileLoc& L, int t, const uint64_t* sm) {
+NTT_HD void store_tile(const TileArgs& a, const TileLoc& L, int t, const uint64_t* sm) {
     if (!L.valid) return;
-    uint64_t* dst = a.out + (L.row << C::LOGN);
+    const uint32_t gt = L.gbase | place<C>(2u * (uint32_t)t);
+    uint64_t* dst = a.out + (L.row << C::LOGN) + gt;
     const uint64_t q = a.lc[L.limb].q, two_q = a.lc[L.limb].two_q;
+    const uint64_t one_p = a.lc[L.limb].one_p;
+    const uint32_t b = swz(2u * (uint32_t)t);
 #pragma unroll
     for (int i = 0; i < C::R / 2; ++i) {
-        uint32_t k = (uint32_t)t + (uint32_t)i * C::T;
-        uint32_t e = 2 * k;
-        uint32_t g = gidx<C>(L, e);
-        uint64_t x = sm[swz(e)], y = sm[swz(e + 1)];
+        const uint32_t c = swz(2u * (uint32_t)i * C::T);
+        uint64_t x = sm[b ^ c], y = sm[(b ^ c) ^ 1u];
         if (C::LAST) {
-            if (!C::INV) {  // [0, 4q) -> [0, q)
+            if (C::MC == 1 && !C::INV) {  // [0, 65q) -> [0, q)
+                x = reduce_full_small(x, one_p, q, two_q);
+                y = reduce_full_small(y, one_p, q, two_q);
+            } else if (C::MC == 1 || !C::INV) {  // [0, 4q) -> [0, q)
                 x = csub(csub(x, two_q), q);
                 y = csub(csub(y, two_q), q);
             } else {        // [0, 2q) -> [0, q)
@@ -314,9 +469,48 @@ NTT_HD void phase_store(const TileArgs& a, const TileLoc& L, int t, const uint64
                 y = csub(y, q);
             }
         }
-        NTT_GMEM_CHECK(g + 1, 1u << C::LOGN);
-        store_pair(dst + g, x, y);
+        const uint32_t off = place<C>(2u * (uint32_t)i * C::T);
+        NTT_GMEM_CHECK(gt + off + 1, 1u << C::LOGN);
+        store_pair(dst + off, x, y);
     }
+}
+
+// ---- pipelined form: the bulk copies of one tile ----
+// Copy c of a tile: c < RUNS -> data run c (natural order in shared memory);
+// else the twiddles of stage S0 + (c - RUNS) into their slots.
+struct CopyDesc {
+    const void* src;
+    uint32_t dst_word;    // offset in the tile's shared-memory words
+    uint32_t bytes;
+};
+
+template <class C>
+NTT_HD CopyDesc tile_copy(const TileArgs& a, const TileLoc& L, int c) {
+    CopyDesc d;
+    if (c < C::RUNS) {
+        const uint64_t* src = (C::FIRST ? a.in : a.out) + (L.row << C::LOGN);
+        d.src = src + (L.gbase | ((uint32_t)c << C::LOGLO));
+        d.dst_word = (uint32_t)c << C::LOGP;
+        d.bytes = C::RUN_BYTES;
+    } else {
+        const uint32_t dd = (uint32_t)(c - C::RUNS);
+        const TwPair* tw = a.tw + ((uint64_t)L.limb << C::LOGN);
+        d.src = tw + (1u << (C::S0 + dd)) + (L.hi << dd);
+        d.dst_word = C::E + 2u * ((1u << dd) - 1);
+        d.bytes = 16u << dd;
+    }
+    return d;
+}
+
+// Tile slot `tin` of a pipeline buffer last held group g_prev's tile; when
+// that tile had the same (limb, hi), its twiddles are still in place and are
+// not copied again (all tiles of a single-modulus batch share them).
+template <class C>
+NTT_HD bool twiddles_reusable(const TileArgs& a, uint64_t g, uint64_t g_prev, bool have_prev, int tin) {
+    if (!have_prev) return false;
+    const TileLoc P = locate<C>(a, g_prev * C::TPC + tin);
+    const TileLoc L = locate<C>(a, g * C::TPC + tin);
+    return P.valid && L.valid && P.limb == L.limb && P.hi == L.hi;
 }
 
 }  // namespace nttgb

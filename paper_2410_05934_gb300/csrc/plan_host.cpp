@@ -120,6 +120,9 @@ int build_plan_host(PlanHost& h, uint32_t log2n, const uint64_t* moduli, uint32_
     h.fwd.resize((size_t)n_moduli * n);
     h.inv.resize((size_t)n_moduli * n);
     h.consts.resize(n_moduli);
+    h.mc = 1;
+    for (uint32_t l = 0; l < n_moduli; ++l)
+        if (moduli[l] >= (1ull << NTT_SMALL_MODULUS_BITS)) h.mc = 0;
     std::vector<uint64_t> pw(n), pwi(n);
     for (uint32_t l = 0; l < n_moduli; ++l) {
         const uint64_t q = moduli[l];
@@ -145,6 +148,8 @@ int build_plan_host(PlanHost& h, uint32_t log2n, const uint64_t* moduli, uint32_
         std::memset(&c, 0, sizeof(c));
         c.q = q;
         c.two_q = 2 * q;
+        c.four_q = 4 * q;
+        c.one_p = shoup_of(1, q);
         c.ninv = pow_mod(n % q, q - 2, q);
         c.ninv_p = shoup_of(c.ninv, q);
         c.w1ninv = mul_mod(v[1].w, c.ninv, q);

@@ -1,0 +1,259 @@
+"""Autotuner of the transform schedules (the switch-point / fused-stage choice
+of Sec. V-D, decided here by measurement).
+
+For a shape (log2 N, limbs, batch, modulus bits) every candidate schedule of
+that N is timed with CUDA events on the launching stream (warm-up, then the
+median of several repetitions; optional L2 flush between repetitions) for the
+forward and the inverse transform.  Results go to a JSON-lines timing DB keyed
+by (GPU name, library build, shape, direction, schedule) so that tuning
+resumes where it stopped and the cost model can train on it.
+
+    python -m paper_2410_05934_gb300.tune --shape 16,24,4 [--shape 10,1,5040]
+
+The heuristic arm (``heuristic_schedule``) is the paper's SM-aware rule
+restated for these kernels: pick the schedule whose number of independent
+work chunks per launch is closest to a whole number of waves of the SM count,
+fewer kernels first.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import time
+
+from . import ntt as _ntt
+from . import workloads as W
+
+DEFAULT_DB = os.environ.get("NTT_TUNE_DB", os.path.join(os.path.expanduser("~"), ".cache", "ntt_gb300",
+                                                        "tune.jsonl"))
+
+
+def moduli_for(log2n, limbs, bits=50):
+    """`limbs` moduli of the requested size class: 50 -> the 50-bit pool (any
+    N <= 2^16); 59 / 62 -> the 59- / 62-bit prime (N <= 1024), repeated."""
+    if bits == 50:
+        return W.POOL50[:limbs]
+    if log2n > 10:
+        raise ValueError("the 59/62-bit primes are NTT-friendly only up to N = 1024")
+    return [W.Q59_N1024 if bits == 59 else W.Q62_N1024] * limbs
+
+
+def build_stamp():
+    from . import build as B
+    try:
+        return open(B.LIB + ".stamp").read().strip()[:16]
+    except OSError:
+        return "unknown"
+
+
+def gpu_name():
+    import torch
+    return torch.cuda.get_device_name(torch.cuda.current_device())
+
+
+class Timer:
+    """Times plan.forward / plan.inverse per schedule on one buffer set."""
+
+    def __init__(self, log2n, limbs, batch, bits=50, flush_l2=None, seed=1):
+        import numpy as np
+        import torch
+        self.torch = torch
+        self.log2n, self.limbs, self.batch = log2n, limbs, batch
+        self.moduli = moduli_for(log2n, limbs, bits)
+        self.plan = _ntt.Plan(log2n, self.moduli, batch)
+        n = 1 << log2n
+        rows = batch * limbs
+        dev = torch.device("cuda", torch.cuda.current_device())
+        # canonical inputs generated on the device (the smallest modulus bounds all rows)
+        qmin = min(self.moduli)
+        g = torch.Generator(device=dev)
+        g.manual_seed(seed)
+        self.x = torch.randint(0, qmin, (rows, n), dtype=torch.int64, device=dev, generator=g)
+        self.y = torch.empty_like(self.x)
+        nbytes = rows * n * 8
+        self.flush_l2 = (nbytes < (256 << 20)) if flush_l2 is None else flush_l2
+        self.flush = torch.empty(512 << 18, dtype=torch.int32, device=dev) if self.flush_l2 else None
+        self.stream = torch.cuda.current_stream()
+        del np
+
+    def time(self, sched, inverse=False, reps=7, warmup=2):
+        torch = self.torch
+        self.plan.schedule = sched
+        fn = self.plan.inverse if inverse else self.plan.forward
+        for _ in range(warmup):
+            fn(self.x, self.y)
+        ms = []
+        for r in range(reps):
+            if self.flush is not None:
+                self.flush.fill_(r)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(self.stream)
+            fn(self.x, self.y)
+            b.record(self.stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms), min(ms), max(ms)
+
+    def close(self):
+        self.plan.close()
+        del self.x, self.y, self.flush
+
+
+def load_db(path=DEFAULT_DB):
+    recs = []
+    if os.path.exists(path):
+        with open(path) as f:
+            for line in f:
+                line = line.strip()
+                if line:
+                    try:
+                        recs.append(json.loads(line))
+                    except ValueError:
+                        pass
+    return recs
+
+
+def _key(r):
+    return (r["gpu"], r["build"], r["log2n"], r["limbs"], r["batch"], r["bits"], r["inverse"], r["sched"])
+
+
+def tune_shape(log2n, limbs, batch, bits=50, db=DEFAULT_DB, reps=7, skip_done=True, directions=(False, True)):
+    """Times every schedule of one shape; appends new records to the DB."""
+    gpu, stamp = gpu_name(), build_stamp()
+    done = {_key(r) for r in load_db(db)} if skip_done else set()
+    timer = None
+    out = []
+    os.makedirs(os.path.dirname(db) or ".", exist_ok=True)
+    try:
+        for inverse in directions:
+            for s in range(_ntt.schedule_count(log2n)):
+                rec = dict(gpu=gpu, build=stamp, log2n=log2n, limbs=limbs, batch=batch, bits=bits,
+                           inverse=bool(inverse), sched=s)
+                if _key(rec) in done:
+                    continue
+                if timer is None:
+                    timer = Timer(log2n, limbs, batch, bits)
+                med, lo, hi = timer.time(s, inverse, reps=reps)
+                rec.update(ms=med, ms_min=lo, ms_max=hi, t=time.time())
+                out.append(rec)
+                with open(db, "a") as f:
+                    f.write(json.dumps(rec) + "\n")
+    finally:
+        if timer is not None:
+            timer.close()
+    return out
+
+
+def best_from_db(log2n, limbs, batch, bits=50, inverse=False, db=DEFAULT_DB, recs=None):
+    """Fastest recorded schedule for this exact shape, or None."""
+    gpu, stamp = gpu_name(), build_stamp()
+    recs = load_db(db) if recs is None else recs
+    cands = [r for r in recs if r["gpu"] == gpu and r["build"] == stamp and r["log2n"] == log2n
+             and r["limbs"] == limbs and r["batch"] == batch and r["bits"] == bits
+             and r["inverse"] == bool(inverse)]
+    if not cands:
+        return None
+    return min(cands, key=lambda r: r["ms"])["sched"]
+
+
+# ---- the paper's SM-aware rule as the heuristic arm --------------------------
+
+def schedule_params(log2n, sched):
+    """Decodes the schedule description into (kernels, rows per CTA, threads per row)."""
+    name = _ntt.schedule_name(log2n, sched)
+    return name
+
+
+def chunks_per_launch(log2n, sched, rows):
+    """Independent work chunks (CTAs) of the first kernel of a schedule."""
+    name = _ntt.schedule_name(log2n, sched)
+    if name.startswith("1k"):
+        # "1k: T thr/row x R coef, <=F fused stages/pass, P rows/CTA"
+        per_cta = int(name.split(",")[-1].split()[0])
+        return math.ceil(rows / per_cta), 1
+    # 2k split a+b: column tiles of 2^a x C -> N / (2^a C) tiles per row, TPC per CTA
+    split = int(name.split()[2].split("+")[0])
+    cols = int(name.split("col tile 2^")[1].split("x")[1].split()[0])
+    tpc = int(name.split("/pass, ")[1].split("/CTA")[0])
+    tiles = rows * (1 << log2n) // ((1 << split) * cols)
+    return math.ceil(tiles / tpc), 2
+
+
+def heuristic_schedule(log2n, rows, sms=152):
+    """Sec. V-D restated: chunks closest to a whole number of SM waves; fewer kernels first."""
+    best, best_score = 0, None
+    for s in range(_ntt.schedule_count(log2n)):
+        ctas, kernels = chunks_per_launch(log2n, s, rows)
+        waves = ctas / sms
+        frac = abs(waves - max(1, round(waves))) / max(1, round(waves))
+        score = (kernels, frac)
+        if best_score is None or score < best_score:
+            best, best_score = s, score
+    return best
+
+
+def probe_peaks(iters=4000, reps=3):
+    """Butterflies/s of the integer-pipe probe for each butterfly kind."""
+    import torch
+    from . import _native
+    L = _native.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    st = torch.cuda.current_stream()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.empty(sms * 8 * 256, dtype=torch.int64, device=dev)
+    out = {}
+    for kind, q in [(0, W.POOL50[0]), (1, W.POOL50[0]), (2, W.POOL50[0]), (3, W.POOL50[0])]:
+        best = 0.0
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            rc = L.ntt_bench_butterflies(q, kind, sms * 8, 256, iters, sink.data_ptr(), st.cuda_stream)
+            if rc:
+                raise RuntimeError("ntt_bench_butterflies: %d" % rc)
+            b.record(st)
+            b.synchronize()
+            best = max(best, sms * 8 * 256 * iters * 8 / (a.elapsed_time(b) * 1e-3))
+        out[kind] = best
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--shape", action="append", default=[], help="log2n,limbs,batch[,bits]")
+    ap.add_argument("--db", default=DEFAULT_DB)
+    ap.add_argument("--reps", type=int, default=7)
+    ap.add_argument("--redo", action="store_true")
+    ap.add_argument("--sched", type=int, default=None, help="time only this schedule")
+    ap.add_argument("--direction", choices=["fwd", "inv", "both"], default="both")
+    ap.add_argument("--probe", action="store_true", help="print the butterfly probe rates")
+    args = ap.parse_args()
+    if args.probe:
+        names = {0: "CT exact", 1: "GS exact", 2: "CT small-modulus", 3: "GS small-modulus"}
+        for k, v in probe_peaks().items():
+            print("probe %-18s %.1f G butterflies/s" % (names[k], v / 1e9))
+    dirs = {"fwd": (False,), "inv": (True,), "both": (False, True)}[args.direction]
+    for sh in args.shape:
+        v = [int(t) for t in sh.split(",")]
+        log2n, limbs, batch = v[:3]
+        bits = v[3] if len(v) > 3 else 50
+        rows = limbs * batch
+        if args.sched is not None:
+            timer = Timer(log2n, limbs, batch, bits)
+            for inv in dirs:
+                med, lo, hi = timer.time(args.sched, inv, reps=args.reps)
+                print("N=2^%d limbs=%d batch=%d %s sched %d: %.4f ms" % (
+                    log2n, limbs, batch, "inv" if inv else "fwd", args.sched, med))
+            timer.close()
+            continue
+        recs = tune_shape(log2n, limbs, batch, bits, db=args.db, reps=args.reps, skip_done=not args.redo,
+                          directions=dirs)
+        for r in recs:
+            coef = rows * (1 << log2n)
+            print("N=2^%d limbs=%d batch=%d %s sched %d: %.4f ms  (%.1f Gcoef/s)  %s" % (
+                log2n, limbs, batch, "inv" if r["inverse"] else "fwd", r["sched"], r["ms"],
+                coef / r["ms"] / 1e6, _ntt.schedule_name(log2n, r["sched"])))
+
+
+if __name__ == "__main__":
+    main()

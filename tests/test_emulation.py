@@ -8,16 +8,20 @@ from paper_2410_05934_gb300 import workloads as W
 import emu
 
 
-def _moduli(log2n):
-    if log2n <= 10:
+def _moduli(log2n, cls="big"):
+    """big: 59/62-bit moduli (exact-quotient class); small: 50-bit (approximate class)."""
+    if log2n <= 10 and cls == "big":
         return [W.Q62_N1024, W.Q59_N1024]
     return [W.POOL50[0], W.POOL50[7]]
 
 
+@pytest.mark.parametrize("cls", ["big", "small"])
 @pytest.mark.parametrize("log2n", range(1, 17))
-def test_every_schedule_matches_oracle(oracle, log2n):
+def test_every_schedule_matches_oracle(oracle, log2n, cls):
+    if cls == "big" and log2n > 10:
+        pytest.skip("no 59/62-bit prime is 1 mod 2N beyond N = 1024")
     n = 1 << log2n
-    mods = _moduli(log2n)
+    mods = _moduli(log2n, cls)
     batch = 2
     plan = emu.EmuPlan(log2n, mods, batch)
     per_row = [mods[r % len(mods)] for r in range(batch * len(mods))]
@@ -60,8 +64,9 @@ def test_in_place_and_row_ranges(oracle, log2n):
     assert np.array_equal(z[:2], x[:2]) and np.array_equal(z[5:], x[5:])
 
 
-def test_extreme_values(oracle):
-    log2n, q = 10, W.Q62_N1024
+@pytest.mark.parametrize("q", [W.Q62_N1024, W.POOL50[0]])
+def test_extreme_values(oracle, q):
+    log2n = 10
     n = 1 << log2n
     plan = emu.EmuPlan(log2n, [q], 3)
     x = np.zeros((3, n), dtype=np.uint64)
@@ -98,3 +103,24 @@ def test_pointwise_barrett_matches_oracle(oracle):
         c = plan.pointwise(a, b)
         for r in range(4):
             assert np.array_equal(c[r], oracle.pointwise(a[r], b[r], q))
+
+
+@pytest.mark.parametrize("log2n,rows", [(8, 13), (10, 11), (12, 7), (16, 3)])
+def test_single_modulus_batches(oracle, log2n, rows):
+    """One modulus for all rows: the pipelined kernels keep a tile slot's
+    twiddles across groups instead of copying them again."""
+    q = W.POOL50[3]
+    n = 1 << log2n
+    plan = emu.EmuPlan(log2n, [q], rows)
+    x = W.rows_uniform(17, log2n, [q] * rows, n)
+    if log2n <= 12:
+        ref = oracle.transform_rows(x, [q] * rows)
+        idx = None
+    else:
+        idx = np.stack([np.array([0, 5, n // 3, n - 1])] * rows).astype(np.uint32)
+        ref = oracle.transform_rows(x, [q] * rows, idx=idx)
+    for s in range(emu.schedule_count(log2n)):
+        out = plan.transform(x, s)
+        got = out if idx is None else out[np.arange(rows)[:, None], idx]
+        assert np.array_equal(got, ref), s
+        assert np.array_equal(plan.transform(out, s, inverse=True), x), s

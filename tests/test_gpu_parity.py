@@ -18,8 +18,9 @@ import paper_2410_05934_gb300 as ntt  # noqa: E402
 from gpu_util import to_dev, to_host  # noqa: E402
 
 
-def _moduli(log2n):
-    if log2n <= 10:
+def _moduli(log2n, cls="big"):
+    """big: 59/62-bit moduli (exact-quotient class); small: 50-bit (approximate class)."""
+    if log2n <= 10 and cls == "big":
         return [W.Q62_N1024, W.Q59_N1024]
     return [W.POOL50[0], W.POOL50[7]]
 
@@ -30,10 +31,13 @@ def _sample_idx(n, rows, k, seed):
     return np.stack([np.concatenate([base, rng.integers(0, n, k)]) for _ in range(rows)]).astype(np.uint32)
 
 
+@pytest.mark.parametrize("cls", ["big", "small"])
 @pytest.mark.parametrize("log2n", range(1, 17))
-def test_every_schedule_bit_exact(oracle, log2n):
+def test_every_schedule_bit_exact(oracle, log2n, cls):
+    if cls == "big" and log2n > 10:
+        pytest.skip("no 59/62-bit prime is 1 mod 2N beyond N = 1024")
     n = 1 << log2n
-    mods = _moduli(log2n)
+    mods = _moduli(log2n, cls)
     batch = 3 if log2n > 12 else 5            # ragged: not a multiple of rows per CTA
     per_row = [mods[r % 2] for r in range(batch * 2)]
     x = W.rows_uniform(101, log2n, per_row, n)
@@ -173,8 +177,8 @@ def test_in_place_row_ranges_and_empty(oracle, log2n):
     assert L.ntt_forward(plan.handle, z.data_ptr() + 8, z.data_ptr(), None) == -5
 
 
-def test_extreme_values(oracle):
-    q = W.Q62_N1024
+@pytest.mark.parametrize("q", [W.Q62_N1024, W.POOL50[0]])
+def test_extreme_values(oracle, q):
     plan = ntt.Plan(10, [q], 4)
     x = np.zeros((4, 1024), dtype=np.uint64)
     x[1, :] = q - 1
