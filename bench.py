@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--schedule", type=int, default=None)
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "mixed_batch", "tfhe_blind_rotation", "plain_n1024"],
+                    help="the line the driver records is the default (CKKS-HMUL-shaped) workload")
     return ap.parse_args()
 
 
@@ -416,10 +419,160 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------- the other workloads --
+
+def _events_loop(torch, stream, steps, fn, flush=None):
+    """Per-step CUDA events on `stream`; L2 flushed before each step if given."""
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    launches = 0
+    for s in range(steps):
+        if flush is not None:
+            flush.fill_(s)
+        starts[s].record(stream)
+        launches += fn()
+        ends[s].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(starts, ends)], launches
+
+
+def _probe(torch, L, q, kind, sms, stream):
+    sink = torch.empty(sms * 8 * 256, dtype=torch.int64, device="cuda")
+    best = 0.0
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        assert L.ntt_bench_butterflies(q, kind, sms * 8, 256, 4000, sink.data_ptr(), stream.cuda_stream) == 0
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = max(best, sms * 8 * 256 * 4000 * 8 / (e0.elapsed_time(e1) * 1e-3))
+    return best
+
+
+def run_other(args):
+    """Lines for the mixed batch, the TFHE-shaped batch and the plain N=1024
+    workload (same schema; the default line is the default workload)."""
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2410_05934_gb300 import build as B
+    B.build_product()
+    import paper_2410_05934_gb300 as ntt
+    from paper_2410_05934_gb300 import _native
+    from paper_2410_05934_gb300 import workloads as W
+    L = _native.load()
+    stream = torch.cuda.current_stream()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    clocks = ClockSampler(local)
+    extra = {}
+    if args.workload == "mixed_batch":
+        spec = W.mixed_requests(seed=W.DEFAULT_SEED + rank)
+        reqs, coef, bfly = [], 0, 0
+        for i, (log2n, limbs, polys) in enumerate(spec):
+            x = W.request_rows_torch(W.DEFAULT_SEED + rank, i, log2n, limbs, polys)
+            reqs.append(dict(log2n=log2n, n_moduli=limbs, n_polys=polys, moduli_offset=0, inverse=0,
+                             **{"in": x, "out": torch.empty_like(x)}))
+            coef += x.numel()
+            bfly += x.shape[0] * (x.shape[1] // 2) * log2n
+        batch = ntt.Batch(reqs, W.POOL50, flags=ntt.NTT_BATCH_GRAPH)
+        flush_t = None                      # ~9 GB of inputs: far larger than L2
+        q_probe = W.POOL50[0]
+        kind = 2
+        for _ in range(max(3, args.warmup)):
+            batch.execute()
+            batch.execute_plain()
+        torch.cuda.synchronize()
+        clocks.start()
+        ms, launches = _events_loop(torch, stream, args.steps, lambda: (batch.execute(), 1)[1], flush_t)
+        clk = clocks.stop()
+        ms_plain, launches_plain = _events_loop(
+            torch, stream, args.steps, lambda: (batch.execute_plain(), batch.info()["last_launches"])[1], flush_t)
+        extra["plain_per_request"] = {
+            "value": coef * args.steps / (sum(ms_plain) * 1e-3), "ms_per_step": sum(ms_plain) / args.steps,
+            "launches_per_step": launches_plain // args.steps,
+            "how": "one launch sequence per request, default schedule of its N, same tables"}
+        extra["speedup_vs_plain"] = sum(ms_plain) / sum(ms)
+        config = {"workload": "mixed_batch", "requests": len(spec), "coefficients": coef,
+                  "distribution": "N in {2^10,2^12,2^14,2^16} (.5/.2/.2/.1), limbs U{1..32}, polys U{1..64}, forward",
+                  "batched": "one persistent kernel under a CUDA graph", "l2": "inputs (%.1f GB) > L2" % (coef * 8 / 1e9)}
+        unit_coef = coef
+    elif args.workload == "tfhe_blind_rotation":
+        w = W.tfhe_blind_rotation()
+        q = w["moduli"][0]
+        xf, xi = to_dev_np(torch, w["fwd"]), to_dev_np(torch, w["inv"])
+        reqs = [dict(log2n=10, n_moduli=1, n_polys=xf.shape[0], inverse=0, **{"in": xf, "out": torch.empty_like(xf)}),
+                dict(log2n=10, n_moduli=1, n_polys=xi.shape[0], inverse=1, **{"in": xi, "out": torch.empty_like(xi)})]
+        batch = ntt.Batch(reqs, [q], flags=ntt.NTT_BATCH_GRAPH)
+        coef = xf.numel() + xi.numel()
+        bfly = (xf.shape[0] + xi.shape[0]) * 512 * 10
+        q_probe, kind = q, 0
+        for _ in range(max(3, args.warmup)):
+            batch.execute()
+            batch.execute_plain()
+        torch.cuda.synchronize()
+        clocks.start()
+        ms, launches = _events_loop(torch, stream, args.steps, lambda: (batch.execute(), 1)[1], flush)
+        clk = clocks.stop()
+        ms_plain, _ = _events_loop(torch, stream, args.steps, lambda: (batch.execute_plain(), 2)[1], flush)
+        extra["plain_per_request"] = {"value": coef * args.steps / (sum(ms_plain) * 1e-3),
+                                      "ms_per_step": sum(ms_plain) / args.steps,
+                                      "how": "forward launch + inverse launch, default schedule"}
+        config = {"workload": "tfhe_blind_rotation", "log2n": 10, "modulus_bits": 62,
+                  "rows": "3780 forward (signed digits) + 1260 inverse", "batched": "one persistent launch (CUDA graph)",
+                  "l2": "flushed before every step"}
+    else:  # plain_n1024
+        w = W.plain_n1024()
+        q = w["moduli"][0]
+        x = to_dev_np(torch, w["x"])
+        plan64, plan32 = ntt.Plan(10, [q], 64), ntt.Plan(10, [q], 32)
+        A = torch.empty_like(x)
+        C = torch.empty_like(x[:32])
+
+        def step():
+            plan64.forward(x, A)
+            plan32.pointwise(A[:32], A[32:], C)
+            plan32.inverse(C, C)
+            return 3
+        coef = 64 * 1024 + 32 * 1024
+        bfly = 96 * 512 * 10
+        q_probe, kind = q, 0
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        clocks.start()
+        ms, launches = _events_loop(torch, stream, args.steps, step, flush)
+        clk = clocks.stop()
+        config = {"workload": "plain_n1024", "log2n": 10, "rows": "64 forward, 32 products, 32 inverse",
+                  "note": "launch-latency bound (1 MB per step); %HBM roofline not meaningful",
+                  "l2": "flushed before every step"}
+    t = sum(ms) * 1e-3
+    peak = _probe(torch, L, q_probe, kind, sms, stream)
+    achieved = bfly * args.steps / t
+    line = {"metric": "NTT coeffs/s (coefficient-transforms per second)", "value": coef * args.steps / t,
+            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": config,
+            "gpu_launches": launches, "clocks": clk,
+            "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
+                         "unit": "Gbutterfly/s", "frac": achieved / peak, "traffic": None,
+                         "peak_source": "in-run butterfly probe (kind %d)" % kind}}
+    line.update(extra)
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+def to_dev_np(torch, x):
+    return torch.from_numpy(np.ascontiguousarray(x).view(np.int64)).cuda()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != WORKLOAD:
+        return run_other(args)
     return run_ours(args)
 
 

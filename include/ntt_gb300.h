@@ -154,6 +154,56 @@ int ntt_plan_last_launches(ntt_plan_t plan, uint32_t* launches);
 int ntt_bench_butterflies(uint64_t q, uint32_t kind, uint32_t blocks, uint32_t threads,
                           uint32_t iters, uint64_t* d_sink, void* cuda_stream);
 
+/*
+ * Uneven mixed batches (Sec. IV-A's batching of many independent transforms
+ * into one launch, applied to whole requests): many requests of different N,
+ * limb count, polynomial count and direction run in ONE persistent kernel
+ * launch that pulls (request, row-range) work items from an atomic queue,
+ * largest items first.  Each request has layout [n_polys][n_moduli][N] and
+ * uses moduli_pool[moduli_offset .. moduli_offset + n_moduli).
+ *   log2n          in [NTT_BATCH_MIN_LOG2N, NTT_MAX_LOG2N]
+ *   inverse        0 forward, 1 inverse
+ *   in / out       caller-owned device buffers (may alias), 16-byte aligned
+ * ntt_batch_plan validates the requests, builds the twiddle tables of every
+ * (N, pool modulus) pair the batch uses, and uploads the work-item list; the
+ * batch plan owns those tables, the item list and the queue counter.  With
+ * NTT_BATCH_GRAPH, execution captures [reset counter, kernel] into a CUDA
+ * graph on first use and replays it afterwards.
+ * ntt_batch_update replaces the requests' in/out pointers (same shapes),
+ * enqueued on `cuda_stream` so the next execution (or graph replay) sees
+ * them.  ntt_batch_execute_plain is the comparison arm: one launch sequence
+ * per request on the same tables (schedules[i] per request, or the default
+ * schedule of its N when schedules is NULL).
+ * Errors: ARG, NOT_PRIME, NOT_NTT_FRIENDLY, MODULUS_TOO_LARGE, ALIGN,
+ * UNSUPPORTED (log2n below NTT_BATCH_MIN_LOG2N), NOMEM, CUDA.
+ */
+#define NTT_BATCH_MIN_LOG2N 10
+#define NTT_BATCH_GRAPH 1u
+
+typedef struct {
+    uint32_t log2n;
+    uint32_t n_moduli;
+    uint32_t n_polys;
+    uint32_t moduli_offset;
+    uint32_t inverse;
+    uint32_t reserved;
+    const uint64_t* in;
+    uint64_t* out;
+} ntt_request_t;
+
+typedef struct ntt_batch_s* ntt_batch_t;
+
+int ntt_batch_plan(ntt_batch_t* out, const ntt_request_t* reqs, uint32_t n_reqs,
+                   const uint64_t* moduli_pool, uint32_t pool_len, uint32_t flags);
+int ntt_batch_update(ntt_batch_t batch, const ntt_request_t* reqs, uint32_t n_reqs, void* cuda_stream);
+int ntt_batch_execute(ntt_batch_t batch, void* cuda_stream);
+int ntt_batch_execute_plain(ntt_batch_t batch, const uint32_t* schedules, void* cuda_stream);
+int ntt_batch_destroy(ntt_batch_t batch);
+/* Device status word of the batch (as ntt_status): synchronises, returns, clears. */
+int ntt_batch_status(ntt_batch_t batch, void* cuda_stream);
+/* Work items, kernel launches of the last execution, and coefficients per execution. */
+int ntt_batch_info(ntt_batch_t batch, uint64_t* items, uint32_t* last_launches, uint64_t* coefficients);
+
 const char* ntt_strerror(int code);
 
 /* Library version string ("ntt_gb300 <major>.<minor> sm_103a"). */

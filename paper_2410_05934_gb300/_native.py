@@ -14,6 +14,15 @@ u32, u64, i32, vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_voi
 U64P = ctypes.POINTER(ctypes.c_uint64)
 U32P = ctypes.POINTER(ctypes.c_uint32)
 
+class NttRequest(ctypes.Structure):
+    """ntt_request_t of the C ABI."""
+    _fields_ = [("log2n", ctypes.c_uint32), ("n_moduli", ctypes.c_uint32), ("n_polys", ctypes.c_uint32),
+                ("moduli_offset", ctypes.c_uint32), ("inverse", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+REQP = ctypes.POINTER(NttRequest)
+
 # (name, restype, argtypes) for every symbol the header declares
 SIGNATURES = [
     ("ntt_plan", i32, [ctypes.POINTER(vp), u32, U64P, u32, u32, u32]),
@@ -32,6 +41,13 @@ SIGNATURES = [
     ("ntt_status", i32, [vp, vp]),
     ("ntt_plan_last_launches", i32, [vp, U32P]),
     ("ntt_bench_butterflies", i32, [u64, u32, u32, u32, u32, vp, vp]),
+    ("ntt_batch_plan", i32, [ctypes.POINTER(vp), REQP, u32, U64P, u32, u32]),
+    ("ntt_batch_update", i32, [vp, REQP, u32, vp]),
+    ("ntt_batch_execute", i32, [vp, vp]),
+    ("ntt_batch_execute_plain", i32, [vp, U32P, vp]),
+    ("ntt_batch_destroy", i32, [vp]),
+    ("ntt_batch_status", i32, [vp, vp]),
+    ("ntt_batch_info", i32, [vp, U64P, U32P, U64P]),
     ("ntt_strerror", ctypes.c_char_p, [i32]),
     ("ntt_version", ctypes.c_char_p, []),
 ]

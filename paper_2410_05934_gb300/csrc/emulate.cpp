@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "ntt_internal.h"
+#include "ntt_batch_cfgs.h"
 #include "ntt_launch.h"
 #include "ntt_schedules.h"
 
@@ -244,6 +245,14 @@ static const EmuEntry* emu_find(uint32_t log2n, uint32_t id) {
     return nullptr;
 }
 
+// the mixed-batch kernel's per-N configurations, direct form
+#define NTT_EMU_BATCH_SINGLE(LOGN, LOGT, LOGRP, TPC) \
+    {LOGN, &emu_s1<LOGN, LOGT, LOGRP, TPC, 0, false>, &emu_s1<LOGN, LOGT, LOGRP, TPC, 0, true>},
+#define NTT_EMU_BATCH_SPLIT(LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB)           \
+    {LOGN, &emu_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, 0, false>,         \
+     &emu_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, 0, true>},
+static const EmuEntry g_emu_batch[] = {NTT_BATCH_CONFIGS(NTT_EMU_BATCH_SINGLE, NTT_EMU_BATCH_SPLIT)};
+
 struct EmuPlan {
     PlanHost h;
     int status = 0;
@@ -298,6 +307,25 @@ int nttemu_transform(void* plan, uint32_t sched, int inverse, const uint64_t* in
     d.check = (p->h.flags & NTT_FLAG_CHECK) ? 1u : 0u;
     d.mc = p->h.mc;
     return (inverse ? e->inv : e->fwd)(d, in, out, row_begin, n_rows);
+}
+
+// Runs the mixed-batch kernel's configuration for the plan's N.
+int nttemu_batch_transform(void* plan, int inverse, const uint64_t* in, uint64_t* out) {
+    EmuPlan* p = static_cast<EmuPlan*>(plan);
+    if (!p || !in || !out) return NTT_ERR_ARG;
+    for (const EmuEntry& e : g_emu_batch) {
+        if (e.log2n != p->h.log2n) continue;
+        PlanDev d;
+        d.fwd = p->h.fwd.data();
+        d.inv = p->h.inv.data();
+        d.lc = p->h.consts.data();
+        d.status = &p->status;
+        d.n_moduli = p->h.n_moduli;
+        d.check = (p->h.flags & NTT_FLAG_CHECK) ? 1u : 0u;
+        d.mc = p->h.mc;
+        return (inverse ? e.inv : e.fwd)(d, in, out, 0, p->h.rows);
+    }
+    return NTT_ERR_UNSUPPORTED;
 }
 
 // Pointwise product with the kernel's arithmetic (Barrett).

@@ -152,6 +152,72 @@ class Plan:
         return out
 
 
+NTT_BATCH_GRAPH = 1
+
+
+class Batch:
+    """ntt_batch_plan: an uneven mixed batch run as one persistent launch.
+
+    requests: list of dicts (or tuples) with log2n, n_moduli, n_polys,
+    moduli_offset, inverse, in, out -- in/out CUDA tensors or device pointers.
+    """
+
+    def __init__(self, requests, moduli_pool, flags=NTT_BATCH_GRAPH):
+        L = load()
+        self._reqs = self._pack(requests)
+        pool = [int(q) for q in moduli_pool]
+        arr = (ctypes.c_uint64 * len(pool))(*pool)
+        h = ctypes.c_void_p()
+        check(L.ntt_batch_plan(ctypes.byref(h), self._reqs, len(self._reqs), arr, len(pool), flags),
+              "ntt_batch_plan")
+        self._h = h
+
+    @staticmethod
+    def _pack(requests):
+        arr = (_native.NttRequest * len(requests))()
+        for i, r in enumerate(requests):
+            d = arr[i]
+            d.log2n, d.n_moduli, d.n_polys = int(r["log2n"]), int(r["n_moduli"]), int(r["n_polys"])
+            d.moduli_offset, d.inverse = int(r.get("moduli_offset", 0)), int(r.get("inverse", 0))
+            d.in_ = _ptr(r["in"], what="in").value
+            d.out = _ptr(r.get("out", r["in"]), what="out").value
+        return arr
+
+    def update(self, requests, stream=None):
+        reqs = self._pack(requests)
+        check(load().ntt_batch_update(self._h, reqs, len(reqs), _stream_handle(stream)), "ntt_batch_update")
+        self._reqs = reqs
+
+    def execute(self, stream=None):
+        check(load().ntt_batch_execute(self._h, _stream_handle(stream)), "ntt_batch_execute")
+
+    def execute_plain(self, schedules=None, stream=None):
+        sched = None
+        if schedules is not None:
+            sched = (ctypes.c_uint32 * len(schedules))(*[int(s) for s in schedules])
+        check(load().ntt_batch_execute_plain(self._h, sched, _stream_handle(stream)), "ntt_batch_execute_plain")
+
+    def status(self, stream=None):
+        return load().ntt_batch_status(self._h, _stream_handle(stream))
+
+    def info(self):
+        items, launches, coef = ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_uint64()
+        check(load().ntt_batch_info(self._h, ctypes.byref(items), ctypes.byref(launches), ctypes.byref(coef)),
+              "ntt_batch_info")
+        return {"items": items.value, "last_launches": launches.value, "coefficients": coef.value}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().ntt_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # C-ABI names as plain functions
 def ntt_plan(log2n, moduli, batch=1, flags=0):
     return Plan(log2n, moduli, batch, flags)

@@ -166,3 +166,78 @@ def request_rows(seed, req_index, log2n, limbs, polys, pool=POOL50):
     for r, q in enumerate(per_row):
         out[r] = uniform_mod(seed, 1000 + req_index, n, q, start=r * n)
     return out
+
+
+# ---- the same generator on a torch device (int64 arithmetic wraps mod 2^64) ----
+
+def _s64(v):
+    v = int(v) & 0xFFFFFFFFFFFFFFFF
+    return v - (1 << 64) if v >= (1 << 63) else v
+
+
+def _lsr(t, k):
+    """logical right shift of int64 bit patterns"""
+    return (t >> k) & ((1 << (64 - k)) - 1)
+
+
+def mix64_torch(z):
+    z = (z ^ _lsr(z, 30)) * _s64(_M1)
+    z = (z ^ _lsr(z, 27)) * _s64(_M2)
+    return z ^ _lsr(z, 31)
+
+
+def uniform_mod_torch(seed, stream, count, q, start=0, device="cuda"):
+    """uniform_mod on a torch device: identical values, returned as int64 bit patterns."""
+    import torch
+    q = int(q)
+    shift = 64 - q.bit_length()
+    key = int(stream_key(seed, stream))
+    i = torch.arange(start, start + count, dtype=torch.int64, device=device)
+
+    def draw(attempt):
+        ctr = i + (attempt * ATTEMPT_STRIDE + 1)
+        return _lsr(mix64_torch(ctr * _s64(GAMMA) + _s64(key)), shift)
+
+    out = draw(0)
+    attempt = 1
+    bad = out >= q
+    while bool(bad.any()):
+        out = torch.where(bad, draw(attempt), out)
+        bad = out >= q
+        attempt += 1
+    return out
+
+
+def uniform_mod_torch_idx(seed, stream, idx, q):
+    """uniform_mod at arbitrary element indices idx (int64 tensor)."""
+    import torch
+    q = int(q)
+    shift = 64 - q.bit_length()
+    key = int(stream_key(seed, stream))
+
+    def draw(attempt):
+        ctr = idx + (attempt * ATTEMPT_STRIDE + 1)
+        return _lsr(mix64_torch(ctr * _s64(GAMMA) + _s64(key)), shift)
+
+    out = draw(0)
+    attempt = 1
+    bad = out >= q
+    while bool(bad.any()):
+        out = torch.where(bad, draw(attempt), out)
+        bad = out >= q
+        attempt += 1
+    return out
+
+
+def request_rows_torch(seed, req_index, log2n, limbs, polys, pool=POOL50, device="cuda"):
+    """request_rows on a torch device ([polys * limbs, N] int64 bit patterns),
+    one vectorised draw per limb."""
+    import torch
+    n = 1 << log2n
+    out = torch.empty((polys, limbs, n), dtype=torch.int64, device=device)
+    j = torch.arange(n, dtype=torch.int64, device=device)
+    p = torch.arange(polys, dtype=torch.int64, device=device)
+    for l in range(limbs):
+        idx = (p[:, None] * limbs + l) * n + j[None, :]
+        out[:, l, :] = uniform_mod_torch_idx(seed, 1000 + req_index, idx, pool[l])
+    return out.view(polys * limbs, n)

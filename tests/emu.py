@@ -22,6 +22,8 @@ def lib():
         L.nttemu_transform.restype = i32
         L.nttemu_pointwise.argtypes = [vp, U64P, U64P, U64P, u64]
         L.nttemu_status.argtypes = [vp]
+        L.nttemu_batch_transform.argtypes = [vp, i32, U64P, U64P]
+        L.nttemu_batch_transform.restype = i32
         _lib = L
     return _lib
 
@@ -50,6 +52,15 @@ class EmuPlan:
         rc = lib().nttemu_transform(self.h, sched, int(inverse), _p(x), _p(out), row_begin, n_rows)
         if rc:
             raise ValueError("nttemu_transform failed: %d" % rc)
+        return out
+
+    def batch_transform(self, x, inverse=False):
+        """The mixed-batch kernel's configuration for this N (direct form)."""
+        x = np.ascontiguousarray(x, dtype=np.uint64)
+        out = np.zeros_like(x)
+        rc = lib().nttemu_batch_transform(self.h, int(inverse), _p(x), _p(out))
+        if rc:
+            raise ValueError("nttemu_batch_transform failed: %d" % rc)
         return out
 
     def pointwise(self, a, b, n_rows=None):

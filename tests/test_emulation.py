@@ -124,3 +124,20 @@ def test_single_modulus_batches(oracle, log2n, rows):
         got = out if idx is None else out[np.arange(rows)[:, None], idx]
         assert np.array_equal(got, ref), s
         assert np.array_equal(plan.transform(out, s, inverse=True), x), s
+
+
+@pytest.mark.parametrize("log2n", range(10, 17))
+def test_mixed_batch_configs_match_oracle(oracle, log2n):
+    """The per-N tile configurations of the mixed-batch persistent kernel."""
+    n = 1 << log2n
+    mods = [W.POOL50[2], W.POOL50[9], W.POOL50[30]]
+    plan = emu.EmuPlan(log2n, mods, 2)
+    per_row = [mods[r % 3] for r in range(6)]
+    x = W.rows_uniform(23, log2n, per_row, n)
+    idx = np.stack([np.array([0, 1, 7, n // 2, n - 1]) for _ in per_row]).astype(np.uint32)
+    out = plan.batch_transform(x)
+    assert np.array_equal(out[np.arange(6)[:, None], idx], oracle.transform_rows(x, per_row, idx=idx))
+    assert np.array_equal(plan.batch_transform(out, inverse=True), x)
+    inv = plan.batch_transform(x, inverse=True)
+    assert np.array_equal(inv[np.arange(6)[:, None], idx],
+                          oracle.transform_rows(x, per_row, inverse=True, idx=idx))

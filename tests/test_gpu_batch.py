@@ -1,0 +1,111 @@
+"""Mixed batches through the persistent kernel (C ABI ntt_batch_*): every
+request's output matches the oracle, the CUDA-graph replay after a pointer
+update and the plain per-request arm give the same bits, and argument errors
+are reported before any launch."""
+import numpy as np
+import pytest
+
+from paper_2410_05934_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2410_05934_gb300 as ntt  # noqa: E402
+from gpu_util import to_dev, to_host  # noqa: E402
+
+SHAPES = [  # (log2n, limbs, polys, offset, inverse)
+    (10, 3, 5, 0, 0), (16, 2, 2, 4, 0), (12, 1, 7, 2, 1), (14, 5, 1, 0, 0), (11, 2, 3, 9, 1),
+    (13, 4, 2, 1, 0), (15, 1, 3, 0, 1), (10, 1, 1, 30, 1), (16, 3, 1, 0, 1), (12, 6, 2, 3, 0),
+]
+
+
+def _make(seed, shapes=SHAPES, in_place=False):
+    reqs, hosts = [], []
+    for i, (log2n, limbs, polys, off, inv) in enumerate(shapes):
+        x = W.request_rows(seed, i, log2n, limbs, polys, pool=W.POOL50[off:])
+        d = to_dev(x)
+        o = d if (in_place and i % 2) else torch.empty_like(d)
+        reqs.append(dict(log2n=log2n, n_moduli=limbs, n_polys=polys, moduli_offset=off, inverse=inv,
+                         **{"in": d, "out": o}))
+        hosts.append(x)
+    return reqs, hosts
+
+
+def _check(oracle, reqs, hosts, shapes=SHAPES):
+    for (log2n, limbs, polys, off, inv), r, x in zip(shapes, reqs, hosts):
+        n = 1 << log2n
+        got = to_host(r["out"])
+        per_row = [W.POOL50[off + (k % limbs)] for k in range(limbs * polys)]
+        rng = np.random.default_rng(log2n * 7 + off)
+        idx = np.stack([np.concatenate([[0, n - 1], rng.integers(0, n, 6)]) for _ in per_row]).astype(np.uint32)
+        ref = oracle.transform_rows(x, per_row, inverse=bool(inv), idx=idx)
+        assert np.array_equal(got[np.arange(len(per_row))[:, None], idx], ref), (log2n, limbs, polys, inv)
+
+
+def test_persistent_batch_matches_oracle(oracle):
+    reqs, hosts = _make(1)
+    b = ntt.Batch(reqs, W.POOL50, flags=0)
+    b.execute()
+    torch.cuda.synchronize()
+    assert b.info()["last_launches"] == 1
+    _check(oracle, reqs, hosts)
+    assert b.status() == 0
+
+
+def test_graph_replay_with_new_pointers_and_plain_arm(oracle):
+    reqs, hosts = _make(2, in_place=True)
+    saved = [r["in"].clone() for r in reqs]
+    b = ntt.Batch(reqs, W.POOL50, flags=ntt.NTT_BATCH_GRAPH)
+    b.execute()
+    torch.cuda.synchronize()
+    _check(oracle, reqs, hosts)
+    outs_graph = [to_host(r["out"]).copy() for r in reqs]
+    # replay on fresh buffers holding the same inputs
+    reqs2 = [dict(r, **{"in": s.clone()}) for r, s in zip(reqs, saved)]
+    for r in reqs2:
+        r["out"] = torch.empty_like(r["in"])
+    b.update(reqs2)
+    b.execute()
+    torch.cuda.synchronize()
+    for o, r in zip(outs_graph, reqs2):
+        assert np.array_equal(o, to_host(r["out"]))
+    # the per-request arm over the same tables
+    reqs3 = [dict(r, **{"in": s.clone()}) for r, s in zip(reqs, saved)]
+    for r in reqs3:
+        r["out"] = torch.empty_like(r["in"])
+    b.update(reqs3)
+    b.execute_plain()
+    torch.cuda.synchronize()
+    assert b.info()["last_launches"] >= len(reqs3)
+    for o, r in zip(outs_graph, reqs3):
+        assert np.array_equal(o, to_host(r["out"]))
+
+
+def test_batch_argument_errors():
+    d = torch.zeros((4, 1024), dtype=torch.int64, device="cuda")
+    good = dict(log2n=10, n_moduli=2, n_polys=2, moduli_offset=0, inverse=0, **{"in": d, "out": d})
+    for bad, code in [(dict(log2n=9), -10), (dict(moduli_offset=47), -1), (dict(inverse=2), -1),
+                      (dict(n_polys=0), -1)]:
+        with pytest.raises(ntt.NttError) as e:
+            ntt.Batch([dict(good, **bad)], W.POOL50)
+        assert e.value.code == code
+    with pytest.raises(ntt.NttError) as e:
+        ntt.Batch([dict(good, **{"in": d.data_ptr() + 8})], W.POOL50)
+    assert e.value.code == -5
+    with pytest.raises(ntt.NttError) as e:
+        ntt.Batch([dict(good, n_moduli=1)], [7681])                      # not 1 mod 2048
+    assert e.value.code == -3
+
+
+def test_batch_range_check():
+    q = W.POOL50[0]
+    x = np.zeros((2, 1024), dtype=np.uint64)
+    x[1, 3] = q
+    d = to_dev(x)
+    b = ntt.Batch([dict(log2n=10, n_moduli=1, n_polys=2, moduli_offset=0, inverse=0, **{"in": d,
+                        "out": torch.empty_like(d)})], W.POOL50, flags=ntt.NTT_FLAG_CHECK)
+    b.execute()
+    assert b.status() == -8
