@@ -204,6 +204,47 @@ int ntt_batch_status(ntt_batch_t batch, void* cuda_stream);
 /* Work items, kernel launches of the last execution, and coefficients per execution. */
 int ntt_batch_info(ntt_batch_t batch, uint64_t* items, uint32_t* last_launches, uint64_t* coefficients);
 
+/*
+ * Allocation-free execution of a mixed batch (no counterpart in the paper:
+ * this is an interface for callers that cannot call cudaMalloc, e.g. code
+ * that owns all device memory through its own allocator and reserves it at
+ * start-up, plugin interfaces of host frameworks, or request paths where the
+ * implicit device synchronisation of cudaMalloc is not acceptable).
+ *
+ * Runs the same persistent mixed-batch kernel as ntt_batch_execute, but the
+ * kernel's scratch memory (work-queue counter and request descriptors) lives
+ * in one file-scope __device__ array of NTT_STATIC_SCRATCH_BYTES that every
+ * device loading the library holds until process exit.  The call allocates
+ * no device memory; twiddle tables come from plans the caller created
+ * earlier (ntt_plan, at a time when it could allocate).
+ *   reqs[i].plan     a plan with N >= 2^NTT_BATCH_MIN_LOG2N on the current device
+ *   reqs[i].n_polys  polynomials of the plan's layout to transform (0 = its batch)
+ *   reqs[i].inverse  0 forward, 1 inverse
+ *   reqs[i].in/out   device buffers [n_polys][n_moduli][N], 16-byte aligned, may alias
+ * n_reqs must be in [1, NTT_STATIC_MAX_REQUESTS]; more is rejected with
+ * NTT_ERR_ARG before anything is enqueued.  Range errors (NTT_FLAG_CHECK
+ * plans) go to each request's plan status word (ntt_status).
+ * The first call on a device sets that device up (it looks up the array's
+ * device address with cudaGetSymbolAddress and the kernel's occupancy), so
+ * make that first call outside any stream capture.  Every call reuses the
+ * same array and overwrites what the previous call left there (the queue
+ * counter is cleared on the stream at the start of each call); calls whose
+ * executions overlap on the GPU (different streams without ordering, or
+ * concurrent host threads) race on it and must be serialised by the caller.
+ */
+#define NTT_STATIC_SCRATCH_BYTES (64 * 1024)
+#define NTT_STATIC_MAX_REQUESTS 816
+
+typedef struct {
+    ntt_plan_t plan;
+    uint32_t n_polys;
+    uint32_t inverse;
+    const uint64_t* in;
+    uint64_t* out;
+} ntt_plan_request_t;
+
+int ntt_batch_execute_static(const ntt_plan_request_t* reqs, uint32_t n_reqs, void* cuda_stream);
+
 const char* ntt_strerror(int code);
 
 /* Library version string ("ntt_gb300 <major>.<minor> sm_103a"). */

@@ -23,6 +23,15 @@ class NttRequest(ctypes.Structure):
 
 REQP = ctypes.POINTER(NttRequest)
 
+
+class NttPlanRequest(ctypes.Structure):
+    """ntt_plan_request_t of the C ABI (allocation-free batch execution)."""
+    _fields_ = [("plan", ctypes.c_void_p), ("n_polys", ctypes.c_uint32), ("inverse", ctypes.c_uint32),
+                ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+PREQP = ctypes.POINTER(NttPlanRequest)
+
 # (name, restype, argtypes) for every symbol the header declares
 SIGNATURES = [
     ("ntt_plan", i32, [ctypes.POINTER(vp), u32, U64P, u32, u32, u32]),
@@ -48,6 +57,7 @@ SIGNATURES = [
     ("ntt_batch_destroy", i32, [vp]),
     ("ntt_batch_status", i32, [vp, vp]),
     ("ntt_batch_info", i32, [vp, U64P, U32P, U64P]),
+    ("ntt_batch_execute_static", i32, [PREQP, u32, vp]),
     ("ntt_strerror", ctypes.c_char_p, [i32]),
     ("ntt_version", ctypes.c_char_p, []),
 ]

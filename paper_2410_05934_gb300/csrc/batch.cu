@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -151,6 +152,108 @@ struct NTableSet {
     TwPair* d_inv = nullptr;
     LimbConst* d_lc = nullptr;
 };
+
+
+// ---- allocation-free variant: scratch in a file-scope device array ----
+//
+// Layout of g_ntt_static_scratch: the work-queue counter in the first 256
+// bytes, then up to NTT_STATIC_MAX_REQUESTS descriptors.  Work items are not
+// stored: item k belongs to the request whose [item_begin, next item_begin)
+// range holds k (binary search), rows in chunks of rows_per_item(N).
+struct StaticReq {
+    const uint64_t* in;
+    uint64_t* out;
+    const TwPair* tw_fwd;
+    const TwPair* tw_inv;
+    const LimbConst* lc;
+    int* status;
+    uint32_t log2n, n_moduli, inverse, item_begin;
+    uint32_t rows, check, per_item, pad;
+};
+static_assert(sizeof(StaticReq) == 80, "descriptor size");
+static_assert(256 + sizeof(StaticReq) * NTT_STATIC_MAX_REQUESTS <= NTT_STATIC_SCRATCH_BYTES,
+              "descriptors fit the static scratch array");
+
+static __device__ __align__(256) unsigned char g_ntt_static_scratch[NTT_STATIC_SCRATCH_BYTES];
+
+template <int MC>
+__global__ void __launch_bounds__(NTT_BATCH_THREADS, 2)
+    k_ntt_batch_static(const StaticReq* __restrict__ reqs, uint32_t n_reqs, uint32_t n_items,
+                       uint32_t* counter) {
+    extern __shared__ __align__(16) uint64_t smem[];
+    __shared__ uint32_t s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1u);
+        __syncthreads();
+        const uint32_t item = s_item;
+        __syncthreads();
+        if (item >= n_items) break;
+        uint32_t lo = 0, hi = n_reqs;    // last request with item_begin <= item
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (reqs[mid].item_begin <= item) lo = mid; else hi = mid;
+        }
+        const StaticReq sr = reqs[lo];
+        const uint64_t row_begin = (uint64_t)(item - sr.item_begin) * sr.per_item;
+        const uint64_t n_rows = min((uint64_t)sr.per_item, (uint64_t)sr.rows - row_begin);
+        BatchReq rq;
+        rq.in = sr.in;
+        rq.out = sr.out;
+        rq.tw_fwd = sr.tw_fwd;
+        rq.tw_inv = sr.tw_inv;
+        rq.lc = sr.lc;
+        rq.log2n = sr.log2n;
+        rq.n_moduli = sr.n_moduli;
+        rq.inverse = sr.inverse;
+        TileArgs a;
+        a.in = sr.in;
+        a.out = sr.out;
+        a.tw = nullptr;
+        a.lc = sr.lc;
+        a.status = sr.status;
+        a.row_begin = row_begin;
+        a.n_tiles = 0;
+        a.n_moduli = sr.n_moduli;
+        a.check = sr.check;
+        if (sr.inverse)
+            batch_dispatch<true, MC>(a, rq, n_rows, smem);
+        else
+            batch_dispatch<false, MC>(a, rq, n_rows, smem);
+    }
+}
+
+struct StaticDevice {
+    bool ready = false;
+    unsigned char* scratch = nullptr;   // device address of g_ntt_static_scratch
+    int grid[2] = {0, 0};
+};
+static StaticDevice g_static_dev[64];
+static std::mutex g_static_mu;
+
+// Once per device, with that device current: the array's device address
+// (its name is only a host-side stand-in) and the kernel's launch shape.
+static int static_setup(int dev, StaticDevice** out) {
+    if (dev < 0 || dev >= 64) return NTT_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    StaticDevice& d = g_static_dev[dev];
+    if (!d.ready) {
+        void* ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_ntt_static_scratch) != cudaSuccess || !ptr) return NTT_ERR_CUDA;
+        int sms = 0, n0 = 0, n1 = 0;
+        if (cudaFuncSetAttribute(k_ntt_batch_static<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) != cudaSuccess ||
+            cudaFuncSetAttribute(k_ntt_batch_static<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n0, k_ntt_batch_static<0>, NTT_BATCH_THREADS, kBatchSmem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_ntt_batch_static<1>, NTT_BATCH_THREADS, kBatchSmem) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return NTT_ERR_CUDA;
+        d.scratch = static_cast<unsigned char*>(ptr);
+        d.grid[0] = std::max(1, n0) * std::max(1, sms);
+        d.grid[1] = std::max(1, n1) * std::max(1, sms);
+        d.ready = true;
+    }
+    *out = &d;
+    return NTT_OK;
+}
 
 }  // namespace nttgb
 
@@ -443,6 +546,68 @@ int ntt_batch_info(ntt_batch_t b, uint64_t* items, uint32_t* last_launches, uint
     if (last_launches) *last_launches = b->last_launches;
     if (coefficients) *coefficients = b->coefficients;
     return NTT_OK;
+}
+
+int ntt_batch_execute_static(const ntt_plan_request_t* reqs, uint32_t n_reqs, void* cuda_stream) {
+    if (!reqs || n_reqs == 0 || n_reqs > NTT_STATIC_MAX_REQUESTS) return NTT_ERR_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return NTT_ERR_CUDA;
+    // host-side staging of the descriptors (host memory only)
+    std::vector<StaticReq> desc(n_reqs), sorted(n_reqs);
+    std::vector<uint32_t> order(n_reqs);
+    uint32_t mc = 1;
+    for (uint32_t i = 0; i < n_reqs; ++i) {
+        const ntt_plan_request_t& r = reqs[i];
+        const ntt_plan_s* p = r.plan;
+        if (!p || (p->h.flags & NTT_FLAG_HOST_ONLY) || p->device != dev || r.inverse > 1 || !r.in || !r.out)
+            return NTT_ERR_ARG;
+        if (p->h.log2n < NTT_BATCH_MIN_LOG2N) return NTT_ERR_UNSUPPORTED;
+        const uint32_t polys = r.n_polys ? r.n_polys : p->h.batch;
+        if (polys > p->h.batch) return NTT_ERR_ARG;
+        if (!aligned16p(r.in) || !aligned16p(r.out)) return NTT_ERR_ALIGN;
+        StaticReq& d = desc[i];
+        d.in = r.in;
+        d.out = r.out;
+        d.tw_fwd = p->d_fwd;
+        d.tw_inv = p->d_inv;
+        d.lc = p->d_consts;
+        d.status = p->d_status;
+        d.log2n = p->h.log2n;
+        d.n_moduli = p->h.n_moduli;
+        d.inverse = r.inverse;
+        d.rows = polys * p->h.n_moduli;
+        d.check = (p->h.flags & NTT_FLAG_CHECK) ? 1u : 0u;
+        d.per_item = rows_per_item(d.log2n);
+        d.pad = 0;
+        if (!p->h.mc) mc = 0;
+        order[i] = i;
+    }
+    // largest transforms first, then item ranges in that order
+    std::stable_sort(order.begin(), order.end(),
+                     [&](uint32_t x, uint32_t y) { return desc[x].log2n > desc[y].log2n; });
+    uint64_t items = 0;
+    for (uint32_t k = 0; k < n_reqs; ++k) {
+        sorted[k] = desc[order[k]];
+        sorted[k].item_begin = (uint32_t)items;
+        items += (sorted[k].rows + sorted[k].per_item - 1) / sorted[k].per_item;
+    }
+    if (items >= 0xffffffffull) return NTT_ERR_ARG;
+    StaticDevice* sd = nullptr;
+    int rc = static_setup(dev, &sd);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    uint32_t* counter = reinterpret_cast<uint32_t*>(sd->scratch);
+    StaticReq* d_reqs = reinterpret_cast<StaticReq*>(sd->scratch + 256);
+    // pageable source: staged by the runtime before the call returns
+    if (cudaMemcpyAsync(d_reqs, sorted.data(), sizeof(StaticReq) * n_reqs, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(counter, 0, sizeof(uint32_t), st) != cudaSuccess)
+        return NTT_ERR_CUDA;
+    const int grid = (int)std::min<uint64_t>((uint64_t)sd->grid[mc], items);
+    if (mc)
+        k_ntt_batch_static<1><<<grid, NTT_BATCH_THREADS, kBatchSmem, st>>>(d_reqs, n_reqs, (uint32_t)items, counter);
+    else
+        k_ntt_batch_static<0><<<grid, NTT_BATCH_THREADS, kBatchSmem, st>>>(d_reqs, n_reqs, (uint32_t)items, counter);
+    return cudaPeekAtLastError() == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
 }
 
 }  // extern "C"
