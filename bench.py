@@ -48,7 +48,8 @@ def parse():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--schedule", type=int, default=None)
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "mixed_batch", "tfhe_blind_rotation", "plain_n1024"],
+                    choices=[WORKLOAD, "mixed_batch", "tfhe_blind_rotation", "plain_n1024", "cost_model",
+                             "serving"],
                     help="the line the driver records is the default (CKKS-HMUL-shaped) workload")
     return ap.parse_args()
 
@@ -563,6 +564,54 @@ def run_other(args):
     return 0
 
 
+def run_cost_model(args):
+    """Schedule cost model: train on the committed GB300 timing sweep with the
+    library's GPU kernels; regret on 100 held-out shapes vs exhaustive tuning."""
+    from paper_2410_05934_gb300 import costmodel as CM
+    import torch
+    torch.cuda.set_device(dist_env()[2])
+    model, rep = CM.train_and_evaluate(steps=4000)
+    line = {"metric": "schedule regret vs exhaustive autotuning (mean over held-out shapes)",
+            "value": rep["mlp"]["mean"], "unit": "fraction", "n_gpus": 1, "steps": rep["train"]["train_steps"],
+            "warmup": 0, "ms_per_step": 1e3 * rep["train"]["train_seconds"] / rep["train"]["train_steps"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "autotuner timings measured on GB300 (%d)" % rep["timings"],
+            "config": {"workload": "cost_model", "mlp": "4-64-64-8 ReLU, FP32, Adam, cosine lr",
+                       "train_shapes": rep["train"]["train_shapes"], "heldout_shapes": rep["mlp"]["n"]},
+            "regret": {"mlp": rep["mlp"], "sm_rule": rep["sm_rule"], "default": rep["default"]},
+            "decision_us": rep["decision_us"], "train_seconds_gpu": rep["train"]["train_seconds"]}
+    print(json.dumps(line))
+    return 0
+
+
+def run_serving(args):
+    """Poisson stream of mixed-batch-distributed requests at 5k req/s."""
+    import torch
+    torch.cuda.set_device(dist_env()[2])
+    from paper_2410_05934_gb300 import build as B
+    B.build_product()
+    from paper_2410_05934_gb300 import serve
+    pool = serve.RequestPool()
+    n = max(500, args.steps * 200)
+    serve.serve(pool, 5000.0, 200, "per_request", seed=99)        # warm-up
+    clocks = ClockSampler(dist_env()[2])
+    clocks.start()
+    per = serve.serve(pool, 5000.0, n, "per_request", seed=1)
+    clk = clocks.stop()
+    mb = serve.serve(pool, 5000.0, n, "microbatch", window_us=500.0, seed=1)
+    mb2 = serve.serve(pool, 5000.0, n, "microbatch", window_us=2000.0, seed=1)
+    line = {"metric": "p99 latency at 5k req/s (mixed-batch request distribution)", "value": per["p99_ms"],
+            "unit": "ms", "n_gpus": 1, "steps": n, "warmup": 200, "ms_per_step": per["mean_ms"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": {"workload": "serving", "rate_req_s": 5000, "requests": n,
+                                            "policy": "per-request launches, cost-model schedules"},
+            "p50_ms": per["p50_ms"], "throughput_coef_s": per["throughput_coef_s"],
+            "offered_coef_s": per["offered_coef_s"], "clocks": clk,
+            "policies": {"per_request": per, "microbatch_500us": mb, "microbatch_2ms": mb2}}
+    print(json.dumps(line))
+    return 0
+
+
 def to_dev_np(torch, x):
     return torch.from_numpy(np.ascontiguousarray(x).view(np.int64)).cuda()
 
@@ -571,6 +620,10 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "cost_model":
+        return run_cost_model(args)
+    if args.workload == "serving":
+        return run_serving(args)
     if args.workload != WORKLOAD:
         return run_other(args)
     return run_ours(args)

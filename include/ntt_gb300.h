@@ -128,6 +128,13 @@ int poly_mul_pointwise(ntt_plan_t plan, const uint64_t* d_a, const uint64_t* d_b
 int ntt_schedule_count(uint32_t log2n);
 int ntt_schedule_name(uint32_t log2n, uint32_t id, char* buf, size_t len);
 int ntt_plan_set_schedule(ntt_plan_t plan, uint32_t id);
+/* The schedule ntt_plan picks by default for N = 2^log2n and `rows` rows. */
+int ntt_default_schedule(uint32_t log2n, uint64_t rows);
+/* Raw parameters of a schedule: params[0] = kernels (1 or 2), params[1] =
+ * pipelined (0/1), params[2..10] = the nine numbers of its S1/S2 entry
+ * (S1: LOGN, LOGT, LOGRP, TPC, 0...; S2: LOGN, SPLIT, LOGP, LOGTA, LOGRPA,
+ * TPCA, LOGTB, LOGRPB, TPCB).  n must be >= 11. */
+int ntt_schedule_params(uint32_t log2n, uint32_t id, int32_t* params, uint32_t n);
 int ntt_plan_get_schedule(ntt_plan_t plan, uint32_t* id);
 
 /*
@@ -203,6 +210,37 @@ int ntt_batch_destroy(ntt_batch_t batch);
 int ntt_batch_status(ntt_batch_t batch, void* cuda_stream);
 /* Work items, kernel launches of the last execution, and coefficients per execution. */
 int ntt_batch_info(ntt_batch_t batch, uint64_t* items, uint32_t* last_launches, uint64_t* coefficients);
+
+/*
+ * Schedule cost model kernels (the switch-point / fused-stage choice of
+ * Sec. V-D, learned from measured timings): an FP32 MLP
+ * NTT_MLP_IN -> 64 -> 64 -> NTT_MLP_OUT with ReLU hidden layers that maps a
+ * transform shape (log2 N, limbs, batch, modulus bits; scaled features) to
+ * the predicted log-time of every candidate schedule of that N.
+ *   d_params  NTT_MLP_PARAMS floats: W1[64][IN], b1[64], W2[64][64], b2[64],
+ *             W3[OUT][64], b3[OUT] (row-major)
+ *   d_x       [batch][NTT_MLP_IN] features
+ *   d_act     [batch][NTT_MLP_ACTS]: h1[64], h2[64], y[OUT] (written by forward)
+ *   d_target, d_mask  [batch][NTT_MLP_OUT]: target log-times, 1/0 validity
+ *   mask_count        sum of d_mask (the loss is the masked mean squared error)
+ *   d_grad    NTT_MLP_PARAMS floats (written), d_work caller-owned scratch of
+ *             batch * (NTT_MLP_ACTS + 1) floats, d_loss one float or NULL
+ * ntt_mlp_adam applies one Adam step (bias-corrected, step >= 1) in place.
+ * All device pointers are caller-owned; calls are asynchronous on the stream.
+ */
+#define NTT_MLP_IN 4
+#define NTT_MLP_HIDDEN 64
+#define NTT_MLP_OUT 8
+#define NTT_MLP_PARAMS (NTT_MLP_HIDDEN * NTT_MLP_IN + NTT_MLP_HIDDEN + NTT_MLP_HIDDEN * NTT_MLP_HIDDEN + \
+                        NTT_MLP_HIDDEN + NTT_MLP_OUT * NTT_MLP_HIDDEN + NTT_MLP_OUT)
+#define NTT_MLP_ACTS (2 * NTT_MLP_HIDDEN + NTT_MLP_OUT)
+
+int ntt_mlp_forward(const float* d_params, const float* d_x, uint32_t batch, float* d_act, void* cuda_stream);
+int ntt_mlp_backward(const float* d_params, const float* d_x, const float* d_act, const float* d_target,
+                     const float* d_mask, uint32_t batch, float mask_count, float* d_grad, float* d_work,
+                     float* d_loss, void* cuda_stream);
+int ntt_mlp_adam(float* d_params, const float* d_grad, float* d_m, float* d_v, uint32_t n, float lr,
+                 float beta1, float beta2, float eps, uint32_t step, void* cuda_stream);
 
 /*
  * Allocation-free execution of a mixed batch (no counterpart in the paper:

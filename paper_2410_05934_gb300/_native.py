@@ -46,6 +46,8 @@ SIGNATURES = [
     ("ntt_schedule_count", i32, [u32]),
     ("ntt_schedule_name", i32, [u32, u32, ctypes.c_char_p, ctypes.c_size_t]),
     ("ntt_plan_set_schedule", i32, [vp, u32]),
+    ("ntt_default_schedule", i32, [u32, u64]),
+    ("ntt_schedule_params", i32, [u32, u32, ctypes.POINTER(ctypes.c_int32), u32]),
     ("ntt_plan_get_schedule", i32, [vp, U32P]),
     ("ntt_status", i32, [vp, vp]),
     ("ntt_plan_last_launches", i32, [vp, U32P]),
@@ -58,6 +60,10 @@ SIGNATURES = [
     ("ntt_batch_status", i32, [vp, vp]),
     ("ntt_batch_info", i32, [vp, U64P, U32P, U64P]),
     ("ntt_batch_execute_static", i32, [PREQP, u32, vp]),
+    ("ntt_mlp_forward", i32, [vp, vp, u32, vp, vp]),
+    ("ntt_mlp_backward", i32, [vp, vp, vp, vp, vp, u32, ctypes.c_float, vp, vp, vp, vp]),
+    ("ntt_mlp_adam", i32, [vp, vp, vp, vp, u32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                           ctypes.c_float, u32, vp]),
     ("ntt_strerror", ctypes.c_char_p, [i32]),
     ("ntt_version", ctypes.c_char_p, []),
 ]

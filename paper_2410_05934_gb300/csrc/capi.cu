@@ -256,6 +256,20 @@ int ntt_schedule_name(uint32_t log2n, uint32_t id, char* buf, size_t len) {
     return NTT_OK;
 }
 
+int ntt_default_schedule(uint32_t log2n, uint64_t rows) {
+    if (log2n < NTT_MIN_LOG2N || log2n > NTT_MAX_LOG2N) return NTT_ERR_ARG;
+    return (int)default_schedule(log2n, rows);
+}
+
+int ntt_schedule_params(uint32_t log2n, uint32_t id, int32_t* params, uint32_t n) {
+    int i = sched_index(log2n, id);
+    if (i < 0 || !params || n < 11) return NTT_ERR_ARG;
+    params[0] = g_params[i].kind;
+    params[1] = g_params[i].pipe;
+    for (int k = 0; k < 9; ++k) params[2 + k] = g_params[i].v[k];
+    return NTT_OK;
+}
+
 int ntt_plan_set_schedule(ntt_plan_t plan, uint32_t id) {
     if (!plan) return NTT_ERR_ARG;
     if (sched_index(plan->h.log2n, id) < 0) return NTT_ERR_ARG;

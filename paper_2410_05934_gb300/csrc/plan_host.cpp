@@ -5,6 +5,7 @@
 // Twiddles follow the merged-psi negacyclic layout of Eq. 1: forward entry
 // k = psi^{brv(k)}, inverse entry k = psi^{-brv(k)} (brv over log2 N bits),
 // each with its Shoup companion w' = floor(w 2^64 / q).
+#include <algorithm>
 #include <cstring>
 
 #include "ntt_internal.h"
@@ -88,6 +89,33 @@ uint64_t root_2n(uint64_t q, uint32_t log2n) {
 
 uint64_t shoup_of(uint64_t w, uint64_t q) { return (uint64_t)(((u128)w << 64) / q); }
 
+// Shoup companions of many w for one q without a 128-bit division each:
+// with c = floor(2^64 / q) and r0 = 2^64 mod q,
+//   floor(w 2^64 / q) = w c + floor(w r0 / q),
+// and floor(w r0 / q) is the Shoup quotient of w * r0 (r0' = floor(r0 2^64 / q)),
+// exact after one correction step.  w c < 2^64 because w < q.
+struct ShoupGen {
+    uint64_t q, c, r0, r0p;
+    explicit ShoupGen(uint64_t q_) : q(q_) {
+        c = (uint64_t)(((u128)1 << 64) / q);
+        r0 = (uint64_t)(((u128)1 << 64) % q);
+        r0p = shoup_of(r0, q);
+    }
+    uint64_t operator()(uint64_t w) const {
+        uint64_t Q = (uint64_t)(((u128)w * r0p) >> 64);
+        uint64_t rem = w * r0 - Q * q;   // exact remainder + {0, q}
+        if (rem >= q) ++Q;
+        return w * c + Q;
+    }
+};
+
+// a * w mod q for a fixed w in Shoup form (exact)
+static inline uint64_t shoup_mulmod(uint64_t a, uint64_t w, uint64_t wp, uint64_t q) {
+    uint64_t Q = (uint64_t)(((u128)a * wp) >> 64);
+    uint64_t r = a * w - Q * q;
+    return r >= q ? r - q : r;
+}
+
 static uint32_t brv(uint32_t x, uint32_t bits) {
     uint32_t r = 0;
     for (uint32_t i = 0; i < bits; ++i, x >>= 1) r = (r << 1) | (x & 1);
@@ -124,25 +152,40 @@ int build_plan_host(PlanHost& h, uint32_t log2n, const uint64_t* moduli, uint32_
     for (uint32_t l = 0; l < n_moduli; ++l)
         if (moduli[l] >= (1ull << NTT_SMALL_MODULUS_BITS)) h.mc = 0;
     std::vector<uint64_t> pw(n), pwi(n);
+    std::vector<uint32_t> rev(n);
+    for (uint64_t k = 0; k < n; ++k) rev[k] = brv((uint32_t)k, log2n);
     for (uint32_t l = 0; l < n_moduli; ++l) {
         const uint64_t q = moduli[l];
+        // repeated moduli share their tables
+        uint32_t same = l;
+        for (uint32_t m = 0; m < l; ++m)
+            if (moduli[m] == q) { same = m; break; }
+        TwPair* f = &h.fwd[(size_t)l * n];
+        TwPair* v = &h.inv[(size_t)l * n];
+        if (same != l) {
+            std::copy(&h.fwd[(size_t)same * n], &h.fwd[(size_t)same * n] + n, f);
+            std::copy(&h.inv[(size_t)same * n], &h.inv[(size_t)same * n] + n, v);
+            h.psi[l] = h.psi[same];
+            h.consts[l] = h.consts[same];
+            continue;
+        }
         const uint64_t psi = root_2n(q, log2n);
         if (!psi) return NTT_ERR_NOT_NTT_FRIENDLY;
         const uint64_t psi_inv = pow_mod(psi, 2 * n - 1, q);
         h.psi[l] = psi;
+        const uint64_t psi_p = shoup_of(psi, q), psi_inv_p = shoup_of(psi_inv, q);
         pw[0] = pwi[0] = 1;
         for (uint64_t i = 1; i < n; ++i) {
-            pw[i] = mul_mod(pw[i - 1], psi, q);
-            pwi[i] = mul_mod(pwi[i - 1], psi_inv, q);
+            pw[i] = shoup_mulmod(pw[i - 1], psi, psi_p, q);
+            pwi[i] = shoup_mulmod(pwi[i - 1], psi_inv, psi_inv_p, q);
         }
-        TwPair* f = &h.fwd[(size_t)l * n];
-        TwPair* v = &h.inv[(size_t)l * n];
+        const ShoupGen sg(q);
         for (uint64_t k = 0; k < n; ++k) {
-            uint32_t b = brv((uint32_t)k, log2n);
+            const uint32_t b = rev[k];
             f[k].w = pw[b];
-            f[k].wp = shoup_of(pw[b], q);
+            f[k].wp = sg(pw[b]);
             v[k].w = pwi[b];
-            v[k].wp = shoup_of(pwi[b], q);
+            v[k].wp = sg(pwi[b]);
         }
         LimbConst& c = h.consts[l];
         std::memset(&c, 0, sizeof(c));

@@ -53,6 +53,20 @@ def schedule_name(log2n, sched_id):
     return buf.value.decode()
 
 
+def schedule_params(log2n, sched_id):
+    """dict of a schedule's raw parameters (see ntt_schedule_params)."""
+    buf = (ctypes.c_int32 * 11)()
+    check(load().ntt_schedule_params(log2n, sched_id, buf, 11), "ntt_schedule_params")
+    v = list(buf)
+    d = {"kernels": v[0], "pipelined": bool(v[1]), "log2n": v[2]}
+    if v[0] == 1:
+        d.update(logt=v[3], logrp=v[4], tpc=v[5])
+    else:
+        d.update(split=v[3], logp=v[4], logt_col=v[5], logrp_col=v[6], tpc_col=v[7],
+                 logt_row=v[8], logrp_row=v[9], tpc_row=v[10])
+    return d
+
+
 class Plan:
     """ntt_plan(log2n, moduli, batch, flags): tables on the current device."""
 
@@ -66,7 +80,11 @@ class Plan:
         self.log2n, self.n, self.moduli, self.batch = log2n, 1 << log2n, moduli, batch
         self.n_moduli = len(moduli)
         self.rows = batch * len(moduli)
-        if schedule is not None:
+        if schedule == "auto":
+            from .costmodel import choose_schedule
+            bits = max(int(q).bit_length() for q in moduli)
+            self.schedule, self.schedule_source = choose_schedule(log2n, len(moduli), batch, bits)
+        elif schedule is not None:
             self.schedule = schedule
 
     # -- lifetime --

