@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--schedule", type=int, default=None)
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "mixed_batch", "tfhe_blind_rotation", "plain_n1024", "cost_model",
-                             "serving"],
+                             "serving", "hmul_fused", "mixed_small"],
                     help="the line the driver records is the default (CKKS-HMUL-shaped) workload")
     return ap.parse_args()
 
@@ -282,7 +282,10 @@ def run_ours(args):
     for _ in range(4):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        rc = L.ntt_bench_butterflies(mods[0], 0, sms * 8, 256, probe_iters, sink.data_ptr(),
+        # the butterfly of the plan's modulus class: moduli below 2^57 use the
+        # small-modulus class (kind 2), others the exact-quotient class (kind 0)
+        probe_kind = 2 if max(mods) < (1 << 57) else 0
+        rc = L.ntt_bench_butterflies(mods[0], probe_kind, sms * 8, 256, probe_iters, sink.data_ptr(),
                                      stream.cuda_stream)
         assert rc == 0, rc
         e1.record(stream)
@@ -364,12 +367,14 @@ def run_ours(args):
     hbm_src = "measured"
     if not hbm_peak:
         hbm_peak, hbm_src = 6800.0, "fallback"
+    # DRAM bytes of one forward transform from the committed ncu capture, when
+    # it was taken on these kernel sources and this schedule
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(tpath) as f:
             t = json.load(f)
-        if t.get("build_stamp") == open(B.LIB + ".stamp").read().strip() and t.get("schedule") == plan.schedule:
+        if t.get("kernel_stamp") == B.kernel_stamp() and t.get("schedule") == plan.schedule:
             traffic = t.get("fwd_bytes_per_transform")
     except (OSError, ValueError):
         pass
@@ -379,8 +384,8 @@ def run_ours(args):
         "kernel": "ntt_forward (%s)" % ntt.schedule_name(LOG2N, plan.schedule),
         "achieved": achieved_bfly / 1e9, "peak": probe_best / 1e9, "unit": "Gbutterfly/s",
         "frac": achieved_bfly / probe_best,
-        "peak_source": "in-run probe: %d SMs x 8 CTAs x 256 thr x 8 independent Harvey CT butterflies "
-                       "(same arithmetic as the kernels)" % sms,
+        "peak_source": "in-run probe: %d SMs x 8 CTAs x 256 thr x 8 independent forward butterflies "
+                       "with the kernels' arithmetic for these moduli (probe kind %d)" % (sms, probe_kind),
         "imad_slots_per_butterfly": (sms * 64 * (clock_mhz or 2070.0) * 1e6) / probe_best,
         "traffic": traffic,
         "hbm": {"achieved": bytes_fwd / fwd_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
@@ -467,8 +472,15 @@ def run_other(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     clocks = ClockSampler(local)
     extra = {}
-    if args.workload == "mixed_batch":
-        spec = W.mixed_requests(seed=W.DEFAULT_SEED + rank)
+    if args.workload in ("mixed_batch", "mixed_small"):
+        if args.workload == "mixed_batch":
+            spec = W.mixed_requests(seed=W.DEFAULT_SEED + rank)
+            dist_note = "N in {2^10,2^12,2^14,2^16} (.5/.2/.2/.1), limbs U{1..32}, polys U{1..64}, forward"
+        else:
+            # many small independent transforms (the TFHE side of scheme switching)
+            spec = W.mixed_requests(seed=W.DEFAULT_SEED + rank, n_requests=2000, max_limbs=4, max_polys=4,
+                                    log2ns=(10, 11), weights=(0.7, 0.3))
+            dist_note = "2000 requests, N in {2^10, 2^11} (.7/.3), limbs U{1..4}, polys U{1..4}, forward"
         reqs, coef, bfly = [], 0, 0
         for i, (log2n, limbs, polys) in enumerate(spec):
             x = W.request_rows_torch(W.DEFAULT_SEED + rank, i, log2n, limbs, polys)
@@ -494,9 +506,10 @@ def run_other(args):
             "launches_per_step": launches_plain // args.steps,
             "how": "one launch sequence per request, default schedule of its N, same tables"}
         extra["speedup_vs_plain"] = sum(ms_plain) / sum(ms)
-        config = {"workload": "mixed_batch", "requests": len(spec), "coefficients": coef,
-                  "distribution": "N in {2^10,2^12,2^14,2^16} (.5/.2/.2/.1), limbs U{1..32}, polys U{1..64}, forward",
-                  "batched": "one persistent kernel under a CUDA graph", "l2": "inputs (%.1f GB) > L2" % (coef * 8 / 1e9)}
+        config = {"workload": args.workload, "requests": len(spec), "coefficients": coef,
+                  "distribution": dist_note, "batched": "one persistent kernel under a CUDA graph",
+                  "l2": ("inputs (%.1f GB) > L2" % (coef * 8 / 1e9)) if coef * 8 > (256 << 20)
+                  else "inputs (%.0f MB) fit L2: timed warm" % (coef * 8 / 1e6)}
         unit_coef = coef
     elif args.workload == "tfhe_blind_rotation":
         w = W.tfhe_blind_rotation()
@@ -521,6 +534,48 @@ def run_other(args):
                                       "how": "forward launch + inverse launch, default schedule"}
         config = {"workload": "tfhe_blind_rotation", "log2n": 10, "modulus_bits": 62,
                   "rows": "3780 forward (signed digits) + 1260 inverse", "batched": "one persistent launch (CUDA graph)",
+                  "l2": "flushed before every step"}
+    elif args.workload == "hmul_fused":
+        w = W.ckks_hmul_n65536()
+        mods = w["moduli"]
+        Lm, n = len(mods), 1 << 16
+        x = to_dev_np(torch, w["x"].reshape(4 * Lm, n))
+        plan = ntt.Plan(16, mods, 4)
+        limb_plan = ntt.Plan(16, mods, 1)
+        A = torch.empty_like(x)
+        D = torch.empty((3 * Lm, n), dtype=torch.int64, device="cuda")
+        P = torch.empty_like(x)
+        Av, Pv = A.view(4, Lm, n), P.view(4, Lm, n)
+
+        def fused():
+            plan.forward(x, A)
+            n1 = plan.last_launches()
+            plan.hmul_tensor(A[:2 * Lm], A[2 * Lm:], D)
+            return n1 + plan.last_launches()
+
+        def unfused():
+            plan.forward(x, A)
+            for k, (i, j) in enumerate([(0, 0), (0, 1), (1, 0), (1, 1)]):
+                limb_plan.pointwise(Av[i], Av[2 + j], Pv[k])
+            plan.inverse(P, P)
+            return 8
+        coef = (4 + 3) * Lm * n
+        bfly = (4 + 3) * Lm * (n // 2) * 16
+        q_probe, kind = mods[0], 2
+        for _ in range(max(3, args.warmup)):
+            fused()
+            unfused()
+        torch.cuda.synchronize()
+        clocks.start()
+        ms, launches = _events_loop(torch, stream, args.steps, fused, flush)
+        clk = clocks.stop()
+        ms_u, _ = _events_loop(torch, stream, args.steps, unfused, flush)
+        extra["unfused"] = {"ms_per_step": sum(ms_u) / args.steps,
+                            "how": "forward NTT, 4 cross products (4 launches), inverse NTT of 96 rows; "
+                                   "d1 still needs one more addition"}
+        extra["speedup_vs_unfused"] = sum(ms_u) / sum(ms)
+        config = {"workload": "hmul_fused", "log2n": 16, "limbs": Lm,
+                  "step": "NTT of a0,a1,b0,b1 (96 rows) -> tensor product fused into the inverse -> d0,d1,d2 (72 rows)",
                   "l2": "flushed before every step"}
     else:  # plain_n1024
         w = W.plain_n1024()

@@ -116,6 +116,20 @@ int poly_mul_pointwise(ntt_plan_t plan, const uint64_t* d_a, const uint64_t* d_b
                        uint32_t n_polys, void* cuda_stream);
 
 /*
+ * Fused CKKS ciphertext multiplication core (Sec. II-A HMUL; Eq. 1 applied to
+ * the tensor product of two ciphertexts): given ciphertexts a = (a0, a1) and
+ * b = (b0, b1) already in the NTT domain (each [2][n_moduli][N]), computes
+ *   d0 = INTT(a0 (.) b0),  d1 = INTT(a0 (.) b1 + a1 (.) b0),  d2 = INTT(a1 (.) b1)
+ * into d_out ([3][n_moduli][N], coefficient domain).  The products are formed
+ * inside the first kernel of the inverse transform (no separate pointwise
+ * pass).  d_out must not overlap d_a or d_b.  Uses the plan's tables and
+ * moduli (its batch is not used); if the plan's schedule is a pipelined one,
+ * the first direct-form schedule of N is used instead.
+ */
+int ntt_hmul_tensor(ntt_plan_t plan, const uint64_t* d_a, const uint64_t* d_b, uint64_t* d_out,
+                    void* cuda_stream);
+
+/*
  * Schedules (Sec. V-D: the split of the log2 N stages into fused groups and
  * kernel passes, threads per polynomial, polynomials per CTA).  Each N has a
  * small fixed list of candidate schedules; ntt_plan picks a default, an

@@ -55,6 +55,21 @@ def _stamp(kind, flags):
     return h.hexdigest()
 
 
+TILE_KERNEL_SOURCES = ["ntt_arith.cuh", "ntt_tile.cuh", "ntt_kernels.cuh", "ntt_schedules.h",
+                       "kernels_small.cu", "kernels_mid.cu", "kernels_large.cu", "kernels_huge.cu"]
+
+
+def kernel_stamp():
+    """Hash of the transform kernels' sources: identifies the kernels that a
+    hardware-counter capture (profiles/) was taken on."""
+    h = hashlib.sha256()
+    for name in TILE_KERNEL_SOURCES:
+        with open(os.path.join(CSRC, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def _up_to_date(lib, stamp):
     sp = lib + ".stamp"
     return os.path.exists(lib) and os.path.exists(sp) and open(sp).read().strip() == stamp

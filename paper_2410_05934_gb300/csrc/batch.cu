@@ -42,16 +42,18 @@ struct BatchItem {
 };
 
 #define NTT_BATCH_THREADS 256
+static constexpr size_t kBatchSmemBound = 48 * 1024;
 
 // One phase (stage range) of a config over rows [a.row_begin, +n_rows).
 template <class C>
 __device__ __forceinline__ void batch_phase(TileArgs a, uint64_t n_rows, uint64_t* smem) {
     static_assert(C::THREADS == NTT_BATCH_THREADS, "batch configs use 256-thread CTAs");
+    static_assert(C::SMEM_BYTES <= kBatchSmemBound, "batch configs fit the kernel's shared memory");
     a.n_tiles = n_rows << C::LOGTPR;
     const int tin = threadIdx.x >> C::LOGT, t = threadIdx.x & (C::T - 1);
     uint64_t* sm = smem + (size_t)tin * C::TILE_WORDS;
     for (uint64_t g = 0; g * C::TPC < a.n_tiles; ++g) {
-        const TileLoc L = locate<C>(a, g * C::TPC + tin);
+        const TileLoc L = locate_in_group<C>(a, g, tin);
         TileRegs<C> st;
         load_direct<C>(st, a, L, t, sm);
         write_pairs_swizzled<C>(st, L, t, sm);
@@ -91,15 +93,21 @@ __device__ __forceinline__ void batch_split(const TileArgs& a, const BatchReq& r
     }
 }
 
-#define NTT_BATCH_CASE_SINGLE(LOGN, LOGT, LOGRP, TPC) \
-    case LOGN: batch_single<LOGN, LOGT, LOGRP, TPC, INV, MC>(a, rq, n_rows, smem); break;
+// Only the paths with N <= 2^NMAX are compiled into a kernel variant: a
+// batch of short polynomials runs a variant whose register budget is not
+// set by the long-polynomial paths.
+#define NTT_BATCH_CASE_SINGLE(LOGN, LOGT, LOGRP, TPC)                                   \
+    case LOGN:                                                                         \
+        if constexpr (LOGN <= NMAX) batch_single<LOGN, LOGT, LOGRP, TPC, INV, MC>(a, rq, n_rows, smem); \
+        break;
 #define NTT_BATCH_CASE_SPLIT(LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB)                 \
     case LOGN:                                                                                         \
-        batch_split<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, INV, MC>(a, rq, n_rows, \
-                                                                                         smem);         \
+        if constexpr (LOGN <= NMAX)                                                                    \
+            batch_split<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, INV, MC>(a, rq,    \
+                                                                                             n_rows, smem); \
         break;
 
-template <bool INV, int MC>
+template <bool INV, int MC, int NMAX>
 __device__ __forceinline__ void batch_dispatch(const TileArgs& a, const BatchReq& rq, uint64_t n_rows,
                                                uint64_t* smem) {
     switch (rq.log2n) {
@@ -108,12 +116,18 @@ __device__ __forceinline__ void batch_dispatch(const TileArgs& a, const BatchReq
     }
 }
 
-// Largest shared-memory footprint among the batch configurations (N = 2^12
-// single tile and N = 2^16 row phase: 96 KiB).
-static constexpr size_t kBatchSmem = 96 * 1024;
+// Largest shared-memory footprint among the batch configurations (48 KiB).
+static constexpr size_t kBatchSmem = 48 * 1024;
+#define NTT_BATCH_MIN_CTAS 3
+// kernel variants: all N (NMAX 16), or short polynomials only (NMAX 11)
+#define NTT_BATCH_SHORT_NMAX 11
+template <int NMAX>
+struct BatchOcc {
+    static constexpr int ctas = NMAX <= NTT_BATCH_SHORT_NMAX ? 4 : NTT_BATCH_MIN_CTAS;
+};
 
-template <int MC>
-__global__ void __launch_bounds__(NTT_BATCH_THREADS, 2)
+template <int MC, int NMAX>
+__global__ void __launch_bounds__(NTT_BATCH_THREADS, BatchOcc<NMAX>::ctas)
     k_ntt_batch(const BatchReq* __restrict__ reqs, const BatchItem* __restrict__ items, uint32_t n_items,
                 uint32_t* counter, int* status, uint32_t check) {
     extern __shared__ __align__(16) uint64_t smem[];
@@ -136,11 +150,20 @@ __global__ void __launch_bounds__(NTT_BATCH_THREADS, 2)
         a.n_tiles = 0;
         a.n_moduli = rq.n_moduli;
         a.check = check;
+        a.fast32 = 0;
+        a.mod_magic = 0;
+        a.src_mode = 0;
+        a.in_b = nullptr;
         if (rq.inverse)
-            batch_dispatch<true, MC>(a, rq, it.n_rows, smem);
+            batch_dispatch<true, MC, NMAX>(a, rq, it.n_rows, smem);
         else
-            batch_dispatch<false, MC>(a, rq, it.n_rows, smem);
+            batch_dispatch<false, MC, NMAX>(a, rq, it.n_rows, smem);
     }
+}
+
+static const void* batch_kernel(uint32_t mc, uint32_t short_only) {
+    if (mc) return short_only ? (const void*)k_ntt_batch<1, NTT_BATCH_SHORT_NMAX> : (const void*)k_ntt_batch<1, 16>;
+    return short_only ? (const void*)k_ntt_batch<0, NTT_BATCH_SHORT_NMAX> : (const void*)k_ntt_batch<0, 16>;
 }
 
 // rows per work item: about one 2^13-coefficient chunk, whole rows above
@@ -177,7 +200,7 @@ static_assert(256 + sizeof(StaticReq) * NTT_STATIC_MAX_REQUESTS <= NTT_STATIC_SC
 static __device__ __align__(256) unsigned char g_ntt_static_scratch[NTT_STATIC_SCRATCH_BYTES];
 
 template <int MC>
-__global__ void __launch_bounds__(NTT_BATCH_THREADS, 2)
+__global__ void __launch_bounds__(NTT_BATCH_THREADS, NTT_BATCH_MIN_CTAS)
     k_ntt_batch_static(const StaticReq* __restrict__ reqs, uint32_t n_reqs, uint32_t n_items,
                        uint32_t* counter) {
     extern __shared__ __align__(16) uint64_t smem[];
@@ -215,10 +238,14 @@ __global__ void __launch_bounds__(NTT_BATCH_THREADS, 2)
         a.n_tiles = 0;
         a.n_moduli = sr.n_moduli;
         a.check = sr.check;
+        a.fast32 = 0;
+        a.mod_magic = 0;
+        a.src_mode = 0;
+        a.in_b = nullptr;
         if (sr.inverse)
-            batch_dispatch<true, MC>(a, rq, n_rows, smem);
+            batch_dispatch<true, MC, 16>(a, rq, n_rows, smem);
         else
-            batch_dispatch<false, MC>(a, rq, n_rows, smem);
+            batch_dispatch<false, MC, 16>(a, rq, n_rows, smem);
     }
 }
 
@@ -267,6 +294,7 @@ struct ntt_batch_s {
     uint32_t* d_counter = nullptr;
     int* d_status = nullptr;
     uint32_t flags = 0, mc = 0, check = 0;
+    uint32_t short_only = 0;    // every request has N <= 2^NTT_BATCH_SHORT_NMAX
     int device = -1;
     int grid = 0;
     uint64_t coefficients = 0;
@@ -353,6 +381,9 @@ int ntt_batch_plan(ntt_batch_t* out, const ntt_request_t* reqs, uint32_t n_reqs,
                 b->hitems.push_back({i, (uint32_t)std::min<uint64_t>(per, rows - r0), r0});
             b->coefficients += rows << r.log2n;
         }
+        b->short_only = 1;
+        for (const auto& r : b->reqs)
+            if (r.log2n > NTT_BATCH_SHORT_NMAX) b->short_only = 0;
         std::stable_sort(b->hitems.begin(), b->hitems.end(), [&](const BatchItem& x, const BatchItem& y) {
             return b->reqs[x.req].log2n > b->reqs[y.req].log2n;
         });
@@ -404,12 +435,10 @@ int ntt_batch_plan(ntt_batch_t* out, const ntt_request_t* reqs, uint32_t n_reqs,
              cudaMemset(b->d_status, 0, sizeof(int)) == cudaSuccess;
     }
     if (ok) {
-        cudaError_t e = b->mc ? cudaFuncSetAttribute(k_ntt_batch<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem)
-                              : cudaFuncSetAttribute(k_ntt_batch<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem);
+        const void* fn = batch_kernel(b->mc, b->short_only);
         int per_sm = 0, sms = 0;
-        ok = e == cudaSuccess &&
-             (b->mc ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ntt_batch<1>, NTT_BATCH_THREADS, kBatchSmem)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ntt_batch<0>, NTT_BATCH_THREADS, kBatchSmem)) == cudaSuccess &&
+        ok = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) == cudaSuccess &&
+             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NTT_BATCH_THREADS, kBatchSmem) == cudaSuccess &&
              cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) == cudaSuccess;
         b->grid = std::max(1, per_sm) * std::max(1, sms);
         if ((uint64_t)b->grid > b->hitems.size()) b->grid = (int)b->hitems.size();
@@ -446,12 +475,16 @@ int ntt_batch_update(ntt_batch_t b, const ntt_request_t* reqs, uint32_t n_reqs, 
 
 static int batch_enqueue(ntt_batch_t b, cudaStream_t st) {
     if (cudaMemsetAsync(b->d_counter, 0, sizeof(uint32_t), st) != cudaSuccess) return NTT_ERR_CUDA;
-    if (b->mc)
-        k_ntt_batch<1><<<b->grid, NTT_BATCH_THREADS, kBatchSmem, st>>>(b->d_reqs, b->d_items, (uint32_t)b->hitems.size(),
-                                                                      b->d_counter, b->d_status, b->check);
-    else
-        k_ntt_batch<0><<<b->grid, NTT_BATCH_THREADS, kBatchSmem, st>>>(b->d_reqs, b->d_items, (uint32_t)b->hitems.size(),
-                                                                      b->d_counter, b->d_status, b->check);
+    const uint32_t n = (uint32_t)b->hitems.size();
+#define NTT_BATCH_LAUNCH(MC, NMAX) \
+    k_ntt_batch<MC, NMAX><<<b->grid, NTT_BATCH_THREADS, kBatchSmem, st>>>(b->d_reqs, b->d_items, n, b->d_counter, \
+                                                                       b->d_status, b->check)
+    if (b->mc) {
+        if (b->short_only) NTT_BATCH_LAUNCH(1, NTT_BATCH_SHORT_NMAX); else NTT_BATCH_LAUNCH(1, 16);
+    } else {
+        if (b->short_only) NTT_BATCH_LAUNCH(0, NTT_BATCH_SHORT_NMAX); else NTT_BATCH_LAUNCH(0, 16);
+    }
+#undef NTT_BATCH_LAUNCH
     return cudaPeekAtLastError() == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
 }
 
@@ -518,6 +551,8 @@ int ntt_batch_execute_plain(ntt_batch_t b, const uint32_t* schedules, void* cuda
         d.n_moduli = r.n_moduli;
         d.check = b->check;
         d.mc = b->tables[r.log2n].host.mc;
+        d.src_mode = 0;
+        d.in_b = nullptr;
         const LaunchFn fn = r.inverse ? table[idx].inv : table[idx].fwd;
         int rc = fn(d, r.in, r.out, 0, rows, cuda_stream, &b->last_launches);
         if (rc) return rc;

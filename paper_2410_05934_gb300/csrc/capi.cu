@@ -64,13 +64,13 @@ static void sched_describe(int i, char* buf, size_t len) {
     if (s.kind == 1) {
         int r = v[0] - v[1];
         snprintf(buf, len, "1k%s: %d thr/row x %d coef, <=%d fused stages/pass, %d rows/CTA",
-                 s.pipe ? " pipelined" : "", 1 << v[1], 1 << r, v[2], v[3]);
+                 s.pipe == 1 ? " pipelined" : (s.pipe == 2 ? " ro-twiddles" : ""), 1 << v[1], 1 << r, v[2], v[3]);
     } else {
         int ra = v[1] + v[2] - v[3], rb = (v[0] - v[1]) - v[6];
         snprintf(buf, len,
                  "2k%s split %d+%d: col tile 2^%dx%d (%d thr x %d coef, <=%d/pass, %d/CTA); "
                  "row tile 2^%d (%d thr x %d coef, <=%d/pass, %d/CTA)",
-                 s.pipe ? " pipelined" : "", v[1], v[0] - v[1], v[1], 1 << v[2], 1 << v[3], 1 << ra, v[4], v[5], v[0] - v[1],
+                 s.pipe == 1 ? " pipelined" : (s.pipe == 2 ? " ro-twiddles" : ""), v[1], v[0] - v[1], v[1], 1 << v[2], 1 << v[3], 1 << ra, v[4], v[5], v[0] - v[1],
                  1 << v[6], 1 << rb, v[7], v[8]);
     }
 }
@@ -84,10 +84,10 @@ uint32_t default_schedule(uint32_t log2n, uint64_t rows) {
         case 10: return rows < 1024 ? 1u : 0u;   // pipelined / direct, 128 thr x 8 coef
         case 11: return 1u;                      // pipelined, 256 thr x 8 coef
         case 12: return 1u;                      // pipelined, 512 thr x 8 coef
-        case 13: return 1u;                      // direct, 256 thr x 32 coef
-        case 14: return 2u;                      // pipelined column + row kernels (7 + 7)
-        case 15: return 0u;                      // pipelined column + row kernels (7 + 8)
-        case 16: return 1u;                      // direct column + row kernels (8 + 8, 16 coef/thr)
+        case 13: return 3u;                      // column + row kernels (6 + 7)
+        case 14: return 3u;                      // column + row kernels (7 + 7)
+        case 15: return 4u;                      // column + row kernels (7 + 8, 8 coef/thr rows)
+        case 16: return 6u;                      // column + row kernels (7 + 9, 8 coef/thr rows)
         default: return 0u;
     }
 }
@@ -101,6 +101,8 @@ static PlanDev plan_dev(const ntt_plan_s* p) {
     d.n_moduli = p->h.n_moduli;
     d.check = (p->h.flags & NTT_FLAG_CHECK) ? 1u : 0u;
     d.mc = p->h.mc;
+    d.src_mode = 0;
+    d.in_b = nullptr;
     return d;
 }
 
@@ -227,6 +229,32 @@ int ntt_forward_rows(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, uin
 int ntt_inverse_rows(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, uint64_t row_begin,
                      uint64_t n_rows, void* cuda_stream) {
     return transform(plan, true, d_in, d_out, row_begin, n_rows, cuda_stream);
+}
+
+int ntt_hmul_tensor(ntt_plan_t plan, const uint64_t* d_a, const uint64_t* d_b, uint64_t* d_out,
+                    void* cuda_stream) {
+    if (!plan || !d_a || !d_b || !d_out) return NTT_ERR_ARG;
+    if (!aligned16(d_a) || !aligned16(d_b) || !aligned16(d_out)) return NTT_ERR_ALIGN;
+    int rc = check_device(plan);
+    if (rc) return rc;
+    // the tensor product runs in the direct form of the inverse's first kernel
+    int idx = sched_index(plan->h.log2n, plan->schedule);
+    if (idx < 0 || g_params[idx].pipe == 1) {
+        idx = -1;
+        for (uint32_t id = 0; (int)id < schedule_count(plan->h.log2n); ++id) {
+            const int k = sched_index(plan->h.log2n, id);
+            if (g_params[k].pipe != 1) {
+                idx = k;
+                break;
+            }
+        }
+        if (idx < 0) return NTT_ERR_UNSUPPORTED;
+    }
+    plan->last_launches = 0;
+    PlanDev d = plan_dev(plan);
+    d.src_mode = 1;
+    d.in_b = d_b;
+    return g_table[idx].inv(d, d_a, d_out, 0, 3ull * plan->h.n_moduli, cuda_stream, &plan->last_launches);
 }
 
 int poly_mul_pointwise(ntt_plan_t plan, const uint64_t* d_a, const uint64_t* d_b, uint64_t* d_c,

@@ -108,6 +108,11 @@ static TileArgs emu_args(const PlanDev& p, const uint64_t* in, uint64_t* out, ui
     a.n_tiles = n_rows << C::LOGTPR;
     a.n_moduli = p.n_moduli;
     a.check = p.check;
+    // the 32-bit reciprocal path whenever it applies, like the launcher
+    a.fast32 = (row_begin + n_rows < (1ull << 32) && a.n_tiles < (1ull << 32)) ? 1u : 0u;
+    a.mod_magic = fdiv_magic(a.n_moduli);
+    a.src_mode = p.src_mode;
+    a.in_b = p.in_b;
     return a;
 }
 
@@ -126,6 +131,7 @@ template <class C>
 static int emu_kernel(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t row_begin,
                       uint64_t n_rows) {
     if (!verify_cfg<C>()) return NTT_ERR_UNSUPPORTED;
+    if (C::PIPE && C::FIRST && p.src_mode) return NTT_ERR_UNSUPPORTED;   // direct form only
     const TileArgs a = emu_args<C>(p, in, out, row_begin, n_rows);
     const uint64_t groups = (a.n_tiles + C::TPC - 1) / C::TPC;
     std::vector<TileRegs<C>> st(C::THREADS);
@@ -133,7 +139,7 @@ static int emu_kernel(const PlanDev& p, const uint64_t* in, uint64_t* out, uint6
     if (!C::PIPE) {
         std::vector<uint64_t> sm(C::BUF_WORDS, 0xdeadbeefdeadbeefull);
         for (uint64_t g = 0; g < groups; ++g) {
-            for (int tin = 0; tin < C::TPC; ++tin) L[tin] = locate<C>(a, g * C::TPC + tin);
+            for (int tin = 0; tin < C::TPC; ++tin) L[tin] = locate_in_group<C>(a, g, tin);
             for (int tid = 0; tid < C::THREADS; ++tid) {
                 const int tin = tid >> C::LOGT, t = tid & (C::T - 1);
                 uint64_t* sm_t = sm.data() + (size_t)tin * C::TILE_WORDS;
@@ -161,14 +167,14 @@ static int emu_kernel(const PlanDev& p, const uint64_t* in, uint64_t* out, uint6
                 const TileLoc T0 = locate<C>(a, g * C::TPC + tin);
                 if (!T0.valid) continue;
                 expect += (uint32_t)C::DATA_BYTES;
-                if (!twiddles_reusable<C>(a, g, g_prev, have_prev, tin))
+                if (twiddles_needed<C>(a, g, g_prev, have_prev, tin))
                     expect += (uint32_t)(C::TILE_TX_BYTES - C::DATA_BYTES);
             }
             for (int c = 0; c < C::TPC * C::COPIES; ++c) {
                 const int tin = c / C::COPIES, cc = c % C::COPIES;
                 const TileLoc T0 = locate<C>(a, g * C::TPC + tin);
                 if (!T0.valid) continue;
-                if (cc >= C::RUNS && twiddles_reusable<C>(a, g, g_prev, have_prev, tin)) continue;
+                if (cc >= C::RUNS && !twiddles_needed<C>(a, g, g_prev, have_prev, tin)) continue;
                 const CopyDesc d = tile_copy<C>(a, T0, cc);
                 uint64_t* dst = buf + (size_t)tin * C::TILE_WORDS + d.dst_word;
                 NTT_SMEM_CHECK((size_t)tin * C::TILE_WORDS + d.dst_word + d.bytes / 8 - 1, C::BUF_WORDS);
@@ -176,7 +182,7 @@ static int emu_kernel(const PlanDev& p, const uint64_t* in, uint64_t* out, uint6
                 copied += d.bytes;
             }
             if (copied != expect) return NTT_ERR_UNSUPPORTED;
-            for (int tin = 0; tin < C::TPC; ++tin) L[tin] = locate<C>(a, g * C::TPC + tin);
+            for (int tin = 0; tin < C::TPC; ++tin) L[tin] = locate_in_group<C>(a, g, tin);
             for (int tid = 0; tid < C::THREADS; ++tid) {
                 const int tin = tid >> C::LOGT, t = tid & (C::T - 1);
                 relayout_read<C>(st[tid], a, L[tin], t, buf + (size_t)tin * C::TILE_WORDS);
@@ -194,15 +200,15 @@ static int emu_kernel(const PlanDev& p, const uint64_t* in, uint64_t* out, uint6
 template <int LOGN, int LOGT, int LOGRP, int TPC, int PIPE, bool INV>
 static int emu_s1(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t rb, uint64_t nr) {
     if (p.mc == 1)
-        return emu_kernel<TileCfg<LOGN, 0, LOGN, 0, LOGT, LOGRP, TPC, INV, 1, PIPE != 0>>(p, in, out, rb, nr);
-    return emu_kernel<TileCfg<LOGN, 0, LOGN, 0, LOGT, LOGRP, TPC, INV, 0, PIPE != 0>>(p, in, out, rb, nr);
+        return emu_kernel<TileCfg<LOGN, 0, LOGN, 0, LOGT, LOGRP, TPC, INV, 1, PIPE>>(p, in, out, rb, nr);
+    return emu_kernel<TileCfg<LOGN, 0, LOGN, 0, LOGT, LOGRP, TPC, INV, 0, PIPE>>(p, in, out, rb, nr);
 }
 
 template <int LOGN, int SPLIT, int LOGP, int LOGTA, int LOGRPA, int TPCA, int LOGTB, int LOGRPB,
           int TPCB, int PIPE, bool INV, int MC>
 static int emu_s2_mc(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t rb, uint64_t nr) {
-    using CA = TileCfg<LOGN, 0, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, INV, MC, PIPE != 0>;
-    using CB = TileCfg<LOGN, SPLIT, LOGN, 0, LOGTB, LOGRPB, TPCB, INV, MC, PIPE != 0>;
+    using CA = TileCfg<LOGN, 0, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, INV, MC, PIPE>;
+    using CB = TileCfg<LOGN, SPLIT, LOGN, 0, LOGTB, LOGRPB, TPCB, INV, MC, PIPE>;
     int rc;
     if (!INV) {
         rc = emu_kernel<CA>(p, in, out, rb, nr);
@@ -306,6 +312,8 @@ int nttemu_transform(void* plan, uint32_t sched, int inverse, const uint64_t* in
     d.n_moduli = p->h.n_moduli;
     d.check = (p->h.flags & NTT_FLAG_CHECK) ? 1u : 0u;
     d.mc = p->h.mc;
+    d.src_mode = 0;
+    d.in_b = nullptr;
     return (inverse ? e->inv : e->fwd)(d, in, out, row_begin, n_rows);
 }
 
@@ -323,9 +331,31 @@ int nttemu_batch_transform(void* plan, int inverse, const uint64_t* in, uint64_t
         d.n_moduli = p->h.n_moduli;
         d.check = (p->h.flags & NTT_FLAG_CHECK) ? 1u : 0u;
         d.mc = p->h.mc;
+        d.src_mode = 0;
+        d.in_b = nullptr;
         return (inverse ? e.inv : e.fwd)(d, in, out, 0, p->h.rows);
     }
     return NTT_ERR_UNSUPPORTED;
+}
+
+// Tensor product + inverse transform (ntt_hmul_tensor) with schedule `sched`:
+// a, b are [2][n_moduli][N] in the NTT domain, out is [3][n_moduli][N].
+int nttemu_hmul_tensor(void* plan, uint32_t sched, const uint64_t* a, const uint64_t* b, uint64_t* out) {
+    EmuPlan* p = static_cast<EmuPlan*>(plan);
+    if (!p || !a || !b || !out) return NTT_ERR_ARG;
+    const EmuEntry* e = emu_find(p->h.log2n, sched);
+    if (!e) return NTT_ERR_ARG;
+    PlanDev d;
+    d.fwd = p->h.fwd.data();
+    d.inv = p->h.inv.data();
+    d.lc = p->h.consts.data();
+    d.status = &p->status;
+    d.n_moduli = p->h.n_moduli;
+    d.check = 0;
+    d.mc = p->h.mc;
+    d.src_mode = 1;
+    d.in_b = b;
+    return e->inv(d, a, out, 0, 3ull * p->h.n_moduli);
 }
 
 // Pointwise product with the kernel's arithmetic (Barrett).

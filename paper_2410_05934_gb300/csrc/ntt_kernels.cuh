@@ -84,8 +84,7 @@ __global__ void __launch_bounds__(C::THREADS) k_ntt_tile(TileArgs a) {
     const int tid = threadIdx.x;
     const int tin = tid >> C::LOGT;
     const int t = tid & (C::T - 1);
-    const uint64_t tile = (uint64_t)blockIdx.x * C::TPC + tin;
-    const TileLoc L = locate<C>(a, tile);
+    const TileLoc L = locate_in_group<C>(a, blockIdx.x, tin);
     uint64_t* sm = smem + (size_t)tin * C::TILE_WORDS;
     TileRegs<C> st;
     load_direct<C>(st, a, L, t, sm);
@@ -108,7 +107,7 @@ __device__ __forceinline__ void issue_group(const TileArgs& a, uint64_t g, int b
             const TileLoc L = locate<C>(a, g * C::TPC + tin);
             if (!L.valid) continue;
             bytes += (uint32_t)C::DATA_BYTES;
-            if (!twiddles_reusable<C>(a, g, g_prev, have_prev, tin))
+            if (twiddles_needed<C>(a, g, g_prev, have_prev, tin))
                 bytes += (uint32_t)(C::TILE_TX_BYTES - C::DATA_BYTES);
         }
         mbar_arrive_expect_tx(&bars[buf], bytes);
@@ -117,7 +116,7 @@ __device__ __forceinline__ void issue_group(const TileArgs& a, uint64_t g, int b
         const int tin = c / C::COPIES, cc = c % C::COPIES;
         const TileLoc L = locate<C>(a, g * C::TPC + tin);
         if (!L.valid) continue;
-        if (cc >= C::RUNS && twiddles_reusable<C>(a, g, g_prev, have_prev, tin)) continue;
+        if (cc >= C::RUNS && !twiddles_needed<C>(a, g, g_prev, have_prev, tin)) continue;
         const CopyDesc d = tile_copy<C>(a, L, cc);
         uint64_t* dst = smem + (size_t)buf * C::BUF_WORDS + (size_t)tin * C::TILE_WORDS + d.dst_word;
         bulk_load(dst, d.src, d.bytes, &bars[buf]);
@@ -155,7 +154,7 @@ __global__ void __launch_bounds__(C::THREADS) k_ntt_tile_pipe(TileArgs a, uint64
             if (gn < groups) (void)mbar_wait_bounded(&bars[b ^ 1], (parity >> (b ^ 1)) & 1u);
             return;
         }
-        const TileLoc L = locate<C>(a, g * C::TPC + tin);
+        const TileLoc L = locate_in_group<C>(a, g, tin);
         uint64_t* sm = smem + (size_t)b * C::BUF_WORDS + (size_t)tin * C::TILE_WORDS;
         TileRegs<C> st;
         relayout_read<C>(st, a, L, t, sm);
@@ -200,6 +199,11 @@ int launch_tile_kernel(const PlanDev& p, const uint64_t* in, uint64_t* out, uint
     a.n_tiles = n_rows << C::LOGTPR;
     a.n_moduli = p.n_moduli;
     a.check = p.check;
+    a.fast32 = (row_begin + n_rows < (1ull << 32) && a.n_tiles < (1ull << 32)) ? 1u : 0u;
+    a.mod_magic = fdiv_magic(a.n_moduli);
+    a.src_mode = p.src_mode;
+    a.in_b = p.in_b;
+    if (C::PIPE && C::FIRST && p.src_mode) return NTT_ERR_UNSUPPORTED;  // direct form only
     const uint64_t groups = (a.n_tiles + C::TPC - 1) / C::TPC;
     if (groups == 0) return NTT_OK;
     if (groups > 0x7fffffffull) return NTT_ERR_ARG;
@@ -224,10 +228,10 @@ int launch_s1(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t row_
               uint64_t n_rows, void* stream, uint32_t* launches) {
     int rc;
     if (p.mc == 1)
-        rc = launch_tile_kernel<TileCfg<LOGN, 0, LOGN, 0, LOGT, LOGRP, TPC, INV, 1, PIPE != 0>>(
+        rc = launch_tile_kernel<TileCfg<LOGN, 0, LOGN, 0, LOGT, LOGRP, TPC, INV, 1, PIPE>>(
             p, in, out, row_begin, n_rows, (cudaStream_t)stream);
     else
-        rc = launch_tile_kernel<TileCfg<LOGN, 0, LOGN, 0, LOGT, LOGRP, TPC, INV, 0, PIPE != 0>>(
+        rc = launch_tile_kernel<TileCfg<LOGN, 0, LOGN, 0, LOGT, LOGRP, TPC, INV, 0, PIPE>>(
             p, in, out, row_begin, n_rows, (cudaStream_t)stream);
     if (rc == NTT_OK && launches) *launches += 1;
     return rc;
@@ -237,8 +241,8 @@ template <int LOGN, int SPLIT, int LOGP, int LOGTA, int LOGRPA, int TPCA, int LO
           int TPCB, int PIPE, bool INV, int MC>
 int launch_s2_mc(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t row_begin,
                  uint64_t n_rows, cudaStream_t st) {
-    using CA = TileCfg<LOGN, 0, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, INV, MC, PIPE != 0>;
-    using CB = TileCfg<LOGN, SPLIT, LOGN, 0, LOGTB, LOGRPB, TPCB, INV, MC, PIPE != 0>;
+    using CA = TileCfg<LOGN, 0, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, INV, MC, PIPE>;
+    using CB = TileCfg<LOGN, SPLIT, LOGN, 0, LOGTB, LOGRPB, TPCB, INV, MC, PIPE>;
     int rc;
     if (!INV) {
         rc = launch_tile_kernel<CA>(p, in, out, row_begin, n_rows, st);

@@ -15,6 +15,8 @@ struct PlanDev {
     uint32_t n_moduli;
     uint32_t check;
     uint32_t mc;        // modulus class: 1 when every modulus is below 2^57
+    uint32_t src_mode;  // 1: the inverse's first kernel computes the CKKS tensor product
+    const uint64_t* in_b;
 };
 
 // Transforms rows [row_begin, row_begin + n_rows) of the layout that starts

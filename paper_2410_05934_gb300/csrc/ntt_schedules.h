@@ -14,7 +14,9 @@
 //       then a row kernel runs [SPLIT, LOGN) on contiguous blocks of
 //       2^(LOGN - SPLIT).  The inverse runs them in the opposite order.
 //   PIPE = 1 selects the persistent, double-buffered form fed by bulk
-//       asynchronous copies; PIPE = 0 the direct form.
+//       asynchronous copies; PIPE = 0 the direct form; PIPE = 2 the direct
+//       form reading twiddles through the read-only cache instead of staging
+//       them in shared memory.
 //
 // The lists are split by N so that the kernel translation units can be
 // compiled in parallel; NTT_SCHEDULES_ALL keeps the table order (which is
@@ -34,23 +36,27 @@
 
 #define NTT_SCHEDULES_MID(S1, S2)                                                     \
     S1(10, 7, 3, 1, 0) S1(10, 7, 3, 1, 1) S1(10, 6, 4, 2, 0) S1(10, 6, 4, 2, 1)       \
-    S1(10, 5, 5, 4, 0) S1(10, 8, 2, 1, 1) S1(10, 5, 4, 4, 0)                          \
+    S1(10, 5, 5, 4, 0) S1(10, 8, 2, 1, 1) S1(10, 8, 2, 1, 0) S1(10, 7, 3, 1, 2)       \
     S1(11, 8, 3, 1, 0) S1(11, 8, 3, 1, 1) S1(11, 7, 4, 1, 0) S1(11, 7, 4, 1, 1)       \
-    S1(11, 6, 5, 2, 0)                                                                \
+    S1(11, 6, 5, 2, 0) S1(11, 8, 3, 1, 2)                                             \
     S1(12, 9, 3, 1, 0) S1(12, 9, 3, 1, 1) S1(12, 8, 4, 1, 0) S1(12, 8, 4, 1, 1)       \
-    S1(12, 7, 5, 1, 0)
+    S1(12, 7, 5, 1, 0) S1(12, 9, 3, 1, 2)
 
 #define NTT_SCHEDULES_LARGE(S1, S2)                                                   \
     S1(13, 9, 4, 1, 0) S1(13, 8, 5, 1, 0) S1(13, 10, 3, 1, 0)                         \
+    S2(13, 6, 4, 6, 4, 1, 5, 3, 4, 0)                                                 \
     S1(14, 10, 4, 1, 0) S1(14, 9, 5, 1, 0)                                            \
-    S2(14, 7, 4, 7, 4, 1, 4, 4, 8, 1)                                                 \
+    S2(14, 7, 4, 7, 4, 1, 4, 4, 8, 1) S2(14, 7, 4, 7, 4, 1, 4, 3, 8, 0)               \
+    S2(14, 7, 4, 7, 4, 1, 5, 2, 4, 0)                                                 \
     S2(15, 7, 4, 7, 4, 1, 4, 4, 8, 1) S2(15, 7, 4, 6, 5, 1, 3, 5, 16, 0)              \
-    S2(15, 5, 4, 4, 5, 4, 5, 5, 4, 0)
+    S2(15, 5, 4, 4, 5, 4, 5, 5, 4, 0) S2(15, 7, 4, 8, 3, 1, 5, 3, 8, 0)               \
+    S2(15, 7, 4, 7, 4, 1, 5, 3, 4, 0)
 
 #define NTT_SCHEDULES_HUGE(S1, S2)                                                    \
-    S2(16, 8, 4, 8, 4, 1, 4, 4, 8, 1) S2(16, 8, 4, 8, 4, 1, 4, 4, 8, 0)               \
-    S2(16, 8, 4, 7, 5, 1, 3, 5, 16, 1) S2(16, 8, 4, 7, 5, 1, 3, 5, 16, 0)             \
-    S2(16, 6, 4, 5, 5, 4, 5, 5, 4, 0) S2(16, 4, 4, 3, 4, 8, 7, 5, 1, 0)
+    S2(16, 8, 4, 8, 4, 1, 5, 3, 4, 0) S2(16, 8, 4, 8, 4, 1, 4, 4, 8, 0)               \
+    S2(16, 8, 4, 8, 4, 1, 5, 3, 8, 0) S2(16, 8, 4, 8, 4, 1, 5, 3, 2, 0)               \
+    S2(16, 8, 4, 8, 4, 1, 6, 2, 2, 0) S2(16, 8, 4, 9, 3, 1, 5, 3, 4, 0)               \
+    S2(16, 7, 4, 7, 4, 1, 6, 3, 2, 0) S2(16, 6, 4, 5, 5, 4, 5, 5, 4, 0)
 
 #define NTT_SCHEDULES_ALL(S1, S2)                                           \
     NTT_SCHEDULES_SMALL(S1, S2) NTT_SCHEDULES_MID(S1, S2) NTT_SCHEDULES_LARGE(S1, S2) \

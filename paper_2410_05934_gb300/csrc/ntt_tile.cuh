@@ -75,7 +75,34 @@ struct TileArgs {
     uint64_t n_tiles;       // tiles covered by this launch
     uint32_t n_moduli;
     uint32_t check;         // verify canonical inputs (first kernel only)
+    uint32_t fast32;        // tile and row indices below 2^32: use the reciprocal below
+    uint64_t mod_magic;     // ceil(2^64 / n_moduli)  (n_moduli >= 2)
+    // source mode of the first kernel of an inverse transform: 0 = read `in`;
+    // 1 = CKKS tensor product, row r = k * n_moduli + l computes d_k of limb l
+    // from in = [a0; a1] and in_b = [b0; b1] (each [2][n_moduli][N], NTT domain):
+    // d0 = a0 b0, d1 = a0 b1 + a1 b0, d2 = a1 b1
+    uint32_t src_mode;
+    const uint64_t* in_b;
 };
+
+// floor(n / d) for n < 2^32 and 2 <= d < 2^32 from M = ceil(2^64 / d):
+// n M / 2^64 exceeds n / d by less than n / 2^64 < 2^-32, while a non-integer
+// n / d is at least 1/d > 2^-32 below the next integer, so the floor is
+// exact; the 32 x 64-bit product is taken in two halves.
+NTT_HD uint32_t fdiv32(uint32_t n, uint64_t M, uint32_t d) {
+    if (d == 1) return n;
+    const uint32_t mh = (uint32_t)(M >> 32), ml = (uint32_t)M;
+#if defined(__CUDA_ARCH__)
+    const uint64_t t = (uint64_t)n * mh + __umulhi(n, ml);
+#else
+    const uint64_t t = (uint64_t)n * mh + (((uint64_t)n * ml) >> 32);
+#endif
+    return (uint32_t)(t >> 32);
+}
+
+inline uint64_t fdiv_magic(uint64_t d) {
+    return d < 2 ? 0 : (uint64_t)((((unsigned __int128)1 << 64) + d - 1) / d);
+}
 
 #define NTT_STATUS_RANGE (-8)
 #define NTT_STATUS_TIMEOUT (-7)
@@ -95,14 +122,19 @@ NTT_HD constexpr uint32_t spread(uint32_t x, int pe, int r) {
     return ((x >> pe) << (pe + r)) | (x & ((1u << pe) - 1));
 }
 
+// MODE: 0 = direct form (twiddles staged in shared memory when they fit),
+//       1 = pipelined form, 2 = direct form reading twiddles through the
+//           read-only path (no staging; the table stays in L1 when a batch
+//           shares one modulus).
 template <int LOGN_, int S0_, int S1_, int LOGP_, int LOGT_, int LOGRP_, int TPC_, bool INV_,
-          int MC_ = 0, bool PIPE_ = false>
+          int MC_ = 0, int MODE_ = 0>
 struct TileCfg {
     static constexpr int LOGN = LOGN_, S0 = S0_, S1 = S1_, LOGP = LOGP_, LOGT = LOGT_;
     static constexpr int TPC = TPC_;
     static constexpr bool INV = INV_;
     static constexpr int MC = MC_;
-    static constexpr bool PIPE = PIPE_;
+    static constexpr int MODE = MODE_;
+    static constexpr bool PIPE = MODE_ == 1;
     static constexpr int A = S1 - S0;
     static constexpr int LOGLO = LOGN - S1;
     static constexpr int LOGE = A + LOGP;
@@ -125,7 +157,7 @@ struct TileCfg {
     // read through the read-only path.
     static constexpr size_t DATA_BYTES = sizeof(uint64_t) * (size_t)E;
     static constexpr size_t TW_BYTES = 16 * ((size_t)1 << A);
-    static constexpr bool TWS = PIPE || (DATA_BYTES + TW_BYTES) * TPC <= 160 * 1024;
+    static constexpr bool TWS = PIPE || (MODE_ == 0 && (DATA_BYTES + TW_BYTES) * TPC <= 160 * 1024);
     static constexpr size_t TILE_BYTES = DATA_BYTES + (TWS ? TW_BYTES : 0);
     static constexpr size_t TILE_WORDS = TILE_BYTES / sizeof(uint64_t);
     static constexpr int NBUF = PIPE ? 2 : 1;
@@ -159,24 +191,62 @@ NTT_HD void pass_range(int p, int& s_lo, int& r) {
 
 struct TileLoc {
     uint64_t row;
+    uint64_t rowq;      // row / n_moduli (polynomial index)
     uint32_t limb;
     uint32_t hi;
     uint32_t gbase;     // g(0): the tile's hi and lo_base bits
+    int32_t tw_off;     // words from this tile's slot to the slot holding its twiddles
     bool valid;
 };
 
+// Tile order: tile = row * 2^LOGTPR + tau (tau = hi block, then lo block).
 template <class C>
 NTT_HD TileLoc locate(const TileArgs& a, uint64_t tile) {
     TileLoc L;
     L.valid = tile < a.n_tiles;
     uint64_t tl = L.valid ? tile : 0;
-    uint64_t row_local = tl >> C::LOGTPR;
-    uint32_t tau = (uint32_t)(tl & ((1ull << C::LOGTPR) - 1));
-    L.row = a.row_begin + row_local;
-    L.limb = (uint32_t)(L.row % a.n_moduli);
+    const uint32_t tau = (uint32_t)(tl & ((1ull << C::LOGTPR) - 1));
+    if (a.fast32) {
+        const uint32_t row = (uint32_t)a.row_begin + (uint32_t)(tl >> C::LOGTPR);
+        const uint32_t rq = fdiv32(row, a.mod_magic, a.n_moduli);
+        L.row = row;
+        L.rowq = rq;
+        L.limb = row - rq * a.n_moduli;
+    } else {
+        L.row = a.row_begin + (tl >> C::LOGTPR);
+        L.rowq = L.row / a.n_moduli;
+        L.limb = (uint32_t)(L.row - L.rowq * a.n_moduli);
+    }
     L.hi = tau >> C::LOGLOBLK;
     uint32_t lo_base = (tau & ((1u << C::LOGLOBLK) - 1)) << C::LOGP;
     L.gbase = (L.hi << (C::LOGN - C::S0)) | lo_base;
+    L.tw_off = 0;
+    return L;
+}
+
+// Twiddle leader of tile slot tin in group g: the first slot of the group
+// that lies in the same run of tiles with equal (limb, hi); only leaders
+// stage twiddles, the others read them from the leader's slot.  Runs in tile
+// order: the 2^LOGLOBLK tiles of one hi block of a row, or all tiles when
+// every tile has the same limb and hi (one modulus and a kernel starting at
+// stage 0, e.g. a single-modulus batch of short polynomials).
+template <class C>
+NTT_HD int tw_leader(const TileArgs& a, uint64_t g, int tin) {
+    const uint64_t t = g * C::TPC + tin;
+    uint64_t start;
+    if (a.n_moduli == 1 && C::S0 == 0) {
+        start = 0;
+    } else {
+        start = t & ~((1ull << C::LOGLOBLK) - 1);
+    }
+    const uint64_t first = g * C::TPC;
+    return (int)((start > first ? start : first) - first);
+}
+
+template <class C>
+NTT_HD TileLoc locate_in_group(const TileArgs& a, uint64_t g, int tin) {
+    TileLoc L = locate<C>(a, g * C::TPC + tin);
+    if (C::TWS && C::TPC > 1 && L.valid) L.tw_off = (tw_leader<C>(a, g, tin) - tin) * (int32_t)C::TILE_WORDS;
     return L;
 }
 
@@ -265,7 +335,7 @@ struct TileRegs {
 template <class C>
 NTT_HD void load_direct(TileRegs<C>& st, const TileArgs& a, const TileLoc& L, int t, uint64_t* sm) {
     if (!L.valid) return;
-    if (C::TWS) {
+    if (C::TWS && L.tw_off == 0) {
         // the tile's 2^A - 1 twiddles: slot i <-> stage S0 + d, d = floor(log2(i + 1))
         const TwPair* tw = a.tw + ((uint64_t)L.limb << C::LOGN);
         TwPair* tws = reinterpret_cast<TwPair*>(sm + C::E);
@@ -277,8 +347,43 @@ NTT_HD void load_direct(TileRegs<C>& st, const TileArgs& a, const TileLoc& L, in
         }
     }
     const uint32_t gt = L.gbase | place<C>(2u * (uint32_t)t);
-    const uint64_t* src = (C::FIRST ? a.in : a.out) + (L.row << C::LOGN) + gt;
     const uint64_t q = a.lc[L.limb].q;
+    if (C::FIRST && C::INV && a.src_mode == 1) {
+        // CKKS tensor product of the limb: rows (0|1) * n_moduli + limb of a and b
+        const LimbConst lc = a.lc[L.limb];
+        const uint64_t lrow = (uint64_t)L.limb << C::LOGN, step = (uint64_t)a.n_moduli << C::LOGN;
+        const uint64_t* a0 = a.in + lrow + gt;
+        const uint64_t* b0 = a.in_b + lrow + gt;
+        const uint32_t k = (uint32_t)L.rowq;    // 0, 1 or 2
+#pragma unroll
+        for (int i = 0; i < C::R / 2; ++i) {
+            const uint32_t off = place<C>(2u * (uint32_t)i * C::T);
+            NTT_GMEM_CHECK(gt + off + 1, 1u << C::LOGN);
+            uint64_t x0, x1, y0, y1, u0, u1, v0, v1;
+            if (k == 0) {
+                load_pair(a0 + off, x0, x1);
+                load_pair(b0 + off, y0, y1);
+            } else if (k == 2) {
+                load_pair(a0 + step + off, x0, x1);
+                load_pair(b0 + step + off, y0, y1);
+            } else {
+                load_pair(a0 + off, x0, x1);
+                load_pair(b0 + step + off, y0, y1);
+                load_pair(a0 + step + off, u0, u1);
+                load_pair(b0 + off, v0, v1);
+            }
+            uint64_t r0 = barrett_mulmod(x0, y0, lc.q, lc.mu, lc.bits);
+            uint64_t r1 = barrett_mulmod(x1, y1, lc.q, lc.mu, lc.bits);
+            if (k == 1) {
+                r0 = csub(r0 + barrett_mulmod(u0, v0, lc.q, lc.mu, lc.bits), lc.q);
+                r1 = csub(r1 + barrett_mulmod(u1, v1, lc.q, lc.mu, lc.bits), lc.q);
+            }
+            st.x[2 * i] = r0;
+            st.x[2 * i + 1] = r1;
+        }
+        return;
+    }
+    const uint64_t* src = (C::FIRST ? a.in : a.out) + (L.row << C::LOGN) + gt;
     bool bad = false;
 #pragma unroll
     for (int i = 0; i < C::R / 2; ++i) {
@@ -369,7 +474,7 @@ NTT_HD void pass_compute(TileRegs<C>& st, const TileArgs& a, const TileLoc& L, i
     constexpr int S_LO = Gm::S_LO, r = Gm::r, GS = Gm::GS;
     const LimbConst lc = a.lc[L.limb];
     const TwPair* tw = a.tw + ((uint64_t)L.limb << C::LOGN);
-    const TwPair* tws = reinterpret_cast<const TwPair*>(sm + C::E);
+    const TwPair* tws = reinterpret_cast<const TwPair*>(sm + C::E + L.tw_off);
     // row-local index bits above the pass: (g >> (LOGN - S_LO)) = hi part | pre_t | pre(gi)
     constexpr int SH = C::LOGN - S_LO;
     const uint32_t pre_t = place<C>(spread((uint32_t)t, Gm::PE, r)) >> SH;
@@ -508,9 +613,18 @@ NTT_HD CopyDesc tile_copy(const TileArgs& a, const TileLoc& L, int c) {
 template <class C>
 NTT_HD bool twiddles_reusable(const TileArgs& a, uint64_t g, uint64_t g_prev, bool have_prev, int tin) {
     if (!have_prev) return false;
-    const TileLoc P = locate<C>(a, g_prev * C::TPC + tin);
+    const TileLoc P = locate_in_group<C>(a, g_prev, tin);
     const TileLoc L = locate<C>(a, g * C::TPC + tin);
-    return P.valid && L.valid && P.limb == L.limb && P.hi == L.hi;
+    return P.valid && P.tw_off == 0 && L.valid && P.limb == L.limb && P.hi == L.hi;
+}
+
+// Whether tile slot tin of group g needs its twiddles copied: only leaders
+// hold twiddles, and a leader skips the copy when they are still in place.
+template <class C>
+NTT_HD bool twiddles_needed(const TileArgs& a, uint64_t g, uint64_t g_prev, bool have_prev, int tin) {
+    const TileLoc L = locate_in_group<C>(a, g, tin);
+    if (!L.valid || L.tw_off != 0) return false;
+    return !twiddles_reusable<C>(a, g, g_prev, have_prev, tin);
 }
 
 }  // namespace nttgb

@@ -58,7 +58,7 @@ def schedule_params(log2n, sched_id):
     buf = (ctypes.c_int32 * 11)()
     check(load().ntt_schedule_params(log2n, sched_id, buf, 11), "ntt_schedule_params")
     v = list(buf)
-    d = {"kernels": v[0], "pipelined": bool(v[1]), "log2n": v[2]}
+    d = {"kernels": v[0], "pipelined": v[1] == 1, "staged_twiddles": v[1] != 2, "log2n": v[2]}
     if v[0] == 1:
         d.update(logt=v[3], logrp=v[4], tpc=v[5])
     else:
@@ -159,6 +159,14 @@ class Plan:
         need = (row_begin + n_rows) * self.n
         check(load().ntt_inverse_rows(self._h, _ptr(x, need, "in"), _ptr(out, need, "out"),
                                       row_begin, n_rows, _stream_handle(stream)), "ntt_inverse_rows")
+        return out
+
+    def hmul_tensor(self, a, b, out, stream=None):
+        """(d0, d1, d2) = INTT of the CKKS tensor product of NTT-domain
+        ciphertexts a = [a0; a1], b = [b0; b1] ([2][n_moduli][N] each)."""
+        per = self.n_moduli * self.n
+        check(load().ntt_hmul_tensor(self._h, _ptr(a, 2 * per, "a"), _ptr(b, 2 * per, "b"),
+                                     _ptr(out, 3 * per, "out"), _stream_handle(stream)), "ntt_hmul_tensor")
         return out
 
     def pointwise(self, a, b, out=None, n_polys=0, stream=None):

@@ -24,6 +24,8 @@ def lib():
         L.nttemu_status.argtypes = [vp]
         L.nttemu_batch_transform.argtypes = [vp, i32, U64P, U64P]
         L.nttemu_batch_transform.restype = i32
+        L.nttemu_hmul_tensor.argtypes = [vp, u32, U64P, U64P, U64P]
+        L.nttemu_hmul_tensor.restype = i32
         _lib = L
     return _lib
 
@@ -61,6 +63,16 @@ class EmuPlan:
         rc = lib().nttemu_batch_transform(self.h, int(inverse), _p(x), _p(out))
         if rc:
             raise ValueError("nttemu_batch_transform failed: %d" % rc)
+        return out
+
+    def hmul_tensor(self, a, b, sched):
+        a = np.ascontiguousarray(a, dtype=np.uint64)
+        b = np.ascontiguousarray(b, dtype=np.uint64)
+        n_mod = a.shape[0] // 2
+        out = np.zeros((3 * n_mod, a.shape[1]), dtype=np.uint64)
+        rc = lib().nttemu_hmul_tensor(self.h, sched, _p(a), _p(b), _p(out))
+        if rc:
+            raise ValueError("nttemu_hmul_tensor failed: %d" % rc)
         return out
 
     def pointwise(self, a, b, n_rows=None):

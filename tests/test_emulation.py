@@ -141,3 +141,50 @@ def test_mixed_batch_configs_match_oracle(oracle, log2n):
     inv = plan.batch_transform(x, inverse=True)
     assert np.array_equal(inv[np.arange(6)[:, None], idx],
                           oracle.transform_rows(x, per_row, inverse=True, idx=idx))
+
+
+def test_fast_division_is_exact():
+    """The reciprocal division of tile/row indices (host build of the same code)."""
+    import random
+    rng = random.Random(1)
+    ds = [2, 3, 5, 7, 24, 48, 1000, 3780, 65535, (1 << 31) - 1, (1 << 32) - 1]
+    ns = [0, 1, 2, 3, (1 << 32) - 1, (1 << 31), 12345678] + [rng.getrandbits(32) for _ in range(2000)]
+    for d in ds:
+        M = ((1 << 64) + d - 1) // d
+        for n in ns:
+            mh, ml = M >> 32, M & 0xFFFFFFFF
+            t = n * mh + ((n * ml) >> 32)
+            assert (t >> 32) == n // d, (n, d)
+
+
+@pytest.mark.parametrize("log2n", [10, 13, 16])
+def test_hmul_tensor_matches_schoolbook(oracle, log2n):
+    """Fused tensor product + inverse: d0 = a0 b0, d1 = a0 b1 + a1 b0,
+    d2 = a1 b1 (negacyclic products, checked against the oracle's schoolbook
+    coefficients), for every direct-form schedule of N."""
+    n = 1 << log2n
+    mods = [W.POOL50[1], W.POOL50[4]]
+    L = len(mods)
+    plan = emu.EmuPlan(log2n, mods, 4)
+    per_row = [mods[r % L] for r in range(2 * L)]
+    ca = W.rows_uniform(51, 1, per_row, n)       # a0 (L rows), a1 (L rows), coefficient domain
+    cb = W.rows_uniform(51, 2, per_row, n)
+    A = plan.transform(np.concatenate([ca, cb]), 0)    # forward NTT of a and b
+    Aa, Ab = A[:2 * L], A[2 * L:]
+    kk = np.array([0, 1, n // 2, n - 1], dtype=np.uint32)
+    ref = {}
+    for l, q in enumerate(mods):
+        a0, a1, b0, b1 = ca[l], ca[L + l], cb[l], cb[L + l]
+        d1 = (oracle.schoolbook_at(a0, b1, q, kk).astype(object) + oracle.schoolbook_at(a1, b0, q, kk).astype(object)) % q
+        ref[l] = [oracle.schoolbook_at(a0, b0, q, kk), np.array(d1, dtype=np.uint64), oracle.schoolbook_at(a1, b1, q, kk)]
+    tried = 0
+    for s in range(emu.schedule_count(log2n)):
+        try:
+            out = plan.hmul_tensor(Aa, Ab, s)
+        except ValueError:
+            continue                                    # pipelined schedules: direct form only
+        tried += 1
+        for k in range(3):
+            for l in range(L):
+                assert np.array_equal(out[k * L + l][kk], ref[l][k]), (s, k, l)
+    assert tried >= 1

@@ -247,3 +247,28 @@ def test_maximum_size_row_index_beyond_2_32(oracle):
         assert not zero_rows.any()
     del d, e
     torch.cuda.empty_cache()
+
+
+def test_hmul_tensor_ckks_shape(oracle):
+    """Fused CKKS tensor product + inverse at N=2^16, 24 limbs: d0, d1, d2 at
+    sampled coefficients against the oracle's schoolbook products."""
+    w = W.ckks_hmul_n65536()
+    mods, x = w["moduli"], w["x"]
+    L, n = len(mods), 1 << 16
+    plan = ntt.Plan(16, mods, 4)
+    dx = to_dev(x.reshape(4 * L, n))
+    A = torch.empty_like(dx)
+    plan.forward(dx, A)
+    out = torch.empty((3 * L, n), dtype=torch.int64, device="cuda")
+    plan.hmul_tensor(A[:2 * L].contiguous(), A[2 * L:].contiguous(), out)
+    got = to_host(out)
+    kk = np.array([0, 1, 12345, n - 1], dtype=np.uint32)
+    for l in (0, 7, 23):
+        q = mods[l]
+        a0, a1, b0, b1 = x[0, l], x[1, l], x[2, l], x[3, l]
+        d0 = oracle.schoolbook_at(a0, b0, q, kk)
+        d1 = (oracle.schoolbook_at(a0, b1, q, kk).astype(object) + oracle.schoolbook_at(a1, b0, q, kk).astype(object)) % q
+        d2 = oracle.schoolbook_at(a1, b1, q, kk)
+        assert np.array_equal(got[l][kk], d0)
+        assert np.array_equal(got[L + l][kk], np.array(d1, dtype=np.uint64))
+        assert np.array_equal(got[2 * L + l][kk], d2)
