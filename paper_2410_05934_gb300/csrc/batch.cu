@@ -64,20 +64,20 @@ __device__ __forceinline__ void batch_phase(TileArgs a, uint64_t n_rows, uint64_
     }
 }
 
-template <int LOGN, int LOGT, int LOGRP, int TPC, bool INV, int MC>
+template <int LOGN, int LOGT, int LOGRP, int TPC, int MODE, bool INV, int MC>
 __device__ __forceinline__ void batch_single(const TileArgs& a, const BatchReq& rq, uint64_t n_rows,
                                              uint64_t* smem) {
     TileArgs b = a;
     b.tw = INV ? rq.tw_inv : rq.tw_fwd;
-    batch_phase<TileCfg<LOGN, 0, LOGN, 0, LOGT, LOGRP, TPC, INV, MC>>(b, n_rows, smem);
+    batch_phase<TileCfg<LOGN, 0, LOGN, 0, LOGT, LOGRP, TPC, INV, MC, MODE>>(b, n_rows, smem);
 }
 
 template <int LOGN, int SPLIT, int LOGP, int LOGTA, int LOGRPA, int TPCA, int LOGTB, int LOGRPB, int TPCB,
-          bool INV, int MC>
+          int MODE, bool INV, int MC>
 __device__ __forceinline__ void batch_split(const TileArgs& a, const BatchReq& rq, uint64_t n_rows,
                                             uint64_t* smem) {
-    using CA = TileCfg<LOGN, 0, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, INV, MC>;
-    using CB = TileCfg<LOGN, SPLIT, LOGN, 0, LOGTB, LOGRPB, TPCB, INV, MC>;
+    using CA = TileCfg<LOGN, 0, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, INV, MC, MODE>;
+    using CB = TileCfg<LOGN, SPLIT, LOGN, 0, LOGTB, LOGRPB, TPCB, INV, MC, MODE>;
     TileArgs b = a;
     b.tw = INV ? rq.tw_inv : rq.tw_fwd;
     // one row at a time so the row phase reads what this CTA's column phase wrote
@@ -96,15 +96,15 @@ __device__ __forceinline__ void batch_split(const TileArgs& a, const BatchReq& r
 // Only the paths with N <= 2^NMAX are compiled into a kernel variant: a
 // batch of short polynomials runs a variant whose register budget is not
 // set by the long-polynomial paths.
-#define NTT_BATCH_CASE_SINGLE(LOGN, LOGT, LOGRP, TPC)                                   \
+#define NTT_BATCH_CASE_SINGLE(LOGN, LOGT, LOGRP, TPC, MODE)                             \
     case LOGN:                                                                         \
-        if constexpr (LOGN <= NMAX) batch_single<LOGN, LOGT, LOGRP, TPC, INV, MC>(a, rq, n_rows, smem); \
+        if constexpr (LOGN <= NMAX) batch_single<LOGN, LOGT, LOGRP, TPC, MODE, INV, MC>(a, rq, n_rows, smem); \
         break;
-#define NTT_BATCH_CASE_SPLIT(LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB)                 \
+#define NTT_BATCH_CASE_SPLIT(LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, MODE)           \
     case LOGN:                                                                                         \
         if constexpr (LOGN <= NMAX)                                                                    \
-            batch_split<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, INV, MC>(a, rq,    \
-                                                                                             n_rows, smem); \
+            batch_split<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, MODE, INV, MC>(   \
+                a, rq, n_rows, smem);                                                                  \
         break;
 
 template <bool INV, int MC, int NMAX>

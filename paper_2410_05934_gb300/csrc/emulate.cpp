@@ -252,11 +252,11 @@ static const EmuEntry* emu_find(uint32_t log2n, uint32_t id) {
 }
 
 // the mixed-batch kernel's per-N configurations, direct form
-#define NTT_EMU_BATCH_SINGLE(LOGN, LOGT, LOGRP, TPC) \
-    {LOGN, &emu_s1<LOGN, LOGT, LOGRP, TPC, 0, false>, &emu_s1<LOGN, LOGT, LOGRP, TPC, 0, true>},
-#define NTT_EMU_BATCH_SPLIT(LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB)           \
-    {LOGN, &emu_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, 0, false>,         \
-     &emu_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, 0, true>},
+#define NTT_EMU_BATCH_SINGLE(LOGN, LOGT, LOGRP, TPC, MODE) \
+    {LOGN, &emu_s1<LOGN, LOGT, LOGRP, TPC, MODE, false>, &emu_s1<LOGN, LOGT, LOGRP, TPC, MODE, true>},
+#define NTT_EMU_BATCH_SPLIT(LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, MODE)        \
+    {LOGN, &emu_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, MODE, false>,      \
+     &emu_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, MODE, true>},
 static const EmuEntry g_emu_batch[] = {NTT_BATCH_CONFIGS(NTT_EMU_BATCH_SINGLE, NTT_EMU_BATCH_SPLIT)};
 
 struct EmuPlan {

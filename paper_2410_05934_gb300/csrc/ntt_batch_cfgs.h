@@ -3,17 +3,19 @@
 // them), at most 8 coefficients per thread (the kernel's register budget is
 // set by its largest path) and at most 48 KiB of shared memory, so three
 // CTAs fit on an SM.
-//   SINGLE(LOGN, LOGT, LOGRP, TPC)   one tile kernel's phases (whole rows)
-//   SPLIT(LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB)
+//   SINGLE(LOGN, LOGT, LOGRP, TPC, MODE)   one tile kernel's phases (whole rows)
+//   SPLIT(LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, MODE)
 //                                    column phase then row phase per row
+// MODE 0 stages twiddles in shared memory, 2 reads them through the
+// read-only cache (short single-modulus rows share one small table).
 // The host emulation checks the same list against the oracle.
 #pragma once
 
 #define NTT_BATCH_CONFIGS(SINGLE, SPLIT)                                   \
-    SINGLE(10, 7, 3, 2)                                                    \
-    SINGLE(11, 8, 3, 1)                                                    \
-    SPLIT(12, 6, 4, 8, 2, 1, 3, 3, 32)                                     \
-    SPLIT(13, 6, 4, 8, 2, 1, 4, 3, 16)                                     \
-    SPLIT(14, 7, 4, 8, 3, 1, 4, 3, 16)                                     \
-    SPLIT(15, 7, 4, 8, 3, 1, 5, 3, 8)                                      \
-    SPLIT(16, 7, 4, 8, 3, 1, 6, 3, 4)
+    SINGLE(10, 7, 3, 2, 2)                                                 \
+    SINGLE(11, 8, 3, 1, 2)                                                 \
+    SPLIT(12, 6, 4, 8, 2, 1, 3, 3, 32, 0)                                  \
+    SPLIT(13, 6, 4, 8, 2, 1, 4, 3, 16, 0)                                  \
+    SPLIT(14, 7, 4, 8, 3, 1, 4, 3, 16, 0)                                  \
+    SPLIT(15, 7, 4, 8, 3, 1, 5, 3, 8, 0)                                   \
+    SPLIT(16, 7, 4, 8, 3, 1, 6, 3, 4, 0)

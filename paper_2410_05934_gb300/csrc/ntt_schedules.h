@@ -44,19 +44,19 @@
 
 #define NTT_SCHEDULES_LARGE(S1, S2)                                                   \
     S1(13, 9, 4, 1, 0) S1(13, 8, 5, 1, 0) S1(13, 10, 3, 1, 0)                         \
-    S2(13, 6, 4, 6, 4, 1, 5, 3, 4, 0)                                                 \
+    S2(13, 6, 4, 6, 4, 1, 5, 3, 4, 0) S2(13, 6, 4, 6, 4, 1, 5, 3, 4, 2)               \
     S1(14, 10, 4, 1, 0) S1(14, 9, 5, 1, 0)                                            \
     S2(14, 7, 4, 7, 4, 1, 4, 4, 8, 1) S2(14, 7, 4, 7, 4, 1, 4, 3, 8, 0)               \
-    S2(14, 7, 4, 7, 4, 1, 5, 2, 4, 0)                                                 \
+    S2(14, 7, 4, 7, 4, 1, 5, 2, 4, 0) S2(14, 7, 4, 7, 4, 1, 4, 3, 8, 2)               \
     S2(15, 7, 4, 7, 4, 1, 4, 4, 8, 1) S2(15, 7, 4, 6, 5, 1, 3, 5, 16, 0)              \
     S2(15, 5, 4, 4, 5, 4, 5, 5, 4, 0) S2(15, 7, 4, 8, 3, 1, 5, 3, 8, 0)               \
-    S2(15, 7, 4, 7, 4, 1, 5, 3, 4, 0)
+    S2(15, 7, 4, 7, 4, 1, 5, 3, 4, 0) S2(15, 7, 4, 7, 4, 1, 5, 3, 4, 2)
 
 #define NTT_SCHEDULES_HUGE(S1, S2)                                                    \
-    S2(16, 8, 4, 8, 4, 1, 5, 3, 4, 0) S2(16, 8, 4, 8, 4, 1, 4, 4, 8, 0)               \
+    S2(16, 8, 4, 8, 4, 1, 5, 3, 4, 0) S2(16, 7, 4, 7, 4, 1, 6, 3, 2, 2)               \
     S2(16, 8, 4, 8, 4, 1, 5, 3, 8, 0) S2(16, 8, 4, 8, 4, 1, 5, 3, 2, 0)               \
     S2(16, 8, 4, 8, 4, 1, 6, 2, 2, 0) S2(16, 8, 4, 9, 3, 1, 5, 3, 4, 0)               \
-    S2(16, 7, 4, 7, 4, 1, 6, 3, 2, 0) S2(16, 6, 4, 5, 5, 4, 5, 5, 4, 0)
+    S2(16, 7, 4, 7, 4, 1, 6, 3, 2, 0) S2(16, 8, 4, 8, 4, 1, 5, 3, 4, 2)
 
 #define NTT_SCHEDULES_ALL(S1, S2)                                           \
     NTT_SCHEDULES_SMALL(S1, S2) NTT_SCHEDULES_MID(S1, S2) NTT_SCHEDULES_LARGE(S1, S2) \
