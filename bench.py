@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--schedule", type=int, default=None)
+    ap.add_argument("--hybrid-min-log2-coef", type=int, default=22,
+                    help="mixed batches: requests of at least 2^k coefficients run their own learned schedule")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "mixed_batch", "tfhe_blind_rotation", "plain_n1024", "cost_model",
                              "serving", "hmul_fused", "mixed_small"],
@@ -488,26 +490,51 @@ def run_other(args):
                              **{"in": x, "out": torch.empty_like(x)}))
             coef += x.numel()
             bfly += x.shape[0] * (x.shape[1] // 2) * log2n
-        batch = ntt.Batch(reqs, W.POOL50, flags=ntt.NTT_BATCH_GRAPH)
+        from paper_2410_05934_gb300.costmodel import choose_schedule, schedule_requests
+        # the batched + learned-schedule form: requests that fill the GPU by
+        # themselves run their chosen schedule on a second graph branch, the
+        # rest are work items of the persistent kernel
+        sreqs = schedule_requests(reqs, W.POOL50, args.hybrid_min_log2_coef)
+        batch = ntt.Batch(sreqs, W.POOL50, flags=ntt.NTT_BATCH_GRAPH)
+        persistent = ntt.Batch(reqs, W.POOL50, flags=ntt.NTT_BATCH_GRAPH)
+        learned = [choose_schedule(r["log2n"], r["n_moduli"], r["n_polys"], 50)[0] for r in reqs]
         flush_t = None                      # ~9 GB of inputs: far larger than L2
         q_probe = W.POOL50[0]
         kind = 2
         for _ in range(max(3, args.warmup)):
             batch.execute()
-            batch.execute_plain()
+            persistent.execute()
+            persistent.execute_plain()
+            persistent.execute_plain(learned)
         torch.cuda.synchronize()
         clocks.start()
-        ms, launches = _events_loop(torch, stream, args.steps, lambda: (batch.execute(), 1)[1], flush_t)
+        ms, launches = _events_loop(torch, stream, args.steps,
+                                    lambda: (batch.execute(), batch.info()["last_launches"])[1], flush_t)
         clk = clocks.stop()
+        ms_pers, _ = _events_loop(torch, stream, args.steps, lambda: (persistent.execute(), 1)[1], flush_t)
         ms_plain, launches_plain = _events_loop(
-            torch, stream, args.steps, lambda: (batch.execute_plain(), batch.info()["last_launches"])[1], flush_t)
+            torch, stream, args.steps, lambda: (persistent.execute_plain(), persistent.info()["last_launches"])[1],
+            flush_t)
+        ms_learned, _ = _events_loop(torch, stream, args.steps,
+                                     lambda: (persistent.execute_plain(learned), 1)[1], flush_t)
+        n_sched = sum(1 for r in sreqs if r["schedule"])
+        extra["persistent_only"] = {
+            "value": coef * args.steps / (sum(ms_pers) * 1e-3), "ms_per_step": sum(ms_pers) / args.steps,
+            "how": "every request as work items of the one persistent kernel (one launch under a CUDA graph)"}
         extra["plain_per_request"] = {
             "value": coef * args.steps / (sum(ms_plain) * 1e-3), "ms_per_step": sum(ms_plain) / args.steps,
             "launches_per_step": launches_plain // args.steps,
             "how": "one launch sequence per request, default schedule of its N, same tables"}
+        extra["plain_learned_schedule"] = {
+            "value": coef * args.steps / (sum(ms_learned) * 1e-3), "ms_per_step": sum(ms_learned) / args.steps,
+            "how": "one launch sequence per request, schedule from the autotuner DB / cost model"}
         extra["speedup_vs_plain"] = sum(ms_plain) / sum(ms)
+        extra["speedup_vs_plain_learned"] = sum(ms_learned) / sum(ms)
         config = {"workload": args.workload, "requests": len(spec), "coefficients": coef,
-                  "distribution": dist_note, "batched": "one persistent kernel under a CUDA graph",
+                  "distribution": dist_note,
+                  "batched": ("one CUDA graph: persistent kernel over %d requests || %d requests of >= 2^%d "
+                              "coefficients on their learned schedules" % (len(spec) - n_sched, n_sched,
+                                                                         args.hybrid_min_log2_coef)),
                   "l2": ("inputs (%.1f GB) > L2" % (coef * 8 / 1e9)) if coef * 8 > (256 << 20)
                   else "inputs (%.0f MB) fit L2: timed warm" % (coef * 8 / 1e6)}
         unit_coef = coef

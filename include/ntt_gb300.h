@@ -184,15 +184,26 @@ int ntt_bench_butterflies(uint64_t q, uint32_t kind, uint32_t blocks, uint32_t t
  * uses moduli_pool[moduli_offset .. moduli_offset + n_moduli).
  *   log2n          in [NTT_BATCH_MIN_LOG2N, NTT_MAX_LOG2N]
  *   inverse        0 forward, 1 inverse
+ *   schedule       0: the request's rows are work items of the persistent
+ *                  kernel.  s + 1 (s < ntt_schedule_count(log2n)): the
+ *                  request runs instead as its own launch sequence with
+ *                  schedule s of its N, on a second branch that forks from
+ *                  and joins the caller's stream around the persistent
+ *                  kernel (both branches live in the same CUDA graph).  Meant
+ *                  for requests large enough to fill the GPU by themselves,
+ *                  whose tuned schedule beats the batch kernel's fixed tiles.
  *   in / out       caller-owned device buffers (may alias), 16-byte aligned
  * ntt_batch_plan validates the requests, builds the twiddle tables of every
  * (N, pool modulus) pair the batch uses, and uploads the work-item list; the
- * batch plan owns those tables, the item list and the queue counter.  With
- * NTT_BATCH_GRAPH, execution captures [reset counter, kernel] into a CUDA
- * graph on first use and replays it afterwards.
+ * batch plan owns those tables, the item list, the queue counter and (with
+ * scheduled requests) a second stream and two events.  With
+ * NTT_BATCH_GRAPH, execution captures [reset counter, kernel] (and the
+ * scheduled requests' launches) into a CUDA graph on first use and replays
+ * it afterwards.
  * ntt_batch_update replaces the requests' in/out pointers (same shapes),
  * enqueued on `cuda_stream` so the next execution (or graph replay) sees
- * them.  ntt_batch_execute_plain is the comparison arm: one launch sequence
+ * them; with scheduled requests the graph is captured again on the next
+ * execution, since their pointers are kernel arguments.  ntt_batch_execute_plain is the comparison arm: one launch sequence
  * per request on the same tables (schedules[i] per request, or the default
  * schedule of its N when schedules is NULL).
  * Errors: ARG, NOT_PRIME, NOT_NTT_FRIENDLY, MODULUS_TOO_LARGE, ALIGN,
@@ -207,7 +218,7 @@ typedef struct {
     uint32_t n_polys;
     uint32_t moduli_offset;
     uint32_t inverse;
-    uint32_t reserved;
+    uint32_t schedule;
     const uint64_t* in;
     uint64_t* out;
 } ntt_request_t;
@@ -222,7 +233,8 @@ int ntt_batch_execute_plain(ntt_batch_t batch, const uint32_t* schedules, void* 
 int ntt_batch_destroy(ntt_batch_t batch);
 /* Device status word of the batch (as ntt_status): synchronises, returns, clears. */
 int ntt_batch_status(ntt_batch_t batch, void* cuda_stream);
-/* Work items, kernel launches of the last execution, and coefficients per execution. */
+/* Work items of the persistent kernel, kernels run by the last execution
+ * (graph replays included), and coefficients per execution. */
 int ntt_batch_info(ntt_batch_t batch, uint64_t* items, uint32_t* last_launches, uint64_t* coefficients);
 
 /*

@@ -17,7 +17,7 @@ U32P = ctypes.POINTER(ctypes.c_uint32)
 class NttRequest(ctypes.Structure):
     """ntt_request_t of the C ABI."""
     _fields_ = [("log2n", ctypes.c_uint32), ("n_moduli", ctypes.c_uint32), ("n_polys", ctypes.c_uint32),
-                ("moduli_offset", ctypes.c_uint32), ("inverse", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("moduli_offset", ctypes.c_uint32), ("inverse", ctypes.c_uint32), ("schedule", ctypes.c_uint32),
                 ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p)]
 
 

@@ -257,6 +257,28 @@ def choose_schedule(log2n, limbs, batch, bits=50, inverse=False, db=DEFAULT_DB, 
     return default_choice(log2n, limbs, batch), "default"
 
 
+def schedule_requests(requests, moduli_pool, min_log2_coef=22):
+    """Mixed-batch requests with their `schedule` field set: requests of at
+    least 2^min_log2_coef coefficients fill the GPU by themselves and run as
+    their own launches with the schedule chosen here (autotuner hit, else the
+    cost model, else the default) + 1; the rest stay work items (0) of the
+    persistent kernel."""
+    out = []
+    for r in requests:
+        r = dict(r)
+        rows = int(r["n_polys"]) * int(r["n_moduli"])
+        if rows << int(r["log2n"]) >= 1 << min_log2_coef:
+            off = int(r.get("moduli_offset", 0))
+            bits = max(int(q).bit_length() for q in moduli_pool[off:off + int(r["n_moduli"])])
+            sid, _ = choose_schedule(int(r["log2n"]), int(r["n_moduli"]), int(r["n_polys"]), bits,
+                                     inverse=bool(r.get("inverse", 0)))
+            r["schedule"] = sid + 1
+        else:
+            r["schedule"] = 0
+        out.append(r)
+    return out
+
+
 def evaluate(model, keys, times):
     """Regret of the model, the paper's SM-aware rule and the built-in default."""
     t0 = time.perf_counter()

@@ -42,7 +42,7 @@ struct BatchItem {
 };
 
 #define NTT_BATCH_THREADS 256
-static constexpr size_t kBatchSmemBound = 48 * 1024;
+static constexpr size_t kBatchSmemBound = 16 * 1024;
 
 // One phase (stage range) of a config over rows [a.row_begin, +n_rows).
 template <class C>
@@ -116,18 +116,21 @@ __device__ __forceinline__ void batch_dispatch(const TileArgs& a, const BatchReq
     }
 }
 
-// Largest shared-memory footprint among the batch configurations (48 KiB).
-static constexpr size_t kBatchSmem = 48 * 1024;
+// Largest shared-memory footprint among the batch configurations (16 KiB).
+static constexpr size_t kBatchSmem = kBatchSmemBound;
 #define NTT_BATCH_MIN_CTAS 3
 // kernel variants: all N (NMAX 16), or short polynomials only (NMAX 11)
 #define NTT_BATCH_SHORT_NMAX 11
-template <int NMAX>
+// CTAs per SM the register budget is set for: the exact-quotient class
+// (q >= 2^57) needs more registers per butterfly than the small-modulus class
+template <int MC, int NMAX>
 struct BatchOcc {
-    static constexpr int ctas = NMAX <= NTT_BATCH_SHORT_NMAX ? 4 : NTT_BATCH_MIN_CTAS;
+    static constexpr int ctas = MC ? (NMAX <= NTT_BATCH_SHORT_NMAX ? 4 : NTT_BATCH_MIN_CTAS)
+                                   : (NMAX <= NTT_BATCH_SHORT_NMAX ? 3 : 2);
 };
 
 template <int MC, int NMAX>
-__global__ void __launch_bounds__(NTT_BATCH_THREADS, BatchOcc<NMAX>::ctas)
+__global__ void __launch_bounds__(NTT_BATCH_THREADS, BatchOcc<MC, NMAX>::ctas)
     k_ntt_batch(const BatchReq* __restrict__ reqs, const BatchItem* __restrict__ items, uint32_t n_items,
                 uint32_t* counter, int* status, uint32_t check) {
     extern __shared__ __align__(16) uint64_t smem[];
@@ -295,10 +298,14 @@ struct ntt_batch_s {
     int* d_status = nullptr;
     uint32_t flags = 0, mc = 0, check = 0;
     uint32_t short_only = 0;    // every request has N <= 2^NTT_BATCH_SHORT_NMAX
+    std::vector<uint32_t> scheduled;   // requests that run as their own launches
+    cudaStream_t side = nullptr;       // their branch, forked from the caller's stream
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int device = -1;
     int grid = 0;
     uint64_t coefficients = 0;
     uint32_t last_launches = 0;
+    uint32_t graph_kernels = 0;        // kernels one replay of the graph runs
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     cudaStream_t graph_stream = nullptr;
@@ -306,9 +313,18 @@ struct ntt_batch_s {
 
 namespace nttgb {
 
-static void batch_free(ntt_batch_s* b) {
+static void batch_drop_graph(ntt_batch_s* b) {
     if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    b->graph_exec = nullptr;
+    b->graph = nullptr;
+}
+
+static void batch_free(ntt_batch_s* b) {
+    batch_drop_graph(b);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
+    if (b->side) cudaStreamDestroy(b->side);
     for (auto& t : b->tables) {
         if (t.d_fwd) cudaFree(t.d_fwd);
         if (t.d_inv) cudaFree(t.d_inv);
@@ -330,6 +346,7 @@ static int validate_reqs(const ntt_request_t* reqs, uint32_t n, uint32_t pool_le
         if (r.log2n > NTT_MAX_LOG2N || r.n_moduli == 0 || r.n_polys == 0 || r.inverse > 1)
             return NTT_ERR_ARG;
         if (r.log2n < NTT_BATCH_MIN_LOG2N) return NTT_ERR_UNSUPPORTED;
+        if (r.schedule > (uint32_t)schedule_count(r.log2n)) return NTT_ERR_ARG;
         if ((uint64_t)r.moduli_offset + r.n_moduli > pool_len) return NTT_ERR_ARG;
         if (!r.in || !r.out) return NTT_ERR_ARG;
         if (!aligned16p(r.in) || !aligned16p(r.out)) return NTT_ERR_ALIGN;
@@ -376,14 +393,18 @@ int ntt_batch_plan(ntt_batch_t* out, const ntt_request_t* reqs, uint32_t n_reqs,
         for (uint32_t i = 0; i < n_reqs; ++i) {
             const auto& r = b->reqs[i];
             const uint64_t rows = (uint64_t)r.n_polys * r.n_moduli;
+            b->coefficients += rows << r.log2n;
+            if (r.schedule) {
+                b->scheduled.push_back(i);
+                continue;
+            }
             const uint32_t per = rows_per_item(r.log2n);
             for (uint64_t r0 = 0; r0 < rows; r0 += per)
                 b->hitems.push_back({i, (uint32_t)std::min<uint64_t>(per, rows - r0), r0});
-            b->coefficients += rows << r.log2n;
         }
         b->short_only = 1;
         for (const auto& r : b->reqs)
-            if (r.log2n > NTT_BATCH_SHORT_NMAX) b->short_only = 0;
+            if (!r.schedule && r.log2n > NTT_BATCH_SHORT_NMAX) b->short_only = 0;
         std::stable_sort(b->hitems.begin(), b->hitems.end(), [&](const BatchItem& x, const BatchItem& y) {
             return b->reqs[x.req].log2n > b->reqs[y.req].log2n;
         });
@@ -425,15 +446,21 @@ int ntt_batch_plan(ntt_batch_t* out, const ntt_request_t* reqs, uint32_t n_reqs,
             d.inverse = r.inverse;
             d.pad = 0;
         }
+        const size_t n_items = std::max<size_t>(1, b->hitems.size());
         ok = cudaMalloc(&b->d_reqs, sizeof(BatchReq) * n_reqs) == cudaSuccess &&
-             cudaMalloc(&b->d_items, sizeof(BatchItem) * b->hitems.size()) == cudaSuccess &&
+             cudaMalloc(&b->d_items, sizeof(BatchItem) * n_items) == cudaSuccess &&
              cudaMalloc(&b->d_counter, sizeof(uint32_t)) == cudaSuccess &&
              cudaMalloc(&b->d_status, sizeof(int)) == cudaSuccess &&
              cudaMemcpy(b->d_reqs, b->hreqs.data(), sizeof(BatchReq) * n_reqs, cudaMemcpyHostToDevice) == cudaSuccess &&
-             cudaMemcpy(b->d_items, b->hitems.data(), sizeof(BatchItem) * b->hitems.size(),
-                        cudaMemcpyHostToDevice) == cudaSuccess &&
+             (b->hitems.empty() ||
+              cudaMemcpy(b->d_items, b->hitems.data(), sizeof(BatchItem) * b->hitems.size(),
+                         cudaMemcpyHostToDevice) == cudaSuccess) &&
              cudaMemset(b->d_status, 0, sizeof(int)) == cudaSuccess;
     }
+    if (ok && !b->scheduled.empty())
+        ok = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) == cudaSuccess;
     if (ok) {
         const void* fn = batch_kernel(b->mc, b->short_only);
         int per_sm = 0, sms = 0;
@@ -468,24 +495,70 @@ int ntt_batch_update(ntt_batch_t b, const ntt_request_t* reqs, uint32_t n_reqs, 
         b->hreqs[i].in = reqs[i].in;
         b->hreqs[i].out = reqs[i].out;
     }
+    // the scheduled requests' pointers are kernel arguments of the captured graph
+    if (!b->scheduled.empty()) batch_drop_graph(b);
     // pageable source: the runtime stages it before returning, so hreqs may change afterwards
     return cudaMemcpyAsync(b->d_reqs, b->hreqs.data(), sizeof(BatchReq) * n_reqs, cudaMemcpyHostToDevice,
                            (cudaStream_t)cuda_stream) == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
 }
 
-static int batch_enqueue(ntt_batch_t b, cudaStream_t st) {
-    if (cudaMemsetAsync(b->d_counter, 0, sizeof(uint32_t), st) != cudaSuccess) return NTT_ERR_CUDA;
+// One launch sequence of request i with schedule `sid` of its N on the batch's tables.
+static int batch_launch_request(ntt_batch_t b, size_t i, uint32_t sid, cudaStream_t st, uint32_t* launches) {
+    int count = 0;
+    const SchedEntry* table = sched_table(&count);
+    const ntt_request_t& r = b->reqs[i];
+    int idx = -1;
+    for (int k = 0, seen = 0; k < count; ++k) {
+        if (table[k].log2n != r.log2n) continue;
+        if ((uint32_t)seen++ == sid) {
+            idx = k;
+            break;
+        }
+    }
+    if (idx < 0) return NTT_ERR_ARG;
+    PlanDev d;
+    d.fwd = b->hreqs[i].tw_fwd;
+    d.inv = b->hreqs[i].tw_inv;
+    d.lc = b->hreqs[i].lc;
+    d.status = b->d_status;
+    d.n_moduli = r.n_moduli;
+    d.check = b->check;
+    d.mc = b->tables[r.log2n].host.mc;
+    d.src_mode = 0;
+    d.in_b = nullptr;
+    const LaunchFn fn = r.inverse ? table[idx].inv : table[idx].fwd;
+    return fn(d, r.in, r.out, 0, (uint64_t)r.n_polys * r.n_moduli, st, launches);
+}
+
+// [fork -> scheduled requests on the side stream] || [reset counter, persistent kernel] -> join
+static int batch_enqueue(ntt_batch_t b, cudaStream_t st, uint32_t* launches) {
+    *launches = 0;
+    if (!b->scheduled.empty()) {
+        if (cudaEventRecord(b->ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(b->side, b->ev_fork, 0) != cudaSuccess)
+            return NTT_ERR_CUDA;
+        for (uint32_t i : b->scheduled) {
+            int rc = batch_launch_request(b, i, b->reqs[i].schedule - 1, b->side, launches);
+            if (rc) return rc;
+        }
+        if (cudaEventRecord(b->ev_join, b->side) != cudaSuccess) return NTT_ERR_CUDA;
+    }
     const uint32_t n = (uint32_t)b->hitems.size();
+    if (n) {
+        if (cudaMemsetAsync(b->d_counter, 0, sizeof(uint32_t), st) != cudaSuccess) return NTT_ERR_CUDA;
 #define NTT_BATCH_LAUNCH(MC, NMAX) \
     k_ntt_batch<MC, NMAX><<<b->grid, NTT_BATCH_THREADS, kBatchSmem, st>>>(b->d_reqs, b->d_items, n, b->d_counter, \
                                                                        b->d_status, b->check)
-    if (b->mc) {
-        if (b->short_only) NTT_BATCH_LAUNCH(1, NTT_BATCH_SHORT_NMAX); else NTT_BATCH_LAUNCH(1, 16);
-    } else {
-        if (b->short_only) NTT_BATCH_LAUNCH(0, NTT_BATCH_SHORT_NMAX); else NTT_BATCH_LAUNCH(0, 16);
-    }
+        if (b->mc) {
+            if (b->short_only) NTT_BATCH_LAUNCH(1, NTT_BATCH_SHORT_NMAX); else NTT_BATCH_LAUNCH(1, 16);
+        } else {
+            if (b->short_only) NTT_BATCH_LAUNCH(0, NTT_BATCH_SHORT_NMAX); else NTT_BATCH_LAUNCH(0, 16);
+        }
 #undef NTT_BATCH_LAUNCH
-    return cudaPeekAtLastError() == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
+        if (cudaPeekAtLastError() != cudaSuccess) return NTT_ERR_CUDA;
+        ++*launches;
+    }
+    if (!b->scheduled.empty() && cudaStreamWaitEvent(st, b->ev_join, 0) != cudaSuccess) return NTT_ERR_CUDA;
+    return NTT_OK;
 }
 
 int ntt_batch_execute(ntt_batch_t b, void* cuda_stream) {
@@ -495,8 +568,9 @@ int ntt_batch_execute(ntt_batch_t b, void* cuda_stream) {
     cudaStream_t st = (cudaStream_t)cuda_stream;
     b->last_launches = 0;
     if (!(b->flags & NTT_BATCH_GRAPH)) {
-        int rc = batch_enqueue(b, st);
-        if (rc == NTT_OK) b->last_launches = 1;
+        uint32_t launches = 0;
+        int rc = batch_enqueue(b, st, &launches);
+        if (rc == NTT_OK) b->last_launches = launches;
         return rc;
     }
     if (!b->graph_exec) {
@@ -505,7 +579,7 @@ int ntt_batch_execute(ntt_batch_t b, void* cuda_stream) {
         if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return NTT_ERR_CUDA;
         int rc = NTT_OK;
         if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = NTT_ERR_CUDA;
-        if (rc == NTT_OK) rc = batch_enqueue(b, cap);
+        if (rc == NTT_OK) rc = batch_enqueue(b, cap, &b->graph_kernels);
         cudaGraph_t g = nullptr;
         if (cudaStreamEndCapture(cap, &g) != cudaSuccess) rc = NTT_ERR_CUDA;
         cudaStreamDestroy(cap);
@@ -519,7 +593,7 @@ int ntt_batch_execute(ntt_batch_t b, void* cuda_stream) {
         b->graph = g;
     }
     if (cudaGraphLaunch(b->graph_exec, st) != cudaSuccess) return NTT_ERR_CUDA;
-    b->last_launches = 1;
+    b->last_launches = b->graph_kernels;
     return NTT_OK;
 }
 
@@ -527,34 +601,11 @@ int ntt_batch_execute_plain(ntt_batch_t b, const uint32_t* schedules, void* cuda
     if (!b) return NTT_ERR_ARG;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != b->device) return NTT_ERR_ARG;
-    int count = 0;
-    const SchedEntry* table = sched_table(&count);
     b->last_launches = 0;
     for (size_t i = 0; i < b->reqs.size(); ++i) {
         const ntt_request_t& r = b->reqs[i];
-        const uint64_t rows = (uint64_t)r.n_polys * r.n_moduli;
-        uint32_t sid = schedules ? schedules[i] : default_schedule(r.log2n, rows);
-        int idx = -1;
-        for (int k = 0, seen = 0; k < count; ++k) {
-            if (table[k].log2n != r.log2n) continue;
-            if ((uint32_t)seen++ == sid) {
-                idx = k;
-                break;
-            }
-        }
-        if (idx < 0) return NTT_ERR_ARG;
-        PlanDev d;
-        d.fwd = b->hreqs[i].tw_fwd;
-        d.inv = b->hreqs[i].tw_inv;
-        d.lc = b->hreqs[i].lc;
-        d.status = b->d_status;
-        d.n_moduli = r.n_moduli;
-        d.check = b->check;
-        d.mc = b->tables[r.log2n].host.mc;
-        d.src_mode = 0;
-        d.in_b = nullptr;
-        const LaunchFn fn = r.inverse ? table[idx].inv : table[idx].fwd;
-        int rc = fn(d, r.in, r.out, 0, rows, cuda_stream, &b->last_launches);
+        const uint32_t sid = schedules ? schedules[i] : default_schedule(r.log2n, (uint64_t)r.n_polys * r.n_moduli);
+        int rc = batch_launch_request(b, i, sid, (cudaStream_t)cuda_stream, &b->last_launches);
         if (rc) return rc;
     }
     return NTT_OK;

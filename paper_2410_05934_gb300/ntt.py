@@ -184,8 +184,11 @@ NTT_BATCH_GRAPH = 1
 class Batch:
     """ntt_batch_plan: an uneven mixed batch run as one persistent launch.
 
-    requests: list of dicts (or tuples) with log2n, n_moduli, n_polys,
-    moduli_offset, inverse, in, out -- in/out CUDA tensors or device pointers.
+    requests: list of dicts with log2n, n_moduli, n_polys, moduli_offset,
+    inverse, schedule, in, out -- in/out CUDA tensors or device pointers;
+    schedule 0 (default) makes the request work items of the persistent
+    kernel, s + 1 runs it as its own launches with schedule s of its N
+    (``costmodel.schedule_requests`` fills it in).
     """
 
     def __init__(self, requests, moduli_pool, flags=NTT_BATCH_GRAPH):
@@ -205,6 +208,7 @@ class Batch:
             d = arr[i]
             d.log2n, d.n_moduli, d.n_polys = int(r["log2n"]), int(r["n_moduli"]), int(r["n_polys"])
             d.moduli_offset, d.inverse = int(r.get("moduli_offset", 0)), int(r.get("inverse", 0))
+            d.schedule = int(r.get("schedule", 0))
             d.in_ = _ptr(r["in"], what="in").value
             d.out = _ptr(r.get("out", r["in"]), what="out").value
         return arr

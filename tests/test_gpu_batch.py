@@ -109,3 +109,48 @@ def test_batch_range_check():
                         "out": torch.empty_like(d)})], W.POOL50, flags=ntt.NTT_FLAG_CHECK)
     b.execute()
     assert b.status() == -8
+
+
+def test_scheduled_requests_in_the_same_graph(oracle):
+    """Requests with a schedule run as their own launches on a second graph
+    branch; together with the persistent kernel's items they give the oracle's
+    bits, also after a pointer update (the graph is captured again)."""
+    reqs, hosts = _make(3)
+    for i, r in enumerate(reqs):
+        if i % 3 != 1:
+            continue
+        r["schedule"] = 1 + (i // 3) % ntt.schedule_count(r["log2n"])
+    n_sched = sum(1 for r in reqs if r.get("schedule"))
+    assert n_sched >= 3
+    b = ntt.Batch(reqs, W.POOL50, flags=ntt.NTT_BATCH_GRAPH)
+    b.execute()
+    torch.cuda.synchronize()
+    info = b.info()
+    assert info["last_launches"] >= 1 + n_sched
+    assert info["items"] > 0
+    _check(oracle, reqs, hosts)
+    outs = [to_host(r["out"]).copy() for r in reqs]
+    reqs2 = [dict(r, **{"in": to_dev(h), "out": torch.empty_like(r["in"])}) for r, h in zip(reqs, hosts)]
+    b.update(reqs2)
+    b.execute()
+    torch.cuda.synchronize()
+    for o, r in zip(outs, reqs2):
+        assert np.array_equal(o, to_host(r["out"]))
+    # every request scheduled: no persistent kernel at all
+    reqs3 = [dict(r, schedule=1, **{"in": to_dev(h), "out": torch.empty_like(r["in"])})
+             for r, h in zip(reqs, hosts)]
+    b3 = ntt.Batch(reqs3, W.POOL50, flags=0)
+    assert b3.info()["items"] == 0
+    b3.execute()
+    torch.cuda.synchronize()
+    for o, r in zip(outs, reqs3):
+        assert np.array_equal(o, to_host(r["out"]))
+    assert b.status() == 0 and b3.status() == 0
+
+
+def test_scheduled_request_argument_error():
+    d = torch.zeros((4, 1024), dtype=torch.int64, device="cuda")
+    r = dict(log2n=10, n_moduli=2, n_polys=2, moduli_offset=0, inverse=0, **{"in": d, "out": d})
+    with pytest.raises(ntt.NttError) as e:
+        ntt.Batch([dict(r, schedule=ntt.schedule_count(10) + 1)], W.POOL50)
+    assert e.value.code == -1

@@ -272,3 +272,27 @@ def test_hmul_tensor_ckks_shape(oracle):
         assert np.array_equal(got[l][kk], d0)
         assert np.array_equal(got[L + l][kk], np.array(d1, dtype=np.uint64))
         assert np.array_equal(got[2 * L + l][kk], d2)
+
+
+def test_hand_derived_known_answers():
+    """The kernels reproduce the hand-worked examples of tests/golden (q = 17)."""
+    from golden.load import negacyclic_q17
+    ntt_cases, mul_cases = negacyclic_q17()
+    for q, log2n, psi, a, A in ntt_cases:
+        p = ntt.Plan(log2n, [q], 1)
+        assert p.root(0) == psi
+        x = to_dev(np.array(a, dtype=np.uint64))
+        y = torch.empty_like(x)
+        p.forward(x, y)
+        assert to_host(y).tolist() == A
+        p.inverse(y, x)
+        assert to_host(x).tolist() == a
+        assert p.status() == 0
+    for q, log2n, a, b, c in mul_cases:
+        p = ntt.Plan(log2n, [q], 1)
+        xa, xb = to_dev(np.array(a, dtype=np.uint64)), to_dev(np.array(b, dtype=np.uint64))
+        p.forward(xa)
+        p.forward(xb)
+        p.pointwise(xa, xb, xa)
+        p.inverse(xa)
+        assert to_host(xa).tolist() == c

@@ -215,3 +215,19 @@ def test_sampled_schoolbook_matches_numpy(oracle, q, log2n):
     idx = [0, 1, n // 2, n - 1, rng.randrange(n)]
     got = oracle.schoolbook_at(a, b, q, idx)
     assert [int(v) for v in got] == [ref[k] for k in idx]
+
+
+def test_hand_derived_known_answers(oracle):
+    """Values worked out by hand from the definition of Eq. 1 (tests/golden)."""
+    from golden.load import negacyclic_q17
+    ntt_cases, mul_cases = negacyclic_q17()
+    assert len(ntt_cases) == 2 and len(mul_cases) == 2
+    for q, log2n, psi, a, A in ntt_cases:
+        assert oracle.psi(q, log2n) == psi
+        assert oracle.ntt_forward(np.array(a, dtype=np.uint64), q).tolist() == A
+        assert oracle.ntt_inverse(np.array(A, dtype=np.uint64), q).tolist() == a
+    for q, log2n, a, b, c in mul_cases:
+        a, b = np.array(a, dtype=np.uint64), np.array(b, dtype=np.uint64)
+        assert oracle.schoolbook(a, b, q).tolist() == c
+        prod = oracle.pointwise(oracle.ntt_forward(a, q), oracle.ntt_forward(b, q), q)
+        assert oracle.ntt_inverse(prod, q).tolist() == c
