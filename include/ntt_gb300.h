@@ -145,7 +145,8 @@ int ntt_plan_set_schedule(ntt_plan_t plan, uint32_t id);
 /* The schedule ntt_plan picks by default for N = 2^log2n and `rows` rows. */
 int ntt_default_schedule(uint32_t log2n, uint64_t rows);
 /* Raw parameters of a schedule: params[0] = kernels (1 or 2), params[1] =
- * pipelined (0/1), params[2..10] = the nine numbers of its S1/S2 entry
+ * kernel form (0 direct, 1 pipelined, 2 read-only-cache twiddles; for two
+ * kernels A | B << 2 with B != 0 = column form A, row form B), params[2..10] = the nine numbers of its S1/S2 entry
  * (S1: LOGN, LOGT, LOGRP, TPC, 0...; S2: LOGN, SPLIT, LOGP, LOGTA, LOGRPA,
  * TPCA, LOGTB, LOGRPB, TPCB).  n must be >= 11. */
 int ntt_schedule_params(uint32_t log2n, uint32_t id, int32_t* params, uint32_t n);

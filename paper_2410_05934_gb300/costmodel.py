@@ -239,10 +239,10 @@ def choose_schedule(log2n, limbs, batch, bits=50, inverse=False, db=DEFAULT_DB, 
     """Schedule for a shape: the exhaustive autotuner result when the timing DB
     holds this exact shape, else the cost model's prediction, else the
     library default.  Returns (schedule id, source)."""
+    from .tune import load_db, schedule_signature
     if "db" not in _CACHE:
-        from .tune import load_db
         _CACHE["db"] = {}
-        for r in load_db(db):
+        for r in load_db(db, current=True):
             k = shape_key(r) + (bool(r.get("inverse", False)),)
             best = _CACHE["db"].get(k)
             if best is None or r["ms"] < best[1]:
@@ -252,8 +252,9 @@ def choose_schedule(log2n, limbs, batch, bits=50, inverse=False, db=DEFAULT_DB, 
         return hit[0], "autotuner"
     if "model" not in _CACHE:
         _CACHE["model"] = CostModel.load(params) if os.path.exists(params) else None
-    if _CACHE["model"] is not None and not inverse:
-        return _CACHE["model"].choose(log2n, limbs, batch, bits), "cost_model"
+    model = _CACHE["model"]
+    if model is not None and not inverse and model.meta.get("sigs", {}).get(str(log2n)) == schedule_signature(log2n):
+        return model.choose(log2n, limbs, batch, bits), "cost_model"
     return default_choice(log2n, limbs, batch), "default"
 
 
@@ -295,17 +296,18 @@ def evaluate(model, keys, times):
 
 def load_db_default():
     from .tune import load_db
-    return load_db(DEFAULT_DB)
+    return load_db(DEFAULT_DB, current=True)
 
 
 def train_and_evaluate(db=DEFAULT_DB, n_heldout=100, steps=4000, lr=3e-3, seed=0, split_seed=7):
-    from .tune import load_db
-    recs = load_db(db)
+    from .tune import load_db, schedule_signature
+    recs = load_db(db, current=True)
     X, T, M, keys, times = dataset(recs)
     tr, ho = split_heldout(keys, n_heldout, split_seed)
     model = CostModel(meta={"db": os.path.basename(db), "records": len(recs), "shapes": len(keys),
                             "heldout": int(len(ho)), "split_seed": split_seed,
-                            "gpu": recs[0]["gpu"] if recs else None, "build": recs[0]["build"] if recs else None})
+                            "gpu": recs[0]["gpu"] if recs else None, "build": recs[0]["build"] if recs else None,
+                            "sigs": {str(n): schedule_signature(n) for n in sorted({int(r["log2n"]) for r in recs})}})
     model.fit(X[tr], T[tr], M[tr], steps=steps, lr=lr, seed=seed)
     report = evaluate(model, [keys[i] for i in ho], [times[i] for i in ho])
     report["train"] = {k: model.meta[k] for k in ("train_steps", "train_shapes", "train_seconds", "final_loss")}

@@ -169,8 +169,9 @@ static const void* batch_kernel(uint32_t mc, uint32_t short_only) {
     return short_only ? (const void*)k_ntt_batch<0, NTT_BATCH_SHORT_NMAX> : (const void*)k_ntt_batch<0, 16>;
 }
 
-// rows per work item: about one 2^13-coefficient chunk, whole rows above
-static uint32_t rows_per_item(uint32_t log2n) { return log2n >= 13 ? 1u : (1u << (13 - log2n)); }
+// rows per work item: one tile group of the batch configuration (two rows at
+// N = 2^10, one row above), so that the queue's last wave is short
+static uint32_t rows_per_item(uint32_t log2n) { return log2n <= 10 ? 2u : 1u; }
 
 struct NTableSet {
     PlanHost host;              // pool prefix tables of one N

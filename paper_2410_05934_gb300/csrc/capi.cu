@@ -58,19 +58,27 @@ int schedule_count(uint32_t log2n) {
     return c;
 }
 
+static const char* form_name(int f) { return f == 1 ? " pipelined" : (f == 2 ? " ro-twiddles" : ""); }
+
 static void sched_describe(int i, char* buf, size_t len) {
     const SchedParams& s = g_params[i];
     const int* v = s.v;
     if (s.kind == 1) {
         int r = v[0] - v[1];
-        snprintf(buf, len, "1k%s: %d thr/row x %d coef, <=%d fused stages/pass, %d rows/CTA",
-                 s.pipe == 1 ? " pipelined" : (s.pipe == 2 ? " ro-twiddles" : ""), 1 << v[1], 1 << r, v[2], v[3]);
+        snprintf(buf, len, "1k%s: %d thr/row x %d coef, <=%d fused stages/pass, %d rows/CTA", form_name(s.pipe),
+                 1 << v[1], 1 << r, v[2], v[3]);
     } else {
         int ra = v[1] + v[2] - v[3], rb = (v[0] - v[1]) - v[6];
+        const int fa = form_col(s.pipe), fb = form_row(s.pipe);
+        char form[48];
+        if (fa == fb)
+            snprintf(form, sizeof form, "%s", form_name(fa));
+        else
+            snprintf(form, sizeof form, " col%s row%s", fa ? form_name(fa) : " direct", form_name(fb));
         snprintf(buf, len,
                  "2k%s split %d+%d: col tile 2^%dx%d (%d thr x %d coef, <=%d/pass, %d/CTA); "
                  "row tile 2^%d (%d thr x %d coef, <=%d/pass, %d/CTA)",
-                 s.pipe == 1 ? " pipelined" : (s.pipe == 2 ? " ro-twiddles" : ""), v[1], v[0] - v[1], v[1], 1 << v[2], 1 << v[3], 1 << ra, v[4], v[5], v[0] - v[1],
+                 form, v[1], v[0] - v[1], v[1], 1 << v[2], 1 << v[3], 1 << ra, v[4], v[5], v[0] - v[1],
                  1 << v[6], 1 << rb, v[7], v[8]);
     }
 }
@@ -238,12 +246,16 @@ int ntt_hmul_tensor(ntt_plan_t plan, const uint64_t* d_a, const uint64_t* d_b, u
     int rc = check_device(plan);
     if (rc) return rc;
     // the tensor product runs in the direct form of the inverse's first kernel
+    // (the row kernel of a two-kernel schedule)
+    auto inverse_first_pipelined = [](int k) {
+        return (g_params[k].kind == 1 ? g_params[k].pipe : form_row(g_params[k].pipe)) == 1;
+    };
     int idx = sched_index(plan->h.log2n, plan->schedule);
-    if (idx < 0 || g_params[idx].pipe == 1) {
+    if (idx < 0 || inverse_first_pipelined(idx)) {
         idx = -1;
         for (uint32_t id = 0; (int)id < schedule_count(plan->h.log2n); ++id) {
             const int k = sched_index(plan->h.log2n, id);
-            if (g_params[k].pipe != 1) {
+            if (!inverse_first_pipelined(k)) {
                 idx = k;
                 break;
             }

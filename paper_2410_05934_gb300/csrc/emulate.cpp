@@ -207,8 +207,8 @@ static int emu_s1(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t 
 template <int LOGN, int SPLIT, int LOGP, int LOGTA, int LOGRPA, int TPCA, int LOGTB, int LOGRPB,
           int TPCB, int PIPE, bool INV, int MC>
 static int emu_s2_mc(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t rb, uint64_t nr) {
-    using CA = TileCfg<LOGN, 0, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, INV, MC, PIPE>;
-    using CB = TileCfg<LOGN, SPLIT, LOGN, 0, LOGTB, LOGRPB, TPCB, INV, MC, PIPE>;
+    using CA = TileCfg<LOGN, 0, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, INV, MC, form_col(PIPE)>;
+    using CB = TileCfg<LOGN, SPLIT, LOGN, 0, LOGTB, LOGRPB, TPCB, INV, MC, form_row(PIPE)>;
     int rc;
     if (!INV) {
         rc = emu_kernel<CA>(p, in, out, rb, nr);

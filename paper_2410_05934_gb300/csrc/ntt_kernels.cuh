@@ -241,8 +241,8 @@ template <int LOGN, int SPLIT, int LOGP, int LOGTA, int LOGRPA, int TPCA, int LO
           int TPCB, int PIPE, bool INV, int MC>
 int launch_s2_mc(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t row_begin,
                  uint64_t n_rows, cudaStream_t st) {
-    using CA = TileCfg<LOGN, 0, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, INV, MC, PIPE>;
-    using CB = TileCfg<LOGN, SPLIT, LOGN, 0, LOGTB, LOGRPB, TPCB, INV, MC, PIPE>;
+    using CA = TileCfg<LOGN, 0, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, INV, MC, form_col(PIPE)>;
+    using CB = TileCfg<LOGN, SPLIT, LOGN, 0, LOGTB, LOGRPB, TPCB, INV, MC, form_row(PIPE)>;
     int rc;
     if (!INV) {
         rc = launch_tile_kernel<CA>(p, in, out, row_begin, n_rows, st);

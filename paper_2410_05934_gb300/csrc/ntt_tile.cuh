@@ -126,6 +126,12 @@ NTT_HD constexpr uint32_t spread(uint32_t x, int pe, int r) {
 //       1 = pipelined form, 2 = direct form reading twiddles through the
 //           read-only path (no staging; the table stays in L1 when a batch
 //           shares one modulus).
+// Kernel forms of a two-kernel schedule entry (its PIPE field): below 4 both
+// kernels use it; A | B << 2 with B != 0 gives the column kernel form A and
+// the row kernel form B.
+constexpr int form_col(int f) { return f & 3; }
+constexpr int form_row(int f) { return f < 4 ? f : (f >> 2) & 3; }
+
 template <int LOGN_, int S0_, int S1_, int LOGP_, int LOGT_, int LOGRP_, int TPC_, bool INV_,
           int MC_ = 0, int MODE_ = 0>
 struct TileCfg {

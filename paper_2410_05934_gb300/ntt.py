@@ -58,7 +58,10 @@ def schedule_params(log2n, sched_id):
     buf = (ctypes.c_int32 * 11)()
     check(load().ntt_schedule_params(log2n, sched_id, buf, 11), "ntt_schedule_params")
     v = list(buf)
-    d = {"kernels": v[0], "pipelined": v[1] == 1, "staged_twiddles": v[1] != 2, "log2n": v[2]}
+    form_col = v[1] & 3
+    form_row = v[1] if v[1] < 4 else (v[1] >> 2) & 3
+    d = {"kernels": v[0], "form": v[1], "pipelined": form_col == 1 or form_row == 1,
+         "staged_twiddles": form_col != 2 and form_row != 2, "log2n": v[2]}
     if v[0] == 1:
         d.update(logt=v[3], logrp=v[4], tpc=v[5])
     else:

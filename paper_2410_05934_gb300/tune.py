@@ -10,12 +10,11 @@ resumes where it stopped and the cost model can train on it.
 
     python -m paper_2410_05934_gb300.tune --shape 16,24,4 [--shape 10,1,5040]
 
-The heuristic arm (``heuristic_schedule``) is the paper's SM-aware rule
-restated for these kernels: pick the schedule whose number of independent
-work chunks per launch is closest to a whole number of waves of the SM count,
-fewer kernels first.
+The heuristic arm, the paper's SM-aware rule restated for these kernels, is
+``costmodel.heuristic_choice``.
 """
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -100,7 +99,28 @@ class Timer:
         del self.x, self.y, self.flush
 
 
-def load_db(path=DEFAULT_DB):
+_SIGS = {}
+
+
+def schedule_signature(log2n):
+    """Hash of N's candidate list (schedule names in id order).  A timing
+    record holds for the list it was measured on: when the list of an N
+    changes, its old records no longer say which schedule is which."""
+    if log2n not in _SIGS:
+        h = hashlib.sha256()
+        for s in range(_ntt.schedule_count(log2n)):
+            h.update(_ntt.schedule_name(log2n, s).encode() + b"\0")
+        _SIGS[log2n] = h.hexdigest()[:12]
+    return _SIGS[log2n]
+
+
+def current_records(recs):
+    """The records measured on the schedule lists this library has."""
+    return [r for r in recs if r.get("sig") == schedule_signature(int(r["log2n"]))]
+
+
+def load_db(path=DEFAULT_DB, current=False):
+    """All records of a timing DB (JSON lines), or only the current ones."""
     recs = []
     if os.path.exists(path):
         with open(path) as f:
@@ -111,11 +131,12 @@ def load_db(path=DEFAULT_DB):
                         recs.append(json.loads(line))
                     except ValueError:
                         pass
-    return recs
+    return current_records(recs) if current else recs
 
 
 def _key(r):
-    return (r["gpu"], r["build"], r["log2n"], r["limbs"], r["batch"], r["bits"], r["inverse"], r["sched"])
+    return (r["gpu"], r["build"], r.get("sig"), r["log2n"], r["limbs"], r["batch"], r["bits"], r["inverse"],
+            r["sched"])
 
 
 def tune_shape(log2n, limbs, batch, bits=50, db=DEFAULT_DB, reps=7, skip_done=True, directions=(False, True)):
@@ -128,8 +149,8 @@ def tune_shape(log2n, limbs, batch, bits=50, db=DEFAULT_DB, reps=7, skip_done=Tr
     try:
         for inverse in directions:
             for s in range(_ntt.schedule_count(log2n)):
-                rec = dict(gpu=gpu, build=stamp, log2n=log2n, limbs=limbs, batch=batch, bits=bits,
-                           inverse=bool(inverse), sched=s)
+                rec = dict(gpu=gpu, build=stamp, sig=schedule_signature(log2n), log2n=log2n, limbs=limbs,
+                           batch=batch, bits=bits, inverse=bool(inverse), sched=s)
                 if _key(rec) in done:
                     continue
                 if timer is None:
@@ -155,42 +176,6 @@ def best_from_db(log2n, limbs, batch, bits=50, inverse=False, db=DEFAULT_DB, rec
     if not cands:
         return None
     return min(cands, key=lambda r: r["ms"])["sched"]
-
-
-# ---- the paper's SM-aware rule as the heuristic arm --------------------------
-
-def schedule_params(log2n, sched):
-    """Decodes the schedule description into (kernels, rows per CTA, threads per row)."""
-    name = _ntt.schedule_name(log2n, sched)
-    return name
-
-
-def chunks_per_launch(log2n, sched, rows):
-    """Independent work chunks (CTAs) of the first kernel of a schedule."""
-    name = _ntt.schedule_name(log2n, sched)
-    if name.startswith("1k"):
-        # "1k: T thr/row x R coef, <=F fused stages/pass, P rows/CTA"
-        per_cta = int(name.split(",")[-1].split()[0])
-        return math.ceil(rows / per_cta), 1
-    # 2k split a+b: column tiles of 2^a x C -> N / (2^a C) tiles per row, TPC per CTA
-    split = int(name.split()[2].split("+")[0])
-    cols = int(name.split("col tile 2^")[1].split("x")[1].split()[0])
-    tpc = int(name.split("/pass, ")[1].split("/CTA")[0])
-    tiles = rows * (1 << log2n) // ((1 << split) * cols)
-    return math.ceil(tiles / tpc), 2
-
-
-def heuristic_schedule(log2n, rows, sms=152):
-    """Sec. V-D restated: chunks closest to a whole number of SM waves; fewer kernels first."""
-    best, best_score = 0, None
-    for s in range(_ntt.schedule_count(log2n)):
-        ctas, kernels = chunks_per_launch(log2n, s, rows)
-        waves = ctas / sms
-        frac = abs(waves - max(1, round(waves))) / max(1, round(waves))
-        score = (kernels, frac)
-        if best_score is None or score < best_score:
-            best, best_score = s, score
-    return best
 
 
 def probe_peaks(iters=4000, reps=3):
@@ -268,8 +253,8 @@ def sweep(shapes, db=DEFAULT_DB, reps=5, warmup=2, directions=(False,), skip_don
                 for inverse in directions:
                     fn = plan.inverse_rows if inverse else plan.forward_rows
                     for s in range(_ntt.schedule_count(log2n)):
-                        rec = dict(gpu=gpu, build=stamp, log2n=log2n, limbs=limbs, batch=batch, bits=bits,
-                                   inverse=bool(inverse), sched=s)
+                        rec = dict(gpu=gpu, build=stamp, sig=schedule_signature(log2n), log2n=log2n,
+                                   limbs=limbs, batch=batch, bits=bits, inverse=bool(inverse), sched=s)
                         if _key(rec) in done:
                             continue
                         plan.schedule = s

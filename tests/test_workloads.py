@@ -36,3 +36,13 @@ def test_mixed_request_distribution():
     polys = np.array([r[2] for r in reqs])
     assert limbs.min() == 1 and limbs.max() == 32 and polys.min() == 1 and polys.max() == 64
     assert W.mixed_requests() == W.mixed_requests()   # deterministic
+
+
+def test_timing_records_follow_the_schedule_list():
+    """A timing record only counts for the candidate list it was measured on."""
+    from paper_2410_05934_gb300 import tune
+    sig10, sig16 = tune.schedule_signature(10), tune.schedule_signature(16)
+    assert sig10 != sig16 and len(sig10) == 12
+    assert tune.schedule_signature(10) == sig10                   # stable
+    recs = [dict(log2n=10, sig=sig10), dict(log2n=16, sig=sig10), dict(log2n=16), dict(log2n=16, sig=sig16)]
+    assert tune.current_records(recs) == [recs[0], recs[3]]
