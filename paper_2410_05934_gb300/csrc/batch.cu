@@ -42,7 +42,7 @@ struct BatchItem {
 };
 
 #define NTT_BATCH_THREADS 256
-static constexpr size_t kBatchSmemBound = 16 * 1024;
+static constexpr size_t kBatchSmemBound = 18 * 1024;
 
 // One phase (stage range) of a config over rows [a.row_begin, +n_rows).
 template <class C>
@@ -76,8 +76,8 @@ template <int LOGN, int SPLIT, int LOGP, int LOGTA, int LOGRPA, int TPCA, int LO
           int MODE, bool INV, int MC>
 __device__ __forceinline__ void batch_split(const TileArgs& a, const BatchReq& rq, uint64_t n_rows,
                                             uint64_t* smem) {
-    using CA = TileCfg<LOGN, 0, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, INV, MC, MODE>;
-    using CB = TileCfg<LOGN, SPLIT, LOGN, 0, LOGTB, LOGRPB, TPCB, INV, MC, MODE>;
+    using CA = TileCfg<LOGN, 0, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, INV, MC, form_col(MODE)>;
+    using CB = TileCfg<LOGN, SPLIT, LOGN, 0, LOGTB, LOGRPB, TPCB, INV, MC, form_row(MODE)>;
     TileArgs b = a;
     b.tw = INV ? rq.tw_inv : rq.tw_fwd;
     // one row at a time so the row phase reads what this CTA's column phase wrote
@@ -116,7 +116,7 @@ __device__ __forceinline__ void batch_dispatch(const TileArgs& a, const BatchReq
     }
 }
 
-// Largest shared-memory footprint among the batch configurations (16 KiB).
+// Largest shared-memory footprint among the batch configurations (18 KiB).
 static constexpr size_t kBatchSmem = kBatchSmemBound;
 #define NTT_BATCH_MIN_CTAS 3
 // kernel variants: all N (NMAX 16), or short polynomials only (NMAX 11)

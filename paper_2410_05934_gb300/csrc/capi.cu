@@ -92,10 +92,10 @@ uint32_t default_schedule(uint32_t log2n, uint64_t rows) {
         case 10: return rows < 256 ? 1u : 7u;    // pipelined / read-only twiddles, 128 thr x 8 coef
         case 11: return rows < 256 ? 1u : 5u;    // pipelined / read-only twiddles, 256 thr x 8 coef
         case 12: return rows < 256 ? 1u : 5u;    // pipelined / read-only twiddles, 512 thr x 8 coef
-        case 13: return 3u;                      // column + row kernels (6 + 7)
-        case 14: return 5u;                      // column + row kernels (7 + 7), read-only twiddles
-        case 15: return 5u;                      // column + row kernels (7 + 8), read-only twiddles
-        case 16: return 1u;                      // column + row kernels (7 + 9), read-only twiddles
+        case 13: return 5u;                      // column + row kernels (6 + 7), rows read-only twiddles
+        case 14: return 6u;                      // column + row kernels (7 + 7), rows read-only twiddles
+        case 15: return 6u;                      // column + row kernels (7 + 8), rows read-only twiddles
+        case 16: return 5u;                      // column + row kernels (7 + 9), rows read-only twiddles
         default: return 0u;
     }
 }

@@ -82,16 +82,18 @@ class Timer:
         fn = self.plan.inverse if inverse else self.plan.forward
         for _ in range(warmup):
             fn(self.x, self.y)
+        inner = _inner_count(torch, self.stream, lambda: fn(self.x, self.y))
         ms = []
         for r in range(reps):
             if self.flush is not None:
                 self.flush.fill_(r)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(self.stream)
-            fn(self.x, self.y)
+            for _ in range(inner):
+                fn(self.x, self.y)
             b.record(self.stream)
             b.synchronize()
-            ms.append(a.elapsed_time(b))
+            ms.append(a.elapsed_time(b) / inner)
         return statistics.median(ms), min(ms), max(ms)
 
     def close(self):
@@ -222,6 +224,22 @@ def random_shapes(count, seed, max_log2_coef=27, sizes=(10, 11, 12, 13, 14, 15, 
     return out
 
 
+MIN_SAMPLE_MS = 0.05
+
+
+def _inner_count(torch, st, launch):
+    """Back-to-back launches per timed sample so that a sample spans at least
+    MIN_SAMPLE_MS: a single launch of a small shape lasts a few microseconds,
+    close to the resolution of event timing."""
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    launch()
+    b.record(st)
+    b.synchronize()
+    one = max(a.elapsed_time(b), 1e-3)
+    return int(min(64, max(1, math.ceil(MIN_SAMPLE_MS / one))))
+
+
 def sweep(shapes, db=DEFAULT_DB, reps=5, warmup=2, directions=(False,), skip_done=True, log=None):
     """Times every schedule of every shape with one plan per (N, limbs, bits)
     and shared buffers; appends to the DB.  Inputs are uniform below 2^49,
@@ -260,17 +278,20 @@ def sweep(shapes, db=DEFAULT_DB, reps=5, warmup=2, directions=(False,), skip_don
                         plan.schedule = s
                         for _ in range(warmup):
                             fn(x, y, 0, rows)
+                        inner = _inner_count(torch, st, lambda: fn(x, y, 0, rows))
                         ms = []
                         for r in range(reps):
                             if small:
                                 flush.fill_(r)
                             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                             a.record(st)
-                            fn(x, y, 0, rows)
+                            for _ in range(inner):
+                                fn(x, y, 0, rows)
                             b.record(st)
                             b.synchronize()
-                            ms.append(a.elapsed_time(b))
-                        rec.update(ms=statistics.median(ms), ms_min=min(ms), ms_max=max(ms), t=time.time())
+                            ms.append(a.elapsed_time(b) / inner)
+                        rec.update(ms=statistics.median(ms), ms_min=min(ms), ms_max=max(ms), inner=inner,
+                                   t=time.time())
                         f.write(json.dumps(rec) + "\n")
                         done.add(_key(rec))
                         n_rec += 1
