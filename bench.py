@@ -51,7 +51,7 @@ def parse():
                     help="mixed batches: requests of at least 2^k coefficients run their own learned schedule")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "mixed_batch", "tfhe_blind_rotation", "plain_n1024", "cost_model",
-                             "serving", "hmul_fused", "mixed_small"],
+                             "serving", "hmul_fused", "mixed_small", "tfhe_cmux"],
                     help="the line the driver records is the default (CKKS-HMUL-shaped) workload")
     return ap.parse_args()
 
@@ -646,6 +646,97 @@ def run_other(args):
     return 0
 
 
+def run_tfhe_cmux(args):
+    """Blind rotation of 1024 TFHE accumulators (N = 1024, the 62-bit prime,
+    gadget B = 2^8, l = 3): 630 batched CMux steps, each with its own RGSW
+    key and one exponent per accumulator (Sec. IV-A: every CMux of an
+    iteration shares the key), in place.  Beside it: the time of the
+    transforms alone (6 forward + 2 inverse rows per ciphertext and step
+    through the plain batched NTT), the least an unfused decompose / NTT /
+    MAC / INTT pipeline would spend."""
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2410_05934_gb300 import build as B
+    B.build_product()
+    import paper_2410_05934_gb300 as ntt
+    from paper_2410_05934_gb300 import _native
+    from paper_2410_05934_gb300 import workloads as W
+    L = _native.load()
+    stream = torch.cuda.current_stream()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    n_slot, n_lwe, levels, log2_base, n = 1024, 630, 3, 8, 1024
+    w = W.tfhe_cmux(seed=W.DEFAULT_SEED + rank, n_ct=n_slot, steps=n_lwe, levels=levels)
+    q = w["moduli"][0]
+    plan = ntt.Plan(10, [q])
+    acc = to_dev_np(torch, w["acc"])
+    keys = to_dev_np(torch, w["key"])
+    rots = torch.from_numpy(w["rot"].astype(np.int32)).cuda()
+
+    def blind_rotation():
+        for i in range(n_lwe):
+            plan.tfhe_cmux_rotate(acc, rots[i], keys[i], levels, log2_base)
+        return n_lwe
+    blind_rotation()
+    torch.cuda.synchronize()
+    steps = max(1, args.steps // 10)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, launches = _events_loop(torch, stream, steps, blind_rotation)
+    clk = clocks.stop()
+    t = sum(ms) * 1e-3
+    cmux = n_slot * n_lwe * steps
+    # the transforms alone, per CMux step: 6 forward and 2 inverse rows per ciphertext
+    fwd_plan, inv_plan = ntt.Plan(10, [q], 2 * levels * n_slot), ntt.Plan(10, [q], 2 * n_slot)
+    xf = torch.empty((2 * levels * n_slot, n), dtype=torch.int64, device="cuda").fill_(1)
+    xi = torch.empty((2 * n_slot, n), dtype=torch.int64, device="cuda").fill_(1)
+
+    def transforms():
+        fwd_plan.forward(xf)
+        inv_plan.inverse(xi)
+        return 2
+    for _ in range(3):
+        transforms()
+    ms_t, _ = _events_loop(torch, stream, 50, transforms)
+    per_step = t / (n_lwe * steps)
+    bfly = cmux * 8 * (n // 2) * 10
+    peak = _probe(torch, L, q, 0, sms, stream)
+    line = {"metric": "NTT coeffs/s (coefficient-transforms per second)", "value": cmux * 8 * n / t,
+            "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": 1, "ms_per_step": 1e3 * t / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "gpu_launches": launches, "clocks": clk,
+            "config": {"workload": "tfhe_cmux", "log2n": 10, "modulus_bits": 62, "slots": n_slot,
+                       "cmux_steps": n_lwe, "gadget": "B = 2^8, l = 3",
+                       "step": "one blind rotation: 630 batched CMux launches (decompose, 6 NTT, MAC with "
+                               "the step's RGSW key, 2 INTT, add) over 1024 accumulators, in place",
+                       "l2": "accumulators (16 MB) stay in L2 across steps, keys (62 MB) stream"},
+            "cmux_per_s": cmux / t, "blind_rotations_per_s": n_slot * steps / t,
+            "us_per_cmux_step": 1e6 * per_step,
+            "transforms_only": {"us_per_cmux_step": 1e3 * sum(ms_t) / 50,
+                                "how": "6144 forward + 2048 inverse N=1024 rows through ntt_forward / "
+                                       "ntt_inverse (no decomposition, no MAC, digits in HBM)"},
+            "roofline": {"bound": "alu", "achieved": bfly / t / 1e9, "peak": peak / 1e9, "unit": "Gbutterfly/s",
+                         "frac": bfly / t / peak, "traffic": None,
+                         "peak_source": "in-run butterfly probe (kind 0, exact class)",
+                         "note": "butterflies of the 8 transforms per CMux; the MAC and the decomposition are "
+                                 "extra work on the same pipes"}}
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import tfhe_oracle as TO
+        t0 = time.perf_counter()
+        kc = TO.key_coefficients(w["key"][0], q)
+        k = 0
+        while k < 2 or time.perf_counter() - t0 < min(args.cpu_seconds, 10.0):
+            TO.cmux_rotate(w["acc"][k], int(w["rot"][0][k]), w["key"][0], q, log2_base, levels, key_coef=kc)
+            k += 1
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": k * 8 * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "%d full CMux steps of step 0 (key brought to coefficients once, "
+                                          "schoolbook ring products)" % k, "cmux_per_s": k / dt}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def run_cost_model(args):
     """Schedule cost model: train on the committed GB300 timing sweep with the
     library's GPU kernels; regret on 100 held-out shapes vs exhaustive tuning."""
@@ -706,6 +797,8 @@ def main():
         return run_cost_model(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "tfhe_cmux":
+        return run_tfhe_cmux(args)
     if args.workload != WORKLOAD:
         return run_other(args)
     return run_ours(args)

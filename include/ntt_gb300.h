@@ -310,6 +310,43 @@ typedef struct {
 
 int ntt_batch_execute_static(const ntt_plan_request_t* reqs, uint32_t n_reqs, void* cuda_stream);
 
+/*
+ * TFHE external product and CMux step, batched over n_ct RLWE ciphertexts
+ * that share one RGSW key: the batched CMux gate of Sec. IV-A (all
+ * ciphertexts of one blind-rotation iteration use the same key RGSW(s_i));
+ * blind rotation itself (Sec. II-B) repeats the CMux step once per LWE
+ * coefficient.  One kernel launch, no scratch memory: each ciphertext is
+ * decomposed, transformed, multiplied with the key and transformed back on
+ * one SM.  The plan must hold one modulus q (prime, q = 1 mod 2N, q < 2^62)
+ * and N = 2^10 or 2^11; it supplies the twiddle tables and the status word.
+ *   d_in, d_acc   [n_ct][2][N] RLWE ciphertexts (B(x), A(x)), canonical
+ *   d_rot         [n_ct] exponents a of x^a, taken mod 2N (CMux only)
+ *   d_key         [2 levels][2][N] RGSW rows in the NTT domain (the forward
+ *                 transform's bit-reversed order), canonical; row
+ *                 i * levels + j multiplies digit level j of input polynomial i
+ *   levels, log2_base  the gadget B = 2^log2_base, l = levels:
+ *                 1 <= l <= NTT_TFHE_MAX_LEVELS, l * log2_base <= 32, B^l < q
+ *   d_out         [n_ct][2][N]; may be the same buffer as d_in / d_acc, no
+ *                 other overlap.  d_in, d_acc, d_key, d_out 16-byte aligned.
+ * Decomposition (the gadget over a prime q; the paper does not spell it out):
+ * t = round(v B^l / q) mod B^l written with signed digits e_0..e_(l-1) in
+ * [-B/2, B/2), e_0 most significant, each digit taken mod q.
+ *   tfhe_external_product: out_c = sum_{i, j} e_j(d_i) * K[i l + j][c]
+ *   tfhe_cmux_rotate:      out = acc + K [x] (x^a acc - acc)
+ * with products in Z_q[x]/(x^N + 1).  Asynchronous on cuda_stream.
+ * Errors: ARG (plan with several moduli, bad gadget, null pointers), ALIGN,
+ * UNSUPPORTED (N), CUDA; with NTT_FLAG_CHECK plans a non-canonical input is
+ * reported as NTT_ERR_RANGE through ntt_status.
+ */
+#define NTT_TFHE_MIN_LOG2N 10
+#define NTT_TFHE_MAX_LOG2N 11
+#define NTT_TFHE_MAX_LEVELS 8
+
+int tfhe_external_product(ntt_plan_t plan, const uint64_t* d_in, const uint64_t* d_key, uint32_t levels,
+                          uint32_t log2_base, uint64_t* d_out, uint64_t n_ct, void* cuda_stream);
+int tfhe_cmux_rotate(ntt_plan_t plan, const uint64_t* d_acc, const uint32_t* d_rot, const uint64_t* d_key,
+                     uint32_t levels, uint32_t log2_base, uint64_t* d_out, uint64_t n_ct, void* cuda_stream);
+
 const char* ntt_strerror(int code);
 
 /* Library version string ("ntt_gb300 <major>.<minor> sm_103a"). */

@@ -65,6 +65,8 @@ SIGNATURES = [
     ("ntt_mlp_backward", i32, [vp, vp, vp, vp, vp, u32, ctypes.c_float, vp, vp, vp, vp]),
     ("ntt_mlp_adam", i32, [vp, vp, vp, vp, u32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                            ctypes.c_float, u32, vp]),
+    ("tfhe_external_product", i32, [vp, vp, vp, u32, u32, vp, u64, vp]),
+    ("tfhe_cmux_rotate", i32, [vp, vp, vp, vp, u32, u32, vp, u64, vp]),
     ("ntt_strerror", ctypes.c_char_p, [i32]),
     ("ntt_version", ctypes.c_char_p, []),
 ]

@@ -13,6 +13,7 @@
 #include "ntt_batch_cfgs.h"
 #include "ntt_launch.h"
 #include "ntt_schedules.h"
+#include "tfhe_cmux.cuh"
 
 namespace nttgb {
 
@@ -264,6 +265,71 @@ struct EmuPlan {
     int status = 0;
 };
 
+// The CMux kernel of tfhe.cu, CTA by CTA: every step between two barriers
+// runs for all threads before the next one starts.
+template <int LOGN, int MC>
+static int emu_cmux(const CmuxArgs& c, const TileArgs& af, const TileArgs& ai) {
+    using K = CmuxCfg<LOGN, MC>;
+    using F = typename K::F;
+    using I = typename K::I;
+    if (!verify_cfg<F>() || !verify_cfg<I>()) return NTT_ERR_UNSUPPORTED;
+    std::vector<uint64_t> smem(2 * (size_t)K::N, 0xdeadbeefdeadbeefull);
+    std::vector<CmuxRegs<K>> cr(K::THREADS);
+    std::vector<TileRegs<F>> sf(K::THREADS);
+    std::vector<TileRegs<I>> si(K::THREADS);
+    std::vector<TileLoc> L(1);
+    L[0].row = 0;
+    L[0].rowq = 0;
+    L[0].limb = 0;
+    L[0].hi = 0;
+    L[0].gbase = 0;
+    L[0].tw_off = 0;
+    L[0].valid = true;
+    const LimbConst lc = af.lc[0];
+    for (uint64_t ct = 0; ct < c.n_ct; ++ct) {
+        for (int tid = 0; tid < K::THREADS; ++tid)
+            cmux_load<K>(cr[tid], c, ct, tid >> K::LOGT, tid & (K::T - 1));
+        for (uint32_t j = 0; j < c.levels; ++j) {
+            for (int tid = 0; tid < K::THREADS; ++tid) {
+                const int s = tid >> K::LOGT, t = tid & (K::T - 1);
+                cmux_digits<K>(sf[tid], cr[tid], j, c);
+                write_pairs_swizzled<F>(sf[tid], L[0], t, smem.data() + (size_t)s * K::N);
+            }
+            for (int s = 0; s < 2; ++s) {
+                std::vector<TileRegs<F>> part(sf.begin() + s * K::T, sf.begin() + (s + 1) * K::T);
+                emu_passes<F, 0>(part, af, L, smem.data() + (size_t)s * K::N);
+                std::copy(part.begin(), part.end(), sf.begin() + s * K::T);
+            }
+            for (int tid = 0; tid < K::THREADS; ++tid) {
+                const int s = tid >> K::LOGT, t = tid & (K::T - 1);
+                cmux_mac<K>(cr[tid], c, lc, (uint32_t)s * c.levels + j, t, smem.data() + (size_t)s * K::N);
+            }
+        }
+        for (int tid = 0; tid < K::THREADS; ++tid) {
+            const int s = tid >> K::LOGT, t = tid & (K::T - 1);
+            cmux_exchange_put<K>(cr[tid], s, t, smem.data() + (size_t)s * K::N);
+        }
+        for (int tid = 0; tid < K::THREADS; ++tid) {
+            const int s = tid >> K::LOGT, t = tid & (K::T - 1);
+            cmux_exchange_get<K>(cr[tid], lc, s, t, smem.data() + (size_t)(1 - s) * K::N);
+        }
+        for (int tid = 0; tid < K::THREADS; ++tid) {
+            const int s = tid >> K::LOGT, t = tid & (K::T - 1);
+            cmux_inverse_input<K>(si[tid], cr[tid], s);
+            write_pairs_swizzled<I>(si[tid], L[0], t, smem.data() + (size_t)s * K::N);
+        }
+        for (int s = 0; s < 2; ++s) {
+            std::vector<TileRegs<I>> part(si.begin() + s * K::T, si.begin() + (s + 1) * K::T);
+            emu_passes<I, 0>(part, ai, L, smem.data() + (size_t)s * K::N);
+        }
+        for (int tid = 0; tid < K::THREADS; ++tid) {
+            const int s = tid >> K::LOGT, t = tid & (K::T - 1);
+            cmux_store<K>(c, lc, ct, s, t, smem.data() + (size_t)s * K::N);
+        }
+    }
+    return NTT_OK;
+}
+
 }  // namespace nttgb
 
 using namespace nttgb;
@@ -369,6 +435,44 @@ int nttemu_pointwise(void* plan, const uint64_t* a, const uint64_t* b, uint64_t*
             c[r * n + j] = barrett_mulmod(a[r * n + j], b[r * n + j], m.q, m.mu, m.bits);
     }
     return NTT_OK;
+}
+
+// tfhe_external_product (rot == NULL) / tfhe_cmux_rotate on the host, with the
+// same argument rules as the C ABI.
+int nttemu_tfhe_cmux(void* plan, const uint64_t* in, const uint32_t* rot, const uint64_t* key, uint32_t levels,
+                     uint32_t log2_base, uint64_t* out, uint64_t n_ct) {
+    EmuPlan* p = static_cast<EmuPlan*>(plan);
+    if (!p || !in || !key || !out || p->h.n_moduli != 1) return NTT_ERR_ARG;
+    if (p->h.log2n < NTT_TFHE_MIN_LOG2N || p->h.log2n > NTT_TFHE_MAX_LOG2N) return NTT_ERR_UNSUPPORTED;
+    const uint64_t q = p->h.moduli[0];
+    const uint32_t sigma = 63u - (uint32_t)__builtin_clzll(q);
+    if (levels < 1 || levels > NTT_TFHE_MAX_LEVELS || log2_base < 1 || levels * log2_base > 32 ||
+        levels * log2_base > sigma)
+        return NTT_ERR_ARG;
+    CmuxArgs c;
+    c.in = in;
+    c.rot = rot;
+    c.key = key;
+    c.out = out;
+    c.status = &p->status;
+    c.q = q;
+    c.half_q = q >> 1;
+    c.m = (uint64_t)(((unsigned __int128)1 << (64 + sigma)) / q);
+    c.n_ct = n_ct;
+    c.sigma = sigma;
+    c.levels = levels;
+    c.log2_base = log2_base;
+    c.check = (p->h.flags & NTT_FLAG_CHECK) ? 1u : 0u;
+    TileArgs af{};
+    af.lc = p->h.consts.data();
+    af.status = &p->status;
+    af.n_moduli = 1;
+    TileArgs ai = af;
+    af.tw = p->h.fwd.data();
+    ai.tw = p->h.inv.data();
+    const bool small = p->h.mc != 0;
+    if (p->h.log2n == 10) return small ? emu_cmux<10, 1>(c, af, ai) : emu_cmux<10, 0>(c, af, ai);
+    return small ? emu_cmux<11, 1>(c, af, ai) : emu_cmux<11, 0>(c, af, ai);
 }
 
 int nttemu_status(void* plan) {

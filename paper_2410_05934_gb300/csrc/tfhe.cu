@@ -1,0 +1,162 @@
+// C ABI of the batched TFHE external product / CMux step (declared in
+// include/ntt_gb300.h) and its kernel; the per-thread steps live in
+// tfhe_cmux.cuh so that the host emulation runs the same code.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "ntt_gb300.h"
+#include "ntt_internal.h"
+#include "ntt_kernels.cuh"
+#include "tfhe_cmux.cuh"
+
+namespace nttgb {
+
+template <int LOGN, int MC>
+__global__ void __launch_bounds__(CmuxCfg<LOGN, MC>::THREADS, CmuxCfg<LOGN, MC>::MIN_CTAS) k_tfhe_cmux(CmuxArgs c, TileArgs af, TileArgs ai) {
+    using K = CmuxCfg<LOGN, MC>;
+    using F = typename K::F;
+    using I = typename K::I;
+    extern __shared__ __align__(16) uint64_t smem[];
+    const int s = threadIdx.x >> K::LOGT;
+    const int t = threadIdx.x & (K::T - 1);
+    uint64_t* sm = smem + (size_t)s * K::N;
+    const uint64_t* sm_other = smem + (size_t)(1 - s) * K::N;
+    TileLoc L;
+    L.row = 0;
+    L.rowq = 0;
+    L.limb = 0;
+    L.hi = 0;
+    L.gbase = 0;
+    L.tw_off = 0;
+    L.valid = true;
+    const LimbConst lc = af.lc[0];
+    for (uint64_t ct = blockIdx.x; ct < c.n_ct; ct += gridDim.x) {
+        CmuxRegs<K> cr;
+        cmux_load<K>(cr, c, ct, s, t);
+        for (uint32_t j = 0; j < c.levels; ++j) {
+            TileRegs<F> st;
+            cmux_digits<K>(st, cr, j, c);
+            write_pairs_swizzled<F>(st, L, t, sm);
+            __syncthreads();
+            run_passes<F, 0>(st, af, L, t, sm);
+            cmux_mac<K>(cr, c, lc, (uint32_t)s * c.levels + j, t, sm);
+        }
+        cmux_exchange_put<K>(cr, s, t, sm);
+        __syncthreads();
+        cmux_exchange_get<K>(cr, lc, s, t, sm_other);
+        __syncthreads();
+        TileRegs<I> si;
+        cmux_inverse_input<K>(si, cr, s);
+        write_pairs_swizzled<I>(si, L, t, sm);
+        __syncthreads();
+        run_passes<I, 0>(si, ai, L, t, sm);
+        cmux_store<K>(c, lc, ct, s, t, sm);
+        __syncthreads();
+    }
+}
+
+template <int LOGN, int MC>
+static int launch_cmux(const CmuxArgs& c, const TileArgs& af, const TileArgs& ai, cudaStream_t st) {
+    using K = CmuxCfg<LOGN, MC>;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tfhe_cmux<LOGN, MC>, K::THREADS,
+                                                      K::SMEM_BYTES) != cudaSuccess)
+        return NTT_ERR_CUDA;
+    // enough CTAs for several waves; each walks ciphertexts ct, ct + grid, ...
+    const uint64_t cap = (uint64_t)std::max(1, sms) * (uint64_t)std::max(1, per_sm) * 16u;
+    const unsigned grid = (unsigned)std::min<uint64_t>(c.n_ct, cap);
+    k_tfhe_cmux<LOGN, MC><<<grid, K::THREADS, K::SMEM_BYTES, st>>>(c, af, ai);
+    return cudaPeekAtLastError() == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
+}
+
+// Shared argument checks of both entry points; fills c (not in/rot/out) and
+// the two tile argument blocks.
+static int cmux_setup(ntt_plan_t plan, const uint64_t* d_key, uint32_t levels, uint32_t log2_base, uint64_t n_ct,
+                      CmuxArgs& c, TileArgs& af, TileArgs& ai) {
+    if (!plan || !d_key) return NTT_ERR_ARG;
+    if (plan->h.flags & NTT_FLAG_HOST_ONLY) return NTT_ERR_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device) return NTT_ERR_ARG;
+    if (plan->h.n_moduli != 1) return NTT_ERR_ARG;
+    if (plan->h.log2n < NTT_TFHE_MIN_LOG2N || plan->h.log2n > NTT_TFHE_MAX_LOG2N) return NTT_ERR_UNSUPPORTED;
+    if (((uintptr_t)d_key & 15u) != 0) return NTT_ERR_ALIGN;
+    const uint64_t q = plan->h.moduli[0];
+    const uint32_t sigma = 63u - (uint32_t)__builtin_clzll(q);
+    if (levels < 1 || levels > NTT_TFHE_MAX_LEVELS || log2_base < 1 || levels * log2_base > 32 ||
+        levels * log2_base > sigma)
+        return NTT_ERR_ARG;
+    if (n_ct > (1ull << 40)) return NTT_ERR_ARG;
+    c.key = d_key;
+    c.status = plan->d_status;
+    c.q = q;
+    c.half_q = q >> 1;
+    c.m = (uint64_t)(((unsigned __int128)1 << (64 + sigma)) / q);
+    c.n_ct = n_ct;
+    c.sigma = sigma;
+    c.levels = levels;
+    c.log2_base = log2_base;
+    c.check = (plan->h.flags & NTT_FLAG_CHECK) ? 1u : 0u;
+    TileArgs a{};
+    a.lc = plan->d_consts;
+    a.status = plan->d_status;
+    a.n_moduli = 1;
+    af = a;
+    ai = a;
+    af.tw = plan->d_fwd;
+    ai.tw = plan->d_inv;
+    return NTT_OK;
+}
+
+static int cmux_dispatch(ntt_plan_t plan, const CmuxArgs& c, const TileArgs& af, const TileArgs& ai, void* stream) {
+    plan->last_launches = 0;
+    if (c.n_ct == 0) return NTT_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc;
+    const bool small = plan->h.mc != 0;
+    switch (plan->h.log2n) {
+        case 10: rc = small ? launch_cmux<10, 1>(c, af, ai, st) : launch_cmux<10, 0>(c, af, ai, st); break;
+        case 11: rc = small ? launch_cmux<11, 1>(c, af, ai, st) : launch_cmux<11, 0>(c, af, ai, st); break;
+        default: return NTT_ERR_UNSUPPORTED;
+    }
+    if (rc == NTT_OK) plan->last_launches = 1;
+    return rc;
+}
+
+}  // namespace nttgb
+
+using namespace nttgb;
+
+extern "C" {
+
+int tfhe_external_product(ntt_plan_t plan, const uint64_t* d_in, const uint64_t* d_key, uint32_t levels,
+                          uint32_t log2_base, uint64_t* d_out, uint64_t n_ct, void* cuda_stream) {
+    CmuxArgs c;
+    TileArgs af, ai;
+    int rc = cmux_setup(plan, d_key, levels, log2_base, n_ct, c, af, ai);
+    if (rc) return rc;
+    if (!d_in || !d_out) return NTT_ERR_ARG;
+    if (((uintptr_t)d_in & 15u) || ((uintptr_t)d_out & 15u)) return NTT_ERR_ALIGN;
+    c.in = d_in;
+    c.rot = nullptr;
+    c.out = d_out;
+    return cmux_dispatch(plan, c, af, ai, cuda_stream);
+}
+
+int tfhe_cmux_rotate(ntt_plan_t plan, const uint64_t* d_acc, const uint32_t* d_rot, const uint64_t* d_key,
+                     uint32_t levels, uint32_t log2_base, uint64_t* d_out, uint64_t n_ct, void* cuda_stream) {
+    CmuxArgs c;
+    TileArgs af, ai;
+    int rc = cmux_setup(plan, d_key, levels, log2_base, n_ct, c, af, ai);
+    if (rc) return rc;
+    if (!d_acc || !d_rot || !d_out) return NTT_ERR_ARG;
+    if (((uintptr_t)d_acc & 15u) || ((uintptr_t)d_out & 15u) || ((uintptr_t)d_rot & 3u)) return NTT_ERR_ALIGN;
+    c.in = d_acc;
+    c.rot = d_rot;
+    c.out = d_out;
+    return cmux_dispatch(plan, c, af, ai, cuda_stream);
+}
+
+}  // extern "C"

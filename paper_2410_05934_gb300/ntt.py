@@ -172,6 +172,28 @@ class Plan:
                                      _ptr(out, 3 * per, "out"), _stream_handle(stream)), "ntt_hmul_tensor")
         return out
 
+    def tfhe_external_product(self, d, key, levels, log2_base, out=None, stream=None):
+        """K [x] d for d = [n_ct][2][N] RLWE ciphertexts and one RGSW key
+        [2 levels][2][N] in the NTT domain (tfhe_external_product)."""
+        n_ct = d.shape[0] if hasattr(d, "shape") else None
+        out = d if out is None else out
+        check(load().tfhe_external_product(self._h, _ptr(d, what="d"), _ptr(key, 4 * levels * self.n, "key"),
+                                           levels, log2_base, _ptr(out, what="out"),
+                                           n_ct, _stream_handle(stream)), "tfhe_external_product")
+        return out
+
+    def tfhe_cmux_rotate(self, acc, rot, key, levels, log2_base, out=None, stream=None):
+        """acc + K [x] (x^rot acc - acc) per ciphertext (tfhe_cmux_rotate);
+        rot: CUDA int32 tensor of exponents, one per ciphertext."""
+        n_ct = acc.shape[0]
+        out = acc if out is None else out
+        if not rot.is_cuda or rot.element_size() != 4 or rot.numel() < n_ct or not rot.is_contiguous():
+            raise ValueError("rot must be a contiguous CUDA tensor of 32-bit exponents, one per ciphertext")
+        check(load().tfhe_cmux_rotate(self._h, _ptr(acc, what="acc"), ctypes.c_void_p(rot.data_ptr()),
+                                      _ptr(key, 4 * levels * self.n, "key"), levels, log2_base,
+                                      _ptr(out, what="out"), n_ct, _stream_handle(stream)), "tfhe_cmux_rotate")
+        return out
+
     def pointwise(self, a, b, out=None, n_polys=0, stream=None):
         out = a if out is None else out
         need = (n_polys or self.batch) * self.n_moduli * self.n

@@ -142,6 +142,17 @@ def tfhe_blind_rotation(seed=DEFAULT_SEED, n_lwe=630, k1=2, levels=3):
     return dict(log2n=10, moduli=[Q62_N1024], fwd=fwd, inv=inv)
 
 
+def tfhe_cmux(seed=DEFAULT_SEED, n_ct=1024, log2n=10, q=Q62_N1024, levels=3, steps=1):
+    """Batched CMux steps: n_ct RLWE accumulators [n_ct][2][N] uniform mod q,
+    rotation exponents [steps][n_ct] uniform in [0, 2N), and one RGSW key per
+    step [steps][2 levels][2][N] uniform mod q (NTT domain)."""
+    n = 1 << log2n
+    acc = uniform_mod(seed, 6, n_ct * 2 * n, q).reshape(n_ct, 2, n)
+    rot = (draws(seed, 7, steps * n_ct) >> np.uint64(64 - (log2n + 1))).astype(np.uint32).reshape(steps, n_ct)
+    key = uniform_mod(seed, 8, steps * 2 * levels * 2 * n, q).reshape(steps, 2 * levels, 2, n)
+    return dict(log2n=log2n, moduli=[q], levels=levels, acc=acc, rot=rot, key=key)
+
+
 def mixed_requests(seed=DEFAULT_SEED, n_requests=200, max_limbs=32, max_polys=64,
                    log2ns=(10, 12, 14, 16), weights=(0.5, 0.2, 0.2, 0.1)):
     """The uneven request list: (log2n, limbs, polys) per request."""

@@ -26,6 +26,8 @@ def lib():
         L.nttemu_batch_transform.restype = i32
         L.nttemu_hmul_tensor.argtypes = [vp, u32, U64P, U64P, U64P]
         L.nttemu_hmul_tensor.restype = i32
+        L.nttemu_tfhe_cmux.argtypes = [vp, U64P, ctypes.POINTER(ctypes.c_uint32), U64P, u32, u32, U64P, u64]
+        L.nttemu_tfhe_cmux.restype = i32
         _lib = L
     return _lib
 
@@ -73,6 +75,20 @@ class EmuPlan:
         rc = lib().nttemu_hmul_tensor(self.h, sched, _p(a), _p(b), _p(out))
         if rc:
             raise ValueError("nttemu_hmul_tensor failed: %d" % rc)
+        return out
+
+    def tfhe(self, d, key, levels, log2_base, rot=None, out=None):
+        """tfhe_external_product (rot None) or tfhe_cmux_rotate of d [n_ct][2][N]."""
+        d = np.ascontiguousarray(d, dtype=np.uint64)
+        key = np.ascontiguousarray(key, dtype=np.uint64)
+        out = np.zeros_like(d) if out is None else out
+        rp = None
+        if rot is not None:
+            rot = np.ascontiguousarray(rot, dtype=np.uint32)
+            rp = rot.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+        rc = lib().nttemu_tfhe_cmux(self.h, _p(d), rp, _p(key), levels, log2_base, _p(out), d.shape[0])
+        if rc:
+            raise ValueError("nttemu_tfhe_cmux failed: %d" % rc)
         return out
 
     def pointwise(self, a, b, n_rows=None):

@@ -188,3 +188,50 @@ def test_hmul_tensor_matches_schoolbook(oracle, log2n):
             for l in range(L):
                 assert np.array_equal(out[k * L + l][kk], ref[l][k]), (s, k, l)
     assert tried >= 1
+
+
+@pytest.mark.parametrize("log2n,q", [(10, W.Q62_N1024), (10, W.POOL50[0]), (11, W.POOL50[3])])
+def test_tfhe_cmux_and_external_product_match_oracle(log2n, q):
+    """The CMux kernel's steps (decompose, NTT, MAC, exchange, INTT) on the
+    host, against the schoolbook oracle of the external product and CMux."""
+    from oracle import tfhe_oracle as TO
+    n, levels, log2_base = 1 << log2n, 3, 8
+    rng = np.random.default_rng(log2n + q % 7)
+    d = rng.integers(0, q, (2, 2, n), dtype=np.uint64)
+    key = rng.integers(0, q, (2 * levels, 2, n), dtype=np.uint64)
+    rot = np.array([5, 2 * n - 3], dtype=np.uint32)
+    plan = emu.EmuPlan(log2n, [q])
+    kc = TO.key_coefficients(key, q)
+    idx = [0, 1, 7, n // 2, n - 1]
+    ep = plan.tfhe(d, key, levels, log2_base)
+    cm = plan.tfhe(d, key, levels, log2_base, rot=rot)
+    assert plan.status() == 0
+    for c in range(2):
+        assert np.array_equal(ep[c][:, idx], TO.external_product(d[c], key, q, log2_base, levels, key_coef=kc, idx=idx))
+        assert np.array_equal(cm[c][:, idx], TO.cmux_rotate(d[c], int(rot[c]), key, q, log2_base, levels,
+                                                            key_coef=kc, idx=idx))
+    # in place, other gadgets, and a full-row comparison on one ciphertext
+    for levels2, base2 in [(2, 10), (4, 6), (1, 16)]:
+        key2 = rng.integers(0, q, (2 * levels2, 2, n), dtype=np.uint64)
+        x = d.copy()
+        plan.tfhe(x, key2, levels2, base2, rot=rot, out=x)
+        assert np.array_equal(x[0], TO.cmux_rotate(d[0], int(rot[0]), key2, q, base2, levels2))
+
+
+def test_tfhe_argument_rules():
+    q = W.Q62_N1024
+    plan = emu.EmuPlan(10, [q])
+    d = np.zeros((1, 2, 1024), dtype=np.uint64)
+    for levels, base in [(0, 8), (9, 3), (3, 11), (1, 33)]:
+        with pytest.raises(ValueError):
+            plan.tfhe(d, np.zeros((2 * max(levels, 1), 2, 1024), dtype=np.uint64), levels, base)
+    with pytest.raises(ValueError):
+        emu.EmuPlan(9, [q]).tfhe(d[:, :, :512], np.zeros((6, 2, 512), dtype=np.uint64), 3, 8)
+    with pytest.raises(ValueError):
+        emu.EmuPlan(10, [q, W.Q59_N1024]).tfhe(d, np.zeros((6, 2, 1024), dtype=np.uint64), 3, 8)
+    # range check: a non-canonical coefficient sets the status word
+    chk = emu.EmuPlan(10, [q], flags=2)
+    bad = d.copy()
+    bad[0, 1, 3] = q
+    chk.tfhe(bad, np.zeros((6, 2, 1024), dtype=np.uint64), 3, 8)
+    assert chk.status() == -8
