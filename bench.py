@@ -51,7 +51,7 @@ def parse():
                     help="mixed batches: requests of at least 2^k coefficients run their own learned schedule")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "mixed_batch", "tfhe_blind_rotation", "plain_n1024", "cost_model",
-                             "serving", "hmul_fused", "mixed_small", "tfhe_cmux"],
+                             "serving", "hmul_fused", "mixed_small", "tfhe_cmux", "ckks_bconv"],
                     help="the line the driver records is the default (CKKS-HMUL-shaped) workload")
     return ap.parse_args()
 
@@ -737,6 +737,72 @@ def run_tfhe_cmux(args):
     return 0
 
 
+def run_ckks_bconv(args):
+    """Key-switching basis conversion (ModUp of hybrid key switching with one
+    digit): a ciphertext's 2 x 24 limbs at N = 2^16 converted to 24 special
+    primes, one ntt_bconv launch per step, L2 flushed before every step."""
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2410_05934_gb300 import build as B
+    B.build_product()
+    import paper_2410_05934_gb300 as ntt
+    from paper_2410_05934_gb300 import _native
+    from paper_2410_05934_gb300 import workloads as W
+    L_ = _native.load()
+    stream = torch.cuda.current_stream()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    w = W.ckks_bconv(seed=W.DEFAULT_SEED + rank)
+    Q, P, x = w["Q"], w["P"], w["x"]
+    polys, L, K, n = x.shape[0], len(Q), len(P), x.shape[2]
+    conv = ntt.BConv(Q, P)
+    xd = to_dev_np(torch, x)
+    out = torch.empty((polys, K, n), dtype=torch.int64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    def step():
+        conv(xd, out, 16)
+        return 1
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, launches = _events_loop(torch, stream, args.steps, step, flush)
+    clk = clocks.stop()
+    t = sum(ms) * 1e-3
+    coef = polys * n * args.steps
+    macs = coef * L * K
+    peak = _probe(torch, L_, Q[0], 4, sms, stream)
+    hbm_bytes = coef * (L + K) * 8
+    line = {"metric": "RNS basis conversion, coefficients/s (one coefficient = all its limbs)",
+            "value": coef / t, "unit": "coeffs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64", "data": "synthetic", "gpu_launches": launches, "clocks": clk,
+            "config": {"workload": "ckks_bconv", "log2n": 16, "polys": polys, "from_limbs": L, "to_limbs": K,
+                       "moduli": "Q = 24 largest 50-bit primes = 1 mod 2^17, P = the next 24",
+                       "l2": "flushed before every step (512 MiB write, outside the step events)"},
+            "roofline": {"bound": "alu", "achieved": macs / t / 1e9, "peak": peak / 1e9, "unit": "GMAC/s",
+                         "frac": macs / t / peak, "traffic": None,
+                         "peak_source": "in-run probe (kind 4: 64x64->128-bit multiply-accumulate)",
+                         "hbm": {"achieved_gbs": hbm_bytes / t / 1e9,
+                                 "bytes_per_coefficient": (L + K) * 8}}}
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import rns_oracle as RO
+        t0 = time.perf_counter()
+        k = 0
+        while k < 64 or time.perf_counter() - t0 < min(args.cpu_seconds, 10.0):
+            RO.bconv(x[0][:, k * 64:(k + 1) * 64], Q, P)
+            k += 1
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": k * 64 / dt, "unit": "coeffs/s", "cores": 1, "kind": "oracle",
+                                "sample": "%d coefficients of polynomial 0 (the definition in Python integers, "
+                                          "one core)" % (k * 64)}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def run_cost_model(args):
     """Schedule cost model: train on the committed GB300 timing sweep with the
     library's GPU kernels; regret on 100 held-out shapes vs exhaustive tuning."""
@@ -799,6 +865,8 @@ def main():
         return run_serving(args)
     if args.workload == "tfhe_cmux":
         return run_tfhe_cmux(args)
+    if args.workload == "ckks_bconv":
+        return run_ckks_bconv(args)
     if args.workload != WORKLOAD:
         return run_other(args)
     return run_ours(args)

@@ -168,8 +168,10 @@ int ntt_plan_last_launches(ntt_plan_t plan, uint32_t* launches);
  * butterflies in registers with the exact arithmetic of the transform
  * kernels (kind 0: Harvey CT forward butterfly, kind 1: Harvey GS inverse
  * butterfly, both for any q < 2^62; kinds 2 and 3: the forward and inverse
- * butterflies of the small-modulus class, q < 2^57).  Total butterflies =
- * blocks * threads * iters * 8; time it with events on `cuda_stream`.
+ * butterflies of the small-modulus class, q < 2^57; kind 4: a 64 x 64 ->
+ * 128-bit multiply-accumulate, the inner step of ntt_bconv, counted as one
+ * operation).  Total operations = blocks * threads * iters * 8; time it with
+ * events on `cuda_stream`.
  * d_sink (blocks * threads uint64, caller-owned) only defeats dead-code
  * elimination.  Not part of the paper: a measurement aid.
  */
@@ -333,7 +335,8 @@ int ntt_batch_execute_static(const ntt_plan_request_t* reqs, uint32_t n_reqs, vo
  * [-B/2, B/2), e_0 most significant, each digit taken mod q.
  *   tfhe_external_product: out_c = sum_{i, j} e_j(d_i) * K[i l + j][c]
  *   tfhe_cmux_rotate:      out = acc + K [x] (x^a acc - acc)
- * with products in Z_q[x]/(x^N + 1).  Asynchronous on cuda_stream.
+ * with products in Z_q[x]/(x^N + 1).  Asynchronous on cuda_stream; n_ct = 0
+ * launches nothing and does not look at the data pointers.
  * Errors: ARG (plan with several moduli, bad gadget, null pointers), ALIGN,
  * UNSUPPORTED (N), CUDA; with NTT_FLAG_CHECK plans a non-canonical input is
  * reported as NTT_ERR_RANGE through ntt_status.
@@ -346,6 +349,30 @@ int tfhe_external_product(ntt_plan_t plan, const uint64_t* d_in, const uint64_t*
                           uint32_t log2_base, uint64_t* d_out, uint64_t n_ct, void* cuda_stream);
 int tfhe_cmux_rotate(ntt_plan_t plan, const uint64_t* d_acc, const uint32_t* d_rot, const uint64_t* d_key,
                      uint32_t levels, uint32_t log2_base, uint64_t* d_out, uint64_t n_ct, void* cuda_stream);
+
+/*
+ * RNS basis conversion (BConv), the CKKS key-switching operator beside the
+ * NTT (Sec. III, Phase 1): residues of X modulo Q = q_0 ... q_(L-1) become
+ * residues modulo p_0 ... p_(K-1),
+ *   y_j = sum_i [x_i Qhat_i^-1]_{q_i} Qhat_i  mod p_j,   Qhat_i = Q / q_i,
+ * the fast conversion, equal to X + alpha Q (mod p_j) for one integer
+ * 0 <= alpha < L.  Coefficient domain, element by element.
+ *   ntt_bconv_plan  precomputes the constants on the host and copies them to
+ *                   the current device (the plan owns them); every modulus
+ *                   an odd prime < 2^62, distinct within each basis,
+ *                   1 <= L, K <= NTT_BCONV_MAX_MODULI
+ *   ntt_bconv       d_in [n_polys][L][2^log2n] -> d_out [n_polys][K][2^log2n]
+ *                   (device, 8-byte aligned, not overlapping); inputs may be
+ *                   any 64-bit values (each x_i is reduced mod q_i on the way)
+ * Errors: ARG, NOT_PRIME, MODULUS_TOO_LARGE, ALIGN, NOMEM, CUDA.
+ */
+#define NTT_BCONV_MAX_MODULI 64
+typedef struct ntt_bconv_s* ntt_bconv_t;
+
+int ntt_bconv_plan(ntt_bconv_t* out, const uint64_t* q_from, uint32_t L, const uint64_t* p_to, uint32_t K);
+int ntt_bconv(ntt_bconv_t bconv, const uint64_t* d_in, uint64_t* d_out, uint32_t log2n, uint64_t n_polys,
+              void* cuda_stream);
+int ntt_bconv_destroy(ntt_bconv_t bconv);
 
 const char* ntt_strerror(int code);
 

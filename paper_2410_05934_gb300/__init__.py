@@ -3,8 +3,8 @@
 The compute path is the sm_103a library built from ``csrc/`` (C ABI in
 ``include/ntt_gb300.h``); this package only marshals arguments to it.
 """
-from .ntt import (NTT_BATCH_GRAPH, NTT_FLAG_CHECK, NTT_FLAG_HOST_ONLY, Batch, Plan, ntt_forward, ntt_inverse,  # noqa: F401
-                  ntt_plan, poly_mul_pointwise, schedule_count, schedule_name)
+from .ntt import (NTT_BATCH_GRAPH, NTT_FLAG_CHECK, NTT_FLAG_HOST_ONLY, Batch, BConv, Plan, ntt_forward,  # noqa: F401
+                  ntt_inverse, ntt_plan, poly_mul_pointwise, schedule_count, schedule_name)
 from ._native import NttError  # noqa: F401
 
 __version__ = "0.1.0"

@@ -67,6 +67,9 @@ SIGNATURES = [
                            ctypes.c_float, u32, vp]),
     ("tfhe_external_product", i32, [vp, vp, vp, u32, u32, vp, u64, vp]),
     ("tfhe_cmux_rotate", i32, [vp, vp, vp, vp, u32, u32, vp, u64, vp]),
+    ("ntt_bconv_plan", i32, [ctypes.POINTER(vp), U64P, u32, U64P, u32]),
+    ("ntt_bconv", i32, [vp, vp, vp, u32, u64, vp]),
+    ("ntt_bconv_destroy", i32, [vp]),
     ("ntt_strerror", ctypes.c_char_p, [i32]),
     ("ntt_version", ctypes.c_char_p, []),
 ]

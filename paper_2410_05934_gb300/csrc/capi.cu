@@ -343,8 +343,8 @@ int ntt_plan_last_launches(ntt_plan_t plan, uint32_t* launches) {
 
 int ntt_bench_butterflies(uint64_t q, uint32_t kind, uint32_t blocks, uint32_t threads,
                           uint32_t iters, uint64_t* d_sink, void* cuda_stream) {
-    if (q < 3 || q >= (1ull << NTT_MAX_MODULUS_BITS) || kind > 3 ||
-        (kind >= 2 && q >= (1ull << NTT_SMALL_MODULUS_BITS)) || blocks == 0 || threads == 0 ||
+    if (q < 3 || q >= (1ull << NTT_MAX_MODULUS_BITS) || kind > 4 ||
+        ((kind == 2 || kind == 3) && q >= (1ull << NTT_SMALL_MODULUS_BITS)) || blocks == 0 || threads == 0 ||
         threads > 256 || !d_sink)
         return NTT_ERR_ARG;
     return launch_bench_bfly(q, kind, blocks, threads, iters, d_sink, cuda_stream);

@@ -14,6 +14,7 @@
 #include "ntt_launch.h"
 #include "ntt_schedules.h"
 #include "tfhe_cmux.cuh"
+#include "rns.cuh"
 
 namespace nttgb {
 
@@ -473,6 +474,25 @@ int nttemu_tfhe_cmux(void* plan, const uint64_t* in, const uint32_t* rot, const 
     const bool small = p->h.mc != 0;
     if (p->h.log2n == 10) return small ? emu_cmux<10, 1>(c, af, ai) : emu_cmux<10, 0>(c, af, ai);
     return small ? emu_cmux<11, 1>(c, af, ai) : emu_cmux<11, 0>(c, af, ai);
+}
+
+// ntt_bconv on the host: the kernel's per-coefficient arithmetic over
+// in [n_polys][L][n] -> out [n_polys][K][n].
+int nttemu_bconv(const uint64_t* q_from, uint32_t L, const uint64_t* p_to, uint32_t K, const uint64_t* in,
+                 uint64_t* out, uint64_t n, uint64_t n_polys) {
+    std::vector<uint64_t> w;
+    uint32_t chunk = 0;
+    int rc = bconv_constants(q_from, L, p_to, K, w, chunk);
+    if (rc) return rc;
+    const BconvView v = bconv_view(w.data(), L, K, chunk);
+    std::vector<uint64_t> a(L);
+    for (uint64_t poly = 0; poly < n_polys; ++poly)
+        for (uint64_t k = 0; k < n; ++k) {
+            for (uint32_t i = 0; i < L; ++i) a[i] = bconv_a(v, i, in[(poly * L + i) * n + k]);
+            for (uint32_t j = 0; j < K; ++j)
+                out[(poly * K + j) * n + k] = bconv_y(v, j, [&](uint32_t i) { return a[i]; });
+        }
+    return NTT_OK;
 }
 
 int nttemu_status(void* plan) {

@@ -70,7 +70,12 @@ __global__ void __launch_bounds__(256) k_bench_bfly(uint64_t q, uint64_t w0, uin
             if (KIND == 0) ct_butterfly(X[i], Y[i], w, wp, q, two_q);
             else if (KIND == 1) gs_butterfly(X[i], Y[i], w, wp, q, two_q);
             else if (KIND == 2) ct_butterfly_small(X[i], Y[i], w, wp, q, 2 * two_q);
-            else gs_butterfly_small(X[i], Y[i], w, wp, q, 2 * two_q);
+            else if (KIND == 3) gs_butterfly_small(X[i], Y[i], w, wp, q, 2 * two_q);
+            else {   // 64 x 64 -> 128-bit multiply-accumulate (the inner step of the basis conversion)
+                const uint64_t lo = X[i] * w;
+                Y[i] += lo;
+                X[i] += mulhi64(X[i], w) + (Y[i] < lo ? 1u : 0u);
+            }
         }
     }
     uint64_t acc = 0;
@@ -89,7 +94,8 @@ int launch_bench_bfly(uint64_t q, uint32_t kind, uint32_t blocks, uint32_t threa
         case 0: k_bench_bfly<0><<<blocks, threads, 0, st>>>(q, w, wp, iters, sink); break;
         case 1: k_bench_bfly<1><<<blocks, threads, 0, st>>>(q, w, wp, iters, sink); break;
         case 2: k_bench_bfly<2><<<blocks, threads, 0, st>>>(q, w, wp, iters, sink); break;
-        default: k_bench_bfly<3><<<blocks, threads, 0, st>>>(q, w, wp, iters, sink); break;
+        case 3: k_bench_bfly<3><<<blocks, threads, 0, st>>>(q, w, wp, iters, sink); break;
+        default: k_bench_bfly<4><<<blocks, threads, 0, st>>>(q, w, wp, iters, sink); break;
     }
     return cudaPeekAtLastError() == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
 }

@@ -33,6 +33,11 @@ struct PlanHost {
 int build_plan_host(PlanHost& h, uint32_t log2n, const uint64_t* moduli, uint32_t n_moduli,
                     uint32_t batch, uint32_t flags);
 
+// Constant block of an RNS basis conversion Q -> P (layout in rns.cuh) and
+// the number of 128-bit terms one accumulator may hold.
+int bconv_constants(const uint64_t* q_from, uint32_t L, const uint64_t* p_to, uint32_t K,
+                    std::vector<uint64_t>& w, uint32_t& chunk);
+
 // ---- schedules ----
 struct ScheduleInfo {
     uint32_t log2n;

@@ -203,4 +203,59 @@ int build_plan_host(PlanHost& h, uint32_t log2n, const uint64_t* moduli, uint32_
     return NTT_OK;
 }
 
+// ---- RNS basis conversion constants (rns.cuh layout) ----
+
+// Fills the constant block; validates the moduli (odd primes < 2^62,
+// pairwise distinct within and across the two bases).
+int bconv_constants(const uint64_t* q_from, uint32_t L, const uint64_t* p_to, uint32_t K,
+                    std::vector<uint64_t>& w, uint32_t& chunk) {
+    if (!q_from || !p_to || L == 0 || K == 0 || L > NTT_BCONV_MAX_MODULI || K > NTT_BCONV_MAX_MODULI)
+        return NTT_ERR_ARG;
+    std::vector<uint64_t> all(q_from, q_from + L);
+    all.insert(all.end(), p_to, p_to + K);
+    for (uint64_t m : all) {
+        if (m >= (1ull << 62)) return NTT_ERR_MODULUS_TOO_LARGE;
+        if (m < 3 || !is_prime_u64(m)) return NTT_ERR_NOT_PRIME;
+    }
+    for (uint32_t i = 0; i < L; ++i)
+        for (uint32_t k = i + 1; k < L; ++k)
+            if (q_from[i] == q_from[k]) return NTT_ERR_ARG;
+    for (uint32_t j = 0; j < K; ++j)
+        for (uint32_t k = j + 1; k < K; ++k)
+            if (p_to[j] == p_to[k]) return NTT_ERR_ARG;
+    w.assign((size_t)3 * L + 4 * K + (size_t)L * K, 0);
+    uint64_t* q = w.data();
+    uint64_t *qhi = q + L, *qhi_p = q + 2 * L, *p = q + 3 * L;
+    uint64_t *p_one = p + K, *r64 = p + 2 * K, *r64_p = p + 3 * K, *c = p + 4 * K;
+    uint64_t maxq = 0, maxp = 0;
+    for (uint32_t i = 0; i < L; ++i) {
+        q[i] = q_from[i];
+        maxq = std::max(maxq, q[i]);
+        // Qhat_i mod q_i, then its inverse (q_i prime: a^(q-2))
+        uint64_t h = 1;
+        for (uint32_t k = 0; k < L; ++k)
+            if (k != i) h = mul_mod(h, q_from[k] % q[i], q[i]);
+        qhi[i] = pow_mod(h, q[i] - 2, q[i]);
+        qhi_p[i] = shoup_of(qhi[i], q[i]);
+    }
+    for (uint32_t j = 0; j < K; ++j) {
+        p[j] = p_to[j];
+        maxp = std::max(maxp, p[j]);
+        p_one[j] = shoup_of(1, p[j]);
+        r64[j] = (uint64_t)(((u128)1 << 64) % p[j]);
+        r64_p[j] = shoup_of(r64[j], p[j]);
+        for (uint32_t i = 0; i < L; ++i) {
+            uint64_t h = 1;
+            for (uint32_t k = 0; k < L; ++k)
+                if (k != i) h = mul_mod(h, q_from[k] % p[j], p[j]);
+            c[(size_t)i * K + j] = h;
+        }
+    }
+    // terms of one 128-bit sum: chunk * (maxq - 1) * (maxp - 1) < 2^128
+    const u128 term = (u128)(maxq - 1) * (maxp - 1);
+    const u128 n = ~(u128)0 / (term ? term : 1);
+    chunk = (uint32_t)std::min<u128>(n, (u128)(L + 1));
+    return chunk >= 2 ? NTT_OK : NTT_ERR_ARG;
+}
+
 }  // namespace nttgb

@@ -1,0 +1,83 @@
+// RNS basis conversion (BConv) of one coefficient: the CKKS key-switching
+// operator beside the NTT (Sec. III, Phase 1):
+//   a_i = [x_i Qhat_i^-1]_{q_i}                     (Shoup, exact after one csub)
+//   y_j = sum_i a_i [Qhat_i]_{p_j}  mod p_j          (128-bit lazy sum)
+// The products a_i c_ij are summed in a 128-bit accumulator that is folded
+// back below p_j every `chunk` terms (chunk * max q * max p < 2^128), and the
+// final 128-bit value is reduced with two Shoup reductions:
+//   hi 2^64 + lo = [hi]_p [2^64]_p + [lo]_p  (mod p).
+// Host and device, so the host emulation runs the same arithmetic.
+#pragma once
+#include "ntt_arith.cuh"
+
+namespace nttgb {
+
+// Device constant block of a conversion, uint64 words in this order:
+//   q[L], qhi[L], qhi_p[L]            (Qhat_i^-1 mod q_i and its Shoup form)
+//   p[K], p_one[K], r64[K], r64_p[K]  (floor(2^64 / p_j), 2^64 mod p_j, its Shoup form)
+//   c[L][K]                           (Qhat_i mod p_j)
+struct BconvView {
+    const uint64_t *q, *qhi, *qhi_p, *p, *p_one, *r64, *r64_p, *c;
+    uint32_t L, K, chunk;
+};
+
+NTT_HD BconvView bconv_view(const uint64_t* w, uint32_t L, uint32_t K, uint32_t chunk) {
+    BconvView v;
+    v.q = w;
+    v.qhi = w + L;
+    v.qhi_p = w + 2 * L;
+    v.p = w + 3 * L;
+    v.p_one = v.p + K;
+    v.r64 = v.p + 2 * K;
+    v.r64_p = v.p + 3 * K;
+    v.c = v.p + 4 * K;
+    v.L = L;
+    v.K = K;
+    v.chunk = chunk;
+    return v;
+}
+
+NTT_HD uint64_t bconv_ld(const uint64_t* p) {
+#if defined(__CUDA_ARCH__)
+    return __ldg(p);
+#else
+    return *p;
+#endif
+}
+
+// (hi 2^64 + lo) mod p
+NTT_HD uint64_t reduce128(uint64_t hi, uint64_t lo, uint64_t p, uint64_t p_one, uint64_t r64, uint64_t r64_p) {
+    const uint64_t h = csub(shoup_mul(hi, 1, p_one, p), p);
+    const uint64_t l = csub(shoup_mul(lo, 1, p_one, p), p);
+    const uint64_t t = csub(shoup_mul(h, r64, r64_p, p), p);
+    return csub(t + l, p);
+}
+
+// a_i of one coefficient, from x_i (any 64-bit value)
+NTT_HD uint64_t bconv_a(const BconvView& v, uint32_t i, uint64_t x) {
+    const uint64_t q = bconv_ld(v.q + i);
+    return csub(shoup_mul(x, bconv_ld(v.qhi + i), bconv_ld(v.qhi_p + i), q), q);
+}
+
+// y_j of one coefficient from its a_i, read through a(i)
+template <class Get>
+NTT_HD uint64_t bconv_y(const BconvView& v, uint32_t j, Get a) {
+    const uint64_t p = bconv_ld(v.p + j), p_one = bconv_ld(v.p_one + j);
+    const uint64_t r64 = bconv_ld(v.r64 + j), r64_p = bconv_ld(v.r64_p + j);
+    uint64_t hi = 0, lo = 0;
+    uint32_t n = 0;
+    for (uint32_t i = 0; i < v.L; ++i) {
+        const uint64_t ai = a(i), cij = bconv_ld(v.c + (uint64_t)i * v.K + j);
+        const uint64_t pl = ai * cij;
+        lo += pl;
+        hi += mulhi64(ai, cij) + (lo < pl ? 1u : 0u);
+        if (++n == v.chunk) {
+            lo = reduce128(hi, lo, p, p_one, r64, r64_p);
+            hi = 0;
+            n = 1;   // the folded value counts as one more term
+        }
+    }
+    return reduce128(hi, lo, p, p_one, r64, r64_p);
+}
+
+}  // namespace nttgb

@@ -137,6 +137,7 @@ int tfhe_external_product(ntt_plan_t plan, const uint64_t* d_in, const uint64_t*
     TileArgs af, ai;
     int rc = cmux_setup(plan, d_key, levels, log2_base, n_ct, c, af, ai);
     if (rc) return rc;
+    if (n_ct == 0) return cmux_dispatch(plan, c, af, ai, cuda_stream);    // nothing to read or write
     if (!d_in || !d_out) return NTT_ERR_ARG;
     if (((uintptr_t)d_in & 15u) || ((uintptr_t)d_out & 15u)) return NTT_ERR_ALIGN;
     c.in = d_in;
@@ -151,6 +152,7 @@ int tfhe_cmux_rotate(ntt_plan_t plan, const uint64_t* d_acc, const uint32_t* d_r
     TileArgs af, ai;
     int rc = cmux_setup(plan, d_key, levels, log2_base, n_ct, c, af, ai);
     if (rc) return rc;
+    if (n_ct == 0) return cmux_dispatch(plan, c, af, ai, cuda_stream);    // nothing to read or write
     if (!d_acc || !d_rot || !d_out) return NTT_ERR_ARG;
     if (((uintptr_t)d_acc & 15u) || ((uintptr_t)d_out & 15u) || ((uintptr_t)d_rot & 3u)) return NTT_ERR_ALIGN;
     c.in = d_acc;

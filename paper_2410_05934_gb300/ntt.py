@@ -273,6 +273,38 @@ class Batch:
             pass
 
 
+class BConv:
+    """ntt_bconv_plan(Q, P): RNS basis conversion of [n_polys][L][N] residues
+    mod Q into [n_polys][K][N] residues mod P (fast conversion)."""
+
+    def __init__(self, q_from, p_to):
+        L = load()
+        q = (ctypes.c_uint64 * len(q_from))(*[int(v) for v in q_from])
+        p = (ctypes.c_uint64 * len(p_to))(*[int(v) for v in p_to])
+        h = ctypes.c_void_p()
+        check(L.ntt_bconv_plan(ctypes.byref(h), q, len(q_from), p, len(p_to)), "ntt_bconv_plan")
+        self._h = h
+        self.L, self.K = len(q_from), len(p_to)
+
+    def __call__(self, x, out, log2n, n_polys=None, stream=None):
+        n_polys = x.shape[0] if n_polys is None else n_polys
+        n = 1 << log2n
+        check(load().ntt_bconv(self._h, _ptr(x, n_polys * self.L * n, "in"), _ptr(out, n_polys * self.K * n, "out"),
+                               log2n, n_polys, _stream_handle(stream)), "ntt_bconv")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().ntt_bconv_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # C-ABI names as plain functions
 def ntt_plan(log2n, moduli, batch=1, flags=0):
     return Plan(log2n, moduli, batch, flags)

@@ -153,6 +153,17 @@ def tfhe_cmux(seed=DEFAULT_SEED, n_ct=1024, log2n=10, q=Q62_N1024, levels=3, ste
     return dict(log2n=log2n, moduli=[q], levels=levels, acc=acc, rot=rot, key=key)
 
 
+def ckks_bconv(seed=DEFAULT_SEED, log2n=16, L=24, K=24, polys=2):
+    """Key-switching basis conversion of a ciphertext (hybrid key switching
+    with one digit, ModUp): polys x L limbs over Q = POOL50[:L], converted to
+    K special primes P = POOL50[L:L+K]; layout [poly][limb][N]."""
+    n = 1 << log2n
+    Q, P = POOL50[:L], POOL50[L:L + K]
+    per_row = [Q[l] for _ in range(polys) for l in range(L)]
+    x = rows_uniform(seed, 9, per_row, n)
+    return dict(log2n=log2n, Q=Q, P=P, x=x.reshape(polys, L, n))
+
+
 def mixed_requests(seed=DEFAULT_SEED, n_requests=200, max_limbs=32, max_polys=64,
                    log2ns=(10, 12, 14, 16), weights=(0.5, 0.2, 0.2, 0.1)):
     """The uneven request list: (log2n, limbs, polys) per request."""

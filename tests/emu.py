@@ -28,6 +28,8 @@ def lib():
         L.nttemu_hmul_tensor.restype = i32
         L.nttemu_tfhe_cmux.argtypes = [vp, U64P, ctypes.POINTER(ctypes.c_uint32), U64P, u32, u32, U64P, u64]
         L.nttemu_tfhe_cmux.restype = i32
+        L.nttemu_bconv.argtypes = [U64P, u32, U64P, u32, U64P, U64P, u64, u64]
+        L.nttemu_bconv.restype = i32
         _lib = L
     return _lib
 
@@ -100,6 +102,18 @@ class EmuPlan:
 
     def status(self):
         return lib().nttemu_status(self.h)
+
+
+def bconv(x, Q, P):
+    """ntt_bconv's arithmetic on the host: x [n_polys][L][n] -> [n_polys][K][n]."""
+    x = np.ascontiguousarray(x, dtype=np.uint64)
+    q = np.ascontiguousarray(np.array(Q, dtype=np.uint64))
+    p = np.ascontiguousarray(np.array(P, dtype=np.uint64))
+    out = np.zeros((x.shape[0], len(P), x.shape[2]), dtype=np.uint64)
+    rc = lib().nttemu_bconv(_p(q), len(Q), _p(p), len(P), _p(x), _p(out), x.shape[2], x.shape[0])
+    if rc:
+        raise ValueError("nttemu_bconv failed: %d" % rc)
+    return out
 
 
 def schedule_count(log2n):

@@ -235,3 +235,41 @@ def test_tfhe_argument_rules():
     bad[0, 1, 3] = q
     chk.tfhe(bad, np.zeros((6, 2, 1024), dtype=np.uint64), 3, 8)
     assert chk.status() == -8
+
+
+@pytest.mark.parametrize("L,K", [(5, 3), (24, 24), (3, 40)])
+def test_bconv_matches_oracle(L, K):
+    """ntt_bconv's per-coefficient arithmetic (128-bit sums folded every
+    `chunk` terms) against the oracle's definition, on 50- and 62-bit bases."""
+    from oracle import rns_oracle as RO
+    Q = W.POOL50[:L] if L <= 24 else W.POOL50[:L]
+    P = W.POOL50[L:L + K] if L + K <= 48 else [W.Q62_N1024, W.Q59_N1024] + W.POOL50[L + 2:L + K]
+    rng = np.random.default_rng(L * 100 + K)
+    x = np.stack([np.array([rng.integers(0, q, 40, dtype=np.uint64) for q in Q]) for _ in range(2)])
+    got = emu.bconv(x, Q, P)
+    for p in range(2):
+        assert np.array_equal(got[p], RO.bconv(x[p], Q, P))
+
+
+def test_bconv_62_bit_moduli_fold_the_accumulator():
+    """62-bit primes on both sides: chunk = 16 terms, so 40 source limbs fold twice."""
+    from oracle import rns_oracle as RO
+    import sympy
+    qs, c = [], (1 << 62) - 1
+    while len(qs) < 43:
+        if sympy.isprime(c):
+            qs.append(c)
+        c -= 2
+    Q, P = qs[:40], qs[40:]
+    rng = np.random.default_rng(3)
+    x = np.array([[rng.integers(0, q, 8, dtype=np.uint64) for q in Q]])
+    assert np.array_equal(emu.bconv(x, Q, P)[0], RO.bconv(x[0], Q, P))
+
+
+def test_bconv_argument_rules():
+    with pytest.raises(ValueError):
+        emu.bconv(np.zeros((1, 2, 4), np.uint64), [W.POOL50[0], W.POOL50[0]], [W.POOL50[1]])   # repeated
+    with pytest.raises(ValueError):
+        emu.bconv(np.zeros((1, 1, 4), np.uint64), [W.POOL50[0]], [15])                          # not prime
+    with pytest.raises(ValueError):
+        emu.bconv(np.zeros((1, 1, 4), np.uint64), [W.POOL50[0]], [(1 << 62) + 135])             # too large

@@ -1,0 +1,71 @@
+"""RNS basis conversion on the GPU (C ABI ntt_bconv) against the oracle's
+definition: the key-switching shape (24 limbs -> 24 special primes) at
+N = 2^16 on sampled coefficients, full rows at small N, 62-bit bases whose
+128-bit sums fold, non-canonical inputs, empty calls and argument errors."""
+import numpy as np
+import pytest
+
+from paper_2410_05934_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2410_05934_gb300 as ntt  # noqa: E402
+from gpu_util import to_dev, to_host  # noqa: E402
+from oracle import rns_oracle as RO  # noqa: E402
+
+
+def test_key_switching_shape_sampled():
+    w = W.ckks_bconv()
+    Q, P, x = w["Q"], w["P"], w["x"]
+    b = ntt.BConv(Q, P)
+    out = torch.empty((x.shape[0], len(P), 1 << 16), dtype=torch.int64, device="cuda")
+    b(to_dev(x), out, 16)
+    got = to_host(out)
+    rng = np.random.default_rng(1)
+    idx = np.concatenate([[0, 1, 65535], rng.integers(0, 1 << 16, 61)])
+    for p in range(x.shape[0]):
+        assert np.array_equal(got[p][:, idx], RO.bconv(x[p][:, idx], Q, P)), p
+
+
+@pytest.mark.parametrize("log2n,L,K", [(10, 5, 3), (12, 3, 40), (1, 2, 2)])
+def test_full_rows_small(log2n, L, K):
+    Q = W.POOL50[:L]
+    P = W.POOL50[L:L + K] if L + K <= 48 else [W.Q62_N1024, W.Q59_N1024] + W.POOL50[L + 2:L + K]
+    rng = np.random.default_rng(log2n)
+    x = np.stack([np.array([rng.integers(0, q, 1 << log2n, dtype=np.uint64) for q in Q]) for _ in range(3)])
+    out = torch.empty((3, K, 1 << log2n), dtype=torch.int64, device="cuda")
+    ntt.BConv(Q, P)(to_dev(x), out, log2n)
+    got = to_host(out)
+    for p in range(3):
+        assert np.array_equal(got[p], RO.bconv(x[p], Q, P))
+
+
+def test_62_bit_bases_and_noncanonical_inputs():
+    from oracle import oracle as O
+    qs, c = [], (1 << 62) - 1
+    while len(qs) < 43:
+        if O.is_prime(c):
+            qs.append(c)
+        c -= 2
+    Q, P = qs[:40], qs[40:]
+    rng = np.random.default_rng(7)
+    x = np.array([[rng.integers(0, 1 << 63, 256, dtype=np.uint64) | np.uint64(1 << 63) for _ in Q]])
+    out = torch.empty((1, 3, 256), dtype=torch.int64, device="cuda")
+    ntt.BConv(Q, P)(to_dev(x), out, 8)
+    xr = np.array([[int(v) % q for v in row] for row, q in zip(x[0], Q)], dtype=np.uint64)
+    assert np.array_equal(to_host(out)[0], RO.bconv(xr, Q, P))
+
+
+def test_empty_call_and_errors():
+    b = ntt.BConv(W.POOL50[:2], W.POOL50[2:3])
+    x = torch.zeros((1, 2, 16), dtype=torch.int64, device="cuda")
+    b(x, torch.empty((1, 1, 16), dtype=torch.int64, device="cuda"), 4, n_polys=0)
+    for q, p, code in [([W.POOL50[0]] * 2, [W.POOL50[1]], -1), ([W.POOL50[0]], [15], -2),
+                       ([W.POOL50[0]], [(1 << 62) + 135], -4), ([], [W.POOL50[1]], -1)]:
+        with pytest.raises(ntt.NttError) as e:
+            ntt.BConv(q, p)
+        assert e.value.code == code, (q, p)
