@@ -51,7 +51,8 @@ def parse():
                     help="mixed batches: requests of at least 2^k coefficients run their own learned schedule")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "mixed_batch", "tfhe_blind_rotation", "plain_n1024", "cost_model",
-                             "serving", "hmul_fused", "mixed_small", "tfhe_cmux", "ckks_bconv"],
+                             "serving", "hmul_fused", "mixed_small", "tfhe_cmux", "ckks_bconv",
+                             "ckks_rescale"],
                     help="the line the driver records is the default (CKKS-HMUL-shaped) workload")
     return ap.parse_args()
 
@@ -803,6 +804,62 @@ def run_ckks_bconv(args):
     return 0
 
 
+def run_ckks_rescale(args):
+    """CKKS Rescale of a ciphertext in the NTT domain: 2 polynomials x 24
+    limbs at N = 2^16 -> 23 limbs (strided copy of the dropped limb, its
+    INTT, one forward NTT per remaining limb with the Rescale load and
+    epilogue fused), L2 flushed before every step."""
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2410_05934_gb300 import build as B
+    B.build_product()
+    import paper_2410_05934_gb300 as ntt
+    from paper_2410_05934_gb300 import _native
+    from paper_2410_05934_gb300 import workloads as W
+    L_ = _native.load()
+    stream = torch.cuda.current_stream()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    w = W.ckks_hmul_n65536(seed=W.DEFAULT_SEED + rank, limbs=24, polys=2)
+    Q, x = w["moduli"], w["x"]
+    n, L = 1 << 16, len(Q)
+    plan = ntt.Plan(16, Q, 2)
+    xd = to_dev_np(torch, x)
+    out = torch.empty((2, L - 1, n), dtype=torch.int64, device="cuda")
+    work = torch.empty((2, n), dtype=torch.int64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    def step():
+        plan.rescale(xd, out, work)
+        return plan.last_launches()
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, launches = _events_loop(torch, stream, args.steps, step, flush)
+    clk = clocks.stop()
+    t = sum(ms) * 1e-3
+    rows = 2 + 2 * (L - 1)                           # INTT rows + forward rows
+    coef = rows * n * args.steps
+    bfly = rows * (n // 2) * 16 * args.steps
+    peak = _probe(torch, L_, Q[0], 2, sms, stream)
+    line = {"metric": "NTT coeffs/s (coefficient-transforms per second)", "value": coef / t, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "gpu_launches": launches, "clocks": clk,
+            "config": {"workload": "ckks_rescale", "log2n": 16, "polys": 2, "limbs": L,
+                       "step": "Rescale by q_23: copy + INTT of 2 rows, fused NTT + epilogue of 46 rows",
+                       "l2": "flushed before every step (512 MiB write, outside the step events)"},
+            "rescales_per_s": 2 * args.steps / t,
+            "roofline": {"bound": "alu", "achieved": bfly / t / 1e9, "peak": peak / 1e9, "unit": "Gbutterfly/s",
+                         "frac": bfly / t / peak, "traffic": None,
+                         "peak_source": "in-run butterfly probe (kind 2, small-modulus class)"}}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def run_cost_model(args):
     """Schedule cost model: train on the committed GB300 timing sweep with the
     library's GPU kernels; regret on 100 held-out shapes vs exhaustive tuning."""
@@ -867,6 +924,8 @@ def main():
         return run_tfhe_cmux(args)
     if args.workload == "ckks_bconv":
         return run_ckks_bconv(args)
+    if args.workload == "ckks_rescale":
+        return run_ckks_rescale(args)
     if args.workload != WORKLOAD:
         return run_other(args)
     return run_ours(args)

@@ -112,6 +112,26 @@ int ntt_inverse_rows(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, uin
  * mod q_l(r) over n_polys * n_moduli rows (n_polys = 0 means the plan's
  * batch).  Row r uses modulus r mod n_moduli.  d_c may alias d_a or d_b.
  */
+/*
+ * CKKS Rescale of NTT-domain ciphertext limbs (Sec. II-A: after a
+ * multiplication the scale is brought back to Delta and one level is
+ * dropped): for the plan's moduli q_0 .. q_(L-1) and every polynomial,
+ *   out_i = round(X / q_(L-1)) mod q_i,  i < L - 1,
+ * X the integer with residues in_0 .. in_(L-1) (coefficient by coefficient),
+ * computed as INTT of the last limb, then per remaining limb a forward NTT of
+ * c = (h - [w + h]_{q_(L-1)}) mod q_i (h = floor(q_(L-1) / 2), w the last
+ * limb's coefficients) fused with (in_i + NTT(c)) * q_(L-1)^-1 mod q_i.
+ *   d_in    [n_polys][L][N] NTT domain (bit-reversed order), canonical
+ *   d_out   [n_polys][L-1][N] NTT domain; must not overlap d_in or d_work
+ *   d_work  [n_polys][N] caller-owned scratch (the last limb's coefficients)
+ *   n_polys 0 = the plan's batch; at most the plan's batch
+ * The plan needs L >= 2 and a last modulus distinct from the others.  One
+ * strided copy and two or three kernel launches on cuda_stream.
+ * Errors: ARG, ALIGN, UNSUPPORTED, CUDA.
+ */
+int ntt_rescale(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, uint64_t* d_work, uint32_t n_polys,
+                void* cuda_stream);
+
 int poly_mul_pointwise(ntt_plan_t plan, const uint64_t* d_a, const uint64_t* d_b, uint64_t* d_c,
                        uint32_t n_polys, void* cuda_stream);
 

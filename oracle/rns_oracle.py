@@ -74,7 +74,7 @@ def rescale_ntt(x_ntt, Q, idx=None):
     L, n = x_ntt.shape
     ql = int(Q[-1])
     h = ql // 2
-    last = O.ntt_inverse(x_ntt[L - 1], ql)
+    last = O.transform_rows(x_ntt[L - 1:L], [ql], inverse=True, split=n >= 4096)[0]
     r = (last.astype(object) + h) % ql
     width = n if idx is None else len(idx)
     out = np.zeros((L - 1, width), dtype=np.uint64)

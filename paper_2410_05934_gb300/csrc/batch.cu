@@ -157,6 +157,7 @@ __global__ void __launch_bounds__(NTT_BATCH_THREADS, BatchOcc<MC, NMAX>::ctas)
         a.mod_magic = 0;
         a.src_mode = 0;
         a.in_b = nullptr;
+        a.aux_q = 0;
         if (rq.inverse)
             batch_dispatch<true, MC, NMAX>(a, rq, it.n_rows, smem);
         else
@@ -246,6 +247,7 @@ __global__ void __launch_bounds__(NTT_BATCH_THREADS, NTT_BATCH_MIN_CTAS)
         a.mod_magic = 0;
         a.src_mode = 0;
         a.in_b = nullptr;
+        a.aux_q = 0;
         if (sr.inverse)
             batch_dispatch<true, MC, 16>(a, rq, n_rows, smem);
         else
@@ -527,6 +529,7 @@ static int batch_launch_request(ntt_batch_t b, size_t i, uint32_t sid, cudaStrea
     d.mc = b->tables[r.log2n].host.mc;
     d.src_mode = 0;
     d.in_b = nullptr;
+    d.aux_q = 0;
     const LaunchFn fn = r.inverse ? table[idx].inv : table[idx].fwd;
     return fn(d, r.in, r.out, 0, (uint64_t)r.n_polys * r.n_moduli, st, launches);
 }

@@ -111,6 +111,7 @@ static PlanDev plan_dev(const ntt_plan_s* p) {
     d.mc = p->h.mc;
     d.src_mode = 0;
     d.in_b = nullptr;
+    d.aux_q = 0;
     return d;
 }
 
@@ -267,6 +268,65 @@ int ntt_hmul_tensor(ntt_plan_t plan, const uint64_t* d_a, const uint64_t* d_b, u
     d.src_mode = 1;
     d.in_b = d_b;
     return g_table[idx].inv(d, d_a, d_out, 0, 3ull * plan->h.n_moduli, cuda_stream, &plan->last_launches);
+}
+
+int ntt_rescale(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, uint64_t* d_work, uint32_t n_polys,
+                void* cuda_stream) {
+    if (!plan || !d_in || !d_out || !d_work) return NTT_ERR_ARG;
+    if (!aligned16(d_in) || !aligned16(d_out) || !aligned16(d_work)) return NTT_ERR_ALIGN;
+    const uint32_t L = plan->h.n_moduli;
+    if (L < 2) return NTT_ERR_ARG;
+    if (n_polys == 0) n_polys = plan->h.batch;
+    if (n_polys > plan->h.batch) return NTT_ERR_ARG;
+    for (uint32_t i = 0; i + 1 < L; ++i)
+        if (plan->h.consts[i].rs_inv == 0) return NTT_ERR_ARG;     // the last modulus repeats an earlier one
+    int rc = check_device(plan);
+    if (rc) return rc;
+    plan->last_launches = 0;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const uint32_t log2n = plan->h.log2n;
+    const size_t n = (size_t)1 << log2n;
+    // 1. the dropped limb's rows (every L-th row) into the work buffer
+    if (cudaMemcpy2DAsync(d_work, n * sizeof(uint64_t), d_in + (size_t)(L - 1) * n, (size_t)L * n * sizeof(uint64_t),
+                          n * sizeof(uint64_t), n_polys, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return NTT_ERR_CUDA;
+    // 2. back to coefficients under the dropped modulus (the plan's schedule)
+    int idx = sched_index(log2n, plan->schedule);
+    if (idx < 0) return NTT_ERR_UNSUPPORTED;
+    PlanDev last = plan_dev(plan);
+    last.fwd = plan->d_fwd + (size_t)(L - 1) * n;
+    last.inv = plan->d_inv + (size_t)(L - 1) * n;
+    last.lc = plan->d_consts + (L - 1);
+    last.n_moduli = 1;
+    last.check = 0;
+    last.mc = plan->h.consts[L - 1].q < (1ull << NTT_SMALL_MODULUS_BITS) ? 1u : 0u;
+    rc = g_table[idx].inv(last, d_work, d_work, 0, n_polys, cuda_stream, &plan->last_launches);
+    if (rc) return rc;
+    // 3. forward transform of c = (h - [w + h]) mod q_i with the Rescale
+    //    epilogue, over the n_polys x (L - 1) output rows (direct-form first kernel)
+    auto forward_first_pipelined = [](int k) { return (g_params[k].kind == 1 ? g_params[k].pipe
+                                                                          : form_col(g_params[k].pipe)) == 1; };
+    if (forward_first_pipelined(idx)) {
+        idx = -1;
+        for (uint32_t id = 0; (int)id < schedule_count(log2n); ++id) {
+            const int k = sched_index(log2n, id);
+            if (!forward_first_pipelined(k)) {
+                idx = k;
+                break;
+            }
+        }
+        if (idx < 0) return NTT_ERR_UNSUPPORTED;
+    }
+    PlanDev d = plan_dev(plan);
+    d.n_moduli = L - 1;
+    d.check = 0;
+    d.mc = 1;
+    for (uint32_t i = 0; i + 1 < L; ++i)
+        if (plan->h.consts[i].q >= (1ull << NTT_SMALL_MODULUS_BITS)) d.mc = 0;
+    d.src_mode = 2;
+    d.in_b = d_in;
+    d.aux_q = plan->h.moduli[L - 1];
+    return g_table[idx].fwd(d, d_work, d_out, 0, (uint64_t)n_polys * (L - 1), cuda_stream, &plan->last_launches);
 }
 
 int poly_mul_pointwise(ntt_plan_t plan, const uint64_t* d_a, const uint64_t* d_b, uint64_t* d_c,

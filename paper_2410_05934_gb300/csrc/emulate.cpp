@@ -115,6 +115,7 @@ static TileArgs emu_args(const PlanDev& p, const uint64_t* in, uint64_t* out, ui
     a.mod_magic = fdiv_magic(a.n_moduli);
     a.src_mode = p.src_mode;
     a.in_b = p.in_b;
+    a.aux_q = p.aux_q;
     return a;
 }
 
@@ -274,7 +275,7 @@ static int emu_cmux(const CmuxArgs& c, const TileArgs& af, const TileArgs& ai) {
     using F = typename K::F;
     using I = typename K::I;
     if (!verify_cfg<F>() || !verify_cfg<I>()) return NTT_ERR_UNSUPPORTED;
-    std::vector<uint64_t> smem(2 * (size_t)K::N, 0xdeadbeefdeadbeefull);
+    std::vector<uint64_t> smem(K::SMEM_BYTES / sizeof(uint64_t), 0xdeadbeefdeadbeefull);
     std::vector<CmuxRegs<K>> cr(K::THREADS);
     std::vector<TileRegs<F>> sf(K::THREADS);
     std::vector<TileRegs<I>> si(K::THREADS);
@@ -286,7 +287,14 @@ static int emu_cmux(const CmuxArgs& c, const TileArgs& af, const TileArgs& ai) {
     L[0].gbase = 0;
     L[0].tw_off = 0;
     L[0].valid = true;
+    // each slot's own TileLoc (its tw_off points at the staged twiddles)
+    std::vector<TileLoc> Lf[2] = {L, L}, Lv[2] = {L, L};
+    for (int s = 0; s < 2; ++s) {
+        Lf[s][0].tw_off = K::tw_off(s, false);
+        Lv[s][0].tw_off = K::tw_off(s, true);
+    }
     const LimbConst lc = af.lc[0];
+    for (int tid = 0; tid < K::THREADS; ++tid) cmux_stage_twiddles<K>(af.tw, ai.tw, tid, smem.data());
     for (uint64_t ct = 0; ct < c.n_ct; ++ct) {
         for (int tid = 0; tid < K::THREADS; ++tid)
             cmux_load<K>(cr[tid], c, ct, tid >> K::LOGT, tid & (K::T - 1));
@@ -294,11 +302,11 @@ static int emu_cmux(const CmuxArgs& c, const TileArgs& af, const TileArgs& ai) {
             for (int tid = 0; tid < K::THREADS; ++tid) {
                 const int s = tid >> K::LOGT, t = tid & (K::T - 1);
                 cmux_digits<K>(sf[tid], cr[tid], j, c);
-                write_pairs_swizzled<F>(sf[tid], L[0], t, smem.data() + (size_t)s * K::N);
+                write_pairs_swizzled<F>(sf[tid], Lf[s][0], t, smem.data() + (size_t)s * K::N);
             }
             for (int s = 0; s < 2; ++s) {
                 std::vector<TileRegs<F>> part(sf.begin() + s * K::T, sf.begin() + (s + 1) * K::T);
-                emu_passes<F, 0>(part, af, L, smem.data() + (size_t)s * K::N);
+                emu_passes<F, 0>(part, af, Lf[s], smem.data() + (size_t)s * K::N);
                 std::copy(part.begin(), part.end(), sf.begin() + s * K::T);
             }
             for (int tid = 0; tid < K::THREADS; ++tid) {
@@ -317,11 +325,11 @@ static int emu_cmux(const CmuxArgs& c, const TileArgs& af, const TileArgs& ai) {
         for (int tid = 0; tid < K::THREADS; ++tid) {
             const int s = tid >> K::LOGT, t = tid & (K::T - 1);
             cmux_inverse_input<K>(si[tid], cr[tid], s);
-            write_pairs_swizzled<I>(si[tid], L[0], t, smem.data() + (size_t)s * K::N);
+            write_pairs_swizzled<I>(si[tid], Lv[s][0], t, smem.data() + (size_t)s * K::N);
         }
         for (int s = 0; s < 2; ++s) {
             std::vector<TileRegs<I>> part(si.begin() + s * K::T, si.begin() + (s + 1) * K::T);
-            emu_passes<I, 0>(part, ai, L, smem.data() + (size_t)s * K::N);
+            emu_passes<I, 0>(part, ai, Lv[s], smem.data() + (size_t)s * K::N);
         }
         for (int tid = 0; tid < K::THREADS; ++tid) {
             const int s = tid >> K::LOGT, t = tid & (K::T - 1);
@@ -381,6 +389,7 @@ int nttemu_transform(void* plan, uint32_t sched, int inverse, const uint64_t* in
     d.mc = p->h.mc;
     d.src_mode = 0;
     d.in_b = nullptr;
+    d.aux_q = 0;
     return (inverse ? e->inv : e->fwd)(d, in, out, row_begin, n_rows);
 }
 
@@ -400,6 +409,7 @@ int nttemu_batch_transform(void* plan, int inverse, const uint64_t* in, uint64_t
         d.mc = p->h.mc;
         d.src_mode = 0;
         d.in_b = nullptr;
+        d.aux_q = 0;
         return (inverse ? e.inv : e.fwd)(d, in, out, 0, p->h.rows);
     }
     return NTT_ERR_UNSUPPORTED;
@@ -422,6 +432,7 @@ int nttemu_hmul_tensor(void* plan, uint32_t sched, const uint64_t* a, const uint
     d.mc = p->h.mc;
     d.src_mode = 1;
     d.in_b = b;
+    d.aux_q = 0;
     return e->inv(d, a, out, 0, 3ull * p->h.n_moduli);
 }
 
@@ -476,6 +487,46 @@ int nttemu_tfhe_cmux(void* plan, const uint64_t* in, const uint32_t* rot, const 
     return small ? emu_cmux<11, 1>(c, af, ai) : emu_cmux<11, 0>(c, af, ai);
 }
 
+// ntt_rescale on the host with schedule `sched` for both transforms (its
+// first forward kernel must be in the direct form).
+int nttemu_rescale(void* plan, uint32_t sched, const uint64_t* in, uint64_t* out, uint64_t* work, uint32_t n_polys) {
+    EmuPlan* p = static_cast<EmuPlan*>(plan);
+    if (!p || !in || !out || !work) return NTT_ERR_ARG;
+    const uint32_t L = p->h.n_moduli;
+    if (L < 2 || n_polys == 0 || n_polys > p->h.batch) return NTT_ERR_ARG;
+    for (uint32_t i = 0; i + 1 < L; ++i)
+        if (p->h.consts[i].rs_inv == 0) return NTT_ERR_ARG;
+    const EmuEntry* e = emu_find(p->h.log2n, sched);
+    if (!e) return NTT_ERR_ARG;
+    const size_t n = (size_t)1 << p->h.log2n;
+    for (uint32_t k = 0; k < n_polys; ++k) memcpy(work + k * n, in + ((size_t)k * L + L - 1) * n, n * sizeof(uint64_t));
+    PlanDev last;
+    last.fwd = p->h.fwd.data() + (size_t)(L - 1) * n;
+    last.inv = p->h.inv.data() + (size_t)(L - 1) * n;
+    last.lc = p->h.consts.data() + (L - 1);
+    last.status = &p->status;
+    last.n_moduli = 1;
+    last.check = 0;
+    last.mc = p->h.consts[L - 1].q < (1ull << NTT_SMALL_MODULUS_BITS) ? 1u : 0u;
+    last.src_mode = 0;
+    last.in_b = nullptr;
+    last.aux_q = 0;
+    int rc = e->inv(last, work, work, 0, n_polys);
+    if (rc) return rc;
+    PlanDev d = last;
+    d.fwd = p->h.fwd.data();
+    d.inv = p->h.inv.data();
+    d.lc = p->h.consts.data();
+    d.n_moduli = L - 1;
+    d.mc = 1;
+    for (uint32_t i = 0; i + 1 < L; ++i)
+        if (p->h.consts[i].q >= (1ull << NTT_SMALL_MODULUS_BITS)) d.mc = 0;
+    d.src_mode = 2;
+    d.in_b = in;
+    d.aux_q = p->h.moduli[L - 1];
+    return e->fwd(d, work, out, 0, (uint64_t)n_polys * (L - 1));
+}
+
 // ntt_bconv on the host: the kernel's per-coefficient arithmetic over
 // in [n_polys][L][n] -> out [n_polys][K][n].
 int nttemu_bconv(const uint64_t* q_from, uint32_t L, const uint64_t* p_to, uint32_t K, const uint64_t* in,
@@ -489,8 +540,18 @@ int nttemu_bconv(const uint64_t* q_from, uint32_t L, const uint64_t* p_to, uint3
     for (uint64_t poly = 0; poly < n_polys; ++poly)
         for (uint64_t k = 0; k < n; ++k) {
             for (uint32_t i = 0; i < L; ++i) a[i] = bconv_a(v, i, in[(poly * L + i) * n + k]);
-            for (uint32_t j = 0; j < K; ++j)
-                out[(poly * K + j) * n + k] = bconv_y(v, j, [&](uint32_t i) { return a[i]; });
+            auto get = [&](uint32_t i) { return a[i]; };
+            uint32_t j = 0;
+            for (; j + 4 <= K; j += 4) {
+                uint64_t y[4];
+                bconv_y<4>(v, j, get, y);
+                for (int u = 0; u < 4; ++u) out[(poly * K + j + u) * n + k] = y[u];
+            }
+            for (; j < K; ++j) {
+                uint64_t y[1];
+                bconv_y<1>(v, j, get, y);
+                out[(poly * K + j) * n + k] = y[0];
+            }
         }
     return NTT_OK;
 }

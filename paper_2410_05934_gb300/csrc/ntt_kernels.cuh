@@ -203,6 +203,7 @@ int launch_tile_kernel(const PlanDev& p, const uint64_t* in, uint64_t* out, uint
     a.mod_magic = fdiv_magic(a.n_moduli);
     a.src_mode = p.src_mode;
     a.in_b = p.in_b;
+    a.aux_q = p.aux_q;
     if (C::PIPE && C::FIRST && p.src_mode) return NTT_ERR_UNSUPPORTED;  // direct form only
     const uint64_t groups = (a.n_tiles + C::TPC - 1) / C::TPC;
     if (groups == 0) return NTT_OK;

@@ -15,8 +15,10 @@ struct PlanDev {
     uint32_t n_moduli;
     uint32_t check;
     uint32_t mc;        // modulus class: 1 when every modulus is below 2^57
-    uint32_t src_mode;  // 1: the inverse's first kernel computes the CKKS tensor product
+    uint32_t src_mode;  // 1: the inverse's first kernel computes the CKKS tensor product;
+                        // 2: the forward transform is the Rescale by aux_q (TileArgs)
     const uint64_t* in_b;
+    uint64_t aux_q;
 };
 
 // Transforms rows [row_begin, row_begin + n_rows) of the layout that starts

@@ -57,6 +57,7 @@ struct LimbConst {
     uint64_t ninv, ninv_p;      // N^-1 mod q and its Shoup form
     uint64_t w1ninv, w1ninv_p;  // psi^{-brv(1)} N^-1 and its Shoup form (last GS stage)
     uint64_t mu;                // Barrett constant floor(2^(2 bits) / q)
+    uint64_t rs_inv, rs_inv_p;  // q_last^-1 mod q and its Shoup form (Rescale; 0 for the last limb)
     uint32_t bits, pad_;
 };
 
@@ -77,12 +78,18 @@ struct TileArgs {
     uint32_t check;         // verify canonical inputs (first kernel only)
     uint32_t fast32;        // tile and row indices below 2^32: use the reciprocal below
     uint64_t mod_magic;     // ceil(2^64 / n_moduli)  (n_moduli >= 2)
-    // source mode of the first kernel of an inverse transform: 0 = read `in`;
-    // 1 = CKKS tensor product, row r = k * n_moduli + l computes d_k of limb l
-    // from in = [a0; a1] and in_b = [b0; b1] (each [2][n_moduli][N], NTT domain):
-    // d0 = a0 b0, d1 = a0 b1 + a1 b0, d2 = a1 b1
+    // source mode: 0 = read `in`;
+    // 1 (first kernel of an inverse) = CKKS tensor product, row r = k * n_moduli + l
+    //   computes d_k of limb l from in = [a0; a1] and in_b = [b0; b1] (each
+    //   [2][n_moduli][N], NTT domain): d0 = a0 b0, d1 = a0 b1 + a1 b0, d2 = a1 b1;
+    // 2 (forward) = Rescale by the modulus aux_q: row r = p * n_moduli + i of
+    //   the output reads the coefficients w of the dropped limb of polynomial p
+    //   from in (row p) and transforms c = (h - [w + h]_aux_q) mod q_i,
+    //   h = floor(aux_q / 2); the last kernel adds row p * (n_moduli + 1) + i
+    //   of in_b (the NTT-domain input) and multiplies by aux_q^-1 mod q_i
     uint32_t src_mode;
     const uint64_t* in_b;
+    uint64_t aux_q;
 };
 
 // floor(n / d) for n < 2^32 and 2 <= d < 2^32 from M = ceil(2^64 / d):
@@ -389,6 +396,26 @@ NTT_HD void load_direct(TileRegs<C>& st, const TileArgs& a, const TileLoc& L, in
         }
         return;
     }
+    if (C::FIRST && !C::INV && a.src_mode == 2) {
+        // Rescale: c = (h - [w + h]_aux_q) mod q from the dropped limb's coefficients
+        const LimbConst lc = a.lc[L.limb];
+        const uint64_t h = a.aux_q >> 1;
+        const uint64_t hq = csub(shoup_mul(h, 1, lc.one_p, lc.q), lc.q);
+        const uint64_t* w = a.in + (L.rowq << C::LOGN) + gt;
+#pragma unroll
+        for (int i = 0; i < C::R / 2; ++i) {
+            const uint32_t off = place<C>(2u * (uint32_t)i * C::T);
+            NTT_GMEM_CHECK(gt + off + 1, 1u << C::LOGN);
+            uint64_t w0, w1;
+            load_pair(w + off, w0, w1);
+            const uint64_t r0 = csub(w0 + h, a.aux_q), r1 = csub(w1 + h, a.aux_q);   // w, h < aux_q
+            const uint64_t m0 = csub(shoup_mul(r0, 1, lc.one_p, lc.q), lc.q);
+            const uint64_t m1 = csub(shoup_mul(r1, 1, lc.one_p, lc.q), lc.q);
+            st.x[2 * i] = hq >= m0 ? hq - m0 : hq + (lc.q - m0);
+            st.x[2 * i + 1] = hq >= m1 ? hq - m1 : hq + (lc.q - m1);
+        }
+        return;
+    }
     const uint64_t* src = (C::FIRST ? a.in : a.out) + (L.row << C::LOGN) + gt;
     bool bad = false;
 #pragma unroll
@@ -582,6 +609,14 @@ NTT_HD void store_tile(const TileArgs& a, const TileLoc& L, int t, const uint64_
         }
         const uint32_t off = place<C>(2u * (uint32_t)i * C::T);
         NTT_GMEM_CHECK(gt + off + 1, 1u << C::LOGN);
+        if (C::LAST && !C::INV && a.src_mode == 2) {
+            // Rescale: (x_i + c) * aux_q^-1 with x_i the NTT-domain input row p * (n_moduli + 1) + i
+            const LimbConst& lc = a.lc[L.limb];
+            uint64_t u, v;
+            load_pair(a.in_b + ((L.row + L.rowq) << C::LOGN) + gt + off, u, v);
+            x = csub(shoup_mul(csub(x + u, q), lc.rs_inv, lc.rs_inv_p, q), q);
+            y = csub(shoup_mul(csub(y + v, q), lc.rs_inv, lc.rs_inv_p, q), q);
+        }
         store_pair(dst + off, x, y);
     }
 }

@@ -199,6 +199,11 @@ int build_plan_host(PlanHost& h, uint32_t log2n, const uint64_t* moduli, uint32_
         c.w1ninv_p = shoup_of(c.w1ninv, q);
         c.bits = bit_length(q);
         c.mu = (uint64_t)(((u128)1 << (2 * c.bits)) / q);
+        if (l + 1 < n_moduli) {      // Rescale drops the last modulus: its inverse mod q
+            const uint64_t ql = moduli[n_moduli - 1] % q;
+            c.rs_inv = ql ? pow_mod(ql, q - 2, q) : 0;
+            c.rs_inv_p = shoup_of(c.rs_inv, q);
+        }
     }
     return NTT_OK;
 }

@@ -35,9 +35,19 @@ __global__ void __launch_bounds__(NTT_BCONV_THREADS) k_bconv(const uint64_t* __r
         for (uint32_t i = 0; i < L; ++i)
             sa[(size_t)i * NTT_BCONV_THREADS + threadIdx.x] = bconv_a(v, i, src[(uint64_t)i << log2n]);
         uint64_t* dst = out + ((poly * K) << log2n) + k;
-        for (uint32_t j = 0; j < K; ++j)
-            dst[(uint64_t)j << log2n] =
-                bconv_y(v, j, [&](uint32_t i) { return sa[(size_t)i * NTT_BCONV_THREADS + threadIdx.x]; });
+        auto a = [&](uint32_t i) { return sa[(size_t)i * NTT_BCONV_THREADS + threadIdx.x]; };
+        uint32_t j = 0;
+        for (; j + 4 <= K; j += 4) {
+            uint64_t y[4];
+            bconv_y<4>(v, j, a, y);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) dst[(uint64_t)(j + u) << log2n] = y[u];
+        }
+        for (; j < K; ++j) {
+            uint64_t y[1];
+            bconv_y<1>(v, j, a, y);
+            dst[(uint64_t)j << log2n] = y[0];
+        }
     }
 }
 

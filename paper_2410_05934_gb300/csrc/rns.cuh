@@ -59,25 +59,42 @@ NTT_HD uint64_t bconv_a(const BconvView& v, uint32_t i, uint64_t x) {
     return csub(shoup_mul(x, bconv_ld(v.qhi + i), bconv_ld(v.qhi_p + i), q), q);
 }
 
-// y_j of one coefficient from its a_i, read through a(i)
-template <class Get>
-NTT_HD uint64_t bconv_y(const BconvView& v, uint32_t j, Get a) {
-    const uint64_t p = bconv_ld(v.p + j), p_one = bconv_ld(v.p_one + j);
-    const uint64_t r64 = bconv_ld(v.r64 + j), r64_p = bconv_ld(v.r64_p + j);
-    uint64_t hi = 0, lo = 0;
+// y_j of one coefficient from its a_i, read through a(i), for the NJ outputs
+// j0 .. j0 + NJ - 1 at once (independent accumulators: NJ-fold ILP, one read
+// of each a_i per NJ outputs)
+template <int NJ, class Get>
+NTT_HD void bconv_y(const BconvView& v, uint32_t j0, Get a, uint64_t (&y)[NJ]) {
+    uint64_t hi[NJ], lo[NJ];
+#pragma unroll
+    for (int u = 0; u < NJ; ++u) hi[u] = lo[u] = 0;
     uint32_t n = 0;
     for (uint32_t i = 0; i < v.L; ++i) {
-        const uint64_t ai = a(i), cij = bconv_ld(v.c + (uint64_t)i * v.K + j);
-        const uint64_t pl = ai * cij;
-        lo += pl;
-        hi += mulhi64(ai, cij) + (lo < pl ? 1u : 0u);
-        if (++n == v.chunk) {
-            lo = reduce128(hi, lo, p, p_one, r64, r64_p);
-            hi = 0;
+        const uint64_t ai = a(i);
+        const uint64_t* ci = v.c + (uint64_t)i * v.K + j0;
+#pragma unroll
+        for (int u = 0; u < NJ; ++u) {
+            const uint64_t cij = bconv_ld(ci + u);
+            const uint64_t pl = ai * cij;
+            lo[u] += pl;
+            hi[u] += mulhi64(ai, cij) + (lo[u] < pl ? 1u : 0u);
+        }
+        if (++n == v.chunk) {      // uniform: only bases whose products approach 2^128 / L fold
+#pragma unroll
+            for (int u = 0; u < NJ; ++u) {
+                const uint32_t j = j0 + u;
+                lo[u] = reduce128(hi[u], lo[u], bconv_ld(v.p + j), bconv_ld(v.p_one + j), bconv_ld(v.r64 + j),
+                                  bconv_ld(v.r64_p + j));
+                hi[u] = 0;
+            }
             n = 1;   // the folded value counts as one more term
         }
     }
-    return reduce128(hi, lo, p, p_one, r64, r64_p);
+#pragma unroll
+    for (int u = 0; u < NJ; ++u) {
+        const uint32_t j = j0 + u;
+        y[u] = reduce128(hi[u], lo[u], bconv_ld(v.p + j), bconv_ld(v.p_one + j), bconv_ld(v.r64 + j),
+                         bconv_ld(v.r64_p + j));
+    }
 }
 
 }  // namespace nttgb

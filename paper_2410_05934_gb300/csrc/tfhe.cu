@@ -28,9 +28,13 @@ __global__ void __launch_bounds__(CmuxCfg<LOGN, MC>::THREADS, CmuxCfg<LOGN, MC>:
     L.limb = 0;
     L.hi = 0;
     L.gbase = 0;
-    L.tw_off = 0;
+    L.tw_off = K::tw_off(s, false);
     L.valid = true;
+    TileLoc Li = L;
+    Li.tw_off = K::tw_off(s, true);
     const LimbConst lc = af.lc[0];
+    cmux_stage_twiddles<K>(af.tw, ai.tw, threadIdx.x, smem);
+    __syncthreads();
     for (uint64_t ct = blockIdx.x; ct < c.n_ct; ct += gridDim.x) {
         CmuxRegs<K> cr;
         cmux_load<K>(cr, c, ct, s, t);
@@ -48,9 +52,9 @@ __global__ void __launch_bounds__(CmuxCfg<LOGN, MC>::THREADS, CmuxCfg<LOGN, MC>:
         __syncthreads();
         TileRegs<I> si;
         cmux_inverse_input<K>(si, cr, s);
-        write_pairs_swizzled<I>(si, L, t, sm);
+        write_pairs_swizzled<I>(si, Li, t, sm);
         __syncthreads();
-        run_passes<I, 0>(si, ai, L, t, sm);
+        run_passes<I, 0>(si, ai, Li, t, sm);
         cmux_store<K>(c, lc, ct, s, t, sm);
         __syncthreads();
     }
@@ -60,7 +64,9 @@ template <int LOGN, int MC>
 static int launch_cmux(const CmuxArgs& c, const TileArgs& af, const TileArgs& ai, cudaStream_t st) {
     using K = CmuxCfg<LOGN, MC>;
     int dev = 0, sms = 0, per_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
+    if (cudaFuncSetAttribute(k_tfhe_cmux<LOGN, MC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)K::SMEM_BYTES) != cudaSuccess ||
+        cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tfhe_cmux<LOGN, MC>, K::THREADS,
                                                       K::SMEM_BYTES) != cudaSuccess)

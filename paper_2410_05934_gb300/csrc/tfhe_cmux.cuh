@@ -33,18 +33,39 @@ struct CmuxArgs {
     uint32_t sigma, levels, log2_base, check;
 };
 
-// 8 coefficients per thread, passes of up to 3 fused stages, two slots
+// 8 coefficients per thread, passes of up to 3 fused stages, two slots.
+// Shared memory (words): [slot 0 row][slot 1 row][forward twiddles][inverse
+// twiddles]; the twiddles are staged once per CTA (every ciphertext uses the
+// same tables) in the tile phases' slot order (slot i = table entry i + 1
+// for a tile that is one whole row), and each slot's TileLoc points its
+// pass twiddles there through tw_off.
 template <int LOGN_, int MC_>
 struct CmuxCfg {
     static constexpr int LOGN = LOGN_, MC = MC_;
     static constexpr int LOGT = LOGN - 3;
-    using F = TileCfg<LOGN, 0, LOGN, 0, LOGT, 3, 1, false, MC, 2>;
-    using I = TileCfg<LOGN, 0, LOGN, 0, LOGT, 3, 1, true, MC, 2>;
+    using F = TileCfg<LOGN, 0, LOGN, 0, LOGT, 3, 1, false, MC, 0>;
+    using I = TileCfg<LOGN, 0, LOGN, 0, LOGT, 3, 1, true, MC, 0>;
     static constexpr int N = 1 << LOGN, T = F::T, R = F::R, THREADS = 2 * T;
-    static constexpr size_t SMEM_BYTES = 2 * F::DATA_BYTES;
-    static constexpr int MIN_CTAS = 512 / THREADS;    // register budget: 128 per thread
-    static_assert(F::E == N && !F::TWS, "one whole row per slot, twiddles from the read-only path");
+    static constexpr int TW_WORDS = 2 * (N - 1);                 // N - 1 TwPairs
+    static constexpr int FWD_TW = 2 * N, INV_TW = 2 * N + TW_WORDS;
+    static constexpr size_t SMEM_BYTES = sizeof(uint64_t) * (size_t)(2 * N + 2 * TW_WORDS);
+    static constexpr int MIN_CTAS = THREADS <= 256 ? 2 : 1;      // register budget: 128 per thread
+    static_assert(F::E == N && F::TWS && I::TWS, "one whole row per slot, twiddles staged in shared memory");
+    // tw_off of slot s: from the slot's row + E to the twiddle region
+    static constexpr int32_t tw_off(int s, bool inv) { return (1 - s) * N + (inv ? TW_WORDS : 0); }
 };
+
+// all threads of the CTA: both tables into their regions
+template <class K>
+NTT_HD void cmux_stage_twiddles(const TwPair* fwd, const TwPair* inv, int tid, uint64_t* smem) {
+    TwPair* f = reinterpret_cast<TwPair*>(smem + K::FWD_TW);
+    TwPair* v = reinterpret_cast<TwPair*>(smem + K::INV_TW);
+    for (int i = tid; i < K::N - 1; i += K::THREADS) {
+        NTT_GMEM_CHECK(i + 1, K::N);
+        f[i] = load_tw(fwd, (uint32_t)i + 1u);
+        v[i] = load_tw(inv, (uint32_t)i + 1u);
+    }
+}
 
 template <class K>
 struct CmuxRegs {

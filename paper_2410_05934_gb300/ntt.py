@@ -172,6 +172,15 @@ class Plan:
                                      _ptr(out, 3 * per, "out"), _stream_handle(stream)), "ntt_hmul_tensor")
         return out
 
+    def rescale(self, x, out, work, n_polys=0, stream=None):
+        """Rescale by the plan's last modulus: x [n_polys][L][N] -> out
+        [n_polys][L-1][N], both NTT domain; work [n_polys][N] scratch."""
+        polys = n_polys or self.batch
+        check(load().ntt_rescale(self._h, _ptr(x, polys * self.n_moduli * self.n, "in"),
+                                 _ptr(out, polys * (self.n_moduli - 1) * self.n, "out"),
+                                 _ptr(work, polys * self.n, "work"), n_polys, _stream_handle(stream)), "ntt_rescale")
+        return out
+
     def tfhe_external_product(self, d, key, levels, log2_base, out=None, stream=None):
         """K [x] d for d = [n_ct][2][N] RLWE ciphertexts and one RGSW key
         [2 levels][2][N] in the NTT domain (tfhe_external_product)."""

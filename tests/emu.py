@@ -30,6 +30,8 @@ def lib():
         L.nttemu_tfhe_cmux.restype = i32
         L.nttemu_bconv.argtypes = [U64P, u32, U64P, u32, U64P, U64P, u64, u64]
         L.nttemu_bconv.restype = i32
+        L.nttemu_rescale.argtypes = [vp, u32, U64P, U64P, U64P, u32]
+        L.nttemu_rescale.restype = i32
         _lib = L
     return _lib
 
@@ -91,6 +93,17 @@ class EmuPlan:
         rc = lib().nttemu_tfhe_cmux(self.h, _p(d), rp, _p(key), levels, log2_base, _p(out), d.shape[0])
         if rc:
             raise ValueError("nttemu_tfhe_cmux failed: %d" % rc)
+        return out
+
+    def rescale(self, x, sched, n_polys):
+        """ntt_rescale with schedule sched: x [n_polys][L][N] (NTT domain) -> [n_polys][L-1][N]."""
+        x = np.ascontiguousarray(x, dtype=np.uint64)
+        n_mod, n = x.shape[1], x.shape[2]
+        out = np.zeros((n_polys, n_mod - 1, n), dtype=np.uint64)
+        work = np.zeros((n_polys, n), dtype=np.uint64)
+        rc = lib().nttemu_rescale(self.h, sched, _p(x), _p(out), _p(work), n_polys)
+        if rc:
+            raise ValueError("nttemu_rescale failed: %d" % rc)
         return out
 
     def pointwise(self, a, b, n_rows=None):

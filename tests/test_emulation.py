@@ -273,3 +273,28 @@ def test_bconv_argument_rules():
         emu.bconv(np.zeros((1, 1, 4), np.uint64), [W.POOL50[0]], [15])                          # not prime
     with pytest.raises(ValueError):
         emu.bconv(np.zeros((1, 1, 4), np.uint64), [W.POOL50[0]], [(1 << 62) + 135])             # too large
+
+
+@pytest.mark.parametrize("log2n", [10, 12, 13])
+def test_rescale_matches_oracle(log2n):
+    """ntt_rescale's kernels (INTT of the dropped limb, forward transform with
+    the Rescale load and epilogue) for every direct-form schedule of N,
+    against the oracle's definition through the transform definitions."""
+    from oracle import oracle as O
+    from oracle import rns_oracle as RO
+    Q = [W.POOL50[0], W.POOL50[5], W.POOL50[9]] if log2n > 10 else [W.Q62_N1024, W.POOL50[1], W.Q59_N1024]
+    n = 1 << log2n
+    rng = np.random.default_rng(log2n)
+    x = np.stack([np.array([rng.integers(0, q, n, dtype=np.uint64) for q in Q]) for _ in range(2)])
+    plan = emu.EmuPlan(log2n, Q, 2)
+    want = [RO.rescale_ntt(x[p], Q) for p in range(2)]
+    tried = 0
+    for s in range(emu.schedule_count(log2n)):
+        try:
+            got = plan.rescale(x, s, 2)
+        except ValueError:
+            continue                                    # pipelined first kernel
+        tried += 1
+        for p in range(2):
+            assert np.array_equal(got[p], want[p]), (s, p)
+    assert tried >= 1 and plan.status() == 0

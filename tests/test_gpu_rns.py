@@ -69,3 +69,56 @@ def test_empty_call_and_errors():
         with pytest.raises(ntt.NttError) as e:
             ntt.BConv(q, p)
         assert e.value.code == code, (q, p)
+
+
+def test_rescale_ckks_shape_sampled():
+    """2 polynomials x 24 limbs at N = 2^16 (NTT domain) -> 23 limbs."""
+    from oracle import oracle as O
+    n, Q = 1 << 16, W.POOL50[:24]
+    w = W.ckks_hmul_n65536(limbs=24, polys=2)
+    x = w["x"]                                   # treated as NTT-domain limbs
+    plan = ntt.Plan(16, Q, 2)
+    out = torch.empty((2, 23, n), dtype=torch.int64, device="cuda")
+    work = torch.empty((2, n), dtype=torch.int64, device="cuda")
+    plan.rescale(to_dev(x), out, work)
+    assert plan.status() == 0
+    got = to_host(out)
+    idx = [0, 1, 4097, n - 1]
+    for p in range(2):
+        assert np.array_equal(got[p][:, idx], RO.rescale_ntt(x[p], Q, idx=idx)), p
+
+
+@pytest.mark.parametrize("log2n", [10, 12, 14])
+def test_rescale_full_rows_every_schedule(log2n):
+    n = 1 << log2n
+    Q = [W.POOL50[3], W.POOL50[1], W.POOL50[7], W.POOL50[0]]
+    rng = np.random.default_rng(log2n)
+    x = np.stack([np.array([rng.integers(0, q, n, dtype=np.uint64) for q in Q]) for _ in range(3)])
+    want = [RO.rescale_ntt(x[p], Q) for p in range(3)] if log2n <= 12 else None
+    idx = [0, 2, n // 2 + 1, n - 1]
+    if want is None:
+        want = [RO.rescale_ntt(x[p], Q, idx=idx) for p in range(3)]
+    plan = ntt.Plan(log2n, Q, 3)
+    xd = to_dev(x)
+    for s in range(ntt.schedule_count(log2n)):
+        plan.schedule = s                        # a pipelined first kernel falls back to a direct one
+        out = torch.empty((3, 3, n), dtype=torch.int64, device="cuda")
+        plan.rescale(xd, out, torch.empty((3, n), dtype=torch.int64, device="cuda"))
+        got = to_host(out)
+        for p in range(3):
+            g = got[p] if log2n <= 12 else got[p][:, idx]
+            assert np.array_equal(g, want[p]), (s, p)
+    # two of the three polynomials only
+    out = torch.zeros((3, 3, n), dtype=torch.int64, device="cuda")
+    plan.rescale(xd, out, torch.empty((2, n), dtype=torch.int64, device="cuda"), n_polys=2)
+    assert not to_host(out)[2].any()
+
+
+def test_rescale_errors():
+    x = torch.zeros((1, 2, 1024), dtype=torch.int64, device="cuda")
+    w = torch.zeros((1, 1024), dtype=torch.int64, device="cuda")
+    with pytest.raises(ntt.NttError):
+        ntt.Plan(10, [W.POOL50[0]]).rescale(x[:, :1], torch.zeros((1, 1, 1024), dtype=torch.int64, device="cuda"), w)
+    with pytest.raises(ntt.NttError):                      # last modulus repeats the first
+        ntt.Plan(10, [W.POOL50[0], W.POOL50[0]]).rescale(x, torch.zeros((1, 1, 1024), dtype=torch.int64,
+                                                                          device="cuda"), w)
