@@ -344,8 +344,10 @@ int ntt_batch_execute_static(const ntt_plan_request_t* reqs, uint32_t n_reqs, vo
  *   d_in, d_acc   [n_ct][2][N] RLWE ciphertexts (B(x), A(x)), canonical
  *   d_rot         [n_ct] exponents a of x^a, taken mod 2N (CMux only)
  *   d_key         [2 levels][2][N] RGSW rows in the NTT domain (the forward
- *                 transform's bit-reversed order), canonical; row
- *                 i * levels + j multiplies digit level j of input polynomial i
+ *                 transform's bit-reversed order) as {w, floor(w 2^64 / q)}
+ *                 pairs (16 bytes per entry), made once per key by
+ *                 tfhe_key_prepare from canonical values; row i * levels + j
+ *                 multiplies digit level j of input polynomial i
  *   levels, log2_base  the gadget B = 2^log2_base, l = levels:
  *                 1 <= l <= NTT_TFHE_MAX_LEVELS, l * log2_base <= 32, B^l < q
  *   d_out         [n_ct][2][N]; may be the same buffer as d_in / d_acc, no
@@ -365,6 +367,10 @@ int ntt_batch_execute_static(const ntt_plan_request_t* reqs, uint32_t n_reqs, vo
 #define NTT_TFHE_MAX_LOG2N 11
 #define NTT_TFHE_MAX_LEVELS 8
 
+/* d_key [2 levels][2][N] canonical -> d_key_shoup [2 levels][2][N][2] (one
+ * kernel launch; NTT_FLAG_CHECK plans report keys >= q as NTT_ERR_RANGE). */
+int tfhe_key_prepare(ntt_plan_t plan, const uint64_t* d_key, uint32_t levels, uint64_t* d_key_shoup,
+                     void* cuda_stream);
 int tfhe_external_product(ntt_plan_t plan, const uint64_t* d_in, const uint64_t* d_key, uint32_t levels,
                           uint32_t log2_base, uint64_t* d_out, uint64_t n_ct, void* cuda_stream);
 int tfhe_cmux_rotate(ntt_plan_t plan, const uint64_t* d_acc, const uint32_t* d_rot, const uint64_t* d_key,

@@ -66,6 +66,7 @@ SIGNATURES = [
     ("ntt_mlp_backward", i32, [vp, vp, vp, vp, vp, u32, ctypes.c_float, vp, vp, vp, vp]),
     ("ntt_mlp_adam", i32, [vp, vp, vp, vp, u32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                            ctypes.c_float, u32, vp]),
+    ("tfhe_key_prepare", i32, [vp, vp, u32, vp, vp]),
     ("tfhe_external_product", i32, [vp, vp, vp, u32, u32, vp, u64, vp]),
     ("tfhe_cmux_rotate", i32, [vp, vp, vp, vp, u32, u32, vp, u64, vp]),
     ("ntt_bconv_plan", i32, [ctypes.POINTER(vp), U64P, u32, U64P, u32]),

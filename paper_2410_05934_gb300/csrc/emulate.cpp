@@ -461,10 +461,14 @@ int nttemu_tfhe_cmux(void* plan, const uint64_t* in, const uint32_t* rot, const 
     if (levels < 1 || levels > NTT_TFHE_MAX_LEVELS || log2_base < 1 || levels * log2_base > 32 ||
         levels * log2_base > sigma)
         return NTT_ERR_ARG;
+    // the key in the Shoup form that tfhe_key_prepare produces
+    std::vector<TwPair> kp((size_t)4 * levels << p->h.log2n);
+    for (size_t i = 0; i < kp.size(); ++i)
+        kp[i] = TwPair{key[i], (uint64_t)(((unsigned __int128)key[i] << 64) / q)};
     CmuxArgs c;
     c.in = in;
     c.rot = rot;
-    c.key = key;
+    c.key = kp.data();
     c.out = out;
     c.status = &p->status;
     c.q = q;

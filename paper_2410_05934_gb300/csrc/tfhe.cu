@@ -82,6 +82,7 @@ static int launch_cmux(const CmuxArgs& c, const TileArgs& af, const TileArgs& ai
 // the two tile argument blocks.
 static int cmux_setup(ntt_plan_t plan, const uint64_t* d_key, uint32_t levels, uint32_t log2_base, uint64_t n_ct,
                       CmuxArgs& c, TileArgs& af, TileArgs& ai) {
+    // d_key: [2 levels][2][N] pairs {w, floor(w 2^64 / q)} (tfhe_key_prepare)
     if (!plan || !d_key) return NTT_ERR_ARG;
     if (plan->h.flags & NTT_FLAG_HOST_ONLY) return NTT_ERR_ARG;
     int dev = -1;
@@ -95,7 +96,7 @@ static int cmux_setup(ntt_plan_t plan, const uint64_t* d_key, uint32_t levels, u
         levels * log2_base > sigma)
         return NTT_ERR_ARG;
     if (n_ct > (1ull << 40)) return NTT_ERR_ARG;
-    c.key = d_key;
+    c.key = reinterpret_cast<const TwPair*>(d_key);
     c.status = plan->d_status;
     c.q = q;
     c.half_q = q >> 1;
@@ -131,11 +132,38 @@ static int cmux_dispatch(ntt_plan_t plan, const CmuxArgs& c, const TileArgs& af,
     return rc;
 }
 
+// key rows -> {w, floor(w 2^64 / q)} pairs; range check under NTT_FLAG_CHECK
+__global__ void k_tfhe_key_prepare(const uint64_t* __restrict__ key, TwPair* __restrict__ out, uint64_t count,
+                                   uint64_t q, int* status, uint32_t check) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t w = key[i];
+        if (check && w >= q) record_status(status, NTT_STATUS_RANGE);
+        out[i] = TwPair{w, (uint64_t)(((unsigned __int128)w << 64) / q)};
+    }
+}
+
 }  // namespace nttgb
 
 using namespace nttgb;
 
 extern "C" {
+
+int tfhe_key_prepare(ntt_plan_t plan, const uint64_t* d_key, uint32_t levels, uint64_t* d_key_shoup,
+                     void* cuda_stream) {
+    if (!plan || !d_key || !d_key_shoup) return NTT_ERR_ARG;
+    if (plan->h.flags & NTT_FLAG_HOST_ONLY) return NTT_ERR_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device) return NTT_ERR_ARG;
+    if (plan->h.n_moduli != 1 || levels < 1 || levels > NTT_TFHE_MAX_LEVELS) return NTT_ERR_ARG;
+    if (((uintptr_t)d_key & 7u) || ((uintptr_t)d_key_shoup & 15u)) return NTT_ERR_ALIGN;
+    const uint64_t count = (uint64_t)4 * levels << plan->h.log2n;
+    const unsigned grid = (unsigned)std::min<uint64_t>((count + 255) / 256, 4096);
+    k_tfhe_key_prepare<<<grid, 256, 0, (cudaStream_t)cuda_stream>>>(
+        d_key, reinterpret_cast<TwPair*>(d_key_shoup), count, plan->h.moduli[0], plan->d_status,
+        (plan->h.flags & NTT_FLAG_CHECK) ? 1u : 0u);
+    plan->last_launches = 1;
+    return cudaPeekAtLastError() == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
+}
 
 int tfhe_external_product(ntt_plan_t plan, const uint64_t* d_in, const uint64_t* d_key, uint32_t levels,
                           uint32_t log2_base, uint64_t* d_out, uint64_t n_ct, void* cuda_stream) {

@@ -10,6 +10,7 @@
 //             -> forward NTT in shared memory (the tile phases of the NTT)
 //             -> MAC: acc_c += NTT(e_j) * K[s l + j][c] for c = 0, 1
 //   exchange  slot s hands acc_(1-s) to the other slot, adds the one it gets
+//             (key rows in Shoup form: products and sums stay in [0, 2q))
 //   output    INTT of acc_s (slot s), plus d_s for the CMux, stored
 //
 // The digits never leave the SM, the key is read once per ciphertext from
@@ -24,7 +25,7 @@ namespace nttgb {
 struct CmuxArgs {
     const uint64_t* in;       // [n_ct][2][N]: d (external product) or acc (CMux)
     const uint32_t* rot;      // [n_ct] exponents a (taken mod 2N), or null for the external product
-    const uint64_t* key;      // [2 levels][2][N] RGSW rows in the NTT domain, canonical
+    const TwPair* key;        // [2 levels][2][N] RGSW rows in the NTT domain, {w, floor(w 2^64 / q)}
     uint64_t* out;            // [n_ct][2][N]
     int* status;
     uint64_t q, half_q;       // q and floor(q / 2)
@@ -69,8 +70,8 @@ NTT_HD void cmux_stage_twiddles(const TwPair* fwd, const TwPair* inv, int tid, u
 
 template <class K>
 struct CmuxRegs {
-    uint32_t top[K::R];        // t = round(v B^l / q) mod B^l of the slot's coefficients
-    uint64_t acc[2][K::R];     // accumulators of outputs 0 and 1 (pair layout)
+    uint32_t dig[K::R];        // the signed digits of each coefficient, log2_base bits per level
+    uint64_t acc[2][K::R];     // lazy sums of outputs 0 and 1 (pair layout), each < 2 levels q
 };
 
 // round(v 2^bl / q) mod 2^bl for v < q < 2^62, bl = levels * log2_base <= 32
@@ -91,22 +92,27 @@ NTT_HD uint32_t cmux_round_top(uint64_t v, const CmuxArgs& c) {
     return (uint32_t)(e & ((1ull << bl) - 1));
 }
 
-// signed digit j (0 = most significant) of t, as a residue mod q
-NTT_HD uint64_t cmux_digit(uint32_t top, uint32_t j, const CmuxArgs& c) {
-    const uint64_t base = 1ull << c.log2_base, half = base >> 1;
+// the signed digits e_0..e_(l-1) of t (e_0 most significant), packed as
+// log2_base-bit two's-complement fields, level j at bit j * log2_base
+NTT_HD uint32_t cmux_pack_digits(uint32_t top, const CmuxArgs& c) {
+    const uint64_t base = 1ull << c.log2_base, half = base >> 1, mask = base - 1;
     uint64_t t = top;
-    int64_t e = 0;
-    for (int k = (int)c.levels - 1; k >= (int)j; --k) {
-        const uint64_t d = t & (base - 1);
+    uint64_t packed = 0;
+    for (int k = (int)c.levels - 1; k >= 0; --k) {
+        const uint64_t d = t & mask;
         t >>= c.log2_base;
-        if (d >= half) {
-            e = (int64_t)d - (int64_t)base;
-            t += 1;
-        } else {
-            e = (int64_t)d;
-        }
+        if (d >= half) t += 1;                        // e = d - B, carried into the next level
+        packed |= d << (c.log2_base * (uint32_t)k);   // d mod B is e's two's-complement field
     }
-    return e >= 0 ? (uint64_t)e : c.q - (uint64_t)(-e);
+    return (uint32_t)packed;
+}
+
+// digit j of a packed word, as a residue mod q
+NTT_HD uint64_t cmux_digit(uint32_t packed, uint32_t j, const CmuxArgs& c) {
+    const uint32_t sh = c.log2_base * j;
+    const uint64_t d = ((uint64_t)packed >> sh) & ((1ull << c.log2_base) - 1);
+    const uint64_t half = 1ull << (c.log2_base - 1);
+    return d < half ? d : c.q - ((1ull << c.log2_base) - d);
 }
 
 // coefficient k = 2t + 2iT + h of the slot's row <-> register 2i + h (the
@@ -133,7 +139,7 @@ NTT_HD void cmux_load(CmuxRegs<K>& cr, const CmuxArgs& c, uint64_t ct, int s, in
                 const uint64_t rv = e < (uint32_t)K::N ? w : (w ? c.q - w : 0);
                 v = rv >= v ? rv - v : rv + (c.q - v);
             }
-            cr.top[2 * i + h] = cmux_round_top(v, c);
+            cr.dig[2 * i + h] = cmux_pack_digits(cmux_round_top(v, c), c);
         }
     }
     if (c.check && bad) record_status(c.status, NTT_STATUS_RANGE);
@@ -144,39 +150,36 @@ NTT_HD void cmux_load(CmuxRegs<K>& cr, const CmuxArgs& c, uint64_t ct, int s, in
 template <class K>
 NTT_HD void cmux_digits(TileRegs<typename K::F>& st, const CmuxRegs<K>& cr, uint32_t j, const CmuxArgs& c) {
 #pragma unroll
-    for (int r = 0; r < K::R; ++r) st.x[r] = cmux_digit(cr.top[r], j, c);
+    for (int r = 0; r < K::R; ++r) st.x[r] = cmux_digit(cr.dig[r], j, c);
 }
 
-// forward result of level j (in shared memory, lazy range) times key row p
+// forward result of level j (shared memory, any lazy range below 2^64) times
+// key row p in Shoup form: each product lies in [0, 2q) and the sums are
+// kept in [0, 2q) (q < 2^62, so sum + product < 4q < 2^64)
 template <class K>
 NTT_HD void cmux_mac(CmuxRegs<K>& cr, const CmuxArgs& c, const LimbConst& lc, uint32_t p, int t,
                      const uint64_t* sm) {
-    const uint64_t* k0 = c.key + ((uint64_t)(2u * p) << K::LOGN);
-    const uint64_t* k1 = k0 + K::N;
+    const TwPair* k0 = c.key + ((uint64_t)(2u * p) << K::LOGN);
+    const TwPair* k1 = k0 + K::N;
     const uint32_t b = swz(2u * (uint32_t)t);
 #pragma unroll
     for (int i = 0; i < K::R / 2; ++i) {
         const uint32_t cc = swz(2u * (uint32_t)i * K::T);
         NTT_SMEM_CHECK(b ^ cc, K::N);
-        uint64_t x = sm[b ^ cc], y = sm[(b ^ cc) ^ 1u];
-        if (K::MC == 1) {   // [0, 65q) -> [0, q)
-            x = reduce_full_small(x, lc.one_p, lc.q, lc.two_q);
-            y = reduce_full_small(y, lc.one_p, lc.q, lc.two_q);
-        } else {            // [0, 4q) -> [0, q)
-            x = csub(csub(x, lc.two_q), lc.q);
-            y = csub(csub(y, lc.two_q), lc.q);
-        }
+        const uint64_t x = sm[b ^ cc], y = sm[(b ^ cc) ^ 1u];
         const uint32_t k = 2u * (uint32_t)t + 2u * (uint32_t)i * K::T;
         NTT_GMEM_CHECK(k + 1, K::N);
-        uint64_t w0x, w0y, w1x, w1y;
-        load_pair(k0 + k, w0x, w0y);
-        load_pair(k1 + k, w1x, w1y);
-        cr.acc[0][2 * i] = csub(cr.acc[0][2 * i] + barrett_mulmod(x, w0x, lc.q, lc.mu, lc.bits), lc.q);
-        cr.acc[0][2 * i + 1] = csub(cr.acc[0][2 * i + 1] + barrett_mulmod(y, w0y, lc.q, lc.mu, lc.bits), lc.q);
-        cr.acc[1][2 * i] = csub(cr.acc[1][2 * i] + barrett_mulmod(x, w1x, lc.q, lc.mu, lc.bits), lc.q);
-        cr.acc[1][2 * i + 1] = csub(cr.acc[1][2 * i + 1] + barrett_mulmod(y, w1y, lc.q, lc.mu, lc.bits), lc.q);
+        const TwPair a0 = load_tw(k0, k), a1 = load_tw(k0, k + 1);
+        const TwPair b0 = load_tw(k1, k), b1 = load_tw(k1, k + 1);
+        cr.acc[0][2 * i] = csub(cr.acc[0][2 * i] + shoup_mul(x, a0.w, a0.wp, lc.q), lc.two_q);
+        cr.acc[0][2 * i + 1] = csub(cr.acc[0][2 * i + 1] + shoup_mul(y, a1.w, a1.wp, lc.q), lc.two_q);
+        cr.acc[1][2 * i] = csub(cr.acc[1][2 * i] + shoup_mul(x, b0.w, b0.wp, lc.q), lc.two_q);
+        cr.acc[1][2 * i + 1] = csub(cr.acc[1][2 * i + 1] + shoup_mul(y, b1.w, b1.wp, lc.q), lc.two_q);
     }
 }
+
+// a lazy sum in [0, 2q) to [0, q)
+NTT_HD uint64_t cmux_reduce(uint64_t x, const LimbConst& lc) { return csub(x, lc.q); }
 
 // Slot s hands the other output's partial sums over through its own tile
 // and adds what the other slot handed it (same thread index, same
@@ -201,8 +204,8 @@ NTT_HD void cmux_add_pairs(uint64_t (&v)[K::R], const LimbConst& lc, int t, cons
     for (int i = 0; i < K::R / 2; ++i) {
         const uint32_t cc = swz(2u * (uint32_t)i * K::T);
         NTT_SMEM_CHECK(b ^ cc, K::N);
-        v[2 * i] = csub(v[2 * i] + sm[b ^ cc], lc.q);
-        v[2 * i + 1] = csub(v[2 * i + 1] + sm[(b ^ cc) ^ 1u], lc.q);
+        v[2 * i] = csub(cmux_reduce(v[2 * i], lc) + cmux_reduce(sm[b ^ cc], lc), lc.q);
+        v[2 * i + 1] = csub(cmux_reduce(v[2 * i + 1], lc) + cmux_reduce(sm[(b ^ cc) ^ 1u], lc), lc.q);
     }
 }
 

@@ -181,12 +181,24 @@ class Plan:
                                  _ptr(work, polys * self.n, "work"), n_polys, _stream_handle(stream)), "ntt_rescale")
         return out
 
+    def tfhe_key_prepare(self, key, levels, out=None, stream=None):
+        """RGSW key rows [2 levels][2][N] (NTT domain, canonical) -> the
+        {w, floor(w 2^64 / q)} pair form the TFHE kernels read
+        ([2 levels][2][N][2])."""
+        if out is None:
+            import torch
+            out = torch.empty((2 * levels, 2, self.n, 2), dtype=torch.int64, device=key.device)
+        check(load().tfhe_key_prepare(self._h, _ptr(key, 4 * levels * self.n, "key"),
+                                      levels, _ptr(out, 8 * levels * self.n, "out"), _stream_handle(stream)),
+              "tfhe_key_prepare")
+        return out
+
     def tfhe_external_product(self, d, key, levels, log2_base, out=None, stream=None):
         """K [x] d for d = [n_ct][2][N] RLWE ciphertexts and one RGSW key
-        [2 levels][2][N] in the NTT domain (tfhe_external_product)."""
+        prepared by tfhe_key_prepare (tfhe_external_product)."""
         n_ct = d.shape[0] if hasattr(d, "shape") else None
         out = d if out is None else out
-        check(load().tfhe_external_product(self._h, _ptr(d, what="d"), _ptr(key, 4 * levels * self.n, "key"),
+        check(load().tfhe_external_product(self._h, _ptr(d, what="d"), _ptr(key, 8 * levels * self.n, "key"),
                                            levels, log2_base, _ptr(out, what="out"),
                                            n_ct, _stream_handle(stream)), "tfhe_external_product")
         return out
@@ -199,7 +211,7 @@ class Plan:
         if not rot.is_cuda or rot.element_size() != 4 or rot.numel() < n_ct or not rot.is_contiguous():
             raise ValueError("rot must be a contiguous CUDA tensor of 32-bit exponents, one per ciphertext")
         check(load().tfhe_cmux_rotate(self._h, _ptr(acc, what="acc"), ctypes.c_void_p(rot.data_ptr()),
-                                      _ptr(key, 4 * levels * self.n, "key"), levels, log2_base,
+                                      _ptr(key, 8 * levels * self.n, "key"), levels, log2_base,
                                       _ptr(out, what="out"), n_ct, _stream_handle(stream)), "tfhe_cmux_rotate")
         return out
 

@@ -29,7 +29,7 @@ def test_cmux_and_external_product_match_oracle(log2n, q):
     w = W.tfhe_cmux(seed=11 + log2n, n_ct=48, log2n=log2n, q=q, levels=levels)
     acc, rot, key = w["acc"], w["rot"][0], w["key"][0]
     plan = ntt.Plan(log2n, [q])
-    d_acc, d_key = to_dev(acc), to_dev(key)
+    d_acc, d_key = to_dev(acc), plan.tfhe_key_prepare(to_dev(key), levels)
     out_ep = torch.empty_like(d_acc)
     out_cm = torch.empty_like(d_acc)
     plan.tfhe_external_product(d_acc, d_key, levels, log2_base, out=out_ep)
@@ -55,7 +55,8 @@ def test_gadgets_in_place_and_blind_rotation_chain():
     for levels, log2_base in [(1, 16), (2, 10), (4, 6)]:
         key = w["key"][0][:2 * levels]
         x = to_dev(w["acc"])
-        plan.tfhe_cmux_rotate(x, _rot_dev(w["rot"][0]), to_dev(key), levels, log2_base)      # in place
+        plan.tfhe_cmux_rotate(x, _rot_dev(w["rot"][0]), plan.tfhe_key_prepare(to_dev(key), levels), levels,
+                              log2_base)                                                   # in place
         got = to_host(x)
         kc = TO.key_coefficients(key, q)
         for c in (0, 4):
@@ -67,7 +68,8 @@ def test_gadgets_in_place_and_blind_rotation_chain():
     ref = w["acc"][1].copy()
     for step in range(3):
         key = w["key"][step]
-        plan.tfhe_cmux_rotate(x, _rot_dev(w["rot"][step]), to_dev(key), levels, log2_base)
+        plan.tfhe_cmux_rotate(x, _rot_dev(w["rot"][step]), plan.tfhe_key_prepare(to_dev(key), levels), levels,
+                              log2_base)
         ref = TO.cmux_rotate(ref, int(w["rot"][step][1]), key, q, log2_base, levels)
     assert np.array_equal(to_host(x)[1], ref)
     assert plan.status() == 0
@@ -79,10 +81,10 @@ def test_zero_key_is_identity_and_empty_batch():
     plan = ntt.Plan(log2n, [q])
     x = to_dev(w["acc"])
     out = torch.empty_like(x)
-    plan.tfhe_cmux_rotate(x, _rot_dev(w["rot"][0]), torch.zeros((6, 2, 1 << log2n), dtype=torch.int64,
-                                                               device="cuda"), 3, 8, out=out)
+    zero = plan.tfhe_key_prepare(torch.zeros((6, 2, 1 << log2n), dtype=torch.int64, device="cuda"), 3)
+    plan.tfhe_cmux_rotate(x, _rot_dev(w["rot"][0]), zero, 3, 8, out=out)
     assert torch.equal(out, x)
-    plan.tfhe_external_product(x[:0], to_dev(w["key"][0]), 3, 8, out=out[:0])
+    plan.tfhe_external_product(x[:0], zero, 3, 8, out=out[:0])
     assert plan.last_launches() == 0
 
 
@@ -90,7 +92,7 @@ def test_tfhe_argument_errors_and_range_check():
     q = W.Q62_N1024
     plan = ntt.Plan(10, [q])
     x = torch.zeros((2, 2, 1024), dtype=torch.int64, device="cuda")
-    key = torch.zeros((18, 2, 1024), dtype=torch.int64, device="cuda")
+    key = torch.zeros((18, 2, 1024, 2), dtype=torch.int64, device="cuda")
     for levels, base in [(0, 8), (9, 3), (3, 11), (1, 33)]:
         with pytest.raises(ntt.NttError) as e:
             plan.tfhe_external_product(x, key, levels, base)
@@ -98,7 +100,7 @@ def test_tfhe_argument_errors_and_range_check():
     with pytest.raises(ntt.NttError) as e:
         ntt.Plan(12, [W.POOL50[0]]).tfhe_external_product(
             torch.zeros((1, 2, 4096), dtype=torch.int64, device="cuda"),
-            torch.zeros((6, 2, 4096), dtype=torch.int64, device="cuda"), 3, 8)
+            torch.zeros((6, 2, 4096, 2), dtype=torch.int64, device="cuda"), 3, 8)
     assert e.value.code == -10
     with pytest.raises(ntt.NttError) as e:
         ntt.Plan(10, [q, W.Q59_N1024]).tfhe_external_product(x, key, 3, 8)
@@ -107,4 +109,8 @@ def test_tfhe_argument_errors_and_range_check():
     bad = x.clone()
     bad[1, 0, 5] = q
     chk.tfhe_external_product(bad, key, 3, 8, out=torch.empty_like(bad))
+    assert chk.status() == -8
+    badkey = torch.zeros((6, 2, 1024), dtype=torch.int64, device="cuda")
+    badkey[3, 1, 7] = q
+    chk.tfhe_key_prepare(badkey, 3)
     assert chk.status() == -8
