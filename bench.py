@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "mixed_batch", "tfhe_blind_rotation", "plain_n1024", "cost_model",
                              "serving", "hmul_fused", "mixed_small", "tfhe_cmux", "ckks_bconv",
-                             "ckks_rescale"],
+                             "ckks_rescale", "natural_order"],
                     help="the line the driver records is the default (CKKS-HMUL-shaped) workload")
     return ap.parse_args()
 
@@ -863,6 +863,57 @@ def run_ckks_rescale(args):
     return 0
 
 
+def run_natural_order(args):
+    """Forward + inverse NTT of the CKKS-HMUL-shaped batch (96 rows at
+    N = 2^16) with natural-order plans (NTT_FLAG_NATURAL_ORDER: one
+    bit-reversal pass over HBM per transform for the two-kernel schedule),
+    beside the same transforms in bit-reversed order; L2 flushed before every
+    step."""
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2410_05934_gb300 import build as B
+    B.build_product()
+    import paper_2410_05934_gb300 as ntt
+    from paper_2410_05934_gb300 import workloads as W
+    stream = torch.cuda.current_stream()
+    w = W.ckks_hmul_n65536(seed=W.DEFAULT_SEED + rank)
+    x = to_dev_np(torch, w["x"])
+    y = torch.empty_like(x)
+    nat = ntt.Plan(16, w["moduli"], 4, flags=ntt.NTT_FLAG_NATURAL_ORDER)
+    brv = ntt.Plan(16, w["moduli"], 4)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    def step(p):
+        p.forward(x, y)
+        n1 = p.last_launches()
+        p.inverse(y, y)
+        return n1 + p.last_launches()
+    for _ in range(max(3, args.warmup)):
+        step(nat)
+        step(brv)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, launches = _events_loop(torch, stream, args.steps, lambda: step(nat), flush)
+    clk = clocks.stop()
+    ms_b, _ = _events_loop(torch, stream, args.steps, lambda: step(brv), flush)
+    t = sum(ms) * 1e-3
+    coef = 2 * 96 * 65536 * args.steps
+    line = {"metric": "NTT coeffs/s (coefficient-transforms per second)", "value": coef / t, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "gpu_launches": launches, "clocks": clk,
+            "config": {"workload": "natural_order", "log2n": 16, "rows": 96,
+                       "step": "forward (natural-order output) + inverse (natural-order input), 96 rows",
+                       "l2": "flushed before every step (512 MiB write, outside the step events)"},
+            "bit_reversed": {"ms_per_step": sum(ms_b) / args.steps, "value": coef / (sum(ms_b) * 1e-3)},
+            "overhead": sum(ms) / sum(ms_b) - 1.0}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def run_cost_model(args):
     """Schedule cost model: train on the committed GB300 timing sweep with the
     library's GPU kernels; regret on 100 held-out shapes vs exhaustive tuning."""
@@ -929,6 +980,8 @@ def main():
         return run_ckks_bconv(args)
     if args.workload == "ckks_rescale":
         return run_ckks_rescale(args)
+    if args.workload == "natural_order":
+        return run_natural_order(args)
     if args.workload != WORKLOAD:
         return run_other(args)
     return run_ours(args)

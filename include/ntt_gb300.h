@@ -58,6 +58,9 @@ extern "C" {
 #define NTT_FLAG_HOST_ONLY  1u  /* build and validate on the host only: no device
                                    memory, compute entry points return NTT_ERR_ARG */
 #define NTT_FLAG_CHECK      2u  /* kernels check inputs < q (status word)          */
+#define NTT_FLAG_NATURAL_ORDER 4u /* the NTT domain in natural order: ntt_forward
+                                   writes A_nat[j] = a(psi^(2j + 1)), ntt_inverse
+                                   reads that order (see ntt_forward)             */
 
 #define NTT_MIN_LOG2N 1
 #define NTT_MAX_LOG2N 16
@@ -92,6 +95,13 @@ int ntt_plan_shape(ntt_plan_t plan, uint32_t* log2n, uint32_t* n_moduli, uint32_
  * batch * n_moduli rows: d_in -> d_out (may alias).  The inverse is the GS
  * bit-reversed -> natural transform with psi^-1, scaled by N^-1, so that
  * ntt_inverse(ntt_forward(a)) = a.
+ * With NTT_FLAG_NATURAL_ORDER the NTT domain is in natural order instead:
+ * the forward writes A[brv(j)] = a(psi^(2j + 1)) at j and the inverse reads
+ * that order.  One-kernel schedules (N <= 2^12) permute inside the tile at no
+ * extra memory traffic; two-kernel schedules add one bit-reversal pass over
+ * the rows (one more kernel launch).  The fused operators (ntt_hmul_tensor,
+ * ntt_rescale, tfhe_*, ntt_batch_execute_static) take bit-reversed plans only
+ * and return NTT_ERR_UNSUPPORTED for natural-order ones.
  */
 int ntt_forward(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, void* cuda_stream);
 int ntt_inverse(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, void* cuda_stream);

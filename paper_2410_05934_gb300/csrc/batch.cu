@@ -158,6 +158,7 @@ __global__ void __launch_bounds__(NTT_BATCH_THREADS, BatchOcc<MC, NMAX>::ctas)
         a.src_mode = 0;
         a.in_b = nullptr;
         a.aux_q = 0;
+        a.nat = 0;
         if (rq.inverse)
             batch_dispatch<true, MC, NMAX>(a, rq, it.n_rows, smem);
         else
@@ -248,6 +249,7 @@ __global__ void __launch_bounds__(NTT_BATCH_THREADS, NTT_BATCH_MIN_CTAS)
         a.src_mode = 0;
         a.in_b = nullptr;
         a.aux_q = 0;
+        a.nat = 0;
         if (sr.inverse)
             batch_dispatch<true, MC, 16>(a, rq, n_rows, smem);
         else
@@ -530,6 +532,7 @@ static int batch_launch_request(ntt_batch_t b, size_t i, uint32_t sid, cudaStrea
     d.src_mode = 0;
     d.in_b = nullptr;
     d.aux_q = 0;
+    d.nat = 0;
     const LaunchFn fn = r.inverse ? table[idx].inv : table[idx].fwd;
     return fn(d, r.in, r.out, 0, (uint64_t)r.n_polys * r.n_moduli, st, launches);
 }
@@ -651,7 +654,7 @@ int ntt_batch_execute_static(const ntt_plan_request_t* reqs, uint32_t n_reqs, vo
         const ntt_plan_s* p = r.plan;
         if (!p || (p->h.flags & NTT_FLAG_HOST_ONLY) || p->device != dev || r.inverse > 1 || !r.in || !r.out)
             return NTT_ERR_ARG;
-        if (p->h.log2n < NTT_BATCH_MIN_LOG2N) return NTT_ERR_UNSUPPORTED;
+        if (p->h.log2n < NTT_BATCH_MIN_LOG2N || (p->h.flags & NTT_FLAG_NATURAL_ORDER)) return NTT_ERR_UNSUPPORTED;
         const uint32_t polys = r.n_polys ? r.n_polys : p->h.batch;
         if (polys > p->h.batch) return NTT_ERR_ARG;
         if (!aligned16p(r.in) || !aligned16p(r.out)) return NTT_ERR_ALIGN;

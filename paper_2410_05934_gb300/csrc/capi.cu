@@ -112,6 +112,7 @@ static PlanDev plan_dev(const ntt_plan_s* p) {
     d.src_mode = 0;
     d.in_b = nullptr;
     d.aux_q = 0;
+    d.nat = 0;
     return d;
 }
 
@@ -123,6 +124,8 @@ static int check_device(const ntt_plan_s* p) {
     if (cudaGetDevice(&dev) != cudaSuccess) return NTT_ERR_CUDA;
     return dev == p->device ? NTT_OK : NTT_ERR_ARG;
 }
+
+static bool natural(const ntt_plan_s* p) { return (p->h.flags & NTT_FLAG_NATURAL_ORDER) != 0; }
 
 static int transform(ntt_plan_t plan, bool inverse, const uint64_t* in, uint64_t* out,
                      uint64_t row_begin, uint64_t n_rows, void* stream) {
@@ -137,7 +140,22 @@ static int transform(ntt_plan_t plan, bool inverse, const uint64_t* in, uint64_t
     if (n_rows == 0) return NTT_OK;
     PlanDev d = plan_dev(plan);
     const SchedEntry& e = g_table[idx];
-    return (inverse ? e.inv : e.fwd)(d, in, out, row_begin, n_rows, stream, &plan->last_launches);
+    const LaunchFn fn = inverse ? e.inv : e.fwd;
+    if (!natural(plan)) return fn(d, in, out, row_begin, n_rows, stream, &plan->last_launches);
+    // natural order: a one-kernel schedule holds whole rows and permutes in
+    // shared memory; two-kernel schedules add a bit-reversal pass over HBM
+    if (g_params[idx].kind == 1) {
+        d.nat = 1;
+        return fn(d, in, out, row_begin, n_rows, stream, &plan->last_launches);
+    }
+    if (!inverse) {
+        rc = fn(d, in, out, row_begin, n_rows, stream, &plan->last_launches);
+        if (rc) return rc;
+        return launch_bitrev_rows(out, out, row_begin, n_rows, plan->h.log2n, stream, &plan->last_launches);
+    }
+    rc = launch_bitrev_rows(in, out, row_begin, n_rows, plan->h.log2n, stream, &plan->last_launches);
+    if (rc) return rc;
+    return fn(d, out, out, row_begin, n_rows, stream, &plan->last_launches);
 }
 
 static void free_device(ntt_plan_s* p) {
@@ -244,6 +262,7 @@ int ntt_hmul_tensor(ntt_plan_t plan, const uint64_t* d_a, const uint64_t* d_b, u
                     void* cuda_stream) {
     if (!plan || !d_a || !d_b || !d_out) return NTT_ERR_ARG;
     if (!aligned16(d_a) || !aligned16(d_b) || !aligned16(d_out)) return NTT_ERR_ALIGN;
+    if (natural(plan)) return NTT_ERR_UNSUPPORTED;
     int rc = check_device(plan);
     if (rc) return rc;
     // the tensor product runs in the direct form of the inverse's first kernel
@@ -276,6 +295,7 @@ int ntt_rescale(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, uint64_t
     if (!aligned16(d_in) || !aligned16(d_out) || !aligned16(d_work)) return NTT_ERR_ALIGN;
     const uint32_t L = plan->h.n_moduli;
     if (L < 2) return NTT_ERR_ARG;
+    if (natural(plan)) return NTT_ERR_UNSUPPORTED;
     if (n_polys == 0) n_polys = plan->h.batch;
     if (n_polys > plan->h.batch) return NTT_ERR_ARG;
     for (uint32_t i = 0; i + 1 < L; ++i)

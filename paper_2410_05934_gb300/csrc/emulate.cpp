@@ -116,6 +116,7 @@ static TileArgs emu_args(const PlanDev& p, const uint64_t* in, uint64_t* out, ui
     a.src_mode = p.src_mode;
     a.in_b = p.in_b;
     a.aux_q = p.aux_q;
+    a.nat = p.nat;
     return a;
 }
 
@@ -147,7 +148,7 @@ static int emu_kernel(const PlanDev& p, const uint64_t* in, uint64_t* out, uint6
                 const int tin = tid >> C::LOGT, t = tid & (C::T - 1);
                 uint64_t* sm_t = sm.data() + (size_t)tin * C::TILE_WORDS;
                 load_direct<C>(st[tid], a, L[tin], t, sm_t);
-                write_pairs_swizzled<C>(st[tid], L[tin], t, sm_t);
+                write_input_tile<C>(st[tid], a, L[tin], t, sm_t);
             }
             emu_compute_store<C>(a, L, sm.data(), st);
         }
@@ -192,7 +193,7 @@ static int emu_kernel(const PlanDev& p, const uint64_t* in, uint64_t* out, uint6
             }
             for (int tid = 0; tid < C::THREADS; ++tid) {
                 const int tin = tid >> C::LOGT, t = tid & (C::T - 1);
-                write_pairs_swizzled<C>(st[tid], L[tin], t, buf + (size_t)tin * C::TILE_WORDS);
+                write_input_tile<C>(st[tid], a, L[tin], t, buf + (size_t)tin * C::TILE_WORDS);
             }
             emu_compute_store<C>(a, L, buf, st);
         }
@@ -235,12 +236,13 @@ typedef int (*EmuFn)(const PlanDev&, const uint64_t*, uint64_t*, uint64_t, uint6
 struct EmuEntry {
     uint32_t log2n;
     EmuFn fwd, inv;
+    uint32_t kernels;
 };
 #define NTT_EMU_S1(LOGN, LOGT, LOGRP, TPC, PIPE) \
-    {LOGN, &emu_s1<LOGN, LOGT, LOGRP, TPC, PIPE, false>, &emu_s1<LOGN, LOGT, LOGRP, TPC, PIPE, true>},
+    {LOGN, &emu_s1<LOGN, LOGT, LOGRP, TPC, PIPE, false>, &emu_s1<LOGN, LOGT, LOGRP, TPC, PIPE, true>, 1},
 #define NTT_EMU_S2(LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE)          \
     {LOGN, &emu_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE, false>,   \
-     &emu_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE, true>},
+     &emu_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE, true>, 2},
 static const EmuEntry g_emu[] = {NTT_SCHEDULES_ALL(NTT_EMU_S1, NTT_EMU_S2)};
 static const int g_emu_count = (int)(sizeof(g_emu) / sizeof(g_emu[0]));
 
@@ -256,10 +258,10 @@ static const EmuEntry* emu_find(uint32_t log2n, uint32_t id) {
 
 // the mixed-batch kernel's per-N configurations, direct form
 #define NTT_EMU_BATCH_SINGLE(LOGN, LOGT, LOGRP, TPC, MODE) \
-    {LOGN, &emu_s1<LOGN, LOGT, LOGRP, TPC, MODE, false>, &emu_s1<LOGN, LOGT, LOGRP, TPC, MODE, true>},
+    {LOGN, &emu_s1<LOGN, LOGT, LOGRP, TPC, MODE, false>, &emu_s1<LOGN, LOGT, LOGRP, TPC, MODE, true>, 1},
 #define NTT_EMU_BATCH_SPLIT(LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, MODE)        \
     {LOGN, &emu_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, MODE, false>,      \
-     &emu_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, MODE, true>},
+     &emu_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, MODE, true>, 2},
 static const EmuEntry g_emu_batch[] = {NTT_BATCH_CONFIGS(NTT_EMU_BATCH_SINGLE, NTT_EMU_BATCH_SPLIT)};
 
 struct EmuPlan {
@@ -371,7 +373,34 @@ int nttemu_schedule_count(uint32_t log2n) {
     return c;
 }
 
-// Runs schedule `sched` of the plan's N over rows [row_begin, row_begin + n_rows).
+// the bit-reversal pass of two-kernel natural-order transforms, with the
+// kernel's tile functions (256 pseudo-threads per tile)
+static void emu_bitrev_rows(const uint64_t* in, uint64_t* out, uint64_t row_begin, uint64_t n_rows, uint32_t log2n) {
+    const BrvGeom g = brv_geom((int)log2n);
+    std::vector<uint64_t> sm(2 * NTT_BRV_PITCH * 32, 0xdeadbeefdeadbeefull);
+    const bool in_place = in == out;
+    for (uint64_t u = 0; u < (n_rows << g.M); ++u) {
+        const uint64_t base = (row_begin + (u >> g.M)) << log2n;
+        const uint32_t b = (uint32_t)(u & ((1ull << g.M) - 1)), b2 = brv_bits(b, g.M);
+        if (in_place) {
+            if (b > b2) continue;
+            for (int tid = 0; tid < 256; ++tid) {
+                brv_tile_load(in + base, g, b, tid, 256, sm.data());
+                if (b2 != b) brv_tile_load(in + base, g, b2, tid, 256, sm.data() + NTT_BRV_PITCH * 32);
+            }
+            for (int tid = 0; tid < 256; ++tid) {
+                brv_tile_store(out + base, g, b, tid, 256, sm.data());
+                if (b2 != b) brv_tile_store(out + base, g, b2, tid, 256, sm.data() + NTT_BRV_PITCH * 32);
+            }
+        } else {
+            for (int tid = 0; tid < 256; ++tid) brv_tile_load(in + base, g, b, tid, 256, sm.data());
+            for (int tid = 0; tid < 256; ++tid) brv_tile_store(out + base, g, b, tid, 256, sm.data());
+        }
+    }
+}
+
+// Runs schedule `sched` of the plan's N over rows [row_begin, row_begin + n_rows)
+// (natural order when the plan has NTT_FLAG_NATURAL_ORDER, as ntt_forward does).
 int nttemu_transform(void* plan, uint32_t sched, int inverse, const uint64_t* in, uint64_t* out,
                      uint64_t row_begin, uint64_t n_rows) {
     EmuPlan* p = static_cast<EmuPlan*>(plan);
@@ -390,7 +419,21 @@ int nttemu_transform(void* plan, uint32_t sched, int inverse, const uint64_t* in
     d.src_mode = 0;
     d.in_b = nullptr;
     d.aux_q = 0;
-    return (inverse ? e->inv : e->fwd)(d, in, out, row_begin, n_rows);
+    d.nat = 0;
+    const EmuFn fn = inverse ? e->inv : e->fwd;
+    if (!(p->h.flags & NTT_FLAG_NATURAL_ORDER)) return fn(d, in, out, row_begin, n_rows);
+    if (e->kernels == 1) {
+        d.nat = 1;
+        return fn(d, in, out, row_begin, n_rows);
+    }
+    if (!inverse) {
+        const int rc = fn(d, in, out, row_begin, n_rows);
+        if (rc) return rc;
+        emu_bitrev_rows(out, out, row_begin, n_rows, p->h.log2n);
+        return NTT_OK;
+    }
+    emu_bitrev_rows(in, out, row_begin, n_rows, p->h.log2n);
+    return fn(d, out, out, row_begin, n_rows);
 }
 
 // Runs the mixed-batch kernel's configuration for the plan's N.
@@ -410,6 +453,8 @@ int nttemu_batch_transform(void* plan, int inverse, const uint64_t* in, uint64_t
         d.src_mode = 0;
         d.in_b = nullptr;
         d.aux_q = 0;
+        d.nat = 0;
+    d.nat = 0;
         return (inverse ? e.inv : e.fwd)(d, in, out, 0, p->h.rows);
     }
     return NTT_ERR_UNSUPPORTED;
@@ -433,6 +478,7 @@ int nttemu_hmul_tensor(void* plan, uint32_t sched, const uint64_t* a, const uint
     d.src_mode = 1;
     d.in_b = b;
     d.aux_q = 0;
+    d.nat = 0;
     return e->inv(d, a, out, 0, 3ull * p->h.n_moduli);
 }
 
@@ -515,6 +561,7 @@ int nttemu_rescale(void* plan, uint32_t sched, const uint64_t* in, uint64_t* out
     last.src_mode = 0;
     last.in_b = nullptr;
     last.aux_q = 0;
+    last.nat = 0;
     int rc = e->inv(last, work, work, 0, n_polys);
     if (rc) return rc;
     PlanDev d = last;

@@ -3,6 +3,8 @@
 // HBM-bound: 24 bytes move per coefficient for one 64x64-bit product.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "ntt_gb300.h"
 #include "ntt_launch.h"
 
@@ -82,6 +84,49 @@ __global__ void __launch_bounds__(256) k_bench_bfly(uint64_t q, uint64_t w0, uin
 #pragma unroll
     for (int i = 0; i < P; ++i) acc ^= X[i] ^ Y[i];
     if (acc == 0x5eed5eed5eedull) sink[tid] = acc;   // practically never taken
+}
+
+// Bit-reversal permutation of rows [row_begin, row_begin + n_rows): unit
+// u = (row, tile b).  In place, the CTA of the smaller of b and brv(b) swaps
+// the pair (both tiles are read before either is written); out of place,
+// every tile goes to its image.
+__global__ void __launch_bounds__(256) k_bitrev_rows(const uint64_t* in, uint64_t* out, uint64_t row_begin,
+                                                     uint64_t n_rows, int log2n, int in_place) {
+    __shared__ __align__(16) uint64_t sm[2 * NTT_BRV_PITCH * 32];
+    const BrvGeom g = brv_geom(log2n);
+    const uint64_t units = n_rows << g.M;
+    for (uint64_t u = blockIdx.x; u < units; u += gridDim.x) {
+        const uint64_t row = row_begin + (u >> g.M);
+        const uint32_t b = (uint32_t)(u & ((1ull << g.M) - 1)), b2 = brv_bits(b, g.M);
+        const uint64_t base = row << log2n;
+        if (in_place) {
+            if (b > b2) continue;           // uniform over the CTA
+            brv_tile_load(in + base, g, b, threadIdx.x, blockDim.x, sm);
+            if (b2 != b) brv_tile_load(in + base, g, b2, threadIdx.x, blockDim.x, sm + NTT_BRV_PITCH * 32);
+            __syncthreads();
+            brv_tile_store(out + base, g, b, threadIdx.x, blockDim.x, sm);
+            if (b2 != b) brv_tile_store(out + base, g, b2, threadIdx.x, blockDim.x, sm + NTT_BRV_PITCH * 32);
+        } else {
+            brv_tile_load(in + base, g, b, threadIdx.x, blockDim.x, sm);
+            __syncthreads();
+            brv_tile_store(out + base, g, b, threadIdx.x, blockDim.x, sm);
+        }
+        __syncthreads();
+    }
+}
+
+int launch_bitrev_rows(const uint64_t* in, uint64_t* out, uint64_t row_begin, uint64_t n_rows, uint32_t log2n,
+                       void* stream, uint32_t* launches) {
+    if (n_rows == 0) return NTT_OK;
+    const BrvGeom g = brv_geom((int)log2n);
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return NTT_ERR_CUDA;
+    const uint64_t units = n_rows << g.M;
+    const unsigned grid = (unsigned)std::min<uint64_t>(units, (uint64_t)std::max(1, sms) * 32u);
+    k_bitrev_rows<<<grid, 256, 0, (cudaStream_t)stream>>>(in, out, row_begin, n_rows, (int)log2n, in == out ? 1 : 0);
+    if (launches) ++*launches;
+    return cudaPeekAtLastError() == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
 }
 
 int launch_bench_bfly(uint64_t q, uint32_t kind, uint32_t blocks, uint32_t threads, uint32_t iters,

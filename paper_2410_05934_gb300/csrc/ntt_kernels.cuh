@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(C::THREADS) k_ntt_tile(TileArgs a) {
     uint64_t* sm = smem + (size_t)tin * C::TILE_WORDS;
     TileRegs<C> st;
     load_direct<C>(st, a, L, t, sm);
-    write_pairs_swizzled<C>(st, L, t, sm);
+    write_input_tile<C>(st, a, L, t, sm);
     __syncthreads();
     run_passes<C, 0>(st, a, L, t, sm);
     store_tile<C>(a, L, t, sm);
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(C::THREADS) k_ntt_tile_pipe(TileArgs a, uint64
         TileRegs<C> st;
         relayout_read<C>(st, a, L, t, sm);
         __syncthreads();
-        write_pairs_swizzled<C>(st, L, t, sm);
+        write_input_tile<C>(st, a, L, t, sm);
         __syncthreads();
         run_passes<C, 0>(st, a, L, t, sm);
         store_tile<C>(a, L, t, sm);
@@ -204,6 +204,7 @@ int launch_tile_kernel(const PlanDev& p, const uint64_t* in, uint64_t* out, uint
     a.src_mode = p.src_mode;
     a.in_b = p.in_b;
     a.aux_q = p.aux_q;
+    a.nat = p.nat;
     if (C::PIPE && C::FIRST && p.src_mode) return NTT_ERR_UNSUPPORTED;  // direct form only
     const uint64_t groups = (a.n_tiles + C::TPC - 1) / C::TPC;
     if (groups == 0) return NTT_OK;

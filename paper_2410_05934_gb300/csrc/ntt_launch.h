@@ -19,6 +19,7 @@ struct PlanDev {
                         // 2: the forward transform is the Rescale by aux_q (TileArgs)
     const uint64_t* in_b;
     uint64_t aux_q;
+    uint32_t nat;       // natural-order forward output / inverse input (full-row kernels)
 };
 
 // Transforms rows [row_begin, row_begin + n_rows) of the layout that starts
@@ -39,6 +40,10 @@ int launch_s2(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t row_
 int launch_pointwise(const PlanDev& p, uint32_t log2n, const uint64_t* a, const uint64_t* b,
                      uint64_t* c, uint64_t row_begin, uint64_t n_rows, void* stream,
                      uint32_t* launches);
+
+// bit-reversal permutation of rows (in == out: in place)
+int launch_bitrev_rows(const uint64_t* in, uint64_t* out, uint64_t row_begin, uint64_t n_rows, uint32_t log2n,
+                       void* stream, uint32_t* launches);
 
 int launch_bench_bfly(uint64_t q, uint32_t kind, uint32_t blocks, uint32_t threads, uint32_t iters,
                       uint64_t* sink, void* stream);

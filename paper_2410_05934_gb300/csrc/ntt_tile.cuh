@@ -90,6 +90,9 @@ struct TileArgs {
     uint32_t src_mode;
     const uint64_t* in_b;
     uint64_t aux_q;
+    // natural order (full-row tiles only): the forward's last kernel stores
+    // A[brv(j)] at j, the inverse's first kernel takes its input that way
+    uint32_t nat;
 };
 
 // floor(n / d) for n < 2^32 and 2 <= d < 2^32 from M = ceil(2^64 / d):
@@ -125,6 +128,17 @@ NTT_HD constexpr uint32_t swz(uint32_t e) {
 }
 
 // Places the bits of x around an r-bit hole at position pe (linear in x).
+// the low `bits` bits of k reversed
+NTT_HD uint32_t brv_bits(uint32_t k, int bits) {
+#if defined(__CUDA_ARCH__)
+    return bits == 0 ? 0u : __brev(k) >> (32 - bits);
+#else
+    uint32_t r = 0;
+    for (int i = 0; i < bits; ++i) r |= ((k >> i) & 1u) << (bits - 1 - i);
+    return r;
+#endif
+}
+
 NTT_HD constexpr uint32_t spread(uint32_t x, int pe, int r) {
     return ((x >> pe) << (pe + r)) | (x & ((1u << pe) - 1));
 }
@@ -443,6 +457,67 @@ NTT_HD void write_pairs_swizzled(const TileRegs<C>& st, const TileLoc& L, int t,
     }
 }
 
+// ---- bit-reversal permutation of whole rows, tile by tile ----
+// With K = min(5, log2n / 2) and M = log2n - 2K, row index (a, b, c) (a and
+// c of K bits, b of M bits, a most significant) moves to (brv(c), brv(b),
+// brv(a)): tile b (all a, c) becomes tile brv(b), transposed with both
+// coordinates reversed.  Loads and stores run along c (contiguous).
+struct BrvGeom {
+    int K, M;
+};
+NTT_HD BrvGeom brv_geom(int log2n) {
+    BrvGeom g;
+    g.K = log2n / 2 < 5 ? log2n / 2 : 5;
+    g.M = log2n - 2 * g.K;
+    return g;
+}
+#define NTT_BRV_PITCH 33    // 2^5 + 1 words per tile row in shared memory
+
+// tile b of row `src` -> sm (threads tid, tid + nthreads, ...)
+NTT_HD void brv_tile_load(const uint64_t* src, BrvGeom g, uint32_t b, int tid, int nthreads, uint64_t* sm) {
+    const uint32_t side = 1u << g.K;
+    for (uint32_t idx = (uint32_t)tid; idx < side * side; idx += (uint32_t)nthreads) {
+        const uint32_t a = idx >> g.K, c = idx & (side - 1);
+        const uint64_t j = ((uint64_t)a << (g.M + g.K)) | ((uint64_t)b << g.K) | c;
+        NTT_SMEM_CHECK(a * NTT_BRV_PITCH + c, NTT_BRV_PITCH * 32);
+        sm[a * NTT_BRV_PITCH + c] = src[j];
+    }
+}
+
+// sm (tile b) -> its place in row `dst`: tile brv(b), position (a2, c2)
+// takes the element loaded at (brv(c2), brv(a2))
+NTT_HD void brv_tile_store(uint64_t* dst, BrvGeom g, uint32_t b, int tid, int nthreads, const uint64_t* sm) {
+    const uint32_t side = 1u << g.K, b2 = brv_bits(b, g.M);
+    for (uint32_t idx = (uint32_t)tid; idx < side * side; idx += (uint32_t)nthreads) {
+        const uint32_t a2 = idx >> g.K, c2 = idx & (side - 1);
+        const uint32_t a = brv_bits(c2, g.K), c = brv_bits(a2, g.K);
+        const uint64_t j = ((uint64_t)a2 << (g.M + g.K)) | ((uint64_t)b2 << g.K) | c2;
+        NTT_SMEM_CHECK(a * NTT_BRV_PITCH + c, NTT_BRV_PITCH * 32);
+        dst[j] = sm[a * NTT_BRV_PITCH + c];
+    }
+}
+
+// The first kernel's registers -> shared memory.  A full-row tile of an
+// inverse transform whose input is in natural order (a.nat) places element
+// j of the row at tile position brv(j); everything else uses the pair layout.
+template <class C>
+NTT_HD void write_input_tile(const TileRegs<C>& st, const TileArgs& a, const TileLoc& L, int t, uint64_t* sm) {
+    if (C::FIRST && C::INV && C::A == C::LOGN && a.nat) {
+        if (!L.valid) return;
+#pragma unroll
+        for (int i = 0; i < C::R / 2; ++i) {
+            const uint32_t k = 2u * (uint32_t)t + 2u * (uint32_t)i * C::T;
+            const uint32_t e0 = brv_bits(k, C::LOGN), e1 = brv_bits(k + 1, C::LOGN);
+            NTT_SMEM_CHECK(swz(e0), C::E);
+            NTT_SMEM_CHECK(swz(e1), C::E);
+            sm[swz(e0)] = st.x[2 * i];
+            sm[swz(e1)] = st.x[2 * i + 1];
+        }
+        return;
+    }
+    write_pairs_swizzled<C>(st, L, t, sm);
+}
+
 // natural-order shared memory (pipelined staging) -> registers in the pair
 // layout; checks canonical inputs for the first kernel of a transform
 template <class C>
@@ -591,10 +666,22 @@ NTT_HD void store_tile(const TileArgs& a, const TileLoc& L, int t, const uint64_
     const uint64_t q = a.lc[L.limb].q, two_q = a.lc[L.limb].two_q;
     const uint64_t one_p = a.lc[L.limb].one_p;
     const uint32_t b = swz(2u * (uint32_t)t);
+    const bool nat = C::LAST && !C::INV && C::A == C::LOGN && a.nat;
 #pragma unroll
     for (int i = 0; i < C::R / 2; ++i) {
         const uint32_t c = swz(2u * (uint32_t)i * C::T);
-        uint64_t x = sm[b ^ c], y = sm[(b ^ c) ^ 1u];
+        uint64_t x, y;
+        if (nat) {      // output j holds tile position brv(j)
+            const uint32_t k = 2u * (uint32_t)t + 2u * (uint32_t)i * C::T;
+            const uint32_t s0 = swz(brv_bits(k, C::LOGN)), s1 = swz(brv_bits(k + 1, C::LOGN));
+            NTT_SMEM_CHECK(s0, C::E);
+            NTT_SMEM_CHECK(s1, C::E);
+            x = sm[s0];
+            y = sm[s1];
+        } else {
+            x = sm[b ^ c];
+            y = sm[(b ^ c) ^ 1u];
+        }
         if (C::LAST) {
             if (C::MC == 1 && !C::INV) {  // [0, 65q) -> [0, q)
                 x = reduce_full_small(x, one_p, q, two_q);

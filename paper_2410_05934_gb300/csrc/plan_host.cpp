@@ -128,7 +128,7 @@ int build_plan_host(PlanHost& h, uint32_t log2n, const uint64_t* moduli, uint32_
                     uint32_t batch, uint32_t flags) {
     if (log2n < NTT_MIN_LOG2N || log2n > NTT_MAX_LOG2N) return NTT_ERR_ARG;
     if (!moduli || n_moduli == 0 || batch == 0) return NTT_ERR_ARG;
-    if (flags & ~(NTT_FLAG_HOST_ONLY | NTT_FLAG_CHECK)) return NTT_ERR_ARG;
+    if (flags & ~(NTT_FLAG_HOST_ONLY | NTT_FLAG_CHECK | NTT_FLAG_NATURAL_ORDER)) return NTT_ERR_ARG;
     const uint64_t n = 1ull << log2n;
     const u128 total = (u128)batch * n_moduli * n;
     if (total >= ((u128)1 << 40)) return NTT_ERR_ARG;

@@ -88,6 +88,7 @@ static int cmux_setup(ntt_plan_t plan, const uint64_t* d_key, uint32_t levels, u
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device) return NTT_ERR_ARG;
     if (plan->h.n_moduli != 1) return NTT_ERR_ARG;
+    if (plan->h.flags & NTT_FLAG_NATURAL_ORDER) return NTT_ERR_UNSUPPORTED;
     if (plan->h.log2n < NTT_TFHE_MIN_LOG2N || plan->h.log2n > NTT_TFHE_MAX_LOG2N) return NTT_ERR_UNSUPPORTED;
     if (((uintptr_t)d_key & 15u) != 0) return NTT_ERR_ALIGN;
     const uint64_t q = plan->h.moduli[0];

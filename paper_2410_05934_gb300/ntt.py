@@ -13,6 +13,7 @@ from ._native import U32P, U64P, check, load
 
 NTT_FLAG_HOST_ONLY = 1
 NTT_FLAG_CHECK = 2
+NTT_FLAG_NATURAL_ORDER = 4
 
 
 def _stream_handle(stream):

@@ -298,3 +298,30 @@ def test_rescale_matches_oracle(log2n):
         for p in range(2):
             assert np.array_equal(got[p], want[p]), (s, p)
     assert tried >= 1 and plan.status() == 0
+
+
+@pytest.mark.parametrize("log2n", [1, 3, 10, 12, 13, 14])
+def test_natural_order_every_schedule(log2n):
+    """NTT_FLAG_NATURAL_ORDER: the forward writes A[brv(j)] at j (fused into
+    the store of one-kernel schedules, a tile bit-reversal pass otherwise) and
+    the inverse reads that order back."""
+    from oracle import oracle as O
+    n = 1 << log2n
+    q = W.POOL50[2] if log2n > 10 else W.Q62_N1024
+    rng = np.random.default_rng(log2n)
+    x = np.array([rng.integers(0, q, n, dtype=np.uint64) for _ in range(3)])
+    brv = np.array([O.bitrev(j, log2n) for j in range(n)], dtype=np.int64)
+    ref = O.transform_rows(x, [q] * 3)            # bit-reversed order
+    want = ref[:, brv]
+    plan = emu.EmuPlan(log2n, [q], 3, flags=4)
+    for s in range(emu.schedule_count(log2n)):
+        got = plan.transform(x, s)
+        assert np.array_equal(got, want), s
+        back = plan.transform(got, s, inverse=True)
+        assert np.array_equal(back, x), s
+        y = got.copy()
+        plan.transform(y, s, inverse=True, out=y)   # in place (tile pairs swap)
+        assert np.array_equal(y, x), s
+    # a row range
+    part = plan.transform(x, 0, row_begin=1, n_rows=1, out=np.zeros_like(x))
+    assert np.array_equal(part[1], want[1]) and not part[0].any() and not part[2].any()

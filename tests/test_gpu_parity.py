@@ -296,3 +296,41 @@ def test_hand_derived_known_answers():
         p.pointwise(xa, xb, xa)
         p.inverse(xa)
         assert to_host(xa).tolist() == c
+
+
+@pytest.mark.parametrize("log2n", [10, 13, 16])
+def test_natural_order_plans(oracle, log2n):
+    """NTT_FLAG_NATURAL_ORDER: forward output A[brv(j)] at j, inverse back,
+    in place too; sampled against the oracle at N = 2^16."""
+    n = 1 << log2n
+    mods = _moduli(log2n, "small")
+    x = W.rows_uniform(23, log2n, mods * 2, n)
+    p = ntt.Plan(log2n, mods, 2, flags=4)
+    d = to_dev(x)
+    out = torch.empty_like(d)
+    p.forward(d, out)
+    got = to_host(out)
+    rng = np.random.default_rng(log2n)
+    idx = np.stack([np.concatenate([[0, 1, n - 1], rng.integers(0, n, 13)]) for _ in range(4)]).astype(np.uint32)
+    brv = np.array([[oracle.bitrev(int(j), log2n) for j in row] for row in idx], dtype=np.uint32)
+    ref = oracle.transform_rows(x, [mods[r % 2] for r in range(4)], idx=brv)
+    assert np.array_equal(got[np.arange(4)[:, None], idx], ref)
+    back = torch.empty_like(d)
+    p.inverse(out, back)
+    assert torch.equal(back, d)
+    p.inverse(out)                                   # in place
+    assert torch.equal(out, d)
+    assert p.status() == 0
+
+
+def test_natural_order_plans_reject_fused_operators():
+    q = W.Q62_N1024
+    p = ntt.Plan(10, [q], 3, flags=4)
+    z = torch.zeros((3, 1024), dtype=torch.int64, device="cuda")
+    with pytest.raises(ntt.NttError) as e:
+        p.hmul_tensor(z[:2], z[:2], torch.zeros((3, 1024), dtype=torch.int64, device="cuda"))
+    assert e.value.code == -10
+    with pytest.raises(ntt.NttError) as e:
+        p.tfhe_external_product(torch.zeros((1, 2, 1024), dtype=torch.int64, device="cuda"),
+                                torch.zeros((6, 2, 1024, 2), dtype=torch.int64, device="cuda"), 3, 8)
+    assert e.value.code == -10
