@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "mixed_batch", "tfhe_blind_rotation", "plain_n1024", "cost_model",
                              "serving", "hmul_fused", "mixed_small", "tfhe_cmux", "ckks_bconv",
-                             "ckks_rescale", "natural_order"],
+                             "ckks_rescale", "natural_order", "word32"],
                     help="the line the driver records is the default (CKKS-HMUL-shaped) workload")
     return ap.parse_args()
 
@@ -914,6 +914,74 @@ def run_natural_order(args):
     return 0
 
 
+def run_word32(args):
+    """The TFHE blind-rotation-shaped batch (3780 forward + 1260 inverse rows
+    at N = 1024) with a 30-bit prime on 32-bit words (NTT_FLAG_WORD32),
+    beside the same batch with the 62-bit prime on 64-bit words; two
+    launches per step each, L2 flushed before every step."""
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2410_05934_gb300 import build as B
+    B.build_product()
+    import paper_2410_05934_gb300 as ntt
+    from paper_2410_05934_gb300 import _native
+    from paper_2410_05934_gb300 import workloads as W
+    L_ = _native.load()
+    stream = torch.cuda.current_stream()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    q30, n = 1073692673, 1024
+    xf = W.signed_digits_mod(W.DEFAULT_SEED + rank, 3, 3780 * n, q30).reshape(3780, n)
+    xi = W.uniform_mod(W.DEFAULT_SEED + rank, 4, 1260 * n, q30).reshape(1260, n)
+    f32 = torch.from_numpy(xf.astype(np.uint32).view(np.int32)).cuda()
+    i32 = torch.from_numpy(xi.astype(np.uint32).view(np.int32)).cuda()
+    pf = ntt.Plan(10, [q30], 3780, flags=ntt.NTT_FLAG_WORD32)
+    pi = ntt.Plan(10, [q30], 1260, flags=ntt.NTT_FLAG_WORD32)
+    w64 = W.tfhe_blind_rotation()
+    f64, i64 = to_dev_np(torch, w64["fwd"]), to_dev_np(torch, w64["inv"])
+    pf64, pi64 = ntt.Plan(10, w64["moduli"], 3780), ntt.Plan(10, w64["moduli"], 1260)
+    of32, oi32, of64, oi64 = (torch.empty_like(t) for t in (f32, i32, f64, i64))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    def step32():
+        pf.forward(f32, of32)
+        pi.inverse(i32, oi32)
+        return 2
+
+    def step64():
+        pf64.forward(f64, of64)
+        pi64.inverse(i64, oi64)
+        return 2
+    for _ in range(max(3, args.warmup)):
+        step32()
+        step64()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, launches = _events_loop(torch, stream, args.steps, step32, flush)
+    clk = clocks.stop()
+    ms64, _ = _events_loop(torch, stream, args.steps, step64, flush)
+    t = sum(ms) * 1e-3
+    coef = (3780 + 1260) * n * args.steps
+    bfly = (3780 + 1260) * (n // 2) * 10 * args.steps
+    peak = _probe(torch, L_, q30, 5, sms, stream)
+    line = {"metric": "NTT coeffs/s (coefficient-transforms per second)", "value": coef / t, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "gpu_launches": launches, "clocks": clk,
+            "config": {"workload": "word32", "log2n": 10, "modulus_bits": 30,
+                       "rows": "3780 forward (signed digits) + 1260 inverse", "l2": "flushed before every step"},
+            "word64_62bit": {"ms_per_step": sum(ms64) / args.steps, "value": coef / (sum(ms64) * 1e-3)},
+            "speedup_vs_word64": sum(ms64) / sum(ms),
+            "roofline": {"bound": "alu", "achieved": bfly / t / 1e9, "peak": peak / 1e9, "unit": "Gbutterfly/s",
+                         "frac": bfly / t / peak, "traffic": None,
+                         "peak_source": "in-run butterfly probe (kind 5, 32-bit forward butterfly)",
+                         "hbm": {"achieved_gbs": coef * 8 / t / 1e9, "bytes_per_coefficient": 8}}}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def run_cost_model(args):
     """Schedule cost model: train on the committed GB300 timing sweep with the
     library's GPU kernels; regret on 100 held-out shapes vs exhaustive tuning."""
@@ -982,6 +1050,8 @@ def main():
         return run_ckks_rescale(args)
     if args.workload == "natural_order":
         return run_natural_order(args)
+    if args.workload == "word32":
+        return run_word32(args)
     if args.workload != WORKLOAD:
         return run_other(args)
     return run_ours(args)

@@ -61,6 +61,13 @@ extern "C" {
 #define NTT_FLAG_NATURAL_ORDER 4u /* the NTT domain in natural order: ntt_forward
                                    writes A_nat[j] = a(psi^(2j + 1)), ntt_inverse
                                    reads that order (see ntt_forward)             */
+#define NTT_FLAG_WORD32     8u  /* 32-bit words: every modulus < 2^30, N <= 2^12;
+                                   ntt_forward / ntt_inverse(_rows) and
+                                   poly_mul_pointwise read and write uint32
+                                   coefficients (same layout); the fused
+                                   operators and natural order are not offered */
+#define NTT_WORD32_MAX_LOG2N 12
+#define NTT_WORD32_MAX_MODULUS_BITS 30
 
 #define NTT_MIN_LOG2N 1
 #define NTT_MAX_LOG2N 16
@@ -200,7 +207,8 @@ int ntt_plan_last_launches(ntt_plan_t plan, uint32_t* launches);
  * butterfly, both for any q < 2^62; kinds 2 and 3: the forward and inverse
  * butterflies of the small-modulus class, q < 2^57; kind 4: a 64 x 64 ->
  * 128-bit multiply-accumulate, the inner step of ntt_bconv, counted as one
- * operation).  Total operations = blocks * threads * iters * 8; time it with
+ * operation; kind 5: the 32-bit forward butterfly of NTT_FLAG_WORD32 plans,
+ * q < 2^30).  Total operations = blocks * threads * iters * 8; time it with
  * events on `cuda_stream`.
  * d_sink (blocks * threads uint64, caller-owned) only defeats dead-code
  * elimination.  Not part of the paper: a measurement aid.

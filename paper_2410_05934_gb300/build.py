@@ -30,7 +30,7 @@ CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-Wall", "-Wno-unused-function",
              "-I", INCLUDE, "-I", CSRC]
 
 PRODUCT_SOURCES = ["capi.cu", "kernels_small.cu", "kernels_mid.cu", "kernels_large.cu", "kernels_huge.cu",
-                   "kernels_misc.cu", "batch.cu", "costmodel.cu", "tfhe.cu", "rns.cu", "plan_host.cpp"]
+                   "kernels_misc.cu", "batch.cu", "costmodel.cu", "tfhe.cu", "rns.cu", "ntt32.cu", "plan_host.cpp"]
 EMU_SOURCES = ["plan_host.cpp", "emulate.cpp"]
 
 

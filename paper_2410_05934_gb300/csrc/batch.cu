@@ -654,7 +654,7 @@ int ntt_batch_execute_static(const ntt_plan_request_t* reqs, uint32_t n_reqs, vo
         const ntt_plan_s* p = r.plan;
         if (!p || (p->h.flags & NTT_FLAG_HOST_ONLY) || p->device != dev || r.inverse > 1 || !r.in || !r.out)
             return NTT_ERR_ARG;
-        if (p->h.log2n < NTT_BATCH_MIN_LOG2N || (p->h.flags & NTT_FLAG_NATURAL_ORDER)) return NTT_ERR_UNSUPPORTED;
+        if (p->h.log2n < NTT_BATCH_MIN_LOG2N || (p->h.flags & (NTT_FLAG_NATURAL_ORDER | NTT_FLAG_WORD32))) return NTT_ERR_UNSUPPORTED;
         const uint32_t polys = r.n_polys ? r.n_polys : p->h.batch;
         if (polys > p->h.batch) return NTT_ERR_ARG;
         if (!aligned16p(r.in) || !aligned16p(r.out)) return NTT_ERR_ALIGN;

@@ -125,6 +125,19 @@ static int check_device(const ntt_plan_s* p) {
     return dev == p->device ? NTT_OK : NTT_ERR_ARG;
 }
 
+static bool word32(const ntt_plan_s* p) { return (p->h.flags & NTT_FLAG_WORD32) != 0; }
+
+static Plan32Dev plan32_dev(const ntt_plan_s* p) {
+    Plan32Dev d;
+    d.fwd = p->d_fwd32;
+    d.inv = p->d_inv32;
+    d.lc = p->d_consts32;
+    d.status = p->d_status;
+    d.n_moduli = p->h.n_moduli;
+    d.check = (p->h.flags & NTT_FLAG_CHECK) ? 1u : 0u;
+    return d;
+}
+
 static bool natural(const ntt_plan_s* p) { return (p->h.flags & NTT_FLAG_NATURAL_ORDER) != 0; }
 
 static int transform(ntt_plan_t plan, bool inverse, const uint64_t* in, uint64_t* out,
@@ -138,6 +151,10 @@ static int transform(ntt_plan_t plan, bool inverse, const uint64_t* in, uint64_t
     if (idx < 0) return NTT_ERR_UNSUPPORTED;
     plan->last_launches = 0;
     if (n_rows == 0) return NTT_OK;
+    if (word32(plan))
+        return launch_ntt32(plan32_dev(plan), inverse, reinterpret_cast<const uint32_t*>(in),
+                            reinterpret_cast<uint32_t*>(out), row_begin, n_rows, plan->h.log2n, stream,
+                            &plan->last_launches);
     PlanDev d = plan_dev(plan);
     const SchedEntry& e = g_table[idx];
     const LaunchFn fn = inverse ? e.inv : e.fwd;
@@ -163,10 +180,17 @@ static void free_device(ntt_plan_s* p) {
     if (p->d_inv) cudaFree(p->d_inv);
     if (p->d_consts) cudaFree(p->d_consts);
     if (p->d_status) cudaFree(p->d_status);
+    if (p->d_fwd32) cudaFree(p->d_fwd32);
+    if (p->d_inv32) cudaFree(p->d_inv32);
+    if (p->d_consts32) cudaFree(p->d_consts32);
     p->d_fwd = p->d_inv = nullptr;
     p->d_consts = nullptr;
     p->d_status = nullptr;
+    p->d_fwd32 = p->d_inv32 = nullptr;
+    p->d_consts32 = nullptr;
 }
+
+
 
 }  // namespace nttgb
 
@@ -191,7 +215,29 @@ int ntt_plan(ntt_plan_t* out, uint32_t log2n, const uint64_t* moduli, uint32_t n
         return rc;
     }
     p->schedule = default_schedule(log2n, p->h.rows);
-    if (!(flags & NTT_FLAG_HOST_ONLY)) {
+    if (!(flags & NTT_FLAG_HOST_ONLY) && (flags & NTT_FLAG_WORD32)) {
+        const size_t tw_bytes = p->h.fwd32.size() * sizeof(Tw32);
+        const size_t lc_bytes = p->h.consts32.size() * sizeof(LimbConst32);
+        bool ok = cudaGetDevice(&p->device) == cudaSuccess &&
+                  cudaMalloc(&p->d_fwd32, tw_bytes) == cudaSuccess &&
+                  cudaMalloc(&p->d_inv32, tw_bytes) == cudaSuccess &&
+                  cudaMalloc(&p->d_consts32, lc_bytes) == cudaSuccess &&
+                  cudaMalloc(&p->d_status, sizeof(int)) == cudaSuccess &&
+                  cudaMemcpy(p->d_fwd32, p->h.fwd32.data(), tw_bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(p->d_inv32, p->h.inv32.data(), tw_bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(p->d_consts32, p->h.consts32.data(), lc_bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemset(p->d_status, 0, sizeof(int)) == cudaSuccess;
+        if (!ok) {
+            free_device(p);
+            delete p;
+            cudaGetLastError();
+            return NTT_ERR_CUDA;
+        }
+        std::vector<TwPair>().swap(p->h.fwd);
+        std::vector<TwPair>().swap(p->h.inv);
+        std::vector<Tw32>().swap(p->h.fwd32);
+        std::vector<Tw32>().swap(p->h.inv32);
+    } else if (!(flags & NTT_FLAG_HOST_ONLY)) {
         const size_t tw_bytes = p->h.fwd.size() * sizeof(TwPair);
         const size_t lc_bytes = p->h.consts.size() * sizeof(LimbConst);
         bool ok = cudaGetDevice(&p->device) == cudaSuccess &&
@@ -262,7 +308,7 @@ int ntt_hmul_tensor(ntt_plan_t plan, const uint64_t* d_a, const uint64_t* d_b, u
                     void* cuda_stream) {
     if (!plan || !d_a || !d_b || !d_out) return NTT_ERR_ARG;
     if (!aligned16(d_a) || !aligned16(d_b) || !aligned16(d_out)) return NTT_ERR_ALIGN;
-    if (natural(plan)) return NTT_ERR_UNSUPPORTED;
+    if (natural(plan) || word32(plan)) return NTT_ERR_UNSUPPORTED;
     int rc = check_device(plan);
     if (rc) return rc;
     // the tensor product runs in the direct form of the inverse's first kernel
@@ -295,7 +341,7 @@ int ntt_rescale(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, uint64_t
     if (!aligned16(d_in) || !aligned16(d_out) || !aligned16(d_work)) return NTT_ERR_ALIGN;
     const uint32_t L = plan->h.n_moduli;
     if (L < 2) return NTT_ERR_ARG;
-    if (natural(plan)) return NTT_ERR_UNSUPPORTED;
+    if (natural(plan) || word32(plan)) return NTT_ERR_UNSUPPORTED;
     if (n_polys == 0) n_polys = plan->h.batch;
     if (n_polys > plan->h.batch) return NTT_ERR_ARG;
     for (uint32_t i = 0; i + 1 < L; ++i)
@@ -358,6 +404,10 @@ int poly_mul_pointwise(ntt_plan_t plan, const uint64_t* d_a, const uint64_t* d_b
     int rc = check_device(plan);
     if (rc) return rc;
     plan->last_launches = 0;
+    if (word32(plan))
+        return launch_pointwise32(plan32_dev(plan), plan->h.log2n, reinterpret_cast<const uint32_t*>(d_a),
+                                  reinterpret_cast<const uint32_t*>(d_b), reinterpret_cast<uint32_t*>(d_c),
+                                  (uint64_t)n_polys * plan->h.n_moduli, cuda_stream, &plan->last_launches);
     PlanDev d = plan_dev(plan);
     return launch_pointwise(d, plan->h.log2n, d_a, d_b, d_c, 0,
                             (uint64_t)n_polys * plan->h.n_moduli, cuda_stream,
@@ -423,8 +473,9 @@ int ntt_plan_last_launches(ntt_plan_t plan, uint32_t* launches) {
 
 int ntt_bench_butterflies(uint64_t q, uint32_t kind, uint32_t blocks, uint32_t threads,
                           uint32_t iters, uint64_t* d_sink, void* cuda_stream) {
-    if (q < 3 || q >= (1ull << NTT_MAX_MODULUS_BITS) || kind > 4 ||
-        ((kind == 2 || kind == 3) && q >= (1ull << NTT_SMALL_MODULUS_BITS)) || blocks == 0 || threads == 0 ||
+    if (q < 3 || q >= (1ull << NTT_MAX_MODULUS_BITS) || kind > 5 ||
+        ((kind == 2 || kind == 3) && q >= (1ull << NTT_SMALL_MODULUS_BITS)) ||
+        (kind == 5 && q >= (1ull << NTT_WORD32_MAX_MODULUS_BITS)) || blocks == 0 || threads == 0 ||
         threads > 256 || !d_sink)
         return NTT_ERR_ARG;
     return launch_bench_bfly(q, kind, blocks, threads, iters, d_sink, cuda_stream);

@@ -269,6 +269,43 @@ struct EmuPlan {
     int status = 0;
 };
 
+// The 32-bit kernel of ntt32.cu, CTA by CTA and pass by pass.
+template <class C, int I>
+static void emu_passes32(std::vector<Regs32<C>>& st, const Args32& a, const std::vector<Loc32>& L,
+                         std::vector<uint32_t>& sm) {
+    if constexpr (I < C::NPASS) {
+        constexpr int P = C::INV ? (C::NPASS - 1 - I) : I;
+        for (int tid = 0; tid < C::THREADS; ++tid) {
+            const int tin = tid >> C::LOGT, t = tid & (C::T - 1);
+            pass32<C, P>(st[tid], a, L[tin], t, sm.data() + (size_t)tin * C::E);
+        }
+        emu_passes32<C, I + 1>(st, a, L, sm);
+    }
+}
+
+template <int LOGN, bool INV>
+static int emu_ntt32(const Args32& a) {
+    using C = typename Cfg32Sel<LOGN, INV>::C;
+    if (!verify_cfg<C>()) return NTT_ERR_UNSUPPORTED;
+    const uint32_t ctas = (a.n_rows + C::TPC - 1) / C::TPC;
+    std::vector<Regs32<C>> st(C::THREADS);
+    std::vector<Loc32> L(C::TPC);
+    std::vector<uint32_t> sm((size_t)C::E * C::TPC, 0xdeadbeefu);
+    for (uint32_t cta = 0; cta < ctas; ++cta) {
+        for (int tin = 0; tin < C::TPC; ++tin) L[tin] = locate32<C>(a, cta, tin);
+        for (int tid = 0; tid < C::THREADS; ++tid) {
+            const int tin = tid >> C::LOGT, t = tid & (C::T - 1);
+            load32<C>(st[tid], a, L[tin], t, sm.data() + (size_t)tin * C::E);
+        }
+        emu_passes32<C, 0>(st, a, L, sm);
+        for (int tid = 0; tid < C::THREADS; ++tid) {
+            const int tin = tid >> C::LOGT, t = tid & (C::T - 1);
+            store32<C>(a, L[tin], t, sm.data() + (size_t)tin * C::E);
+        }
+    }
+    return NTT_OK;
+}
+
 // The CMux kernel of tfhe.cu, CTA by CTA: every step between two barriers
 // runs for all threads before the next one starts.
 template <int LOGN, int MC>
@@ -535,6 +572,45 @@ int nttemu_tfhe_cmux(void* plan, const uint64_t* in, const uint32_t* rot, const 
     const bool small = p->h.mc != 0;
     if (p->h.log2n == 10) return small ? emu_cmux<10, 1>(c, af, ai) : emu_cmux<10, 0>(c, af, ai);
     return small ? emu_cmux<11, 1>(c, af, ai) : emu_cmux<11, 0>(c, af, ai);
+}
+
+// A NTT_FLAG_WORD32 plan's transform (ntt_forward / ntt_inverse on uint32
+// rows) or pointwise product on the host.
+int nttemu_transform32(void* plan, int inverse, const uint32_t* in, uint32_t* out, uint64_t row_begin,
+                       uint64_t n_rows) {
+    EmuPlan* p = static_cast<EmuPlan*>(plan);
+    if (!p || !in || !out || !(p->h.flags & NTT_FLAG_WORD32)) return NTT_ERR_ARG;
+    if (row_begin > p->h.rows || n_rows > p->h.rows - row_begin) return NTT_ERR_ARG;
+    Args32 a;
+    a.in = in;
+    a.out = out;
+    a.tw = inverse ? p->h.inv32.data() : p->h.fwd32.data();
+    a.lc = p->h.consts32.data();
+    a.status = &p->status;
+    a.row_begin = (uint32_t)row_begin;
+    a.n_rows = (uint32_t)n_rows;
+    a.n_moduli = p->h.n_moduli;
+    a.check = (p->h.flags & NTT_FLAG_CHECK) ? 1u : 0u;
+    a.mod_magic = fdiv_magic(p->h.n_moduli);
+#define NTT_EMU32_CASE(LOGN) \
+    case LOGN: return inverse ? emu_ntt32<LOGN, true>(a) : emu_ntt32<LOGN, false>(a);
+    switch (p->h.log2n) {
+        NTT_EMU32_CASE(1) NTT_EMU32_CASE(2) NTT_EMU32_CASE(3) NTT_EMU32_CASE(4) NTT_EMU32_CASE(5)
+        NTT_EMU32_CASE(6) NTT_EMU32_CASE(7) NTT_EMU32_CASE(8) NTT_EMU32_CASE(9) NTT_EMU32_CASE(10)
+        NTT_EMU32_CASE(11) NTT_EMU32_CASE(12)
+        default: return NTT_ERR_UNSUPPORTED;
+    }
+#undef NTT_EMU32_CASE
+}
+
+int nttemu_pointwise32(void* plan, const uint32_t* x, const uint32_t* y, uint32_t* c, uint64_t n_rows) {
+    EmuPlan* p = static_cast<EmuPlan*>(plan);
+    if (!p || !(p->h.flags & NTT_FLAG_WORD32) || n_rows > p->h.rows) return NTT_ERR_ARG;
+    const uint64_t n = 1ull << p->h.log2n;
+    for (uint64_t r = 0; r < n_rows; ++r)
+        for (uint64_t j = 0; j < n; ++j)
+            c[r * n + j] = mulmod32(x[r * n + j], y[r * n + j], p->h.consts32[r % p->h.n_moduli]);
+    return NTT_OK;
 }
 
 // ntt_rescale on the host with schedule `sched` for both transforms (its

@@ -7,6 +7,7 @@
 
 #include "ntt_gb300.h"
 #include "ntt_launch.h"
+#include "ntt32.cuh"
 
 namespace nttgb {
 
@@ -129,8 +130,36 @@ int launch_bitrev_rows(const uint64_t* in, uint64_t* out, uint64_t row_begin, ui
     return cudaPeekAtLastError() == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
 }
 
+// 32-bit Harvey CT butterflies (the arithmetic of the NTT_FLAG_WORD32 kernels)
+__global__ void __launch_bounds__(256) k_bench_bfly32(uint32_t q, uint32_t w, uint32_t wp, uint32_t iters,
+                                                      uint64_t* sink) {
+    constexpr int P = 8;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t X[P], Y[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        X[i] = (uint32_t)((tid * 7919u + (uint64_t)i * 104729u) % q);
+        Y[i] = (uint32_t)((tid * 31u + (uint64_t)i * 17u) % q);
+    }
+    const Tw32 tw{w, wp};
+    for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < P; ++i) ct32(X[i], Y[i], tw, q, 2 * q);
+    }
+    uint32_t acc = 0;
+#pragma unroll
+    for (int i = 0; i < P; ++i) acc ^= X[i] ^ Y[i];
+    if (acc == 0x5eed5eedu) sink[tid] = acc;   // practically never taken
+}
+
 int launch_bench_bfly(uint64_t q, uint32_t kind, uint32_t blocks, uint32_t threads, uint32_t iters,
                       uint64_t* sink, void* stream) {
+    if (kind == 5) {
+        const uint32_t w = (uint32_t)(q / 3);
+        const uint32_t wp = (uint32_t)(((uint64_t)w << 32) / q);
+        k_bench_bfly32<<<blocks, threads, 0, (cudaStream_t)stream>>>((uint32_t)q, w, wp, iters, sink);
+        return cudaPeekAtLastError() == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
+    }
     // a fixed twiddle in Shoup form: w = q/3 rounded, w' = floor(w 2^64 / q)
     const uint64_t w = q / 3;
     const uint64_t wp = (uint64_t)(((unsigned __int128)w << 64) / q);

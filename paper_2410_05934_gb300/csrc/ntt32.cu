@@ -1,0 +1,97 @@
+// 32-bit-word transforms and pointwise product (plans with NTT_FLAG_WORD32):
+// kernels, launchers and the 32-bit tables built from the plan's host tables.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "ntt_gb300.h"
+#include "ntt_internal.h"
+#include "ntt32.cuh"
+#include "ntt_kernels.cuh"
+
+namespace nttgb {
+
+template <class C, int I>
+__device__ __forceinline__ void run_passes32(Regs32<C>& st, const Args32& a, const Loc32& L, int t, uint32_t* sm) {
+    if constexpr (I < C::NPASS) {
+        constexpr int P = C::INV ? (C::NPASS - 1 - I) : I;
+        pass32<C, P>(st, a, L, t, sm);
+        __syncthreads();
+        run_passes32<C, I + 1>(st, a, L, t, sm);
+    }
+}
+
+template <class C>
+__global__ void __launch_bounds__(C::THREADS) k_ntt32(Args32 a) {
+    extern __shared__ __align__(16) uint32_t smem32[];
+    const int tin = threadIdx.x >> C::LOGT;
+    const int t = threadIdx.x & (C::T - 1);
+    const Loc32 L = locate32<C>(a, blockIdx.x, tin);
+    uint32_t* sm = smem32 + (size_t)tin * C::E;
+    Regs32<C> st;
+    load32<C>(st, a, L, t, sm);
+    __syncthreads();
+    run_passes32<C, 0>(st, a, L, t, sm);
+    store32<C>(a, L, t, sm);
+}
+
+template <int LOGN, bool INV>
+static int launch32_n(const Args32& a, cudaStream_t st) {
+    using C = typename Cfg32Sel<LOGN, INV>::C;
+    const uint64_t ctas = ((uint64_t)a.n_rows + C::TPC - 1) / C::TPC;
+    if (ctas == 0) return NTT_OK;
+    if (ctas > 0x7fffffffull) return NTT_ERR_ARG;
+    k_ntt32<C><<<(unsigned)ctas, C::THREADS, sizeof(uint32_t) * C::E * C::TPC, st>>>(a);
+    return cudaPeekAtLastError() == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
+}
+
+#define NTT32_CASE(LOGN) \
+    case LOGN: return inverse ? launch32_n<LOGN, true>(a, st) : launch32_n<LOGN, false>(a, st);
+
+int launch_ntt32(const Plan32Dev& p, bool inverse, const uint32_t* in, uint32_t* out, uint64_t row_begin,
+                 uint64_t n_rows, uint32_t log2n, void* stream, uint32_t* launches) {
+    if (n_rows == 0) return NTT_OK;
+    if (row_begin + n_rows > 0xffffffffull) return NTT_ERR_ARG;
+    Args32 a;
+    a.in = in;
+    a.out = out;
+    a.tw = inverse ? p.inv : p.fwd;
+    a.lc = p.lc;
+    a.status = p.status;
+    a.row_begin = (uint32_t)row_begin;
+    a.n_rows = (uint32_t)n_rows;
+    a.n_moduli = p.n_moduli;
+    a.check = p.check;
+    a.mod_magic = fdiv_magic(p.n_moduli);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (launches) ++*launches;
+    switch (log2n) {
+        NTT32_CASE(1) NTT32_CASE(2) NTT32_CASE(3) NTT32_CASE(4) NTT32_CASE(5) NTT32_CASE(6)
+        NTT32_CASE(7) NTT32_CASE(8) NTT32_CASE(9) NTT32_CASE(10) NTT32_CASE(11) NTT32_CASE(12)
+        default: return NTT_ERR_UNSUPPORTED;
+    }
+}
+
+__global__ void k_pointwise32(const uint32_t* __restrict__ a, const uint32_t* __restrict__ b, uint32_t* c,
+                              const LimbConst32* __restrict__ lc, uint32_t n_moduli, uint32_t log2n, uint64_t total) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x) {
+        const LimbConst32 m = lc[(i >> log2n) % n_moduli];
+        c[i] = mulmod32(a[i], b[i], m);
+    }
+}
+
+int launch_pointwise32(const Plan32Dev& p, uint32_t log2n, const uint32_t* a, const uint32_t* b, uint32_t* c,
+                       uint64_t n_rows, void* stream, uint32_t* launches) {
+    const uint64_t total = n_rows << log2n;
+    if (total == 0) return NTT_OK;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return NTT_ERR_CUDA;
+    const unsigned grid = (unsigned)std::min<uint64_t>((total + 255) / 256, (uint64_t)std::max(1, sms) * 32u);
+    k_pointwise32<<<grid, 256, 0, (cudaStream_t)stream>>>(a, b, c, p.lc, p.n_moduli, log2n, total);
+    if (launches) ++*launches;
+    return cudaPeekAtLastError() == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
+}
+
+}  // namespace nttgb

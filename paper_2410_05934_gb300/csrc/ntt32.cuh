@@ -1,0 +1,242 @@
+// 32-bit-word transform for moduli below 2^30 (the TFHE-size primes, Sec.
+// II-B mentions 32-bit TFHE moduli): coefficients and twiddles are uint32,
+// a Shoup product is one 32-bit low multiply, one 32-bit high multiply and
+// one more low multiply (against ~20 multiply-pipe slots for the 64-bit
+// butterfly), and Harvey's bounds fit because 4q < 2^32.
+//
+// One kernel per transform, one whole row per tile (N <= 2^12), 8
+// coefficients per thread: the tile geometry (pass layout, swizzle, twiddle
+// indices) is the one of the 64-bit tile kernels (ntt_tile.cuh), applied to
+// 32-bit words.  Host and device, like the 64-bit phases.
+#pragma once
+#include "ntt_tile.cuh"
+
+namespace nttgb {
+
+struct alignas(8) Tw32 {
+    uint32_t w, wp;             // wp = floor(w 2^32 / q)
+};
+
+struct LimbConst32 {
+    uint32_t q, two_q;
+    uint32_t ninv, ninv_p;      // N^-1 and its Shoup form
+    uint32_t w1ninv, w1ninv_p;  // psi^{-brv(1)} N^-1 and its Shoup form
+    uint64_t mu;                // floor(2^64 / q): Barrett constant of the pointwise product
+};
+
+struct Args32 {
+    const uint32_t* in;
+    uint32_t* out;
+    const Tw32* tw;             // [n_moduli][N]
+    const LimbConst32* lc;      // [n_moduli]
+    int* status;
+    uint32_t row_begin, n_rows; // rows of this launch (plan layout)
+    uint32_t n_moduli, check;
+    uint64_t mod_magic;         // ceil(2^64 / n_moduli)
+};
+
+NTT_HD uint32_t mulhi32(uint32_t a, uint32_t b) {
+#if defined(__CUDA_ARCH__)
+    return __umulhi(a, b);
+#else
+    return (uint32_t)(((uint64_t)a * b) >> 32);
+#endif
+}
+
+// y w mod q lazily, in [0, 2q) for any y < 2^32
+NTT_HD uint32_t shoup32(uint32_t y, uint32_t w, uint32_t wp, uint32_t q) { return y * w - mulhi32(y, wp) * q; }
+NTT_HD uint32_t csub32(uint32_t x, uint32_t m) { return x >= m ? x - m : x; }
+
+// Harvey CT: [0, 4q) -> [0, 4q)
+NTT_HD void ct32(uint32_t& X, uint32_t& Y, Tw32 w, uint32_t q, uint32_t two_q) {
+    const uint32_t x = csub32(X, two_q);
+    const uint32_t t = shoup32(Y, w.w, w.wp, q);
+    X = x + t;
+    Y = x - t + two_q;
+}
+
+// Harvey GS: [0, 2q) -> [0, 2q); the stage-0 variant folds N^-1 in
+NTT_HD void gs32(uint32_t& X, uint32_t& Y, Tw32 w, uint32_t q, uint32_t two_q) {
+    const uint32_t s = csub32(X + Y, two_q);
+    const uint32_t d = X - Y + two_q;
+    Y = shoup32(d, w.w, w.wp, q);
+    X = s;
+}
+
+NTT_HD void gs32_scaled(uint32_t& X, uint32_t& Y, const LimbConst32& c) {
+    const uint32_t s = X + Y, d = X - Y + c.two_q;   // [0, 4q)
+    X = shoup32(s, c.ninv, c.ninv_p, c.q);
+    Y = shoup32(d, c.w1ninv, c.w1ninv_p, c.q);
+}
+
+NTT_HD Tw32 load_tw32(const Tw32* tw, uint32_t k) {
+#if defined(__CUDA_ARCH__)
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(tw) + k);
+    return Tw32{v.x, v.y};
+#else
+    return tw[k];
+#endif
+}
+
+// one whole row per tile: C = TileCfg<LOGN, 0, LOGN, 0, LOGT, 3, TPC, INV, 1, 2> for the geometry
+template <class C>
+struct Regs32 {
+    uint32_t x[C::R];
+};
+
+struct Loc32 {
+    uint32_t row, limb;
+    bool valid;
+};
+
+template <class C>
+NTT_HD Loc32 locate32(const Args32& a, uint32_t cta, int tin) {
+    Loc32 L;
+    const uint32_t r = cta * (uint32_t)C::TPC + (uint32_t)tin;
+    L.valid = r < a.n_rows;
+    L.row = a.row_begin + (L.valid ? r : 0u);
+    const uint32_t rq = a.n_moduli == 1 ? L.row : fdiv32(L.row, a.mod_magic, a.n_moduli);
+    L.limb = a.n_moduli == 1 ? 0u : L.row - rq * a.n_moduli;
+    return L;
+}
+
+// global -> registers (pair layout: thread t holds k = 2t + 2iT and k + 1)
+// -> swizzled shared memory
+template <class C>
+NTT_HD void load32(Regs32<C>& st, const Args32& a, const Loc32& L, int t, uint32_t* sm) {
+    if (!L.valid) return;
+    const uint32_t* src = a.in + ((uint64_t)L.row << C::LOGN);
+    const uint32_t q = a.lc[L.limb].q;
+    bool bad = false;
+#pragma unroll
+    for (int i = 0; i < C::R / 2; ++i) {
+        const uint32_t k = 2u * (uint32_t)t + 2u * (uint32_t)i * C::T;
+        NTT_GMEM_CHECK(k + 1, 1u << C::LOGN);
+#if defined(__CUDA_ARCH__)
+        const uint2 v = *reinterpret_cast<const uint2*>(src + k);
+        st.x[2 * i] = v.x;
+        st.x[2 * i + 1] = v.y;
+#else
+        st.x[2 * i] = src[k];
+        st.x[2 * i + 1] = src[k + 1];
+#endif
+        bad |= st.x[2 * i] >= q || st.x[2 * i + 1] >= q;
+    }
+    if (a.check && bad) record_status(a.status, NTT_STATUS_RANGE);
+    const uint32_t b = swz(2u * (uint32_t)t);
+#pragma unroll
+    for (int i = 0; i < C::R / 2; ++i) {
+        const uint32_t c = swz(2u * (uint32_t)i * C::T);
+        NTT_SMEM_CHECK(b ^ c, C::E);
+        sm[b ^ c] = st.x[2 * i];
+        sm[(b ^ c) ^ 1u] = st.x[2 * i + 1];
+    }
+}
+
+// pass P: read its registers, run its fused stages, write them back
+template <class C, int P>
+NTT_HD void pass32(Regs32<C>& st, const Args32& a, const Loc32& L, int t, uint32_t* sm) {
+    if (!L.valid) return;
+    using Gm = PassGeom<C, P>;
+    constexpr int S_LO = Gm::S_LO, r = Gm::r, GS = Gm::GS;
+    const uint32_t b = swz(spread((uint32_t)t, Gm::PE, Gm::r));
+#pragma unroll
+    for (int j = 0; j < C::R; ++j) {
+        const uint32_t addr = b ^ swz(Gm::ej(j));
+        NTT_SMEM_CHECK(addr, C::E);
+        st.x[j] = sm[addr];
+    }
+    const LimbConst32 lc = a.lc[L.limb];
+    const Tw32* tw = a.tw + ((uint64_t)L.limb << C::LOGN);
+    constexpr int SH = C::LOGN - S_LO;
+    const uint32_t pre_t = place<C>(spread((uint32_t)t, Gm::PE, r)) >> SH;
+#pragma unroll
+    for (int gi = 0; gi < Gm::G; ++gi) {
+        const uint32_t pre = pre_t | (place<C>(Gm::ej(gi * GS)) >> SH);
+        uint32_t* x = st.x + gi * GS;
+        if (!C::INV) {
+#pragma unroll
+            for (int v = 0; v < r; ++v) {
+                const int s = S_LO + v;
+                const int d = 1 << (r - 1 - v);
+                const uint32_t k0 = (1u << s) + (pre << v);
+#pragma unroll
+                for (int jl = 0; jl < GS; ++jl) {
+                    if (jl & d) continue;
+                    const uint32_t k = k0 + ((uint32_t)jl >> (r - v));
+                    NTT_GMEM_CHECK(k, 1u << C::LOGN);
+                    ct32(x[jl], x[jl + d], load_tw32(tw, k), lc.q, lc.two_q);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int v = r - 1; v >= 0; --v) {
+                const int s = S_LO + v;
+                const int d = 1 << (r - 1 - v);
+                const uint32_t k0 = (1u << s) + (pre << v);
+#pragma unroll
+                for (int jl = 0; jl < GS; ++jl) {
+                    if (jl & d) continue;
+                    if (s == 0) {
+                        gs32_scaled(x[jl], x[jl + d], lc);
+                    } else {
+                        const uint32_t k = k0 + ((uint32_t)jl >> (r - v));
+                        NTT_GMEM_CHECK(k, 1u << C::LOGN);
+                        gs32(x[jl], x[jl + d], load_tw32(tw, k), lc.q, lc.two_q);
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < C::R; ++j) {
+        const uint32_t addr = b ^ swz(Gm::ej(j));
+        sm[addr] = st.x[j];
+    }
+}
+
+// shared memory -> canonical -> global
+template <class C>
+NTT_HD void store32(const Args32& a, const Loc32& L, int t, const uint32_t* sm) {
+    if (!L.valid) return;
+    uint32_t* dst = a.out + ((uint64_t)L.row << C::LOGN);
+    const uint32_t q = a.lc[L.limb].q, two_q = a.lc[L.limb].two_q;
+    const uint32_t b = swz(2u * (uint32_t)t);
+#pragma unroll
+    for (int i = 0; i < C::R / 2; ++i) {
+        const uint32_t c = swz(2u * (uint32_t)i * C::T);
+        uint32_t x = sm[b ^ c], y = sm[(b ^ c) ^ 1u];
+        if (!C::INV) {          // [0, 4q) -> [0, q)
+            x = csub32(csub32(x, two_q), q);
+            y = csub32(csub32(y, two_q), q);
+        } else {                // [0, 2q) -> [0, q)
+            x = csub32(x, q);
+            y = csub32(y, q);
+        }
+        const uint32_t k = 2u * (uint32_t)t + 2u * (uint32_t)i * C::T;
+        NTT_GMEM_CHECK(k + 1, 1u << C::LOGN);
+#if defined(__CUDA_ARCH__)
+        *reinterpret_cast<uint2*>(dst + k) = make_uint2(x, y);
+#else
+        dst[k] = x;
+        dst[k + 1] = y;
+#endif
+    }
+}
+
+// c = a b mod q for a, b < q < 2^30: p = a b < 2^60, p - floor(p mu / 2^64) q in [0, 2q)
+NTT_HD uint32_t mulmod32(uint32_t x, uint32_t y, const LimbConst32& c) {
+    const uint64_t p = (uint64_t)x * y;
+    return csub32((uint32_t)(p - mulhi64(p, c.mu) * c.q), c.q);
+}
+
+// the 32-bit configuration of a ring size: 8 coefficients per thread (or the
+// whole row for N <= 8), passes of up to 3 stages, 256-thread CTAs
+template <int LOGN, bool INV>
+struct Cfg32Sel {
+    static constexpr int LOGT = LOGN > 3 ? LOGN - 3 : 0;
+    static constexpr int TPC = (256 >> LOGT) > 0 ? (256 >> LOGT) : 1;
+    using C = TileCfg<LOGN, 0, LOGN, 0, LOGT, 3, TPC, INV, 1, 2>;
+};
+
+}  // namespace nttgb

@@ -7,6 +7,7 @@
 
 #include "ntt_gb300.h"
 #include "ntt_tile.cuh"
+#include "ntt32.cuh"
 
 namespace nttgb {
 
@@ -26,6 +27,8 @@ struct PlanHost {
     std::vector<uint64_t> moduli, psi;
     std::vector<TwPair> fwd, inv;      // [n_moduli][N]
     std::vector<LimbConst> consts;     // [n_moduli]
+    std::vector<Tw32> fwd32, inv32;    // NTT_FLAG_WORD32 plans: 32-bit tables
+    std::vector<LimbConst32> consts32;
 };
 
 // Validates the arguments and fills the host tables.  Returns NTT_OK or an
@@ -58,6 +61,9 @@ struct ntt_plan_s {
     nttgb::TwPair* d_inv = nullptr;
     nttgb::LimbConst* d_consts = nullptr;
     int* d_status = nullptr;
+    nttgb::Tw32* d_fwd32 = nullptr;
+    nttgb::Tw32* d_inv32 = nullptr;
+    nttgb::LimbConst32* d_consts32 = nullptr;
     uint32_t schedule = 0;
     uint32_t last_launches = 0;
 };

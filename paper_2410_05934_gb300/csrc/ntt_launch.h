@@ -41,6 +41,22 @@ int launch_pointwise(const PlanDev& p, uint32_t log2n, const uint64_t* a, const 
                      uint64_t* c, uint64_t row_begin, uint64_t n_rows, void* stream,
                      uint32_t* launches);
 
+// 32-bit-word plans (NTT_FLAG_WORD32)
+struct Tw32;
+struct LimbConst32;
+struct Plan32Dev {
+    const Tw32* fwd;
+    const Tw32* inv;
+    const LimbConst32* lc;
+    int* status;
+    uint32_t n_moduli;
+    uint32_t check;
+};
+int launch_ntt32(const Plan32Dev& p, bool inverse, const uint32_t* in, uint32_t* out, uint64_t row_begin,
+                 uint64_t n_rows, uint32_t log2n, void* stream, uint32_t* launches);
+int launch_pointwise32(const Plan32Dev& p, uint32_t log2n, const uint32_t* a, const uint32_t* b, uint32_t* c,
+                       uint64_t n_rows, void* stream, uint32_t* launches);
+
 // bit-reversal permutation of rows (in == out: in place)
 int launch_bitrev_rows(const uint64_t* in, uint64_t* out, uint64_t row_begin, uint64_t n_rows, uint32_t log2n,
                        void* stream, uint32_t* launches);

@@ -128,13 +128,17 @@ int build_plan_host(PlanHost& h, uint32_t log2n, const uint64_t* moduli, uint32_
                     uint32_t batch, uint32_t flags) {
     if (log2n < NTT_MIN_LOG2N || log2n > NTT_MAX_LOG2N) return NTT_ERR_ARG;
     if (!moduli || n_moduli == 0 || batch == 0) return NTT_ERR_ARG;
-    if (flags & ~(NTT_FLAG_HOST_ONLY | NTT_FLAG_CHECK | NTT_FLAG_NATURAL_ORDER)) return NTT_ERR_ARG;
+    if (flags & ~(NTT_FLAG_HOST_ONLY | NTT_FLAG_CHECK | NTT_FLAG_NATURAL_ORDER | NTT_FLAG_WORD32)) return NTT_ERR_ARG;
+    const bool word32 = (flags & NTT_FLAG_WORD32) != 0;
+    if (word32 && ((flags & NTT_FLAG_NATURAL_ORDER) || log2n > NTT_WORD32_MAX_LOG2N)) return NTT_ERR_UNSUPPORTED;
     const uint64_t n = 1ull << log2n;
     const u128 total = (u128)batch * n_moduli * n;
     if (total >= ((u128)1 << 40)) return NTT_ERR_ARG;
+    if (word32 && (u128)batch * n_moduli >= ((u128)1 << 32)) return NTT_ERR_ARG;
     for (uint32_t l = 0; l < n_moduli; ++l) {
         uint64_t q = moduli[l];
         if (q >= (1ull << NTT_MAX_MODULUS_BITS)) return NTT_ERR_MODULUS_TOO_LARGE;
+        if (word32 && q >= (1ull << NTT_WORD32_MAX_MODULUS_BITS)) return NTT_ERR_MODULUS_TOO_LARGE;
         if (!is_prime_u64(q)) return NTT_ERR_NOT_PRIME;
         if ((q - 1) % (2 * n)) return NTT_ERR_NOT_NTT_FRIENDLY;
     }
@@ -203,6 +207,28 @@ int build_plan_host(PlanHost& h, uint32_t log2n, const uint64_t* moduli, uint32_
             const uint64_t ql = moduli[n_moduli - 1] % q;
             c.rs_inv = ql ? pow_mod(ql, q - 2, q) : 0;
             c.rs_inv_p = shoup_of(c.rs_inv, q);
+        }
+    }
+    if (word32) {      // 32-bit tables: w' = floor(w 2^32 / q)
+        auto sp32 = [](uint64_t w, uint64_t q) { return (uint32_t)((w << 32) / q); };
+        h.fwd32.resize(h.fwd.size());
+        h.inv32.resize(h.inv.size());
+        for (size_t k = 0; k < h.fwd.size(); ++k) {
+            const uint64_t q = moduli[k >> log2n];
+            h.fwd32[k] = Tw32{(uint32_t)h.fwd[k].w, sp32(h.fwd[k].w, q)};
+            h.inv32[k] = Tw32{(uint32_t)h.inv[k].w, sp32(h.inv[k].w, q)};
+        }
+        h.consts32.resize(n_moduli);
+        for (uint32_t l = 0; l < n_moduli; ++l) {
+            const LimbConst& c = h.consts[l];
+            LimbConst32& d = h.consts32[l];
+            d.q = (uint32_t)c.q;
+            d.two_q = (uint32_t)c.two_q;
+            d.ninv = (uint32_t)c.ninv;
+            d.ninv_p = sp32(c.ninv, c.q);
+            d.w1ninv = (uint32_t)c.w1ninv;
+            d.w1ninv_p = sp32(c.w1ninv, c.q);
+            d.mu = (uint64_t)(((u128)1 << 64) / c.q);
         }
     }
     return NTT_OK;

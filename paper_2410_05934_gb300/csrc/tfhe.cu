@@ -88,7 +88,7 @@ static int cmux_setup(ntt_plan_t plan, const uint64_t* d_key, uint32_t levels, u
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device) return NTT_ERR_ARG;
     if (plan->h.n_moduli != 1) return NTT_ERR_ARG;
-    if (plan->h.flags & NTT_FLAG_NATURAL_ORDER) return NTT_ERR_UNSUPPORTED;
+    if (plan->h.flags & (NTT_FLAG_NATURAL_ORDER | NTT_FLAG_WORD32)) return NTT_ERR_UNSUPPORTED;
     if (plan->h.log2n < NTT_TFHE_MIN_LOG2N || plan->h.log2n > NTT_TFHE_MAX_LOG2N) return NTT_ERR_UNSUPPORTED;
     if (((uintptr_t)d_key & 15u) != 0) return NTT_ERR_ALIGN;
     const uint64_t q = plan->h.moduli[0];
@@ -156,6 +156,7 @@ int tfhe_key_prepare(ntt_plan_t plan, const uint64_t* d_key, uint32_t levels, ui
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device) return NTT_ERR_ARG;
     if (plan->h.n_moduli != 1 || levels < 1 || levels > NTT_TFHE_MAX_LEVELS) return NTT_ERR_ARG;
+    if (plan->h.flags & NTT_FLAG_WORD32) return NTT_ERR_UNSUPPORTED;
     if (((uintptr_t)d_key & 7u) || ((uintptr_t)d_key_shoup & 15u)) return NTT_ERR_ALIGN;
     const uint64_t count = (uint64_t)4 * levels << plan->h.log2n;
     const unsigned grid = (unsigned)std::min<uint64_t>((count + 255) / 256, 4096);

@@ -14,6 +14,7 @@ from ._native import U32P, U64P, check, load
 NTT_FLAG_HOST_ONLY = 1
 NTT_FLAG_CHECK = 2
 NTT_FLAG_NATURAL_ORDER = 4
+NTT_FLAG_WORD32 = 8
 
 
 def _stream_handle(stream):
@@ -30,13 +31,13 @@ def _stream_handle(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _ptr(x, min_elems=None, what="tensor"):
+def _ptr(x, min_elems=None, what="tensor", word=8):
     if isinstance(x, int):
         return ctypes.c_void_p(x)
     if not x.is_cuda:
         raise ValueError("%s must be a CUDA tensor" % what)
-    if x.element_size() != 8 or x.is_floating_point():
-        raise ValueError("%s must hold 64-bit integers" % what)
+    if x.element_size() != word or x.is_floating_point():
+        raise ValueError("%s must hold %d-bit integers" % (what, 8 * word))
     if not x.is_contiguous():
         raise ValueError("%s must be contiguous" % what)
     if min_elems is not None and x.numel() < min_elems:
@@ -83,6 +84,7 @@ class Plan:
         self._h = h
         self.log2n, self.n, self.moduli, self.batch = log2n, 1 << log2n, moduli, batch
         self.n_moduli = len(moduli)
+        self.word = 4 if flags & NTT_FLAG_WORD32 else 8     # bytes per coefficient
         self.rows = batch * len(moduli)
         if schedule == "auto":
             from .costmodel import choose_schedule
@@ -142,26 +144,26 @@ class Plan:
     def forward(self, x, out=None, stream=None):
         out = x if out is None else out
         need = self.rows * self.n
-        check(load().ntt_forward(self._h, _ptr(x, need, "in"), _ptr(out, need, "out"),
+        check(load().ntt_forward(self._h, _ptr(x, need, "in", self.word), _ptr(out, need, "out", self.word),
                                  _stream_handle(stream)), "ntt_forward")
         return out
 
     def inverse(self, x, out=None, stream=None):
         out = x if out is None else out
         need = self.rows * self.n
-        check(load().ntt_inverse(self._h, _ptr(x, need, "in"), _ptr(out, need, "out"),
+        check(load().ntt_inverse(self._h, _ptr(x, need, "in", self.word), _ptr(out, need, "out", self.word),
                                  _stream_handle(stream)), "ntt_inverse")
         return out
 
     def forward_rows(self, x, out, row_begin, n_rows, stream=None):
         need = (row_begin + n_rows) * self.n
-        check(load().ntt_forward_rows(self._h, _ptr(x, need, "in"), _ptr(out, need, "out"),
+        check(load().ntt_forward_rows(self._h, _ptr(x, need, "in", self.word), _ptr(out, need, "out", self.word),
                                       row_begin, n_rows, _stream_handle(stream)), "ntt_forward_rows")
         return out
 
     def inverse_rows(self, x, out, row_begin, n_rows, stream=None):
         need = (row_begin + n_rows) * self.n
-        check(load().ntt_inverse_rows(self._h, _ptr(x, need, "in"), _ptr(out, need, "out"),
+        check(load().ntt_inverse_rows(self._h, _ptr(x, need, "in", self.word), _ptr(out, need, "out", self.word),
                                       row_begin, n_rows, _stream_handle(stream)), "ntt_inverse_rows")
         return out
 
@@ -219,8 +221,8 @@ class Plan:
     def pointwise(self, a, b, out=None, n_polys=0, stream=None):
         out = a if out is None else out
         need = (n_polys or self.batch) * self.n_moduli * self.n
-        check(load().poly_mul_pointwise(self._h, _ptr(a, need, "a"), _ptr(b, need, "b"),
-                                        _ptr(out, need, "c"), n_polys, _stream_handle(stream)),
+        check(load().poly_mul_pointwise(self._h, _ptr(a, need, "a", self.word), _ptr(b, need, "b", self.word),
+                                        _ptr(out, need, "c", self.word), n_polys, _stream_handle(stream)),
               "poly_mul_pointwise")
         return out
 

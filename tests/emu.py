@@ -32,6 +32,11 @@ def lib():
         L.nttemu_bconv.restype = i32
         L.nttemu_rescale.argtypes = [vp, u32, U64P, U64P, U64P, u32]
         L.nttemu_rescale.restype = i32
+        U32P = ctypes.POINTER(ctypes.c_uint32)
+        L.nttemu_transform32.argtypes = [vp, i32, U32P, U32P, u64, u64]
+        L.nttemu_transform32.restype = i32
+        L.nttemu_pointwise32.argtypes = [vp, U32P, U32P, U32P, u64]
+        L.nttemu_pointwise32.restype = i32
         _lib = L
     return _lib
 
@@ -105,6 +110,29 @@ class EmuPlan:
         if rc:
             raise ValueError("nttemu_rescale failed: %d" % rc)
         return out
+
+    def transform32(self, x, inverse=False, out=None, row_begin=0, n_rows=None):
+        """A NTT_FLAG_WORD32 plan's transform on uint32 rows."""
+        U32P = ctypes.POINTER(ctypes.c_uint32)
+        x = np.ascontiguousarray(x, dtype=np.uint32)
+        out = np.zeros_like(x) if out is None else out
+        n_rows = self.rows - row_begin if n_rows is None else n_rows
+        rc = lib().nttemu_transform32(self.h, int(inverse), x.ctypes.data_as(U32P), out.ctypes.data_as(U32P),
+                                      row_begin, n_rows)
+        if rc:
+            raise ValueError("nttemu_transform32 failed: %d" % rc)
+        return out
+
+    def pointwise32(self, a, b):
+        U32P = ctypes.POINTER(ctypes.c_uint32)
+        a = np.ascontiguousarray(a, dtype=np.uint32)
+        b = np.ascontiguousarray(b, dtype=np.uint32)
+        c = np.zeros_like(a)
+        rc = lib().nttemu_pointwise32(self.h, a.ctypes.data_as(U32P), b.ctypes.data_as(U32P),
+                                      c.ctypes.data_as(U32P), self.rows)
+        if rc:
+            raise ValueError("nttemu_pointwise32 failed: %d" % rc)
+        return c
 
     def pointwise(self, a, b, n_rows=None):
         a = np.ascontiguousarray(a, dtype=np.uint64)

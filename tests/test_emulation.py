@@ -325,3 +325,41 @@ def test_natural_order_every_schedule(log2n):
     # a row range
     part = plan.transform(x, 0, row_begin=1, n_rows=1, out=np.zeros_like(x))
     assert np.array_equal(part[1], want[1]) and not part[0].any() and not part[2].any()
+
+
+Q30 = [1073692673, 1073668097, 1073651713]   # the largest primes < 2^30 that are 1 mod 2^13
+
+
+@pytest.mark.parametrize("log2n", list(range(1, 13)))
+def test_word32_plans_match_oracle(log2n):
+    """NTT_FLAG_WORD32: the 32-bit kernel's phases against the oracle (the
+    same transform definition), plus the round trip and the pointwise product."""
+    from oracle import oracle as O
+    n = 1 << log2n
+    mods = Q30[:2]
+    rng = np.random.default_rng(log2n)
+    x = np.array([rng.integers(0, mods[r % 2], n, dtype=np.uint64) for r in range(6)])
+    plan = emu.EmuPlan(log2n, mods, 3, flags=8)
+    got = plan.transform32(x.astype(np.uint32))
+    assert np.array_equal(got.astype(np.uint64), O.transform_rows(x, [mods[r % 2] for r in range(6)]))
+    assert np.array_equal(plan.transform32(got, inverse=True).astype(np.uint64), x)
+    prod = plan.pointwise32(got, got[::-1].copy())
+    want = np.array([[int(a) * int(b) % mods[r % 2] for a, b in zip(got[r], got[5 - r])] for r in range(6)],
+                    dtype=np.uint64)
+    assert np.array_equal(prod.astype(np.uint64), want)
+    # extreme values and a row range
+    top = np.array([[m - 1] * n for m in (mods * 3)[:6]], dtype=np.uint64)
+    assert np.array_equal(plan.transform32(top.astype(np.uint32)).astype(np.uint64),
+                          O.transform_rows(top, [mods[r % 2] for r in range(6)]))
+    part = plan.transform32(x.astype(np.uint32), row_begin=3, n_rows=2)
+    assert not part[:3].any() and not part[5].any() and np.array_equal(part[3:5], got[3:5])
+    assert plan.status() == 0
+
+
+def test_word32_plan_rules():
+    with pytest.raises(ValueError):
+        emu.EmuPlan(13, Q30[:1], 1, flags=8)                  # N > 2^12
+    with pytest.raises(ValueError):
+        emu.EmuPlan(10, [W.POOL50[0]], 1, flags=8)            # modulus >= 2^30
+    with pytest.raises(ValueError):
+        emu.EmuPlan(10, Q30[:1], 1, flags=8 | 4)              # natural order

@@ -334,3 +334,58 @@ def test_natural_order_plans_reject_fused_operators():
         p.tfhe_external_product(torch.zeros((1, 2, 1024), dtype=torch.int64, device="cuda"),
                                 torch.zeros((6, 2, 1024, 2), dtype=torch.int64, device="cuda"), 3, 8)
     assert e.value.code == -10
+
+
+Q30 = [1073692673, 1073668097]   # the largest primes < 2^30 that are 1 mod 2^13
+
+
+def _to_dev32(x):
+    return torch.from_numpy(np.ascontiguousarray(x).astype(np.uint32).view(np.int32)).cuda()
+
+
+def _to_host32(t):
+    return t.cpu().numpy().view(np.uint32).astype(np.uint64)
+
+
+@pytest.mark.parametrize("log2n", list(range(1, 13)))
+def test_word32_plans(oracle, log2n):
+    """NTT_FLAG_WORD32: uint32 rows, 30-bit primes, every N up to 2^12."""
+    n = 1 << log2n
+    x = W.rows_uniform(29, log2n, Q30 * 3, n)
+    p = ntt.Plan(log2n, Q30, 3, flags=ntt.NTT_FLAG_WORD32)
+    d = _to_dev32(x)
+    out = torch.empty_like(d)
+    p.forward(d, out)
+    got = _to_host32(out)
+    assert np.array_equal(got, oracle.transform_rows(x, Q30 * 3))
+    back = torch.empty_like(d)
+    p.inverse(out, back)
+    assert torch.equal(back, d)
+    prod = torch.empty_like(d)
+    p.pointwise(out, out, prod)
+    want = np.array([[int(a) * int(a) % Q30[r % 2] for a in got[r]] for r in range(6)], dtype=np.uint64)
+    assert np.array_equal(_to_host32(prod), want)
+    assert p.status() == 0
+
+
+def test_word32_tfhe_shape_and_rules(oracle):
+    """3780 rows at N = 1024 (the TFHE forward batch) sampled; range check; rules."""
+    q = Q30[0]
+    x = W.rows_uniform(31, 10, [q] * 3780, 1024)
+    p = ntt.Plan(10, [q], 3780, flags=ntt.NTT_FLAG_WORD32)
+    d = _to_dev32(x)
+    p.forward(d)
+    got = _to_host32(d)
+    rows = np.array([0, 1, 1777, 3779])
+    assert np.array_equal(got[rows], oracle.transform_rows(x[rows], [q] * 4))
+    chk = ntt.Plan(10, [q], 1, flags=ntt.NTT_FLAG_WORD32 | ntt.NTT_FLAG_CHECK)
+    bad = torch.zeros((1, 1024), dtype=torch.int32, device="cuda")
+    bad[0, 9] = q
+    chk.forward(bad)
+    assert chk.status() == -8
+    with pytest.raises(ntt.NttError):
+        ntt.Plan(13, [Q30[0]], 1, flags=ntt.NTT_FLAG_WORD32)
+    with pytest.raises(ntt.NttError):
+        ntt.Plan(10, [W.POOL50[0]], 1, flags=ntt.NTT_FLAG_WORD32)
+    with pytest.raises(ValueError):
+        p.forward(torch.zeros((3780, 1024), dtype=torch.int64, device="cuda"))   # 64-bit buffer
