@@ -154,3 +154,34 @@ def test_scheduled_request_argument_error():
     with pytest.raises(ntt.NttError) as e:
         ntt.Batch([dict(r, schedule=ntt.schedule_count(10) + 1)], W.POOL50)
     assert e.value.code == -1
+
+
+def test_full_mixed_batch_as_benchmarked(oracle):
+    """The 200-request mixed batch at its full size (about 1.1 G coefficients)
+    in the configuration the bench times: requests of >= 2^22 coefficients on
+    their learned schedules on the second graph branch, the rest in the
+    persistent kernel; sampled rows and outputs of every request."""
+    from paper_2410_05934_gb300.costmodel import schedule_requests
+    spec = W.mixed_requests(seed=W.DEFAULT_SEED)
+    reqs = []
+    for i, (log2n, limbs, polys) in enumerate(spec):
+        x = W.request_rows_torch(W.DEFAULT_SEED, i, log2n, limbs, polys)
+        reqs.append(dict(log2n=log2n, n_moduli=limbs, n_polys=polys, moduli_offset=0, inverse=0,
+                         **{"in": x, "out": torch.empty_like(x)}))
+    sreqs = schedule_requests(reqs, W.POOL50, 22)
+    assert any(r["schedule"] for r in sreqs) and any(not r["schedule"] for r in sreqs)
+    b = ntt.Batch(sreqs, W.POOL50, flags=ntt.NTT_BATCH_GRAPH)
+    b.execute()
+    b.execute()                                      # a graph replay gives the same bits
+    torch.cuda.synchronize()
+    assert b.status() == 0
+    rng = np.random.default_rng(200)
+    for i, (log2n, limbs, polys) in enumerate(spec):
+        n, rows = 1 << log2n, limbs * polys
+        pick = sorted(set([0, rows - 1] + rng.integers(0, rows, 1).tolist()))
+        x = np.stack([W.uniform_mod(W.DEFAULT_SEED, 1000 + i, n, W.POOL50[r % limbs], start=r * n) for r in pick])
+        idx = np.stack([np.concatenate([[0, n - 1], rng.integers(0, n, 4)]) for _ in pick]).astype(np.uint32)
+        ref = oracle.transform_rows(x, [W.POOL50[r % limbs] for r in pick], idx=idx)
+        got = to_host(sreqs[i]["out"][pick])
+        assert np.array_equal(got[np.arange(len(pick))[:, None], idx], ref), (i, log2n, limbs, polys)
+        sreqs[i]["in"] = sreqs[i]["out"] = None       # free as we go

@@ -114,3 +114,21 @@ def test_tfhe_argument_errors_and_range_check():
     badkey[3, 1, 7] = q
     chk.tfhe_key_prepare(badkey, 3)
     assert chk.status() == -8
+
+
+def test_full_size_cmux_step_as_benchmarked():
+    """One CMux step over the bench's 1024 accumulators (N = 1024, 62-bit q,
+    B = 2^8, l = 3), in place, sampled ciphertexts against the oracle."""
+    q, log2n, levels, log2_base = W.Q62_N1024, 10, 3, 8
+    w = W.tfhe_cmux(n_ct=1024, steps=1, levels=levels)
+    plan = ntt.Plan(log2n, [q])
+    acc = to_dev(w["acc"])
+    plan.tfhe_cmux_rotate(acc, _rot_dev(w["rot"][0]), plan.tfhe_key_prepare(to_dev(w["key"][0]), levels), levels,
+                          log2_base)
+    got = to_host(acc)
+    kc = TO.key_coefficients(w["key"][0], q)
+    rng = np.random.default_rng(5)
+    for c in [0, 511, 1023] + rng.integers(0, 1024, 3).tolist():
+        idx = sorted(set([0, 1023] + rng.integers(0, 1024, 6).tolist()))
+        assert np.array_equal(got[c][:, idx], TO.cmux_rotate(w["acc"][c], int(w["rot"][0][c]), w["key"][0], q,
+                                                             log2_base, levels, key_coef=kc, idx=idx)), c
