@@ -326,49 +326,37 @@ static int emu_cmux(const CmuxArgs& c, const TileArgs& af, const TileArgs& ai) {
     L[0].gbase = 0;
     L[0].tw_off = 0;
     L[0].valid = true;
-    // each slot's own TileLoc (its tw_off points at the staged twiddles)
-    std::vector<TileLoc> Lf[2] = {L, L}, Lv[2] = {L, L};
-    for (int s = 0; s < 2; ++s) {
-        Lf[s][0].tw_off = K::tw_off(s, false);
-        Lv[s][0].tw_off = K::tw_off(s, true);
-    }
     const LimbConst lc = af.lc[0];
-    for (int tid = 0; tid < K::THREADS; ++tid) cmux_stage_twiddles<K>(af.tw, ai.tw, tid, smem.data());
     for (uint64_t ct = 0; ct < c.n_ct; ++ct) {
         for (int tid = 0; tid < K::THREADS; ++tid)
-            cmux_load<K>(cr[tid], c, ct, tid >> K::LOGT, tid & (K::T - 1));
+            cmux_load<K>(cr[tid], c, ct, tid >> K::LOGT, tid & (K::T - 1), smem.data());
         for (uint32_t j = 0; j < c.levels; ++j) {
             for (int tid = 0; tid < K::THREADS; ++tid) {
                 const int s = tid >> K::LOGT, t = tid & (K::T - 1);
                 cmux_digits<K>(sf[tid], cr[tid], j, c);
-                write_pairs_swizzled<F>(sf[tid], Lf[s][0], t, smem.data() + (size_t)s * K::N);
+                write_pairs_swizzled<F>(sf[tid], L[0], t, smem.data() + (size_t)s * K::N);
             }
             for (int s = 0; s < 2; ++s) {
                 std::vector<TileRegs<F>> part(sf.begin() + s * K::T, sf.begin() + (s + 1) * K::T);
-                emu_passes<F, 0>(part, af, Lf[s], smem.data() + (size_t)s * K::N);
+                emu_passes<F, 0>(part, af, L, smem.data() + (size_t)s * K::N);
                 std::copy(part.begin(), part.end(), sf.begin() + s * K::T);
             }
             for (int tid = 0; tid < K::THREADS; ++tid) {
                 const int s = tid >> K::LOGT, t = tid & (K::T - 1);
-                cmux_mac<K>(cr[tid], c, lc, (uint32_t)s * c.levels + j, t, smem.data() + (size_t)s * K::N);
+                cmux_mac<K>(c, lc, (uint32_t)s * c.levels + j, s, t, smem.data());
             }
         }
         for (int tid = 0; tid < K::THREADS; ++tid) {
             const int s = tid >> K::LOGT, t = tid & (K::T - 1);
-            cmux_exchange_put<K>(cr[tid], s, t, smem.data() + (size_t)s * K::N);
+            cmux_inverse_input<K>(si[tid], lc, s, t, smem.data());
         }
         for (int tid = 0; tid < K::THREADS; ++tid) {
             const int s = tid >> K::LOGT, t = tid & (K::T - 1);
-            cmux_exchange_get<K>(cr[tid], lc, s, t, smem.data() + (size_t)(1 - s) * K::N);
-        }
-        for (int tid = 0; tid < K::THREADS; ++tid) {
-            const int s = tid >> K::LOGT, t = tid & (K::T - 1);
-            cmux_inverse_input<K>(si[tid], cr[tid], s);
-            write_pairs_swizzled<I>(si[tid], Lv[s][0], t, smem.data() + (size_t)s * K::N);
+            write_pairs_swizzled<I>(si[tid], L[0], t, smem.data() + (size_t)s * K::N);
         }
         for (int s = 0; s < 2; ++s) {
             std::vector<TileRegs<I>> part(si.begin() + s * K::T, si.begin() + (s + 1) * K::T);
-            emu_passes<I, 0>(part, ai, Lv[s], smem.data() + (size_t)s * K::N);
+            emu_passes<I, 0>(part, ai, L, smem.data() + (size_t)s * K::N);
         }
         for (int tid = 0; tid < K::THREADS; ++tid) {
             const int s = tid >> K::LOGT, t = tid & (K::T - 1);

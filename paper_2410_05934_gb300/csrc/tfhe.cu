@@ -21,40 +21,32 @@ __global__ void __launch_bounds__(CmuxCfg<LOGN, MC>::THREADS, CmuxCfg<LOGN, MC>:
     const int s = threadIdx.x >> K::LOGT;
     const int t = threadIdx.x & (K::T - 1);
     uint64_t* sm = smem + (size_t)s * K::N;
-    const uint64_t* sm_other = smem + (size_t)(1 - s) * K::N;
     TileLoc L;
     L.row = 0;
     L.rowq = 0;
     L.limb = 0;
     L.hi = 0;
     L.gbase = 0;
-    L.tw_off = K::tw_off(s, false);
+    L.tw_off = 0;
     L.valid = true;
-    TileLoc Li = L;
-    Li.tw_off = K::tw_off(s, true);
     const LimbConst lc = af.lc[0];
-    cmux_stage_twiddles<K>(af.tw, ai.tw, threadIdx.x, smem);
-    __syncthreads();
     for (uint64_t ct = blockIdx.x; ct < c.n_ct; ct += gridDim.x) {
         CmuxRegs<K> cr;
-        cmux_load<K>(cr, c, ct, s, t);
+        cmux_load<K>(cr, c, ct, s, t, smem);
         for (uint32_t j = 0; j < c.levels; ++j) {
             TileRegs<F> st;
             cmux_digits<K>(st, cr, j, c);
             write_pairs_swizzled<F>(st, L, t, sm);
             __syncthreads();
             run_passes<F, 0>(st, af, L, t, sm);
-            cmux_mac<K>(cr, c, lc, (uint32_t)s * c.levels + j, t, sm);
+            cmux_mac<K>(c, lc, (uint32_t)s * c.levels + j, s, t, smem);
         }
-        cmux_exchange_put<K>(cr, s, t, sm);
-        __syncthreads();
-        cmux_exchange_get<K>(cr, lc, s, t, sm_other);
         __syncthreads();
         TileRegs<I> si;
-        cmux_inverse_input<K>(si, cr, s);
-        write_pairs_swizzled<I>(si, Li, t, sm);
+        cmux_inverse_input<K>(si, lc, s, t, smem);
+        write_pairs_swizzled<I>(si, L, t, sm);
         __syncthreads();
-        run_passes<I, 0>(si, ai, Li, t, sm);
+        run_passes<I, 0>(si, ai, L, t, sm);
         cmux_store<K>(c, lc, ct, s, t, sm);
         __syncthreads();
     }

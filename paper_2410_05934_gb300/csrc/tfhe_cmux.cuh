@@ -9,8 +9,9 @@
 //     level j = 0..l-1:  signed digit e_j of t (mod q)
 //             -> forward NTT in shared memory (the tile phases of the NTT)
 //             -> MAC: acc_c += NTT(e_j) * K[s l + j][c] for c = 0, 1
-//   exchange  slot s hands acc_(1-s) to the other slot, adds the one it gets
-//             (key rows in Shoup form: products and sums stay in [0, 2q))
+//   output s  the two slots' partial sums of output s, added after a barrier
+//             (key rows in Shoup form: products and sums stay in [0, 2q);
+//             the sums live in shared memory)
 //   output    INTT of acc_s (slot s), plus d_s for the CMux, stored
 //
 // The digits never leave the SM, the key is read once per ciphertext from
@@ -35,43 +36,26 @@ struct CmuxArgs {
 };
 
 // 8 coefficients per thread, passes of up to 3 fused stages, two slots.
-// Shared memory (words): [slot 0 row][slot 1 row][forward twiddles][inverse
-// twiddles]; the twiddles are staged once per CTA (every ciphertext uses the
-// same tables) in the tile phases' slot order (slot i = table entry i + 1
-// for a tile that is one whole row), and each slot's TileLoc points its
-// pass twiddles there through tw_off.
+// Shared memory (words): [slot 0 row][slot 1 row][partial sums (slot s,
+// output c) at (2 + 2 s + c) N]; the MAC sums live in shared memory, not in
+// registers, so three CTAs fit on an SM; twiddles come through the
+// read-only cache.
 template <int LOGN_, int MC_>
 struct CmuxCfg {
     static constexpr int LOGN = LOGN_, MC = MC_;
     static constexpr int LOGT = LOGN - 3;
-    using F = TileCfg<LOGN, 0, LOGN, 0, LOGT, 3, 1, false, MC, 0>;
-    using I = TileCfg<LOGN, 0, LOGN, 0, LOGT, 3, 1, true, MC, 0>;
+    using F = TileCfg<LOGN, 0, LOGN, 0, LOGT, 3, 1, false, MC, 2>;
+    using I = TileCfg<LOGN, 0, LOGN, 0, LOGT, 3, 1, true, MC, 2>;
     static constexpr int N = 1 << LOGN, T = F::T, R = F::R, THREADS = 2 * T;
-    static constexpr int TW_WORDS = 2 * (N - 1);                 // N - 1 TwPairs
-    static constexpr int FWD_TW = 2 * N, INV_TW = 2 * N + TW_WORDS;
-    static constexpr size_t SMEM_BYTES = sizeof(uint64_t) * (size_t)(2 * N + 2 * TW_WORDS);
-    static constexpr int MIN_CTAS = THREADS <= 256 ? 2 : 1;      // register budget: 128 per thread
-    static_assert(F::E == N && F::TWS && I::TWS, "one whole row per slot, twiddles staged in shared memory");
-    // tw_off of slot s: from the slot's row + E to the twiddle region
-    static constexpr int32_t tw_off(int s, bool inv) { return (1 - s) * N + (inv ? TW_WORDS : 0); }
+    static constexpr size_t SMEM_BYTES = sizeof(uint64_t) * (size_t)(6 * N);
+    static constexpr int MIN_CTAS = THREADS <= 256 ? 3 : 1;      // register budget: 85 per thread
+    static_assert(F::E == N && !F::TWS && !I::TWS, "one whole row per slot, read-only-cache twiddles");
+    static constexpr size_t acc_off(int s, int c) { return (size_t)(2 + 2 * s + c) * N; }
 };
-
-// all threads of the CTA: both tables into their regions
-template <class K>
-NTT_HD void cmux_stage_twiddles(const TwPair* fwd, const TwPair* inv, int tid, uint64_t* smem) {
-    TwPair* f = reinterpret_cast<TwPair*>(smem + K::FWD_TW);
-    TwPair* v = reinterpret_cast<TwPair*>(smem + K::INV_TW);
-    for (int i = tid; i < K::N - 1; i += K::THREADS) {
-        NTT_GMEM_CHECK(i + 1, K::N);
-        f[i] = load_tw(fwd, (uint32_t)i + 1u);
-        v[i] = load_tw(inv, (uint32_t)i + 1u);
-    }
-}
 
 template <class K>
 struct CmuxRegs {
     uint32_t dig[K::R];        // the signed digits of each coefficient, log2_base bits per level
-    uint64_t acc[2][K::R];     // lazy sums of outputs 0 and 1 (pair layout), each < 2 levels q
 };
 
 // round(v 2^bl / q) mod 2^bl for v < q < 2^62, bl = levels * log2_base <= 32
@@ -118,7 +102,7 @@ NTT_HD uint64_t cmux_digit(uint32_t packed, uint32_t j, const CmuxArgs& c) {
 // coefficient k = 2t + 2iT + h of the slot's row <-> register 2i + h (the
 // pair layout of the tile phases, for a tile that is one whole row)
 template <class K>
-NTT_HD void cmux_load(CmuxRegs<K>& cr, const CmuxArgs& c, uint64_t ct, int s, int t) {
+NTT_HD void cmux_load(CmuxRegs<K>& cr, const CmuxArgs& c, uint64_t ct, int s, int t, uint64_t* smem) {
     const uint64_t* row = c.in + ((ct * 2 + (uint64_t)s) << K::LOGN);
     const uint32_t a = c.rot ? (c.rot[ct] & (2u * K::N - 1u)) : 0u;
     bool bad = false;
@@ -143,8 +127,17 @@ NTT_HD void cmux_load(CmuxRegs<K>& cr, const CmuxArgs& c, uint64_t ct, int s, in
         }
     }
     if (c.check && bad) record_status(c.status, NTT_STATUS_RANGE);
+    // this thread's positions of the slot's two partial sums start at zero
+    uint64_t* acc0 = smem + K::acc_off(s, 0);
+    uint64_t* acc1 = smem + K::acc_off(s, 1);
+    const uint32_t b = swz(2u * (uint32_t)t);
 #pragma unroll
-    for (int r = 0; r < K::R; ++r) cr.acc[0][r] = cr.acc[1][r] = 0;
+    for (int i = 0; i < K::R / 2; ++i) {
+        const uint32_t cc = swz(2u * (uint32_t)i * K::T);
+        NTT_SMEM_CHECK(b ^ cc, K::N);
+        acc0[b ^ cc] = acc0[(b ^ cc) ^ 1u] = 0;
+        acc1[b ^ cc] = acc1[(b ^ cc) ^ 1u] = 0;
+    }
 }
 
 template <class K>
@@ -153,82 +146,50 @@ NTT_HD void cmux_digits(TileRegs<typename K::F>& st, const CmuxRegs<K>& cr, uint
     for (int r = 0; r < K::R; ++r) st.x[r] = cmux_digit(cr.dig[r], j, c);
 }
 
-// forward result of level j (shared memory, any lazy range below 2^64) times
-// key row p in Shoup form: each product lies in [0, 2q) and the sums are
-// kept in [0, 2q) (q < 2^62, so sum + product < 4q < 2^64)
+// forward result of level j (the slot's row, any lazy range below 2^64)
+// times key row p in Shoup form, added to the slot's partial sums (each
+// product in [0, 2q), sums kept in [0, 2q) since q < 2^62).  Every thread
+// reads and writes only its own positions.
 template <class K>
-NTT_HD void cmux_mac(CmuxRegs<K>& cr, const CmuxArgs& c, const LimbConst& lc, uint32_t p, int t,
-                     const uint64_t* sm) {
+NTT_HD void cmux_mac(const CmuxArgs& c, const LimbConst& lc, uint32_t p, int s, int t, uint64_t* smem) {
     const TwPair* k0 = c.key + ((uint64_t)(2u * p) << K::LOGN);
     const TwPair* k1 = k0 + K::N;
+    const uint64_t* sm = smem + (size_t)s * K::N;
+    uint64_t* acc0 = smem + K::acc_off(s, 0);
+    uint64_t* acc1 = smem + K::acc_off(s, 1);
     const uint32_t b = swz(2u * (uint32_t)t);
 #pragma unroll
     for (int i = 0; i < K::R / 2; ++i) {
         const uint32_t cc = swz(2u * (uint32_t)i * K::T);
-        NTT_SMEM_CHECK(b ^ cc, K::N);
-        const uint64_t x = sm[b ^ cc], y = sm[(b ^ cc) ^ 1u];
+        const uint32_t e0 = b ^ cc, e1 = e0 ^ 1u;
+        NTT_SMEM_CHECK(e0, K::N);
+        const uint64_t x = sm[e0], y = sm[e1];
         const uint32_t k = 2u * (uint32_t)t + 2u * (uint32_t)i * K::T;
         NTT_GMEM_CHECK(k + 1, K::N);
         const TwPair a0 = load_tw(k0, k), a1 = load_tw(k0, k + 1);
         const TwPair b0 = load_tw(k1, k), b1 = load_tw(k1, k + 1);
-        cr.acc[0][2 * i] = csub(cr.acc[0][2 * i] + shoup_mul(x, a0.w, a0.wp, lc.q), lc.two_q);
-        cr.acc[0][2 * i + 1] = csub(cr.acc[0][2 * i + 1] + shoup_mul(y, a1.w, a1.wp, lc.q), lc.two_q);
-        cr.acc[1][2 * i] = csub(cr.acc[1][2 * i] + shoup_mul(x, b0.w, b0.wp, lc.q), lc.two_q);
-        cr.acc[1][2 * i + 1] = csub(cr.acc[1][2 * i + 1] + shoup_mul(y, b1.w, b1.wp, lc.q), lc.two_q);
+        acc0[e0] = csub(acc0[e0] + shoup_mul(x, a0.w, a0.wp, lc.q), lc.two_q);
+        acc0[e1] = csub(acc0[e1] + shoup_mul(y, a1.w, a1.wp, lc.q), lc.two_q);
+        acc1[e0] = csub(acc1[e0] + shoup_mul(x, b0.w, b0.wp, lc.q), lc.two_q);
+        acc1[e1] = csub(acc1[e1] + shoup_mul(y, b1.w, b1.wp, lc.q), lc.two_q);
     }
 }
 
-// a lazy sum in [0, 2q) to [0, q)
-NTT_HD uint64_t cmux_reduce(uint64_t x, const LimbConst& lc) { return csub(x, lc.q); }
-
-// Slot s hands the other output's partial sums over through its own tile
-// and adds what the other slot handed it (same thread index, same
-// positions).  The accumulator of each slot is picked with a branch, so the
-// arrays stay in registers.
+// after a barrier: output s = partial sum of slot 0 + partial sum of slot 1,
+// canonical, into the inverse's registers (pair layout)
 template <class K>
-NTT_HD void cmux_put_pairs(const uint64_t (&v)[K::R], int t, uint64_t* sm) {
+NTT_HD void cmux_inverse_input(TileRegs<typename K::I>& st, const LimbConst& lc, int s, int t, const uint64_t* smem) {
+    const uint64_t* p0 = smem + K::acc_off(0, s);
+    const uint64_t* p1 = smem + K::acc_off(1, s);
     const uint32_t b = swz(2u * (uint32_t)t);
 #pragma unroll
     for (int i = 0; i < K::R / 2; ++i) {
         const uint32_t cc = swz(2u * (uint32_t)i * K::T);
-        NTT_SMEM_CHECK(b ^ cc, K::N);
-        sm[b ^ cc] = v[2 * i];
-        sm[(b ^ cc) ^ 1u] = v[2 * i + 1];
+        const uint32_t e0 = b ^ cc, e1 = e0 ^ 1u;
+        NTT_SMEM_CHECK(e0, K::N);
+        st.x[2 * i] = csub(csub(p0[e0], lc.q) + csub(p1[e0], lc.q), lc.q);
+        st.x[2 * i + 1] = csub(csub(p0[e1], lc.q) + csub(p1[e1], lc.q), lc.q);
     }
-}
-
-template <class K>
-NTT_HD void cmux_add_pairs(uint64_t (&v)[K::R], const LimbConst& lc, int t, const uint64_t* sm) {
-    const uint32_t b = swz(2u * (uint32_t)t);
-#pragma unroll
-    for (int i = 0; i < K::R / 2; ++i) {
-        const uint32_t cc = swz(2u * (uint32_t)i * K::T);
-        NTT_SMEM_CHECK(b ^ cc, K::N);
-        v[2 * i] = csub(cmux_reduce(v[2 * i], lc) + cmux_reduce(sm[b ^ cc], lc), lc.q);
-        v[2 * i + 1] = csub(cmux_reduce(v[2 * i + 1], lc) + cmux_reduce(sm[(b ^ cc) ^ 1u], lc), lc.q);
-    }
-}
-
-template <class K>
-NTT_HD void cmux_exchange_put(const CmuxRegs<K>& cr, int s, int t, uint64_t* sm) {
-    if (s == 0)
-        cmux_put_pairs<K>(cr.acc[1], t, sm);
-    else
-        cmux_put_pairs<K>(cr.acc[0], t, sm);
-}
-
-template <class K>
-NTT_HD void cmux_exchange_get(CmuxRegs<K>& cr, const LimbConst& lc, int s, int t, const uint64_t* sm_other) {
-    if (s == 0)
-        cmux_add_pairs<K>(cr.acc[0], lc, t, sm_other);
-    else
-        cmux_add_pairs<K>(cr.acc[1], lc, t, sm_other);
-}
-
-template <class K>
-NTT_HD void cmux_inverse_input(TileRegs<typename K::I>& st, const CmuxRegs<K>& cr, int s) {
-#pragma unroll
-    for (int r = 0; r < K::R; ++r) st.x[r] = s == 0 ? cr.acc[0][r] : cr.acc[1][r];
 }
 
 // inverse result (shared memory) -> canonical, plus d_s for the CMux -> out
