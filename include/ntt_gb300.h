@@ -228,16 +228,17 @@ int ntt_bench_butterflies(uint64_t q, uint32_t kind, uint32_t blocks, uint32_t t
  *   schedule       0: the request's rows are work items of the persistent
  *                  kernel.  s + 1 (s < ntt_schedule_count(log2n)): the
  *                  request runs instead as its own launch sequence with
- *                  schedule s of its N, on a second branch that forks from
- *                  and joins the caller's stream around the persistent
- *                  kernel (both branches live in the same CUDA graph).  Meant
+ *                  schedule s of its N, on one of up to four branches that
+ *                  fork from and join the caller's stream around the
+ *                  persistent kernel (all in the same CUDA graph; the k-th
+ *                  scheduled request goes to branch k mod 4).  Meant
  *                  for requests large enough to fill the GPU by themselves,
  *                  whose tuned schedule beats the batch kernel's fixed tiles.
  *   in / out       caller-owned device buffers (may alias), 16-byte aligned
  * ntt_batch_plan validates the requests, builds the twiddle tables of every
  * (N, pool modulus) pair the batch uses, and uploads the work-item list; the
  * batch plan owns those tables, the item list, the queue counter and (with
- * scheduled requests) a second stream and two events.  With
+ * scheduled requests) up to four more streams and five events.  With
  * NTT_BATCH_GRAPH, execution captures [reset counter, kernel] (and the
  * scheduled requests' launches) into a CUDA graph on first use and replays
  * it afterwards.

@@ -42,6 +42,7 @@ struct BatchItem {
 };
 
 #define NTT_BATCH_THREADS 256
+#define NTT_BATCH_BRANCHES 4     // concurrent graph branches for the scheduled requests
 static constexpr size_t kBatchSmemBound = 18 * 1024;
 
 // One phase (stage range) of a config over rows [a.row_begin, +n_rows).
@@ -304,8 +305,12 @@ struct ntt_batch_s {
     uint32_t flags = 0, mc = 0, check = 0;
     uint32_t short_only = 0;    // every request has N <= 2^NTT_BATCH_SHORT_NMAX
     std::vector<uint32_t> scheduled;   // requests that run as their own launches
-    cudaStream_t side = nullptr;       // their branch, forked from the caller's stream
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // their branches (request k on branch k mod n_branches), forked from and
+    // joined to the caller's stream
+    uint32_t n_branches = 0;
+    cudaStream_t side[NTT_BATCH_BRANCHES] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[NTT_BATCH_BRANCHES] = {};
     int device = -1;
     int grid = 0;
     uint64_t coefficients = 0;
@@ -328,8 +333,10 @@ static void batch_drop_graph(ntt_batch_s* b) {
 static void batch_free(ntt_batch_s* b) {
     batch_drop_graph(b);
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
-    if (b->ev_join) cudaEventDestroy(b->ev_join);
-    if (b->side) cudaStreamDestroy(b->side);
+    for (int k = 0; k < NTT_BATCH_BRANCHES; ++k) {
+        if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+        if (b->side[k]) cudaStreamDestroy(b->side[k]);
+    }
     for (auto& t : b->tables) {
         if (t.d_fwd) cudaFree(t.d_fwd);
         if (t.d_inv) cudaFree(t.d_inv);
@@ -462,10 +469,13 @@ int ntt_batch_plan(ntt_batch_t* out, const ntt_request_t* reqs, uint32_t n_reqs,
                          cudaMemcpyHostToDevice) == cudaSuccess) &&
              cudaMemset(b->d_status, 0, sizeof(int)) == cudaSuccess;
     }
-    if (ok && !b->scheduled.empty())
-        ok = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) == cudaSuccess &&
-             cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
-             cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) == cudaSuccess;
+    if (ok && !b->scheduled.empty()) {
+        b->n_branches = (uint32_t)std::min<size_t>(NTT_BATCH_BRANCHES, b->scheduled.size());
+        ok = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+        for (uint32_t k = 0; ok && k < b->n_branches; ++k)
+            ok = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming) == cudaSuccess;
+    }
     if (ok) {
         const void* fn = batch_kernel(b->mc, b->short_only);
         int per_sm = 0, sms = 0;
@@ -537,17 +547,21 @@ static int batch_launch_request(ntt_batch_t b, size_t i, uint32_t sid, cudaStrea
     return fn(d, r.in, r.out, 0, (uint64_t)r.n_polys * r.n_moduli, st, launches);
 }
 
-// [fork -> scheduled requests on the side stream] || [reset counter, persistent kernel] -> join
+// [fork -> scheduled requests on up to NTT_BATCH_BRANCHES branches] ||
+// [reset counter, persistent kernel] -> join
 static int batch_enqueue(ntt_batch_t b, cudaStream_t st, uint32_t* launches) {
     *launches = 0;
     if (!b->scheduled.empty()) {
-        if (cudaEventRecord(b->ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(b->side, b->ev_fork, 0) != cudaSuccess)
-            return NTT_ERR_CUDA;
-        for (uint32_t i : b->scheduled) {
-            int rc = batch_launch_request(b, i, b->reqs[i].schedule - 1, b->side, launches);
+        if (cudaEventRecord(b->ev_fork, st) != cudaSuccess) return NTT_ERR_CUDA;
+        for (uint32_t k = 0; k < b->n_branches; ++k)
+            if (cudaStreamWaitEvent(b->side[k], b->ev_fork, 0) != cudaSuccess) return NTT_ERR_CUDA;
+        for (size_t k = 0; k < b->scheduled.size(); ++k) {
+            const uint32_t i = b->scheduled[k];
+            int rc = batch_launch_request(b, i, b->reqs[i].schedule - 1, b->side[k % b->n_branches], launches);
             if (rc) return rc;
         }
-        if (cudaEventRecord(b->ev_join, b->side) != cudaSuccess) return NTT_ERR_CUDA;
+        for (uint32_t k = 0; k < b->n_branches; ++k)
+            if (cudaEventRecord(b->ev_join[k], b->side[k]) != cudaSuccess) return NTT_ERR_CUDA;
     }
     const uint32_t n = (uint32_t)b->hitems.size();
     if (n) {
@@ -564,7 +578,8 @@ static int batch_enqueue(ntt_batch_t b, cudaStream_t st, uint32_t* launches) {
         if (cudaPeekAtLastError() != cudaSuccess) return NTT_ERR_CUDA;
         ++*launches;
     }
-    if (!b->scheduled.empty() && cudaStreamWaitEvent(st, b->ev_join, 0) != cudaSuccess) return NTT_ERR_CUDA;
+    for (uint32_t k = 0; k < b->n_branches; ++k)
+        if (cudaStreamWaitEvent(st, b->ev_join[k], 0) != cudaSuccess) return NTT_ERR_CUDA;
     return NTT_OK;
 }
 
