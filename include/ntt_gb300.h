@@ -130,6 +130,27 @@ int ntt_inverse_rows(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, uin
  * batch).  Row r uses modulus r mod n_moduli.  d_c may alias d_a or d_b.
  */
 /*
+ * Pointwise product fused into the inverse transform (Eq. 1's
+ * INTT(NTT(a) (.) NTT(b)), the CKKS cross products of a ciphertext
+ * multiplication): for every output polynomial p < batch and limb l,
+ *   out[p][l] = INTT( a[a_poly[p]][l] (.) b[b_poly[p]][l] )  mod q_l,
+ * the product formed while the inverse's first kernel loads its tile (no
+ * product buffer, no extra launch).
+ *   d_a, d_b     NTT-domain polynomials [a_polys][n_moduli][N] and
+ *                [b_polys][n_moduli][N], canonical; may alias each other
+ *   a_poly, b_poly  host arrays of `batch` polynomial indices (< a_polys,
+ *                < b_polys), at most NTT_MUL_MAX_MAPPED entries; both NULL =
+ *                polynomial p of each (then a_polys, b_polys >= batch)
+ *   d_out        [batch][n_moduli][N]; must not overlap d_a or d_b
+ * Errors: ARG (bad index or count), ALIGN, UNSUPPORTED (natural-order or
+ * 32-bit plans), CUDA.
+ */
+#define NTT_MUL_MAX_MAPPED 32
+int ntt_inverse_mul(ntt_plan_t plan, const uint64_t* d_a, const uint32_t* a_poly, uint32_t a_polys,
+                    const uint64_t* d_b, const uint32_t* b_poly, uint32_t b_polys, uint64_t* d_out,
+                    void* cuda_stream);
+
+/*
  * CKKS Rescale of NTT-domain ciphertext limbs (Sec. II-A: after a
  * multiplication the scale is brought back to Delta and one level is
  * dropped): for the plan's moduli q_0 .. q_(L-1) and every polynomial,

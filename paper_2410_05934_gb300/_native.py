@@ -45,6 +45,7 @@ SIGNATURES = [
     ("poly_mul_pointwise", i32, [vp, vp, vp, vp, u32, vp]),
     ("ntt_hmul_tensor", i32, [vp, vp, vp, vp, vp]),
     ("ntt_rescale", i32, [vp, vp, vp, vp, u32, vp]),
+    ("ntt_inverse_mul", i32, [vp, vp, U32P, u32, vp, U32P, u32, vp, vp]),
     ("ntt_schedule_count", i32, [u32]),
     ("ntt_schedule_name", i32, [u32, u32, ctypes.c_char_p, ctypes.c_size_t]),
     ("ntt_plan_set_schedule", i32, [vp, u32]),

@@ -160,6 +160,7 @@ __global__ void __launch_bounds__(NTT_BATCH_THREADS, BatchOcc<MC, NMAX>::ctas)
         a.in_b = nullptr;
         a.aux_q = 0;
         a.nat = 0;
+        a.has_map = 0;
         if (rq.inverse)
             batch_dispatch<true, MC, NMAX>(a, rq, it.n_rows, smem);
         else
@@ -251,6 +252,7 @@ __global__ void __launch_bounds__(NTT_BATCH_THREADS, NTT_BATCH_MIN_CTAS)
         a.in_b = nullptr;
         a.aux_q = 0;
         a.nat = 0;
+        a.has_map = 0;
         if (sr.inverse)
             batch_dispatch<true, MC, 16>(a, rq, n_rows, smem);
         else
@@ -543,6 +545,7 @@ static int batch_launch_request(ntt_batch_t b, size_t i, uint32_t sid, cudaStrea
     d.in_b = nullptr;
     d.aux_q = 0;
     d.nat = 0;
+    d.has_map = 0;
     const LaunchFn fn = r.inverse ? table[idx].inv : table[idx].fwd;
     return fn(d, r.in, r.out, 0, (uint64_t)r.n_polys * r.n_moduli, st, launches);
 }

@@ -113,6 +113,7 @@ static PlanDev plan_dev(const ntt_plan_s* p) {
     d.in_b = nullptr;
     d.aux_q = 0;
     d.nat = 0;
+    d.has_map = 0;
     return d;
 }
 
@@ -333,6 +334,48 @@ int ntt_hmul_tensor(ntt_plan_t plan, const uint64_t* d_a, const uint64_t* d_b, u
     d.src_mode = 1;
     d.in_b = d_b;
     return g_table[idx].inv(d, d_a, d_out, 0, 3ull * plan->h.n_moduli, cuda_stream, &plan->last_launches);
+}
+
+int ntt_inverse_mul(ntt_plan_t plan, const uint64_t* d_a, const uint32_t* a_poly, uint32_t a_polys,
+                    const uint64_t* d_b, const uint32_t* b_poly, uint32_t b_polys, uint64_t* d_out, void* cuda_stream) {
+    if (!plan || !d_a || !d_b || !d_out) return NTT_ERR_ARG;
+    if (!aligned16(d_a) || !aligned16(d_b) || !aligned16(d_out)) return NTT_ERR_ALIGN;
+    if (natural(plan) || word32(plan)) return NTT_ERR_UNSUPPORTED;
+    const uint32_t batch = plan->h.batch;
+    PlanDev d = plan_dev(plan);
+    if (a_poly || b_poly) {
+        if (!a_poly || !b_poly || batch > NTT_MUL_MAX_MAPPED) return NTT_ERR_ARG;
+        for (uint32_t p = 0; p < batch; ++p) {
+            if (a_poly[p] >= a_polys || b_poly[p] >= b_polys) return NTT_ERR_ARG;
+            d.a_map[p] = (uint8_t)a_poly[p];
+            d.b_map[p] = (uint8_t)b_poly[p];
+        }
+        d.has_map = 1;
+    } else if (a_polys < batch || b_polys < batch) {
+        return NTT_ERR_ARG;
+    }
+    int rc = check_device(plan);
+    if (rc) return rc;
+    // the product is formed in the inverse's first kernel: a direct form
+    auto inverse_first_pipelined = [](int k) {
+        return (g_params[k].kind == 1 ? g_params[k].pipe : form_row(g_params[k].pipe)) == 1;
+    };
+    int idx = sched_index(plan->h.log2n, plan->schedule);
+    if (idx < 0 || inverse_first_pipelined(idx)) {
+        idx = -1;
+        for (uint32_t id = 0; (int)id < schedule_count(plan->h.log2n); ++id) {
+            const int k = sched_index(plan->h.log2n, id);
+            if (!inverse_first_pipelined(k)) {
+                idx = k;
+                break;
+            }
+        }
+        if (idx < 0) return NTT_ERR_UNSUPPORTED;
+    }
+    plan->last_launches = 0;
+    d.src_mode = 3;
+    d.in_b = d_b;
+    return g_table[idx].inv(d, d_a, d_out, 0, plan->h.rows, cuda_stream, &plan->last_launches);
 }
 
 int ntt_rescale(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, uint64_t* d_work, uint32_t n_polys,

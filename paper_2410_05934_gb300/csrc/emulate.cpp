@@ -117,6 +117,11 @@ static TileArgs emu_args(const PlanDev& p, const uint64_t* in, uint64_t* out, ui
     a.in_b = p.in_b;
     a.aux_q = p.aux_q;
     a.nat = p.nat;
+    a.has_map = p.has_map;
+    for (int i = 0; i < NTT_MUL_MAX_MAPPED; ++i) {
+        a.a_map[i] = p.a_map[i];
+        a.b_map[i] = p.b_map[i];
+    }
     return a;
 }
 
@@ -445,6 +450,7 @@ int nttemu_transform(void* plan, uint32_t sched, int inverse, const uint64_t* in
     d.in_b = nullptr;
     d.aux_q = 0;
     d.nat = 0;
+    d.has_map = 0;
     const EmuFn fn = inverse ? e->inv : e->fwd;
     if (!(p->h.flags & NTT_FLAG_NATURAL_ORDER)) return fn(d, in, out, row_begin, n_rows);
     if (e->kernels == 1) {
@@ -479,6 +485,7 @@ int nttemu_batch_transform(void* plan, int inverse, const uint64_t* in, uint64_t
         d.in_b = nullptr;
         d.aux_q = 0;
         d.nat = 0;
+        d.has_map = 0;
     d.nat = 0;
         return (inverse ? e.inv : e.fwd)(d, in, out, 0, p->h.rows);
     }
@@ -504,6 +511,7 @@ int nttemu_hmul_tensor(void* plan, uint32_t sched, const uint64_t* a, const uint
     d.in_b = b;
     d.aux_q = 0;
     d.nat = 0;
+    d.has_map = 0;
     return e->inv(d, a, out, 0, 3ull * p->h.n_moduli);
 }
 
@@ -601,6 +609,37 @@ int nttemu_pointwise32(void* plan, const uint32_t* x, const uint32_t* y, uint32_
     return NTT_OK;
 }
 
+// ntt_inverse_mul on the host with schedule `sched` (direct-form first kernel)
+int nttemu_inverse_mul(void* plan, uint32_t sched, const uint64_t* a, const uint32_t* a_poly, const uint64_t* b,
+                       const uint32_t* b_poly, uint64_t* out) {
+    EmuPlan* p = static_cast<EmuPlan*>(plan);
+    if (!p || !a || !b || !out) return NTT_ERR_ARG;
+    const EmuEntry* e = emu_find(p->h.log2n, sched);
+    if (!e) return NTT_ERR_ARG;
+    PlanDev d;
+    d.fwd = p->h.fwd.data();
+    d.inv = p->h.inv.data();
+    d.lc = p->h.consts.data();
+    d.status = &p->status;
+    d.n_moduli = p->h.n_moduli;
+    d.check = 0;
+    d.mc = p->h.mc;
+    d.src_mode = 3;
+    d.in_b = b;
+    d.aux_q = 0;
+    d.nat = 0;
+    d.has_map = 0;
+    if (a_poly || b_poly) {
+        if (!a_poly || !b_poly || p->h.batch > NTT_MUL_MAX_MAPPED) return NTT_ERR_ARG;
+        for (uint32_t k = 0; k < p->h.batch; ++k) {
+            d.a_map[k] = (uint8_t)a_poly[k];
+            d.b_map[k] = (uint8_t)b_poly[k];
+        }
+        d.has_map = 1;
+    }
+    return e->inv(d, a, out, 0, p->h.rows);
+}
+
 // ntt_rescale on the host with schedule `sched` for both transforms (its
 // first forward kernel must be in the direct form).
 int nttemu_rescale(void* plan, uint32_t sched, const uint64_t* in, uint64_t* out, uint64_t* work, uint32_t n_polys) {
@@ -626,6 +665,7 @@ int nttemu_rescale(void* plan, uint32_t sched, const uint64_t* in, uint64_t* out
     last.in_b = nullptr;
     last.aux_q = 0;
     last.nat = 0;
+    last.has_map = 0;
     int rc = e->inv(last, work, work, 0, n_polys);
     if (rc) return rc;
     PlanDev d = last;

@@ -205,6 +205,11 @@ int launch_tile_kernel(const PlanDev& p, const uint64_t* in, uint64_t* out, uint
     a.in_b = p.in_b;
     a.aux_q = p.aux_q;
     a.nat = p.nat;
+    a.has_map = p.has_map;
+    for (int i = 0; i < NTT_MUL_MAX_MAPPED; ++i) {
+        a.a_map[i] = p.a_map[i];
+        a.b_map[i] = p.b_map[i];
+    }
     if (C::PIPE && C::FIRST && p.src_mode) return NTT_ERR_UNSUPPORTED;  // direct form only
     const uint64_t groups = (a.n_tiles + C::TPC - 1) / C::TPC;
     if (groups == 0) return NTT_OK;

@@ -16,10 +16,13 @@ struct PlanDev {
     uint32_t check;
     uint32_t mc;        // modulus class: 1 when every modulus is below 2^57
     uint32_t src_mode;  // 1: the inverse's first kernel computes the CKKS tensor product;
-                        // 2: the forward transform is the Rescale by aux_q (TileArgs)
+                        // 2: the forward transform is the Rescale by aux_q (TileArgs);
+                        // 3: the inverse's first kernel multiplies two rows pointwise
     const uint64_t* in_b;
     uint64_t aux_q;
     uint32_t nat;       // natural-order forward output / inverse input (full-row kernels)
+    uint32_t has_map;        // source mode 3: polynomial maps of the two factors
+    uint8_t a_map[NTT_MUL_MAX_MAPPED], b_map[NTT_MUL_MAX_MAPPED];
 };
 
 // Transforms rows [row_begin, row_begin + n_rows) of the layout that starts

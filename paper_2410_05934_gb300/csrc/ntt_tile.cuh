@@ -66,6 +66,10 @@ struct LimbConst {
 // subtraction in the forward transform).
 #define NTT_SMALL_MODULUS_BITS 57
 
+#ifndef NTT_MUL_MAX_MAPPED
+#define NTT_MUL_MAX_MAPPED 32     // polynomials of one ntt_inverse_mul call with index maps
+#endif
+
 struct TileArgs {
     const uint64_t* in;
     uint64_t* out;
@@ -93,6 +97,12 @@ struct TileArgs {
     // natural order (full-row tiles only): the forward's last kernel stores
     // A[brv(j)] at j, the inverse's first kernel takes its input that way
     uint32_t nat;
+    // source mode 3 (first kernel of an inverse) = pointwise product: row
+    // p * n_moduli + l reads row a_map[p] * n_moduli + l of `in` and row
+    // b_map[p] * n_moduli + l of `in_b` (with has_map = 0: polynomial p of
+    // both) and transforms their product mod q_l
+    uint32_t has_map;
+    uint8_t a_map[NTT_MUL_MAX_MAPPED], b_map[NTT_MUL_MAX_MAPPED];
 };
 
 // floor(n / d) for n < 2^32 and 2 <= d < 2^32 from M = ceil(2^64 / d):
@@ -427,6 +437,23 @@ NTT_HD void load_direct(TileRegs<C>& st, const TileArgs& a, const TileLoc& L, in
             const uint64_t m1 = csub(shoup_mul(r1, 1, lc.one_p, lc.q), lc.q);
             st.x[2 * i] = hq >= m0 ? hq - m0 : hq + (lc.q - m0);
             st.x[2 * i + 1] = hq >= m1 ? hq - m1 : hq + (lc.q - m1);
+        }
+        return;
+    }
+    if (C::FIRST && C::INV && a.src_mode == 3) {
+        const LimbConst lc = a.lc[L.limb];
+        const uint64_t pa = a.has_map ? a.a_map[L.rowq] : L.rowq, pb = a.has_map ? a.b_map[L.rowq] : L.rowq;
+        const uint64_t* x = a.in + ((pa * a.n_moduli + L.limb) << C::LOGN) + gt;
+        const uint64_t* y = a.in_b + ((pb * a.n_moduli + L.limb) << C::LOGN) + gt;
+#pragma unroll
+        for (int i = 0; i < C::R / 2; ++i) {
+            const uint32_t off = place<C>(2u * (uint32_t)i * C::T);
+            NTT_GMEM_CHECK(gt + off + 1, 1u << C::LOGN);
+            uint64_t x0, x1, y0, y1;
+            load_pair(x + off, x0, x1);
+            load_pair(y + off, y0, y1);
+            st.x[2 * i] = barrett_mulmod(x0, y0, lc.q, lc.mu, lc.bits);
+            st.x[2 * i + 1] = barrett_mulmod(x1, y1, lc.q, lc.mu, lc.bits);
         }
         return;
     }

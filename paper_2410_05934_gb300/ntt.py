@@ -175,6 +175,20 @@ class Plan:
                                      _ptr(out, 3 * per, "out"), _stream_handle(stream)), "ntt_hmul_tensor")
         return out
 
+    def inverse_mul(self, a, b, out, a_poly=None, b_poly=None, stream=None):
+        """out[p] = INTT(a[a_poly[p]] (.) b[b_poly[p]]) per limb, the product
+        formed inside the inverse's first kernel (ntt_inverse_mul)."""
+        per = self.n_moduli * self.n
+        a_polys = a.numel() // per
+        b_polys = b.numel() // per
+        am = bm = None
+        if a_poly is not None or b_poly is not None:
+            am = (ctypes.c_uint32 * len(a_poly))(*[int(v) for v in a_poly])
+            bm = (ctypes.c_uint32 * len(b_poly))(*[int(v) for v in b_poly])
+        check(load().ntt_inverse_mul(self._h, _ptr(a, what="a"), am, a_polys, _ptr(b, what="b"), bm, b_polys,
+                                     _ptr(out, self.batch * per, "out"), _stream_handle(stream)), "ntt_inverse_mul")
+        return out
+
     def rescale(self, x, out, work, n_polys=0, stream=None):
         """Rescale by the plan's last modulus: x [n_polys][L][N] -> out
         [n_polys][L-1][N], both NTT domain; work [n_polys][N] scratch."""

@@ -33,6 +33,9 @@ def lib():
         L.nttemu_rescale.argtypes = [vp, u32, U64P, U64P, U64P, u32]
         L.nttemu_rescale.restype = i32
         U32P = ctypes.POINTER(ctypes.c_uint32)
+        L.nttemu_inverse_mul.argtypes = [vp, u32, U64P, ctypes.POINTER(ctypes.c_uint32), U64P,
+                                         ctypes.POINTER(ctypes.c_uint32), U64P]
+        L.nttemu_inverse_mul.restype = i32
         L.nttemu_transform32.argtypes = [vp, i32, U32P, U32P, u64, u64]
         L.nttemu_transform32.restype = i32
         L.nttemu_pointwise32.argtypes = [vp, U32P, U32P, U32P, u64]
@@ -98,6 +101,22 @@ class EmuPlan:
         rc = lib().nttemu_tfhe_cmux(self.h, _p(d), rp, _p(key), levels, log2_base, _p(out), d.shape[0])
         if rc:
             raise ValueError("nttemu_tfhe_cmux failed: %d" % rc)
+        return out
+
+    def inverse_mul(self, a, b, sched, a_poly=None, b_poly=None):
+        """ntt_inverse_mul with schedule sched: [batch][n_moduli][N] output."""
+        U32P = ctypes.POINTER(ctypes.c_uint32)
+        a = np.ascontiguousarray(a, dtype=np.uint64)
+        b = np.ascontiguousarray(b, dtype=np.uint64)
+        out = np.zeros((self.rows, self.n), dtype=np.uint64)
+        am = bm = None
+        if a_poly is not None:
+            am = np.ascontiguousarray(a_poly, dtype=np.uint32)
+            bm = np.ascontiguousarray(b_poly, dtype=np.uint32)
+        rc = lib().nttemu_inverse_mul(self.h, sched, _p(a), None if am is None else am.ctypes.data_as(U32P), _p(b),
+                                      None if bm is None else bm.ctypes.data_as(U32P), _p(out))
+        if rc:
+            raise ValueError("nttemu_inverse_mul failed: %d" % rc)
         return out
 
     def rescale(self, x, sched, n_polys):

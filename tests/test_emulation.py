@@ -363,3 +363,34 @@ def test_word32_plan_rules():
         emu.EmuPlan(10, [W.POOL50[0]], 1, flags=8)            # modulus >= 2^30
     with pytest.raises(ValueError):
         emu.EmuPlan(10, Q30[:1], 1, flags=8 | 4)              # natural order
+
+
+@pytest.mark.parametrize("log2n", [4, 10, 13])
+def test_inverse_mul_every_direct_schedule(log2n):
+    """ntt_inverse_mul: the product formed in the inverse's first kernel, with
+    the CKKS cross-product maps, equals INTT of the oracle's pointwise product."""
+    from oracle import oracle as O
+    n, mods = 1 << log2n, [W.POOL50[0], W.POOL50[4]]
+    rng = np.random.default_rng(log2n)
+    A = np.array([rng.integers(0, mods[r % 2], n, dtype=np.uint64) for r in range(8)])   # 4 polys x 2 limbs
+    a_poly, b_poly = [0, 0, 1, 1], [2, 3, 2, 3]
+    rows_a = [a_poly[k // 2] * 2 + k % 2 for k in range(8)]
+    rows_b = [b_poly[k // 2] * 2 + k % 2 for k in range(8)]
+    prod = np.array([O.pointwise(A[ra], A[rb], mods[k % 2]) for k, (ra, rb) in enumerate(zip(rows_a, rows_b))])
+    want = O.transform_rows(prod, [mods[k % 2] for k in range(8)], inverse=True)
+    plan = emu.EmuPlan(log2n, mods, 4)
+    tried = 0
+    for s in range(emu.schedule_count(log2n)):
+        try:
+            got = plan.inverse_mul(A, A, s, a_poly, b_poly)
+        except ValueError:
+            continue                                    # pipelined first kernel
+        tried += 1
+        assert np.array_equal(got, want), s
+    assert tried >= 1
+    # identity maps
+    B = A[::-1].copy()[[6, 7, 4, 5, 2, 3, 0, 1]]
+    got = plan.inverse_mul(A, B, 0)
+    want2 = O.transform_rows(np.array([O.pointwise(A[r], B[r], mods[r % 2]) for r in range(8)]),
+                             [mods[k % 2] for k in range(8)], inverse=True)
+    assert np.array_equal(got, want2)

@@ -127,6 +127,10 @@ def test_ckks_hmul_n65536_workload(oracle):
         for l in (0, 11, 23):
             kk = np.array([0, 1, 4097, n - 1], dtype=np.uint32)
             assert np.array_equal(c[k, l][kk], oracle.schoolbook_at(x[i, l], x[2 + j, l], mods[l], kk))
+    # the same cross products formed inside the inverse's first kernel (the bench's step)
+    fused = torch.empty_like(prods)
+    plan.inverse_mul(A, A, fused, a_poly=[0, 0, 1, 1], b_poly=[2, 3, 2, 3])
+    assert torch.equal(fused, prods)
     back = torch.empty_like(dx)
     plan.inverse(A, back)
     assert torch.equal(back, dx)
@@ -321,6 +325,29 @@ def test_natural_order_plans(oracle, log2n):
     p.inverse(out)                                   # in place
     assert torch.equal(out, d)
     assert p.status() == 0
+
+
+@pytest.mark.parametrize("log2n", [10, 12, 14])
+def test_inverse_mul_every_schedule(oracle, log2n):
+    """ntt_inverse_mul (the product formed in the inverse's first kernel) on
+    every schedule, identity and cross-product maps, against the oracle."""
+    n, mods = 1 << log2n, _moduli(log2n, "small")
+    x = W.rows_uniform(41, log2n, mods * 4, n)              # 4 polys x 2 limbs, NTT domain
+    per = [mods[r % 2] for r in range(8)]
+    rows_a = [p * 2 + l for p in (0, 0, 1, 1) for l in range(2)]
+    rows_b = [p * 2 + l for p in (2, 3, 2, 3) for l in range(2)]
+    idx = _sample_idx(n, 8, 10, log2n)
+    prod = np.array([oracle.pointwise(x[ra], x[rb], per[k]) for k, (ra, rb) in enumerate(zip(rows_a, rows_b))])
+    want = oracle.transform_rows(prod, per, inverse=True, idx=idx)
+    plan = ntt.Plan(log2n, mods, 4)
+    d = to_dev(x)
+    for s in range(ntt.schedule_count(log2n)):
+        plan.schedule = s                           # a pipelined first kernel falls back to a direct one
+        out = torch.empty_like(d)
+        plan.inverse_mul(d, d, out, a_poly=[0, 0, 1, 1], b_poly=[2, 3, 2, 3])
+        assert np.array_equal(to_host(out)[np.arange(8)[:, None], idx], want), s
+    with pytest.raises(ntt.NttError):
+        plan.inverse_mul(d, d, out, a_poly=[0, 0, 1, 4], b_poly=[2, 3, 2, 3])     # index out of range
 
 
 def test_natural_order_plans_reject_fused_operators():
