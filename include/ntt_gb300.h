@@ -428,8 +428,9 @@ int tfhe_cmux_rotate(ntt_plan_t plan, const uint64_t* d_acc, const uint32_t* d_r
  *                   an odd prime < 2^62, distinct within each basis,
  *                   1 <= L, K <= NTT_BCONV_MAX_MODULI
  *   ntt_bconv       d_in [n_polys][L][2^log2n] -> d_out [n_polys][K][2^log2n]
- *                   (device, 8-byte aligned, not overlapping); inputs may be
- *                   any 64-bit values (each x_i is reduced mod q_i on the way)
+ *                   (device, 16-byte aligned, not overlapping; log2n >= 1);
+ *                   inputs may be any 64-bit values (each x_i is reduced mod
+ *                   q_i on the way)
  * Errors: ARG, NOT_PRIME, MODULUS_TOO_LARGE, ALIGN, NOMEM, CUDA.
  */
 #define NTT_BCONV_MAX_MODULI 64

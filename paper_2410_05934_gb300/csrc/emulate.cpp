@@ -695,17 +695,18 @@ int nttemu_bconv(const uint64_t* q_from, uint32_t L, const uint64_t* p_to, uint3
     for (uint64_t poly = 0; poly < n_polys; ++poly)
         for (uint64_t k = 0; k < n; ++k) {
             for (uint32_t i = 0; i < L; ++i) a[i] = bconv_a(v, i, in[(poly * L + i) * n + k]);
-            auto get = [&](uint32_t i) { return a[i]; };
+            auto get = [&](int, uint32_t i) { return a[i]; };
+            auto cij = [&](uint32_t i, uint32_t j) { return w[3 * L + 4 * K + (size_t)i * K + j]; };
             uint32_t j = 0;
             for (; j + 4 <= K; j += 4) {
-                uint64_t y[4];
-                bconv_y<4>(v, j, get, y);
-                for (int u = 0; u < 4; ++u) out[(poly * K + j + u) * n + k] = y[u];
+                uint64_t y[1][4];
+                bconv_y<4, 1>(v, j, get, cij, y);
+                for (int u = 0; u < 4; ++u) out[(poly * K + j + u) * n + k] = y[0][u];
             }
             for (; j < K; ++j) {
-                uint64_t y[1];
-                bconv_y<1>(v, j, get, y);
-                out[(poly * K + j) * n + k] = y[0];
+                uint64_t y[1][1];
+                bconv_y<1, 1>(v, j, get, cij, y);
+                out[(poly * K + j) * n + k] = y[0][0];
             }
         }
     return NTT_OK;

@@ -59,32 +59,42 @@ NTT_HD uint64_t bconv_a(const BconvView& v, uint32_t i, uint64_t x) {
     return csub(shoup_mul(x, bconv_ld(v.qhi + i), bconv_ld(v.qhi_p + i), q), q);
 }
 
-// y_j of one coefficient from its a_i, read through a(i), for the NJ outputs
-// j0 .. j0 + NJ - 1 at once (independent accumulators: NJ-fold ILP, one read
-// of each a_i per NJ outputs)
-template <int NJ, class Get>
-NTT_HD void bconv_y(const BconvView& v, uint32_t j0, Get a, uint64_t (&y)[NJ]) {
-    uint64_t hi[NJ], lo[NJ];
+// y_j of NC coefficients from their a_i, read through a(c, i), for the NJ
+// outputs j0 .. j0 + NJ - 1 at once (independent accumulators: NJ x NC-fold
+// ILP; each constant c_ij, read through cij(i, j), serves NC products)
+template <int NJ, int NC, class GetA, class GetC>
+NTT_HD void bconv_y(const BconvView& v, uint32_t j0, GetA a, GetC cij, uint64_t (&y)[NC][NJ]) {
+    uint64_t hi[NC][NJ], lo[NC][NJ];
 #pragma unroll
-    for (int u = 0; u < NJ; ++u) hi[u] = lo[u] = 0;
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int u = 0; u < NJ; ++u) hi[c][u] = lo[c][u] = 0;
     uint32_t n = 0;
     for (uint32_t i = 0; i < v.L; ++i) {
-        const uint64_t ai = a(i);
-        const uint64_t* ci = v.c + (uint64_t)i * v.K + j0;
+        uint64_t ai[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) ai[c] = a(c, i);
 #pragma unroll
         for (int u = 0; u < NJ; ++u) {
-            const uint64_t cij = bconv_ld(ci + u);
-            const uint64_t pl = ai * cij;
-            lo[u] += pl;
-            hi[u] += mulhi64(ai, cij) + (lo[u] < pl ? 1u : 0u);
+            const uint64_t w = cij(i, j0 + u);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const uint64_t pl = ai[c] * w;
+                lo[c][u] += pl;
+                hi[c][u] += mulhi64(ai[c], w) + (lo[c][u] < pl ? 1u : 0u);
+            }
         }
         if (++n == v.chunk) {      // uniform: only bases whose products approach 2^128 / L fold
 #pragma unroll
             for (int u = 0; u < NJ; ++u) {
                 const uint32_t j = j0 + u;
-                lo[u] = reduce128(hi[u], lo[u], bconv_ld(v.p + j), bconv_ld(v.p_one + j), bconv_ld(v.r64 + j),
-                                  bconv_ld(v.r64_p + j));
-                hi[u] = 0;
+                const uint64_t p = bconv_ld(v.p + j), p_one = bconv_ld(v.p_one + j);
+                const uint64_t r64 = bconv_ld(v.r64 + j), r64_p = bconv_ld(v.r64_p + j);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    lo[c][u] = reduce128(hi[c][u], lo[c][u], p, p_one, r64, r64_p);
+                    hi[c][u] = 0;
+                }
             }
             n = 1;   // the folded value counts as one more term
         }
@@ -92,8 +102,10 @@ NTT_HD void bconv_y(const BconvView& v, uint32_t j0, Get a, uint64_t (&y)[NJ]) {
 #pragma unroll
     for (int u = 0; u < NJ; ++u) {
         const uint32_t j = j0 + u;
-        y[u] = reduce128(hi[u], lo[u], bconv_ld(v.p + j), bconv_ld(v.p_one + j), bconv_ld(v.r64 + j),
-                         bconv_ld(v.r64_p + j));
+        const uint64_t p = bconv_ld(v.p + j), p_one = bconv_ld(v.p_one + j);
+        const uint64_t r64 = bconv_ld(v.r64 + j), r64_p = bconv_ld(v.r64_p + j);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) y[c][u] = reduce128(hi[c][u], lo[c][u], p, p_one, r64, r64_p);
     }
 }
 
