@@ -171,6 +171,24 @@ def oracle_sample(seconds_target, nthreads=None):
     return count / dt, nthreads, desc, dt
 
 
+def radix2_sample():
+    """The second CPU baseline: the whole step's transforms (96 forward + 96
+    inverse rows at N = 2^16) through the plain radix-2 O(N log N) transforms
+    with Shoup twiddles, rows spread over all host cores."""
+    from oracle import oracle as O
+    from paper_2410_05934_gb300 import workloads as W
+    n = 1 << LOG2N
+    nthreads = os.cpu_count() or 1
+    w = W.ckks_hmul_n65536()
+    x = w["x"].reshape(-1, n)
+    O.radix2_rows(x[:nthreads], w["moduli"], nthreads=nthreads)      # tables and pages warm
+    t0 = time.perf_counter()
+    f = O.radix2_rows(x, w["moduli"], nthreads=nthreads)
+    O.radix2_rows(f, w["moduli"], inverse=True, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return 2 * x.size / dt, nthreads, dt
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -452,6 +470,11 @@ def run_ours(args):
         v, cores, desc, dt = oracle_sample(args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": desc, "seconds": dt}
+        v2, cores2, dt2 = radix2_sample()
+        line["cpu_radix2"] = {"value": v2, "unit": UNIT, "cores": cores2,
+                              "kind": "plain radix-2 O(N log N) transforms, Shoup twiddles (oracle/ntt_radix2.c)",
+                              "sample": "the whole step's 96 forward + 96 inverse rows at N=65536 (tables "
+                                        "built inside the timed call)", "seconds": dt2}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -9,6 +9,8 @@ Contents:
   ntt_oracle.c  plain C, O(N^2) definitions of Sec. II-D / Eq. 1 with 128-bit
                 products (forward NTT, inverse NTT, pointwise product,
                 schoolbook negacyclic product, Miller-Rabin, psi).
+  ntt_radix2.c  plain iterative radix-2 transforms, O(N log N): the second,
+                fairer CPU timing baseline (pinned against ntt_oracle.c).
   oracle.py     ctypes binding returning numpy arrays.
   mlp_oracle.py float64 numpy forward/backward of the schedule cost model.
   build.py      compiles ntt_oracle.c with gcc.

@@ -51,6 +51,8 @@ def bind(path):
     L.oracle_transform_rows.argtypes = [i32, U64P, U64P, u32, u32, U64P, U64P, U32P, u32, i32]
     L.oracle_transform_rows_split.restype = i32
     L.oracle_transform_rows_split.argtypes = [i32, U64P, U64P, u32, u32, U64P, U64P, u32, i32]
+    L.oracle_radix2_rows.restype = i32
+    L.oracle_radix2_rows.argtypes = [i32, U64P, U64P, u32, u32, U64P, u32, i32]
     return L
 
 
@@ -193,4 +195,26 @@ def transform_rows(x, q_row, inverse=False, idx=None, nthreads=None, split=False
                                          qp, pp, ip, idx.shape[1], nthreads)
     if rc:
         raise MemoryError("oracle transform failed")
+    return out
+
+
+# ---- the O(N log N) CPU baseline (ntt_radix2.c) -----------------------------
+
+def radix2_rows(x, moduli, inverse=False, nthreads=None):
+    """Rows of x ([rows][N], row r over moduli[r % len(moduli)]) through the
+    plain radix-2 transforms: the same results as transform_rows, in
+    O(N log N) per row.  A timing baseline; parity is checked against the
+    O(N^2) definitions."""
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.uint64))
+    rows, n = x.shape
+    log2n = n.bit_length() - 1
+    moduli = np.ascontiguousarray(np.asarray(moduli, dtype=np.uint64))
+    nthreads = default_threads() if nthreads is None else nthreads
+    out = np.zeros((rows, n), dtype=np.uint64)
+    _, xp = _u64(x)
+    _, mp = _u64(moduli)
+    rc = lib().oracle_radix2_rows(int(inverse), xp, out.ctypes.data_as(U64P), rows, log2n, mp, moduli.size,
+                                  nthreads)
+    if rc:
+        raise ValueError("radix-2 baseline: bad modulus or size")
     return out

@@ -697,18 +697,36 @@ int nttemu_bconv(const uint64_t* q_from, uint32_t L, const uint64_t* p_to, uint3
             for (uint32_t i = 0; i < L; ++i) a[i] = bconv_a(v, i, in[(poly * L + i) * n + k]);
             auto get = [&](int, uint32_t i) { return a[i]; };
             auto cij = [&](uint32_t i, uint32_t j) { return w[3 * L + 4 * K + (size_t)i * K + j]; };
-            uint32_t j = 0;
-            for (; j + 4 <= K; j += 4) {
-                uint64_t y[1][4];
-                bconv_y<4, 1>(v, j, get, cij, y);
-                for (int u = 0; u < 4; ++u) out[(poly * K + j + u) * n + k] = y[0][u];
-            }
-            for (; j < K; ++j) {
-                uint64_t y[1][1];
-                bconv_y<1, 1>(v, j, get, cij, y);
-                out[(poly * K + j) * n + k] = y[0][0];
+            // the kernel's split: warp w of 4 takes outputs [K w / 4, K (w + 1) / 4) in runs of 4, 2, 1
+            for (uint32_t w = 0; w < 4; ++w) {
+                uint32_t j = K * w / 4;
+                const uint32_t j_hi = K * (w + 1) / 4;
+                for (; j + 4 <= j_hi; j += 4) {
+                    uint64_t y[1][4];
+                    bconv_y<4, 1>(v, j, get, cij, y);
+                    for (int u = 0; u < 4; ++u) out[(poly * K + j + u) * n + k] = y[0][u];
+                }
+                for (; j + 2 <= j_hi; j += 2) {
+                    uint64_t y[1][2];
+                    bconv_y<2, 1>(v, j, get, cij, y);
+                    for (int u = 0; u < 2; ++u) out[(poly * K + j + u) * n + k] = y[0][u];
+                }
+                for (; j < j_hi; ++j) {
+                    uint64_t y[1][1];
+                    bconv_y<1, 1>(v, j, get, cij, y);
+                    out[(poly * K + j) * n + k] = y[0][0];
+                }
             }
         }
+    return NTT_OK;
+}
+
+// reduce_65q with the plan's constants of one limb, on n values (x < 65 q)
+int nttemu_reduce_65q(void* plan, uint32_t limb, const uint64_t* x, uint64_t* out, uint64_t n) {
+    EmuPlan* p = static_cast<EmuPlan*>(plan);
+    if (!p || limb >= p->h.n_moduli) return NTT_ERR_ARG;
+    const LimbConst& c = p->h.consts[limb];
+    for (uint64_t i = 0; i < n; ++i) out[i] = reduce_65q(x[i], c.red_m, c.bits, c.q);
     return NTT_OK;
 }
 

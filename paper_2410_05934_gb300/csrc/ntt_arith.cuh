@@ -108,11 +108,22 @@ NTT_HD void gs_butterfly_scaled_small(uint64_t& X, uint64_t& Y, uint64_t ninv, u
     Y = shoup_mul_approx(d, wn, wn_p, q);
 }
 
-// Any x < 2^64 to [0, q): x * 1 in Shoup form (w' = floor(2^64 / q)) lands in
-// [0, 4q), then two conditional subtractions.
-NTT_HD uint64_t reduce_full_small(uint64_t x, uint64_t one_p, uint64_t q, uint64_t two_q) {
-    uint64_t r = shoup_mul_approx(x, 1, one_p, q);
-    return csub(csub(r, two_q), q);
+// x in [0, 65q) to [0, q) for q < 2^57 of bit length k (the forward
+// transform's output bound in modulus class 1).  With sh = max(k - 25, 0),
+// t = floor(x / 2^sh) < 65 * 2^25 < 2^32 and m = floor(2^(32 + sh) / q) < 2^32,
+// the estimate Qe = floor(t m / 2^32) of Q = floor(x / q) is short by less
+// than t / 2^32 + 2^sh / q + 1 < 0.51 + 2^-24 + 1 < 2, so x - Qe q lies in
+// [0, 2q): one conditional subtraction.  Qe <= 65, so Qe q needs only the
+// low 64 bits of a 32 x 64 product.
+NTT_HD uint64_t reduce_65q(uint64_t x, uint32_t m, uint32_t k, uint64_t q) {
+    const uint32_t sh = k > 25 ? k - 25 : 0;
+    const uint32_t t = (uint32_t)(x >> sh);
+#if defined(__CUDA_ARCH__)
+    const uint32_t qe = __umulhi(t, m);
+#else
+    const uint32_t qe = (uint32_t)(((uint64_t)t * m) >> 32);
+#endif
+    return csub(x - (uint64_t)qe * q, q);
 }
 
 // Last GS stage with the N^-1 scaling folded in:

@@ -64,7 +64,46 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
         : "memory");
 }
 
-template <class C, int I>
+template <int ID, int COUNT>
+__device__ __forceinline__ void named_barrier() {
+    asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(COUNT) : "memory");
+}
+
+// barrier 1 + tin for tile slots 0 .. TILES - 1 (literal ids, so a CTA
+// reserves only the barriers it uses)
+template <int COUNT, int TILES, int K = 0>
+__device__ __forceinline__ void tile_barrier(int tin) {
+    if constexpr (K + 1 < TILES) {
+        if (tin == K) {
+            named_barrier<1 + K, COUNT>();
+            return;
+        }
+        tile_barrier<COUNT, TILES, K + 1>(tin);
+    } else {
+        named_barrier<1 + K, COUNT>();
+    }
+}
+
+// Orders one tile's shared-memory words between passes.  The passes of a
+// tile read and write only that tile's words (staged twiddles are written
+// before the CTA-wide barrier that precedes the first pass and are read-only
+// afterwards), so only the tile's own threads synchronise: a tile of at most
+// one warp with __syncwarp, a wider tile on a named barrier of its own
+// (ids 1..TILES; id 0 is __syncthreads).  TILES is the number of tiles side
+// by side in the CTA: C::TPC, or 2 in the CMux kernel, whose two slots each
+// run a one-tile config.
+template <class C, int TILES = C::TPC>
+__device__ __forceinline__ void tile_sync() {
+    if constexpr (TILES == 1 || TILES > 8) {
+        __syncthreads();
+    } else if constexpr (C::T <= 32) {
+        __syncwarp();
+    } else {
+        tile_barrier<C::T, TILES>((int)threadIdx.x >> C::LOGT);
+    }
+}
+
+template <class C, int I, int TILES = C::TPC>
 __device__ __forceinline__ void run_passes(TileRegs<C>& st, const TileArgs& a, const TileLoc& L, int t,
                                            uint64_t* sm) {
     if constexpr (I < C::NPASS) {
@@ -72,8 +111,8 @@ __device__ __forceinline__ void run_passes(TileRegs<C>& st, const TileArgs& a, c
         pass_read<C, P>(st, L, t, sm);
         pass_compute<C, P>(st, a, L, t, sm);
         pass_write<C, P>(st, L, t, sm);
-        __syncthreads();
-        run_passes<C, I + 1>(st, a, L, t, sm);
+        tile_sync<C, TILES>();
+        run_passes<C, I + 1, TILES>(st, a, L, t, sm);
     }
 }
 
@@ -214,17 +253,20 @@ int launch_tile_kernel(const PlanDev& p, const uint64_t* in, uint64_t* out, uint
     const uint64_t groups = (a.n_tiles + C::TPC - 1) / C::TPC;
     if (groups == 0) return NTT_OK;
     if (groups > 0x7fffffffull) return NTT_ERR_ARG;
-    if (C::SMEM_BYTES > 48 * 1024) {
-        cudaError_t e = C::PIPE
-            ? cudaFuncSetAttribute(k_ntt_tile_pipe<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_BYTES)
-            : cudaFuncSetAttribute(k_ntt_tile<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_BYTES);
-        if (e != cudaSuccess) return NTT_ERR_CUDA;
-    }
-    if (C::PIPE) {
+    // only the kernel of the config's form is instantiated
+    if constexpr (C::PIPE) {
+        if (C::SMEM_BYTES > 48 * 1024 &&
+            cudaFuncSetAttribute(k_ntt_tile_pipe<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)C::SMEM_BYTES) != cudaSuccess)
+            return NTT_ERR_CUDA;
         uint64_t grid = (uint64_t)resident_ctas_per_sm<C>();
         if (grid > groups) grid = groups;
         k_ntt_tile_pipe<C><<<(unsigned)grid, C::THREADS, C::SMEM_BYTES, st>>>(a, groups);
     } else {
+        if (C::SMEM_BYTES > 48 * 1024 &&
+            cudaFuncSetAttribute(k_ntt_tile<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_BYTES) !=
+                cudaSuccess)
+            return NTT_ERR_CUDA;
         k_ntt_tile<C><<<(unsigned)groups, C::THREADS, C::SMEM_BYTES, st>>>(a);
     }
     return cudaPeekAtLastError() == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;

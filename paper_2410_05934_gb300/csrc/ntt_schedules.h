@@ -62,7 +62,12 @@
     S2(16, 8, 4, 8, 4, 1, 5, 3, 4, 0) S2(16, 7, 4, 7, 4, 1, 6, 3, 2, 2)           \
     S2(16, 8, 4, 8, 4, 1, 5, 3, 8, 0) S2(16, 8, 4, 8, 4, 1, 5, 3, 2, 0)           \
     S2(16, 8, 4, 8, 4, 1, 6, 2, 2, 0) S2(16, 7, 4, 7, 4, 1, 6, 3, 2, 8)           \
-    S2(16, 7, 4, 7, 4, 1, 6, 3, 2, 0) S2(16, 8, 4, 8, 4, 1, 5, 3, 4, 2)
+    S2(16, 7, 4, 7, 4, 1, 6, 3, 2, 0) S2(16, 8, 4, 8, 4, 1, 5, 3, 4, 2)           \
+    S2(16, 7, 4, 7, 4, 1, 5, 3, 4, 8) S2(16, 7, 4, 7, 4, 1, 5, 4, 4, 8)           \
+    S2(16, 8, 4, 8, 4, 1, 4, 4, 8, 8) S2(16, 8, 4, 8, 4, 1, 4, 4, 8, 0)           \
+    S2(16, 7, 4, 7, 4, 1, 4, 5, 8, 8) S2(16, 7, 4, 7, 4, 1, 5, 3, 8, 8)           \
+    S2(16, 7, 4, 7, 4, 1, 5, 3, 2, 8) S2(16, 7, 4, 7, 4, 1, 5, 3, 4, 0)           \
+    S2(16, 7, 3, 6, 4, 2, 5, 3, 4, 8)
 
 #define NTT_SCHEDULES_ALL(S1, S2)                                           \
     NTT_SCHEDULES_SMALL(S1, S2) NTT_SCHEDULES_MID(S1, S2) NTT_SCHEDULES_LARGE(S1, S2) \

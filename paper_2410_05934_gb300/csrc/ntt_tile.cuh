@@ -58,7 +58,8 @@ struct LimbConst {
     uint64_t w1ninv, w1ninv_p;  // psi^{-brv(1)} N^-1 and its Shoup form (last GS stage)
     uint64_t mu;                // Barrett constant floor(2^(2 bits) / q)
     uint64_t rs_inv, rs_inv_p;  // q_last^-1 mod q and its Shoup form (Rescale; 0 for the last limb)
-    uint32_t bits, pad_;
+    uint32_t bits;              // bit length of q
+    uint32_t red_m;             // floor(2^(32 + red_sh) / q), red_sh = max(bits - 25, 0): reduce_65q
 };
 
 // Modulus classes: 0 = any q < 2^62 (exact Shoup quotient, Harvey bounds),
@@ -691,7 +692,6 @@ NTT_HD void store_tile(const TileArgs& a, const TileLoc& L, int t, const uint64_
     const uint32_t gt = L.gbase | place<C>(2u * (uint32_t)t);
     uint64_t* dst = a.out + (L.row << C::LOGN) + gt;
     const uint64_t q = a.lc[L.limb].q, two_q = a.lc[L.limb].two_q;
-    const uint64_t one_p = a.lc[L.limb].one_p;
     const uint32_t b = swz(2u * (uint32_t)t);
     const bool nat = C::LAST && !C::INV && C::A == C::LOGN && a.nat;
 #pragma unroll
@@ -711,8 +711,9 @@ NTT_HD void store_tile(const TileArgs& a, const TileLoc& L, int t, const uint64_
         }
         if (C::LAST) {
             if (C::MC == 1 && !C::INV) {  // [0, 65q) -> [0, q)
-                x = reduce_full_small(x, one_p, q, two_q);
-                y = reduce_full_small(y, one_p, q, two_q);
+                const LimbConst& lc = a.lc[L.limb];
+                x = reduce_65q(x, lc.red_m, lc.bits, q);
+                y = reduce_65q(y, lc.red_m, lc.bits, q);
             } else if (C::MC == 1 || !C::INV) {  // [0, 4q) -> [0, q)
                 x = csub(csub(x, two_q), q);
                 y = csub(csub(y, two_q), q);

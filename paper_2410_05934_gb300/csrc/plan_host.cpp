@@ -203,6 +203,10 @@ int build_plan_host(PlanHost& h, uint32_t log2n, const uint64_t* moduli, uint32_
         c.w1ninv_p = shoup_of(c.w1ninv, q);
         c.bits = bit_length(q);
         c.mu = (uint64_t)(((u128)1 << (2 * c.bits)) / q);
+        {
+            const uint32_t sh = c.bits > 25 ? c.bits - 25 : 0;
+            c.red_m = (uint32_t)(((u128)1 << (32 + sh)) / q);
+        }
         if (l + 1 < n_moduli) {      // Rescale drops the last modulus: its inverse mod q
             const uint64_t ql = moduli[n_moduli - 1] % q;
             c.rs_inv = ql ? pow_mod(ql, q - 2, q) : 0;

@@ -1,6 +1,7 @@
 // C ABI of the RNS basis conversion (declared in include/ntt_gb300.h): the
-// plan precomputes the CRT constants on the host, the kernel converts one
-// coefficient per thread (rns.cuh).
+// plan precomputes the CRT constants on the host, the kernel splits each
+// coefficient's conversion over the warps of a CTA (rns.cuh holds the
+// arithmetic).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -20,51 +21,68 @@ struct ntt_bconv_s {
 
 namespace nttgb {
 
-// Each thread converts NTT_BCONV_NC adjacent coefficients (16-byte loads and
-// stores); its a_i live in shared memory, the L x K constants c_ij too (read
-// by the whole warp at one address: a broadcast).
-#define NTT_BCONV_THREADS 128
+// A CTA step converts 64 adjacent coefficients (32 lanes x NTT_BCONV_NC,
+// 16-byte loads and stores) with 4 warps: warp w first computes the a_i of
+// its quarter of the input limbs i into shared memory, then, after a barrier,
+// the outputs j of its quarter of the output limbs from all a_i.  Every a_i is
+// computed once, and the shared footprint (a_i of 64 coefficients plus the
+// L x K constants c_ij, read at one address by the whole warp) stays small
+// enough for ~7 CTAs per SM.
+#define NTT_BCONV_WARPS 4
+#define NTT_BCONV_THREADS (32 * NTT_BCONV_WARPS)
 #define NTT_BCONV_NC 2
+#define NTT_BCONV_CPS (32 * NTT_BCONV_NC)      // coefficients per CTA step
 
 static size_t bconv_smem_bytes(uint32_t L, uint32_t K) {
-    return sizeof(uint64_t) * ((size_t)L * NTT_BCONV_NC * NTT_BCONV_THREADS + (size_t)L * K);
+    return sizeof(uint64_t) * ((size_t)L * NTT_BCONV_CPS + (size_t)L * K);
+}
+
+// outputs j0 .. j0 + NJ - 1 of one lane's NC coefficients
+template <int NJ, class GetA, class GetC>
+__device__ __forceinline__ void bconv_store(const BconvView& v, uint32_t j0, GetA a, GetC cij, uint64_t* dst,
+                                            uint32_t log2n) {
+    uint64_t y[NTT_BCONV_NC][NJ];
+    bconv_y<NJ, NTT_BCONV_NC>(v, j0, a, cij, y);
+#pragma unroll
+    for (int u = 0; u < NJ; ++u)
+        *reinterpret_cast<ulonglong2*>(dst + ((uint64_t)(j0 + u) << log2n)) = make_ulonglong2(y[0][u], y[1][u]);
 }
 
 __global__ void __launch_bounds__(NTT_BCONV_THREADS) k_bconv(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
                                                             const uint64_t* __restrict__ cst, uint32_t L, uint32_t K,
                                                             uint32_t chunk, uint32_t log2n, uint64_t total) {
-    extern __shared__ __align__(16) uint64_t sa[];   // [L][NC][THREADS] a_i, then [L][K] c_ij
-    uint64_t* sc = sa + (size_t)L * NTT_BCONV_NC * NTT_BCONV_THREADS;
+    extern __shared__ __align__(16) uint64_t sa[];   // [L][NC][32] a_i, then [L][K] c_ij
+    uint64_t* sc = sa + (size_t)L * NTT_BCONV_CPS;
     const BconvView v = bconv_view(cst, L, K, chunk);
     for (uint32_t e = threadIdx.x; e < L * K; e += NTT_BCONV_THREADS) sc[e] = bconv_ld(v.c + e);
-    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    const uint32_t i_lo = L * w / NTT_BCONV_WARPS, i_hi = L * (w + 1) / NTT_BCONV_WARPS;
+    const uint32_t j_lo = K * w / NTT_BCONV_WARPS, j_hi = K * (w + 1) / NTT_BCONV_WARPS;
     const uint64_t mask = (1ull << log2n) - 1;
-    const uint64_t groups = total / NTT_BCONV_NC;        // coefficient pairs (N >= 2)
-    for (uint64_t g = (uint64_t)blockIdx.x * NTT_BCONV_THREADS + threadIdx.x; g < groups;
-         g += (uint64_t)gridDim.x * NTT_BCONV_THREADS) {
-        const uint64_t idx = g * NTT_BCONV_NC;
+    const uint64_t steps = (total + NTT_BCONV_CPS - 1) / NTT_BCONV_CPS;
+    auto a = [&](int c, uint32_t i) { return sa[((size_t)i * NTT_BCONV_NC + c) * 32 + lane]; };
+    auto cij = [&](uint32_t i, uint32_t j) { return sc[(size_t)i * K + j]; };
+    for (uint64_t s = blockIdx.x; s < steps; s += gridDim.x) {
+        // a pair never straddles two polynomials (N even), and total is even
+        const uint64_t idx = s * NTT_BCONV_CPS + 2u * lane;
+        const bool valid = idx < total;
         const uint64_t poly = idx >> log2n, k = idx & mask;
-        const uint64_t* src = in + ((poly * L) << log2n) + k;
-        for (uint32_t i = 0; i < L; ++i) {
-            const ulonglong2 x = *reinterpret_cast<const ulonglong2*>(src + ((uint64_t)i << log2n));
-            sa[((size_t)i * NTT_BCONV_NC + 0) * NTT_BCONV_THREADS + threadIdx.x] = bconv_a(v, i, x.x);
-            sa[((size_t)i * NTT_BCONV_NC + 1) * NTT_BCONV_THREADS + threadIdx.x] = bconv_a(v, i, x.y);
+        __syncthreads();    // constants staged / the previous step's a_i consumed
+        if (valid) {
+            const uint64_t* src = in + ((poly * L) << log2n) + k;
+            for (uint32_t i = i_lo; i < i_hi; ++i) {
+                const ulonglong2 x = *reinterpret_cast<const ulonglong2*>(src + ((uint64_t)i << log2n));
+                sa[((size_t)i * NTT_BCONV_NC + 0) * 32 + lane] = bconv_a(v, i, x.x);
+                sa[((size_t)i * NTT_BCONV_NC + 1) * 32 + lane] = bconv_a(v, i, x.y);
+            }
         }
-        uint64_t* dst = out + ((poly * K) << log2n) + k;
-        auto a = [&](int c, uint32_t i) { return sa[((size_t)i * NTT_BCONV_NC + c) * NTT_BCONV_THREADS + threadIdx.x]; };
-        auto cij = [&](uint32_t i, uint32_t j) { return sc[(size_t)i * K + j]; };
-        uint32_t j = 0;
-        for (; j + 4 <= K; j += 4) {
-            uint64_t y[NTT_BCONV_NC][4];
-            bconv_y<4, NTT_BCONV_NC>(v, j, a, cij, y);
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                *reinterpret_cast<ulonglong2*>(dst + ((uint64_t)(j + u) << log2n)) = make_ulonglong2(y[0][u], y[1][u]);
-        }
-        for (; j < K; ++j) {
-            uint64_t y[NTT_BCONV_NC][1];
-            bconv_y<1, NTT_BCONV_NC>(v, j, a, cij, y);
-            *reinterpret_cast<ulonglong2*>(dst + ((uint64_t)j << log2n)) = make_ulonglong2(y[0][0], y[1][0]);
+        __syncthreads();
+        if (valid) {
+            uint64_t* dst = out + ((poly * K) << log2n) + k;
+            uint32_t j = j_lo;
+            for (; j + 4 <= j_hi; j += 4) bconv_store<4>(v, j, a, cij, dst, log2n);
+            for (; j + 2 <= j_hi; j += 2) bconv_store<2>(v, j, a, cij, dst, log2n);
+            for (; j < j_hi; ++j) bconv_store<1>(v, j, a, cij, dst, log2n);
         }
     }
 }
@@ -127,8 +145,13 @@ int ntt_bconv(ntt_bconv_t b, const uint64_t* d_in, uint64_t* d_out, uint32_t log
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return NTT_ERR_CUDA;
     const size_t smem = bconv_smem_bytes(b->L, b->K);
-    const uint64_t blocks = (total / NTT_BCONV_NC + NTT_BCONV_THREADS - 1) / NTT_BCONV_THREADS;
-    const unsigned grid = (unsigned)std::min<uint64_t>(blocks, (uint64_t)std::max(1, sms) * 64u);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bconv, NTT_BCONV_THREADS, smem) != cudaSuccess)
+        return NTT_ERR_CUDA;
+    // one wave of persistent CTAs, each walking steps blockIdx.x, + grid, ...
+    const uint64_t steps = (total + NTT_BCONV_CPS - 1) / NTT_BCONV_CPS;
+    const uint64_t wave = (uint64_t)std::max(1, sms) * (uint64_t)std::max(1, per_sm);
+    const unsigned grid = (unsigned)std::min<uint64_t>(steps, wave);
     k_bconv<<<grid, NTT_BCONV_THREADS, smem, (cudaStream_t)cuda_stream>>>(d_in, d_out, b->d_const, b->L, b->K,
                                                                          b->chunk, log2n, total);
     return cudaPeekAtLastError() == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;

@@ -33,22 +33,24 @@ __global__ void __launch_bounds__(CmuxCfg<LOGN, MC>::THREADS, CmuxCfg<LOGN, MC>:
     for (uint64_t ct = blockIdx.x; ct < c.n_ct; ct += gridDim.x) {
         CmuxRegs<K> cr;
         cmux_load<K>(cr, c, ct, s, t, smem);
+        // the two slots touch only their own row and partial sums until the
+        // exchange, so they synchronise separately (a named barrier each)
         for (uint32_t j = 0; j < c.levels; ++j) {
             TileRegs<F> st;
             cmux_digits<K>(st, cr, j, c);
             write_pairs_swizzled<F>(st, L, t, sm);
-            __syncthreads();
-            run_passes<F, 0>(st, af, L, t, sm);
+            tile_sync<F, 2>();
+            run_passes<F, 0, 2>(st, af, L, t, sm);
             cmux_mac<K>(c, lc, (uint32_t)s * c.levels + j, s, t, smem);
         }
-        __syncthreads();
+        __syncthreads();    // exchange: each slot reads both slots' partial sums
         TileRegs<I> si;
         cmux_inverse_input<K>(si, lc, s, t, smem);
         write_pairs_swizzled<I>(si, L, t, sm);
-        __syncthreads();
-        run_passes<I, 0>(si, ai, L, t, sm);
+        tile_sync<I, 2>();
+        run_passes<I, 0, 2>(si, ai, L, t, sm);
         cmux_store<K>(c, lc, ct, s, t, sm);
-        __syncthreads();
+        __syncthreads();    // partial sums read by the other slot before they are cleared
     }
 }
 

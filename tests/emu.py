@@ -40,6 +40,8 @@ def lib():
         L.nttemu_transform32.restype = i32
         L.nttemu_pointwise32.argtypes = [vp, U32P, U32P, U32P, u64]
         L.nttemu_pointwise32.restype = i32
+        L.nttemu_reduce_65q.argtypes = [vp, u32, U64P, U64P, u64]
+        L.nttemu_reduce_65q.restype = i32
         _lib = L
     return _lib
 
@@ -159,6 +161,14 @@ class EmuPlan:
         c = np.zeros_like(a)
         lib().nttemu_pointwise(self.h, _p(a), _p(b), _p(c), self.rows if n_rows is None else n_rows)
         return c
+
+    def reduce_65q(self, limb, x):
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.uint64))
+        out = np.zeros_like(x)
+        rc = lib().nttemu_reduce_65q(self.h, limb, _p(x), _p(out), x.size)
+        if rc:
+            raise ValueError("nttemu_reduce_65q failed: %d" % rc)
+        return out
 
     def status(self):
         return lib().nttemu_status(self.h)

@@ -251,6 +251,22 @@ def test_bconv_matches_oracle(L, K):
         assert np.array_equal(got[p], RO.bconv(x[p], Q, P))
 
 
+def test_bconv_largest_bases():
+    """64 -> 64 limbs: every output run length of the kernel's 4-warp split."""
+    from oracle import rns_oracle as RO
+    from oracle import oracle as O
+    qs, c = [], (1 << 50) - 1
+    while len(qs) < 128:
+        if O.is_prime(c):
+            qs.append(c)
+        c -= 2
+    rng = np.random.default_rng(9)
+    for L, K in [(64, 64), (7, 6), (1, 1)]:
+        Q, P = qs[:L], qs[64:64 + K]
+        x = np.array([[rng.integers(0, q, 4, dtype=np.uint64) for q in Q]])
+        assert np.array_equal(emu.bconv(x, Q, P)[0], RO.bconv(x[0], Q, P)), (L, K)
+
+
 def test_bconv_62_bit_moduli_fold_the_accumulator():
     """62-bit primes on both sides: chunk = 16 terms, so 40 source limbs fold twice."""
     from oracle import rns_oracle as RO
@@ -394,3 +410,31 @@ def test_inverse_mul_every_direct_schedule(log2n):
     want2 = O.transform_rows(np.array([O.pointwise(A[r], B[r], mods[r % 2]) for r in range(8)]),
                              [mods[k % 2] for k in range(8)], inverse=True)
     assert np.array_equal(got, want2)
+
+
+def test_forward_output_reduction_bounds():
+    """The forward transform's last step in the small-modulus class maps
+    x in [0, 65q) to x mod q with one estimated quotient and one conditional
+    subtraction (reduce_65q): checked against x mod q for primes of every bit
+    length 3..57 on the values where the estimate is tightest (multiples of q
+    and their neighbours, 65q - 1, powers of two) and on random values."""
+    from oracle import oracle as O
+    rng = np.random.default_rng(65)
+    qs = []
+    for bits in range(3, 58):
+        q = (1 << bits) - 3
+        while q > (1 << (bits - 1)) and not (q % 4 == 1 and O.is_prime(q)):
+            q -= 2
+        if q > (1 << (bits - 1)):
+            qs.append(q)
+        qs.append(next(c for c in range((1 << (bits - 1)) + 1, 1 << bits, 4) if O.is_prime(c)))
+    for q in qs:
+        plan = emu.EmuPlan(1, [q], 1)
+        top = 65 * q
+        edges = [0, 1, q - 1, q, q + 1, top - 1, top - q, top - q - 1]
+        edges += [k * q + d for k in range(1, 65) for d in (-1, 0, 1)]
+        edges += [1 << b for b in range(64) if (1 << b) < top]
+        edges += [(1 << b) - 1 for b in range(1, 64) if (1 << b) - 1 < top]
+        x = np.array(edges + [int(v) for v in rng.integers(0, top, 2000, dtype=np.uint64)], dtype=np.uint64)
+        want = np.array([int(v) % q for v in x], dtype=np.uint64)
+        assert np.array_equal(plan.reduce_65q(0, x), want), q

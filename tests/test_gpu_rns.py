@@ -44,6 +44,31 @@ def test_full_rows_small(log2n, L, K):
         assert np.array_equal(got[p], RO.bconv(x[p], Q, P))
 
 
+def _primes_below(top, count):
+    from oracle import oracle as O
+    qs, c = [], top - 1
+    while len(qs) < count:
+        if O.is_prime(c):
+            qs.append(c)
+        c -= 2
+    return qs
+
+
+def test_largest_bases_many_steps():
+    """64 -> 64 limbs (the largest bases, 64 KiB of shared memory per CTA) over
+    more 64-coefficient steps than one wave of CTAs, with a ragged last step."""
+    qs = _primes_below(1 << 50, 128)
+    Q, P = qs[:64], qs[64:]
+    log2n, polys = 5, 2051                      # 65632 coefficients: 1025.5 steps
+    rng = np.random.default_rng(64)
+    x = np.stack([np.array([rng.integers(0, q, 1 << log2n, dtype=np.uint64) for q in Q]) for _ in range(polys)])
+    out = torch.empty((polys, 64, 1 << log2n), dtype=torch.int64, device="cuda")
+    ntt.BConv(Q, P)(to_dev(x), out, log2n)
+    got = to_host(out)
+    for p in [0, 1, 1000, polys - 2, polys - 1]:
+        assert np.array_equal(got[p], RO.bconv(x[p], Q, P)), p
+
+
 def test_62_bit_bases_and_noncanonical_inputs():
     from oracle import oracle as O
     qs, c = [], (1 << 62) - 1

@@ -46,7 +46,7 @@ PINS = [
 
 @pytest.fixture(scope="module")
 def mutant_libs(tmp_path_factory):
-    src = open(obuild.SRC).read()
+    src = open(obuild.SRCS[0]).read()          # ntt_oracle.c; the radix-2 file is linked unchanged
     d = tmp_path_factory.mktemp("mutants")
     libs = {}
     for name, (old, new) in MUTANTS.items():
@@ -55,7 +55,8 @@ def mutant_libs(tmp_path_factory):
         with open(path, "w") as f:
             f.write(src.replace(old, new))
         so = os.path.join(d, name + ".so")
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", "-o", so, path])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", "-o", so, path,
+                               obuild.SRCS[1]])
         libs[name] = so
     return libs
 
