@@ -51,7 +51,7 @@ def parse():
                     help="mixed batches: requests of at least 2^k coefficients run their own learned schedule")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "mixed_batch", "tfhe_blind_rotation", "plain_n1024", "cost_model",
-                             "serving", "hmul_fused", "mixed_small", "tfhe_cmux", "ckks_bconv",
+                             "serving", "hmul_fused", "mixed_small", "tfhe_cmux", "ckks_bconv", "otf_twiddles",
                              "ckks_rescale", "natural_order", "word32"],
                     help="the line the driver records is the default (CKKS-HMUL-shaped) workload")
     return ap.parse_args()
@@ -981,6 +981,67 @@ def run_natural_order(args):
     return 0
 
 
+def run_otf_twiddles(args):
+    """Forward + inverse NTT of the CKKS-HMUL-shaped batch (96 rows at
+    N = 2^16) with on-the-fly twiddles (NTT_FLAG_OTF_TWIDDLES: every twiddle
+    the product of two entries of 512-pair per-limb tables), beside the same
+    transforms with the stored N-entry tables and the same kernel geometry;
+    L2 flushed before every step."""
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2410_05934_gb300 import build as B
+    B.build_product()
+    import paper_2410_05934_gb300 as ntt
+    from paper_2410_05934_gb300 import _native
+    from paper_2410_05934_gb300 import workloads as W
+    L_ = _native.load()
+    stream = torch.cuda.current_stream()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    w = W.ckks_hmul_n65536(seed=W.DEFAULT_SEED + rank)
+    x = to_dev_np(torch, w["x"])
+    y = torch.empty_like(x)
+    otf = ntt.Plan(16, w["moduli"], 4, flags=ntt.NTT_FLAG_OTF_TWIDDLES)
+    tab = ntt.Plan(16, w["moduli"], 4)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    def step(p):
+        p.forward(x, y)
+        n1 = p.last_launches()
+        p.inverse(y, y)
+        return n1 + p.last_launches()
+    for _ in range(max(3, args.warmup)):
+        step(otf)
+        step(tab)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, launches = _events_loop(torch, stream, args.steps, lambda: step(otf), flush)
+    clk = clocks.stop()
+    ms_t, _ = _events_loop(torch, stream, args.steps, lambda: step(tab), flush)
+    peak = _probe(torch, L_, w["moduli"][0], 2, sms, stream)
+    t = sum(ms) * 1e-3
+    coef = 2 * 96 * 65536 * args.steps
+    bfly = 2 * 96 * 32768 * 16 * args.steps
+    otf_entries = 2 ** 8 + 2 ** 8
+    line = {"metric": "NTT coeffs/s (coefficient-transforms per second)", "value": coef / t, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "gpu_launches": launches, "clocks": clk,
+            "config": {"workload": "otf_twiddles", "log2n": 16, "rows": 96,
+                       "step": "forward + inverse, 96 rows, twiddles generated on the fly",
+                       "l2": "flushed before every step (512 MiB write, outside the step events)"},
+            "roofline": {"bound": "alu", "achieved": bfly / t / 1e9, "peak": peak / 1e9, "unit": "Gbutterfly/s",
+                         "frac": bfly / t / peak, "traffic": None,
+                         "peak_source": "in-run butterfly probe (kind 2, small-modulus class)"},
+            "twiddle_bytes_per_transform": {"otf": 24 * otf_entries * 16, "tables": 24 * 65536 * 16},
+            "stored_tables": {"ms_per_step": sum(ms_t) / args.steps, "value": coef / (sum(ms_t) * 1e-3)},
+            "overhead": sum(ms) / sum(ms_t) - 1.0}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def run_word32(args):
     """The TFHE blind-rotation-shaped batch (3780 forward + 1260 inverse rows
     at N = 1024) with a 30-bit prime on 32-bit words (NTT_FLAG_WORD32),
@@ -1061,7 +1122,7 @@ def run_cost_model(args):
             "warmup": 0, "ms_per_step": 1e3 * rep["train"]["train_seconds"] / rep["train"]["train_steps"],
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "autotuner timings measured on GB300 (%d)" % rep["timings"],
-            "config": {"workload": "cost_model", "mlp": "4-64-64-8 ReLU, FP32, Adam, cosine lr",
+            "config": {"workload": "cost_model", "mlp": "4-64-64-12 ReLU, FP32, Adam, cosine lr",
                        "train_shapes": rep["train"]["train_shapes"], "heldout_shapes": rep["mlp"]["n"]},
             "regret": {"mlp": rep["mlp"], "sm_rule": rep["sm_rule"], "default": rep["default"]},
             "decision_us": rep["decision_us"], "train_seconds_gpu": rep["train"]["train_seconds"]}
@@ -1111,6 +1172,8 @@ def main():
         return run_serving(args)
     if args.workload == "tfhe_cmux":
         return run_tfhe_cmux(args)
+    if args.workload == "otf_twiddles":
+        return run_otf_twiddles(args)
     if args.workload == "ckks_bconv":
         return run_ckks_bconv(args)
     if args.workload == "ckks_rescale":

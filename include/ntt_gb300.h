@@ -66,6 +66,17 @@ extern "C" {
                                    poly_mul_pointwise read and write uint32
                                    coefficients (same layout); the fused
                                    operators and natural order are not offered */
+#define NTT_FLAG_OTF_TWIDDLES 16u /* on-the-fly twiddles (N >= 2^10): ntt_forward /
+                                   ntt_inverse(_rows) form each twiddle
+                                   psi^(+-brv(k)) as the product of two entries of
+                                   per-limb tables of 2^ceil(n/2) + 2^floor(n/2)
+                                   pairs (n = log2 N) instead of reading an
+                                   N-entry table: one more Shoup product per
+                                   butterfly, ~1/128 of the twiddle bytes at
+                                   N = 2^16.  Same results bit for bit; the fused
+                                   operators keep the stored tables; not with
+                                   NTT_FLAG_NATURAL_ORDER or NTT_FLAG_WORD32 */
+#define NTT_OTF_MIN_LOG2N 10
 #define NTT_WORD32_MAX_LOG2N 12
 #define NTT_WORD32_MAX_MODULUS_BITS 30
 
@@ -319,7 +330,7 @@ int ntt_batch_info(ntt_batch_t batch, uint64_t* items, uint32_t* last_launches, 
  */
 #define NTT_MLP_IN 4
 #define NTT_MLP_HIDDEN 64
-#define NTT_MLP_OUT 8
+#define NTT_MLP_OUT 12
 #define NTT_MLP_PARAMS (NTT_MLP_HIDDEN * NTT_MLP_IN + NTT_MLP_HIDDEN + NTT_MLP_HIDDEN * NTT_MLP_HIDDEN + \
                         NTT_MLP_HIDDEN + NTT_MLP_OUT * NTT_MLP_HIDDEN + NTT_MLP_OUT)
 #define NTT_MLP_ACTS (2 * NTT_MLP_HIDDEN + NTT_MLP_OUT)

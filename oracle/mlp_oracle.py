@@ -9,7 +9,7 @@ tests/test_costmodel.py by central finite differences in float64.
 """
 import numpy as np
 
-IN, H, OUT = 4, 64, 8
+IN, H, OUT = 4, 64, 12
 
 
 def unpack(p):

@@ -30,6 +30,7 @@ CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-Wall", "-Wno-unused-function",
              "-I", INCLUDE, "-I", CSRC]
 
 PRODUCT_SOURCES = ["capi.cu", "kernels_small.cu", "kernels_mid.cu", "kernels_large.cu", "kernels_huge.cu",
+                   "kernels_otf.cu",
                    "kernels_misc.cu", "batch.cu", "costmodel.cu", "tfhe.cu", "rns.cu", "ntt32.cu", "plan_host.cpp"]
 EMU_SOURCES = ["plan_host.cpp", "emulate.cpp"]
 
@@ -56,7 +57,8 @@ def _stamp(kind, flags):
 
 
 TILE_KERNEL_SOURCES = ["ntt_arith.cuh", "ntt_tile.cuh", "ntt_kernels.cuh", "ntt_schedules.h",
-                       "kernels_small.cu", "kernels_mid.cu", "kernels_large.cu", "kernels_huge.cu"]
+                       "kernels_small.cu", "kernels_mid.cu", "kernels_large.cu", "kernels_huge.cu",
+                       "kernels_otf.cu"]
 
 
 def kernel_stamp():

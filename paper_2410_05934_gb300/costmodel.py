@@ -24,7 +24,7 @@ import numpy as np
 from . import ntt as _ntt
 from ._native import check, load
 
-IN, H, OUT = 4, 64, 8
+IN, H, OUT = 4, 64, 12
 N_PARAMS = H * IN + H + H * H + H + OUT * H + OUT
 N_ACT = 2 * H + OUT
 DATA_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
@@ -163,7 +163,7 @@ class CostModel:
                          final_loss=float(loss.item()))
         return history
 
-    # -- prediction (host, float32: a 4-64-64-8 forward is a few microseconds) --
+    # -- prediction (host, float32: a 4-64-64-12 forward is a few microseconds) --
     def predict(self, X):
         p = self.params
         o = 0
@@ -251,7 +251,8 @@ def choose_schedule(log2n, limbs, batch, bits=50, inverse=False, db=DEFAULT_DB, 
     if hit is not None:
         return hit[0], "autotuner"
     if "model" not in _CACHE:
-        _CACHE["model"] = CostModel.load(params) if os.path.exists(params) else None
+        m = CostModel.load(params) if os.path.exists(params) else None
+        _CACHE["model"] = m if m is not None and m.params.size == N_PARAMS else None   # another layer width
     model = _CACHE["model"]
     if model is not None and not inverse and model.meta.get("sigs", {}).get(str(log2n)) == schedule_signature(log2n):
         return model.choose(log2n, limbs, batch, bits), "cost_model"

@@ -58,7 +58,9 @@ int schedule_count(uint32_t log2n) {
     return c;
 }
 
-static const char* form_name(int f) { return f == 1 ? " pipelined" : (f == 2 ? " ro-twiddles" : ""); }
+static const char* form_name(int f) {
+    return f == 1 ? " pipelined" : (f == 2 ? " ro-twiddles" : (f == 3 ? " otf-twiddles" : ""));
+}
 
 static void sched_describe(int i, char* buf, size_t len) {
     const SchedParams& s = g_params[i];
@@ -140,6 +142,26 @@ static Plan32Dev plan32_dev(const ntt_plan_s* p) {
 }
 
 static bool natural(const ntt_plan_s* p) { return (p->h.flags & NTT_FLAG_NATURAL_ORDER) != 0; }
+static bool otf(const ntt_plan_s* p) { return (p->h.flags & NTT_FLAG_OTF_TWIDDLES) != 0; }
+
+// The on-the-fly-twiddle configuration of each N (ntt_schedules.h): the
+// geometry of the measured default schedule with every kernel in form 3.
+struct OtfEntry {
+    uint32_t log2n;
+    LaunchFn fwd, inv;
+};
+#define NTT_OTF_ENTRY_S1(LOGN, LOGT, LOGRP, TPC, PIPE) \
+    {LOGN, &launch_s1<LOGN, LOGT, LOGRP, TPC, PIPE, false>, &launch_s1<LOGN, LOGT, LOGRP, TPC, PIPE, true>},
+#define NTT_OTF_ENTRY_S2(LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE)              \
+    {LOGN, &launch_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE, false>,         \
+     &launch_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE, true>},
+static const OtfEntry g_otf[] = {NTT_OTF_CONFIGS(NTT_OTF_ENTRY_S1, NTT_OTF_ENTRY_S2)};
+
+static const OtfEntry* otf_entry(uint32_t log2n) {
+    for (const OtfEntry& e : g_otf)
+        if (e.log2n == log2n) return &e;
+    return nullptr;
+}
 
 static int transform(ntt_plan_t plan, bool inverse, const uint64_t* in, uint64_t* out,
                      uint64_t row_begin, uint64_t n_rows, void* stream) {
@@ -157,6 +179,13 @@ static int transform(ntt_plan_t plan, bool inverse, const uint64_t* in, uint64_t
                             reinterpret_cast<uint32_t*>(out), row_begin, n_rows, plan->h.log2n, stream,
                             &plan->last_launches);
     PlanDev d = plan_dev(plan);
+    if (otf(plan)) {     // its own configuration; the plan's schedule id does not apply
+        const OtfEntry* oe = otf_entry(plan->h.log2n);
+        if (!oe) return NTT_ERR_UNSUPPORTED;
+        d.otf_fwd = plan->d_otf_fwd;
+        d.otf_inv = plan->d_otf_inv;
+        return (inverse ? oe->inv : oe->fwd)(d, in, out, row_begin, n_rows, stream, &plan->last_launches);
+    }
     const SchedEntry& e = g_table[idx];
     const LaunchFn fn = inverse ? e.inv : e.fwd;
     if (!natural(plan)) return fn(d, in, out, row_begin, n_rows, stream, &plan->last_launches);
@@ -184,6 +213,9 @@ static void free_device(ntt_plan_s* p) {
     if (p->d_fwd32) cudaFree(p->d_fwd32);
     if (p->d_inv32) cudaFree(p->d_inv32);
     if (p->d_consts32) cudaFree(p->d_consts32);
+    if (p->d_otf_fwd) cudaFree(p->d_otf_fwd);
+    if (p->d_otf_inv) cudaFree(p->d_otf_inv);
+    p->d_otf_fwd = p->d_otf_inv = nullptr;
     p->d_fwd = p->d_inv = nullptr;
     p->d_consts = nullptr;
     p->d_status = nullptr;
@@ -250,6 +282,13 @@ int ntt_plan(ntt_plan_t* out, uint32_t log2n, const uint64_t* moduli, uint32_t n
                   cudaMemcpy(p->d_inv, p->h.inv.data(), tw_bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
                   cudaMemcpy(p->d_consts, p->h.consts.data(), lc_bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
                   cudaMemset(p->d_status, 0, sizeof(int)) == cudaSuccess;
+        if (ok && otf(p)) {
+            const size_t otf_bytes = p->h.otf_fwd.size() * sizeof(TwPair);
+            ok = cudaMalloc(&p->d_otf_fwd, otf_bytes) == cudaSuccess &&
+                 cudaMalloc(&p->d_otf_inv, otf_bytes) == cudaSuccess &&
+                 cudaMemcpy(p->d_otf_fwd, p->h.otf_fwd.data(), otf_bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
+                 cudaMemcpy(p->d_otf_inv, p->h.otf_inv.data(), otf_bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+        }
         if (!ok) {
             free_device(p);
             delete p;

@@ -122,6 +122,7 @@ static TileArgs emu_args(const PlanDev& p, const uint64_t* in, uint64_t* out, ui
         a.a_map[i] = p.a_map[i];
         a.b_map[i] = p.b_map[i];
     }
+    a.otf = C::INV ? p.otf_inv : p.otf_fwd;
     return a;
 }
 
@@ -268,6 +269,8 @@ static const EmuEntry* emu_find(uint32_t log2n, uint32_t id) {
     {LOGN, &emu_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, MODE, false>,      \
      &emu_s2<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, MODE, true>, 2},
 static const EmuEntry g_emu_batch[] = {NTT_BATCH_CONFIGS(NTT_EMU_BATCH_SINGLE, NTT_EMU_BATCH_SPLIT)};
+// the on-the-fly-twiddle configurations (NTT_FLAG_OTF_TWIDDLES plans)
+static const EmuEntry g_emu_otf[] = {NTT_OTF_CONFIGS(NTT_EMU_S1, NTT_EMU_S2)};
 
 struct EmuPlan {
     PlanHost h;
@@ -451,6 +454,13 @@ int nttemu_transform(void* plan, uint32_t sched, int inverse, const uint64_t* in
     d.aux_q = 0;
     d.nat = 0;
     d.has_map = 0;
+    if (p->h.flags & NTT_FLAG_OTF_TWIDDLES) {     // its own configuration, like ntt_forward
+        d.otf_fwd = p->h.otf_fwd.data();
+        d.otf_inv = p->h.otf_inv.data();
+        for (const EmuEntry& o : g_emu_otf)
+            if (o.log2n == p->h.log2n) return (inverse ? o.inv : o.fwd)(d, in, out, row_begin, n_rows);
+        return NTT_ERR_UNSUPPORTED;
+    }
     const EmuFn fn = inverse ? e->inv : e->fwd;
     if (!(p->h.flags & NTT_FLAG_NATURAL_ORDER)) return fn(d, in, out, row_begin, n_rows);
     if (e->kernels == 1) {

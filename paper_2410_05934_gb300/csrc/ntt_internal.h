@@ -27,6 +27,7 @@ struct PlanHost {
     std::vector<uint64_t> moduli, psi;
     std::vector<TwPair> fwd, inv;      // [n_moduli][N]
     std::vector<LimbConst> consts;     // [n_moduli]
+    std::vector<TwPair> otf_fwd, otf_inv;   // NTT_FLAG_OTF_TWIDDLES: [n_moduli][otf_entries(log2n)]
     std::vector<Tw32> fwd32, inv32;    // NTT_FLAG_WORD32 plans: 32-bit tables
     std::vector<LimbConst32> consts32;
 };
@@ -64,6 +65,8 @@ struct ntt_plan_s {
     nttgb::Tw32* d_fwd32 = nullptr;
     nttgb::Tw32* d_inv32 = nullptr;
     nttgb::LimbConst32* d_consts32 = nullptr;
+    nttgb::TwPair* d_otf_fwd = nullptr;
+    nttgb::TwPair* d_otf_inv = nullptr;
     uint32_t schedule = 0;
     uint32_t last_launches = 0;
 };

@@ -23,6 +23,8 @@ struct PlanDev {
     uint32_t nat;       // natural-order forward output / inverse input (full-row kernels)
     uint32_t has_map;        // source mode 3: polynomial maps of the two factors
     uint8_t a_map[NTT_MUL_MAX_MAPPED], b_map[NTT_MUL_MAX_MAPPED];
+    const TwPair* otf_fwd = nullptr;   // on-the-fly twiddle tables (form 3 kernels)
+    const TwPair* otf_inv = nullptr;
 };
 
 // Transforms rows [row_begin, row_begin + n_rows) of the layout that starts

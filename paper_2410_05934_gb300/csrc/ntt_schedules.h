@@ -64,11 +64,16 @@
     S2(16, 8, 4, 8, 4, 1, 6, 2, 2, 0) S2(16, 7, 4, 7, 4, 1, 6, 3, 2, 8)           \
     S2(16, 7, 4, 7, 4, 1, 6, 3, 2, 0) S2(16, 8, 4, 8, 4, 1, 5, 3, 4, 2)           \
     S2(16, 7, 4, 7, 4, 1, 5, 3, 4, 8) S2(16, 7, 4, 7, 4, 1, 5, 4, 4, 8)           \
-    S2(16, 8, 4, 8, 4, 1, 4, 4, 8, 8) S2(16, 8, 4, 8, 4, 1, 4, 4, 8, 0)           \
-    S2(16, 7, 4, 7, 4, 1, 4, 5, 8, 8) S2(16, 7, 4, 7, 4, 1, 5, 3, 8, 8)           \
-    S2(16, 7, 4, 7, 4, 1, 5, 3, 2, 8) S2(16, 7, 4, 7, 4, 1, 5, 3, 4, 0)           \
-    S2(16, 7, 3, 6, 4, 2, 5, 3, 4, 8)
+    S2(16, 7, 4, 7, 4, 1, 5, 3, 2, 8)
 
 #define NTT_SCHEDULES_ALL(S1, S2)                                           \
     NTT_SCHEDULES_SMALL(S1, S2) NTT_SCHEDULES_MID(S1, S2) NTT_SCHEDULES_LARGE(S1, S2) \
     NTT_SCHEDULES_HUGE(S1, S2)
+
+// On-the-fly-twiddle transforms (NTT_FLAG_OTF_TWIDDLES): one configuration
+// per N >= 2^10, the measured default geometry with every kernel in form 3
+// (twiddles generated from two small per-limb tables, see ntt_tile.cuh).
+#define NTT_OTF_CONFIGS(S1, S2)                                                       \
+    S1(10, 7, 3, 1, 3) S1(11, 8, 3, 1, 3) S1(12, 9, 3, 1, 3)                      \
+    S2(13, 6, 4, 6, 4, 1, 5, 3, 4, 3) S2(14, 7, 4, 7, 4, 1, 4, 3, 8, 3)           \
+    S2(15, 7, 4, 7, 4, 1, 5, 3, 4, 3) S2(16, 7, 4, 7, 4, 1, 6, 3, 2, 3)

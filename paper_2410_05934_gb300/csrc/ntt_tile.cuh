@@ -104,7 +104,16 @@ struct TileArgs {
     // both) and transforms their product mod q_l
     uint32_t has_map;
     uint8_t a_map[NTT_MUL_MAX_MAPPED], b_map[NTT_MUL_MAX_MAPPED];
+    // on-the-fly twiddles (MODE 3): per limb otf_entries(LOGN) pairs, first
+    // psi^(+-lo) for lo < 2^otf_lo_bits, then psi^(+-hi 2^otf_lo_bits)
+    const TwPair* otf;
 };
+
+// on-the-fly twiddle tables of a ring of 2^logn: e = hi 2^lo_bits + lo
+NTT_HD constexpr int otf_lo_bits(int logn) { return (logn + 1) / 2; }
+NTT_HD constexpr uint32_t otf_entries(int logn) {
+    return (1u << otf_lo_bits(logn)) + (1u << (logn - otf_lo_bits(logn)));
+}
 
 // floor(n / d) for n < 2^32 and 2 <= d < 2^32 from M = ceil(2^64 / d):
 // n M / 2^64 exceeds n / d by less than n / 2^64 < 2^-32, while a non-integer
@@ -157,7 +166,10 @@ NTT_HD constexpr uint32_t spread(uint32_t x, int pe, int r) {
 // MODE: 0 = direct form (twiddles staged in shared memory when they fit),
 //       1 = pipelined form, 2 = direct form reading twiddles through the
 //           read-only path (no staging; the table stays in L1 when a batch
-//           shares one modulus).
+//           shares one modulus), 3 = direct form with on-the-fly twiddles:
+//           psi^(+-e), e = brv(k), is applied as two Shoup products with
+//           entries lo = e mod 2^OTF_LO and hi = e >> OTF_LO of two small
+//           per-limb tables (TileArgs.otf).
 // Kernel forms of a two-kernel schedule entry (its PIPE field): below 4 both
 // kernels use it; A | B << 2 with B != 0 gives the column kernel form A and
 // the row kernel form B.
@@ -563,6 +575,18 @@ NTT_HD void relayout_read(TileRegs<C>& st, const TileArgs& a, const TileLoc& L, 
     if (C::FIRST && a.check && bad) record_status(a.status, NTT_STATUS_RANGE);
 }
 
+// The two factors of twiddle entry k (= psi^(+-e), e = brv(k)) from a
+// limb's on-the-fly tables: lo = psi^(+-(e mod 2^LO)), hi = psi^(+-(e >> LO) 2^LO).
+template <class C>
+NTT_HD void otf_twiddle(const TwPair* otf, uint32_t k, TwPair& lo, TwPair& hi) {
+    constexpr int LO = otf_lo_bits(C::LOGN);
+    const uint32_t e = brv_bits(k, C::LOGN);
+    NTT_GMEM_CHECK(k, 1u << C::LOGN);
+    NTT_GMEM_CHECK((1u << LO) + (e >> LO), otf_entries(C::LOGN));
+    lo = load_tw(otf, e & ((1u << LO) - 1));
+    hi = load_tw(otf, (1u << LO) + (e >> LO));
+}
+
 // ---- passes: one fused group of r stages in registers ----
 template <class C, int P>
 struct PassGeom {
@@ -611,6 +635,7 @@ NTT_HD void pass_compute(TileRegs<C>& st, const TileArgs& a, const TileLoc& L, i
     const LimbConst lc = a.lc[L.limb];
     const TwPair* tw = a.tw + ((uint64_t)L.limb << C::LOGN);
     const TwPair* tws = reinterpret_cast<const TwPair*>(sm + C::E + L.tw_off);
+    const TwPair* otf = C::MODE == 3 ? a.otf + (uint64_t)L.limb * otf_entries(C::LOGN) : nullptr;
     // row-local index bits above the pass: (g >> (LOGN - S_LO)) = hi part | pre_t | pre(gi)
     constexpr int SH = C::LOGN - S_LO;
     const uint32_t pre_t = place<C>(spread((uint32_t)t, Gm::PE, r)) >> SH;
@@ -636,6 +661,13 @@ NTT_HD void pass_compute(TileRegs<C>& st, const TileArgs& a, const TileLoc& L, i
                     if (C::TWS) {
                         NTT_SMEM_CHECK(slot0 + off, (1u << C::A) - 1);
                         w = tws[slot0 + off];
+                    } else if (C::MODE == 3) {
+                        // psi^e = psi^lo psi^(hi 2^LO): Y times the first factor here,
+                        // the butterfly's product supplies the second
+                        TwPair w_lo;
+                        otf_twiddle<C>(otf, k0 + off, w_lo, w);
+                        x[jl + d] = C::MC == 1 ? shoup_mul_approx(x[jl + d], w_lo.w, w_lo.wp, lc.q)
+                                               : shoup_mul(x[jl + d], w_lo.w, w_lo.wp, lc.q);
                     } else {
                         NTT_GMEM_CHECK(k0 + off, 1u << C::LOGN);
                         w = load_tw(tw, k0 + off);
@@ -666,10 +698,12 @@ NTT_HD void pass_compute(TileRegs<C>& st, const TileArgs& a, const TileLoc& L, i
                                                 lc.w1ninv_p, lc.q, lc.two_q);
                     } else {
                         const uint32_t off = (uint32_t)jl >> (r - v);
-                        TwPair w;
+                        TwPair w, w_hi{0, 0};
                         if (C::TWS) {
                             NTT_SMEM_CHECK(slot0 + off, (1u << C::A) - 1);
                             w = tws[slot0 + off];
+                        } else if (C::MODE == 3) {
+                            otf_twiddle<C>(otf, k0 + off, w, w_hi);
                         } else {
                             NTT_GMEM_CHECK(k0 + off, 1u << C::LOGN);
                             w = load_tw(tw, k0 + off);
@@ -678,6 +712,9 @@ NTT_HD void pass_compute(TileRegs<C>& st, const TileArgs& a, const TileLoc& L, i
                             gs_butterfly_small(x[jl], x[jl + d], w.w, w.wp, lc.q, lc.four_q);
                         else
                             gs_butterfly(x[jl], x[jl + d], w.w, w.wp, lc.q, lc.two_q);
+                        if (C::MODE == 3)   // the difference times the second factor: still [0, 2q) / [0, 4q)
+                            x[jl + d] = C::MC == 1 ? shoup_mul_approx(x[jl + d], w_hi.w, w_hi.wp, lc.q)
+                                                   : shoup_mul(x[jl + d], w_hi.w, w_hi.wp, lc.q);
                     }
                 }
             }

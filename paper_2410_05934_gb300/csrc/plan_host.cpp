@@ -128,9 +128,14 @@ int build_plan_host(PlanHost& h, uint32_t log2n, const uint64_t* moduli, uint32_
                     uint32_t batch, uint32_t flags) {
     if (log2n < NTT_MIN_LOG2N || log2n > NTT_MAX_LOG2N) return NTT_ERR_ARG;
     if (!moduli || n_moduli == 0 || batch == 0) return NTT_ERR_ARG;
-    if (flags & ~(NTT_FLAG_HOST_ONLY | NTT_FLAG_CHECK | NTT_FLAG_NATURAL_ORDER | NTT_FLAG_WORD32)) return NTT_ERR_ARG;
+    if (flags & ~(NTT_FLAG_HOST_ONLY | NTT_FLAG_CHECK | NTT_FLAG_NATURAL_ORDER | NTT_FLAG_WORD32 |
+                  NTT_FLAG_OTF_TWIDDLES))
+        return NTT_ERR_ARG;
     const bool word32 = (flags & NTT_FLAG_WORD32) != 0;
     if (word32 && ((flags & NTT_FLAG_NATURAL_ORDER) || log2n > NTT_WORD32_MAX_LOG2N)) return NTT_ERR_UNSUPPORTED;
+    if ((flags & NTT_FLAG_OTF_TWIDDLES) &&
+        ((flags & (NTT_FLAG_NATURAL_ORDER | NTT_FLAG_WORD32)) || log2n < NTT_OTF_MIN_LOG2N))
+        return NTT_ERR_UNSUPPORTED;
     const uint64_t n = 1ull << log2n;
     const u128 total = (u128)batch * n_moduli * n;
     if (total >= ((u128)1 << 40)) return NTT_ERR_ARG;
@@ -211,6 +216,23 @@ int build_plan_host(PlanHost& h, uint32_t log2n, const uint64_t* moduli, uint32_
             const uint64_t ql = moduli[n_moduli - 1] % q;
             c.rs_inv = ql ? pow_mod(ql, q - 2, q) : 0;
             c.rs_inv_p = shoup_of(c.rs_inv, q);
+        }
+    }
+    if (flags & NTT_FLAG_OTF_TWIDDLES) {
+        // per limb: psi^(+-lo), lo < 2^LO, then psi^(+-hi 2^LO); table entry
+        // k of the full tables holds the power brv(k), so power e sits at brv(e)
+        const int LO = otf_lo_bits((int)log2n);
+        const uint32_t per = otf_entries((int)log2n);
+        h.otf_fwd.resize((size_t)n_moduli * per);
+        h.otf_inv.resize((size_t)n_moduli * per);
+        for (uint32_t l = 0; l < n_moduli; ++l) {
+            const TwPair* f = &h.fwd[(size_t)l * n];
+            const TwPair* v = &h.inv[(size_t)l * n];
+            for (uint32_t i = 0; i < per; ++i) {
+                const uint32_t e = i < (1u << LO) ? i : (i - (1u << LO)) << LO;
+                h.otf_fwd[(size_t)l * per + i] = f[rev[e]];
+                h.otf_inv[(size_t)l * per + i] = v[rev[e]];
+            }
         }
     }
     if (word32) {      // 32-bit tables: w' = floor(w 2^32 / q)

@@ -15,6 +15,7 @@ NTT_FLAG_HOST_ONLY = 1
 NTT_FLAG_CHECK = 2
 NTT_FLAG_NATURAL_ORDER = 4
 NTT_FLAG_WORD32 = 8
+NTT_FLAG_OTF_TWIDDLES = 16
 
 
 def _stream_handle(stream):

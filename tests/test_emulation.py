@@ -438,3 +438,47 @@ def test_forward_output_reduction_bounds():
         x = np.array(edges + [int(v) for v in rng.integers(0, top, 2000, dtype=np.uint64)], dtype=np.uint64)
         want = np.array([int(v) % q for v in x], dtype=np.uint64)
         assert np.array_equal(plan.reduce_65q(0, x), want), q
+
+
+def _prime_62(log2n):
+    """Largest prime below 2^62 with q = 1 mod 2^(log2n + 1) (exact modulus class)."""
+    from oracle import oracle as O
+    step = 1 << (log2n + 1)
+    q = ((1 << 62) - 1) // step * step + 1
+    while not O.is_prime(q):
+        q -= step
+    return q
+
+
+@pytest.mark.parametrize("log2n", range(10, 17))
+@pytest.mark.parametrize("cls", ["small", "exact"])
+def test_otf_twiddles_match_tables(oracle, log2n, cls):
+    """NTT_FLAG_OTF_TWIDDLES: every twiddle formed from the two small tables
+    gives the same bits as the stored-table transform and the oracle, both
+    modulus classes, forward and inverse, on a ragged row range."""
+    n = 1 << log2n
+    mods = W.POOL50[:3] if cls == "small" else [_prime_62(log2n), W.POOL50[1]]
+    rows = 2 * len(mods)
+    per_row = [mods[r % len(mods)] for r in range(rows)]
+    x = W.rows_uniform(41, log2n, per_row, n)
+    x[0, :] = mods[0] - 1
+    otf = emu.EmuPlan(log2n, mods, 2, flags=16)
+    tab = emu.EmuPlan(log2n, mods, 2)
+    fwd = otf.transform(x, 0)
+    assert np.array_equal(fwd, tab.transform(x, 0))
+    rng = np.random.default_rng(log2n)
+    idx = np.stack([np.concatenate([[0, 1, n - 1], rng.integers(0, n, 9)]) for _ in per_row]).astype(np.uint32)
+    r = np.arange(rows)[:, None]
+    assert np.array_equal(fwd[r, idx], oracle.transform_rows(x, per_row, idx=idx))
+    inv = otf.transform(x, 0, inverse=True)
+    assert np.array_equal(inv, tab.transform(x, 0, inverse=True))
+    assert np.array_equal(otf.transform(fwd, 0, inverse=True), x)
+    part = otf.transform(x, 0, row_begin=1, n_rows=rows - 2)
+    assert np.array_equal(part[1:rows - 1], fwd[1:rows - 1])
+    assert otf.status() == 0
+
+
+def test_otf_twiddle_plan_rules():
+    for log2n, flags in [(9, 16), (12, 16 | 4), (10, 16 | 8)]:
+        with pytest.raises(ValueError):
+            emu.EmuPlan(log2n, [Q30[0] if flags & 8 else W.POOL50[0]], 1, flags=flags)

@@ -416,3 +416,48 @@ def test_word32_tfhe_shape_and_rules(oracle):
         ntt.Plan(10, [W.POOL50[0]], 1, flags=ntt.NTT_FLAG_WORD32)
     with pytest.raises(ValueError):
         p.forward(torch.zeros((3780, 1024), dtype=torch.int64, device="cuda"))   # 64-bit buffer
+
+
+def _prime_62(log2n):
+    step = 1 << (log2n + 1)
+    q = ((1 << 62) - 1) // step * step + 1
+    from oracle import oracle as O
+    while not O.is_prime(q):
+        q -= step
+    return q
+
+
+@pytest.mark.parametrize("log2n", range(10, 17))
+def test_otf_twiddle_plans(oracle, log2n):
+    """NTT_FLAG_OTF_TWIDDLES on the GPU: the same bits as the stored-table
+    plan (both modulus classes), oracle samples, the inverse, a row range."""
+    n = 1 << log2n
+    for mods in (W.POOL50[:3], [_prime_62(log2n), W.POOL50[2]]):
+        rows = 3 * len(mods)
+        per_row = [mods[r % len(mods)] for r in range(rows)]
+        x = W.rows_uniform(43, log2n, per_row, n)
+        otf = ntt.Plan(log2n, mods, 3, flags=ntt.NTT_FLAG_OTF_TWIDDLES)
+        tab = ntt.Plan(log2n, mods, 3)
+        d = to_dev(x)
+        a, b = torch.empty_like(d), torch.empty_like(d)
+        otf.forward(d, a)
+        tab.forward(d, b)
+        assert torch.equal(a, b)
+        got = to_host(a)
+        rng = np.random.default_rng(log2n)
+        idx = np.stack([np.concatenate([[0, n - 1], rng.integers(0, n, 6)]) for _ in per_row]).astype(np.uint32)
+        assert np.array_equal(got[np.arange(rows)[:, None], idx], oracle.transform_rows(x, per_row, idx=idx))
+        otf.inverse(d, a)
+        tab.inverse(d, b)
+        assert torch.equal(a, b)
+        back = torch.empty_like(d)
+        otf.forward(d, a)
+        otf.inverse(a, back)
+        assert torch.equal(back, d)
+        c = d.clone()
+        otf.forward_rows(d, c, 1, rows - 2)
+        assert torch.equal(c[1:rows - 1], a[1:rows - 1]) and torch.equal(c[0], d[0])
+        assert otf.status() == 0
+    for log2n_, flags in [(9, ntt.NTT_FLAG_OTF_TWIDDLES), (12, ntt.NTT_FLAG_OTF_TWIDDLES | ntt.NTT_FLAG_NATURAL_ORDER)]:
+        with pytest.raises(ntt.NttError):
+            ntt.Plan(log2n_, [W.POOL50[0]], 1, flags=flags)
