@@ -136,23 +136,25 @@ NTT_HD void gs_butterfly_scaled(uint64_t& X, uint64_t& Y, uint64_t ninv, uint64_
     Y = shoup_mul(d, wn, wn_p, q);
 }
 
-// Exact a * b mod q for a, b < q by Barrett reduction with k = bitlen(q) and
+// a * b mod q for a, b < q by Barrett reduction with k = bitlen(q) and
 // mu = floor(2^(2k) / q) < 2^63:  x = a b < 2^(2k);  q3 = ((x >> (k-1)) mu) >> (k+1)
 // underestimates floor(x / q) by at most 2, so r = x - q3 q < 3q (Handbook of
-// Applied Cryptography, Alg. 14.42).
-NTT_HD uint64_t barrett_mulmod(uint64_t a, uint64_t b, uint64_t q, uint64_t mu, uint32_t k) {
+// Applied Cryptography, Alg. 14.42).  The lazy form returns r in [0, 3q); the
+// exact form subtracts q up to twice.
+NTT_HD uint64_t barrett_mulmod_lazy(uint64_t a, uint64_t b, uint64_t q, uint64_t mu, uint32_t k) {
     uint64_t lo = a * b;
     uint64_t hi = mulhi64(a, b);
-    // x >> (k - 1), with 1 <= k <= 62: fits in 64 bits since x < 2^(2k)
     uint32_t sh = k - 1;
     uint64_t q1 = sh == 0 ? lo : ((lo >> sh) | (hi << (64 - sh)));
     uint64_t plo = q1 * mu;
     uint64_t phi = mulhi64(q1, mu);
-    uint32_t sh2 = k + 1;  // 2..63
+    uint32_t sh2 = k + 1;
     uint64_t q3 = (plo >> sh2) | (phi << (64 - sh2));
-    uint64_t r = lo - q3 * q;
-    r = csub(r, q);  // [0, 3q) -> [0, 2q)
-    return csub(r, q);
+    return lo - q3 * q;   // [0, 3q)
+}
+
+NTT_HD uint64_t barrett_mulmod(uint64_t a, uint64_t b, uint64_t q, uint64_t mu, uint32_t k) {
+    return csub(csub(barrett_mulmod_lazy(a, b, q, mu, k), q), q);   // [0, 3q) -> [0, q)
 }
 
 }  // namespace nttgb

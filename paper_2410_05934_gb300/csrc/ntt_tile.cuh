@@ -422,11 +422,21 @@ NTT_HD void load_direct(TileRegs<C>& st, const TileArgs& a, const TileLoc& L, in
                 load_pair(a0 + step + off, u0, u1);
                 load_pair(b0 + off, v0, v1);
             }
-            uint64_t r0 = barrett_mulmod(x0, y0, lc.q, lc.mu, lc.bits);
-            uint64_t r1 = barrett_mulmod(x1, y1, lc.q, lc.mu, lc.bits);
-            if (k == 1) {
-                r0 = csub(r0 + barrett_mulmod(u0, v0, lc.q, lc.mu, lc.bits), lc.q);
-                r1 = csub(r1 + barrett_mulmod(u1, v1, lc.q, lc.mu, lc.bits), lc.q);
+            uint64_t r0, r1;
+            if (C::MC == 1) {   // lazily reduced: [0, 3q), or a sum folded into [0, 4q)
+                r0 = barrett_mulmod_lazy(x0, y0, lc.q, lc.mu, lc.bits);
+                r1 = barrett_mulmod_lazy(x1, y1, lc.q, lc.mu, lc.bits);
+                if (k == 1) {
+                    r0 = csub(r0 + barrett_mulmod_lazy(u0, v0, lc.q, lc.mu, lc.bits), lc.two_q);
+                    r1 = csub(r1 + barrett_mulmod_lazy(u1, v1, lc.q, lc.mu, lc.bits), lc.two_q);
+                }
+            } else {
+                r0 = barrett_mulmod(x0, y0, lc.q, lc.mu, lc.bits);
+                r1 = barrett_mulmod(x1, y1, lc.q, lc.mu, lc.bits);
+                if (k == 1) {
+                    r0 = csub(r0 + barrett_mulmod(u0, v0, lc.q, lc.mu, lc.bits), lc.q);
+                    r1 = csub(r1 + barrett_mulmod(u1, v1, lc.q, lc.mu, lc.bits), lc.q);
+                }
             }
             st.x[2 * i] = r0;
             st.x[2 * i + 1] = r1;
@@ -465,8 +475,11 @@ NTT_HD void load_direct(TileRegs<C>& st, const TileArgs& a, const TileLoc& L, in
             uint64_t x0, x1, y0, y1;
             load_pair(x + off, x0, x1);
             load_pair(y + off, y0, y1);
-            st.x[2 * i] = barrett_mulmod(x0, y0, lc.q, lc.mu, lc.bits);
-            st.x[2 * i + 1] = barrett_mulmod(x1, y1, lc.q, lc.mu, lc.bits);
+            // lazily reduced: the GS stages take [0, 4q) in the small-modulus class, [0, 2q) otherwise
+            const uint64_t p0 = barrett_mulmod_lazy(x0, y0, lc.q, lc.mu, lc.bits);
+            const uint64_t p1 = barrett_mulmod_lazy(x1, y1, lc.q, lc.mu, lc.bits);
+            st.x[2 * i] = C::MC == 1 ? p0 : csub(p0, lc.q);
+            st.x[2 * i + 1] = C::MC == 1 ? p1 : csub(p1, lc.q);
         }
         return;
     }

@@ -482,3 +482,27 @@ def test_otf_twiddle_plan_rules():
     for log2n, flags in [(9, 16), (12, 16 | 4), (10, 16 | 8)]:
         with pytest.raises(ValueError):
             emu.EmuPlan(log2n, [Q30[0] if flags & 8 else W.POOL50[0]], 1, flags=flags)
+
+
+@pytest.mark.parametrize("log2n", [10, 13, 16])
+def test_products_at_the_largest_residues(log2n):
+    """The inverse's first kernel forms its products lazily (Barrett remainder
+    in [0, 3q), a tensor-product sum folded into [0, 4q) in the small-modulus
+    class): operands q - 1 everywhere give the largest remainders; the results
+    must still equal the oracle's exact products transformed back."""
+    from oracle import oracle as O
+    n = 1 << log2n
+    for mods in ([W.POOL50[0], W.POOL50[3]], [_prime_62(log2n), W.POOL50[3]]):
+        A = np.array([np.full(n, mods[r % 2] - 1, dtype=np.uint64) for r in range(8)])
+        A[1, ::3] = 1
+        plan = emu.EmuPlan(log2n, mods, 4)
+        a_poly, b_poly = [0, 0, 1, 1], [2, 3, 2, 3]
+        rows_a = [a_poly[k // 2] * 2 + k % 2 for k in range(8)]
+        rows_b = [b_poly[k // 2] * 2 + k % 2 for k in range(8)]
+        prod = np.array([O.pointwise(A[ra], A[rb], mods[k % 2]) for k, (ra, rb) in enumerate(zip(rows_a, rows_b))])
+        s = 5 if log2n >= 13 else 7
+        got = plan.inverse_mul(A, A, s, a_poly, b_poly)
+        idx = np.stack([np.concatenate([[0, 1, n - 1], np.arange(5, n, max(1, n // 24))[:24]])
+                        for _ in range(8)]).astype(np.uint32)
+        want = O.transform_rows(prod, [mods[k % 2] for k in range(8)], inverse=True, idx=idx)
+        assert np.array_equal(got[np.arange(8)[:, None], idx], want)
