@@ -209,6 +209,8 @@ static void free_device(ntt_plan_s* p) {
     if (p->d_fwd) cudaFree(p->d_fwd);
     if (p->d_inv) cudaFree(p->d_inv);
     if (p->d_consts) cudaFree(p->d_consts);
+    if (p->d_consts_mont) cudaFree(p->d_consts_mont);
+    p->d_consts_mont = nullptr;
     if (p->d_status) cudaFree(p->d_status);
     if (p->d_fwd32) cudaFree(p->d_fwd32);
     if (p->d_inv32) cudaFree(p->d_inv32);
@@ -277,10 +279,13 @@ int ntt_plan(ntt_plan_t* out, uint32_t log2n, const uint64_t* moduli, uint32_t n
                   cudaMalloc(&p->d_fwd, tw_bytes) == cudaSuccess &&
                   cudaMalloc(&p->d_inv, tw_bytes) == cudaSuccess &&
                   cudaMalloc(&p->d_consts, lc_bytes) == cudaSuccess &&
+                  cudaMalloc(&p->d_consts_mont, lc_bytes) == cudaSuccess &&
                   cudaMalloc(&p->d_status, sizeof(int)) == cudaSuccess &&
                   cudaMemcpy(p->d_fwd, p->h.fwd.data(), tw_bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
                   cudaMemcpy(p->d_inv, p->h.inv.data(), tw_bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
                   cudaMemcpy(p->d_consts, p->h.consts.data(), lc_bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(p->d_consts_mont, p->h.consts_mont.data(), lc_bytes, cudaMemcpyHostToDevice) ==
+                      cudaSuccess &&
                   cudaMemset(p->d_status, 0, sizeof(int)) == cudaSuccess;
         if (ok && otf(p)) {
             const size_t otf_bytes = p->h.otf_fwd.size() * sizeof(TwPair);
@@ -372,6 +377,7 @@ int ntt_hmul_tensor(ntt_plan_t plan, const uint64_t* d_a, const uint64_t* d_b, u
     PlanDev d = plan_dev(plan);
     d.src_mode = 1;
     d.in_b = d_b;
+    d.lc = plan->d_consts_mont;     // Montgomery products: the last stage scales by N^-1 2^64
     return g_table[idx].inv(d, d_a, d_out, 0, 3ull * plan->h.n_moduli, cuda_stream, &plan->last_launches);
 }
 
@@ -414,6 +420,7 @@ int ntt_inverse_mul(ntt_plan_t plan, const uint64_t* d_a, const uint32_t* a_poly
     plan->last_launches = 0;
     d.src_mode = 3;
     d.in_b = d_b;
+    d.lc = plan->d_consts_mont;     // Montgomery products: the last stage scales by N^-1 2^64
     return g_table[idx].inv(d, d_a, d_out, 0, plan->h.rows, cuda_stream, &plan->last_launches);
 }
 

@@ -53,7 +53,8 @@ static bool verify_cfg() {
         for (int t = 0; t < C::T; ++t)
             for (int j = 0; j < C::R; ++j) {
                 uint32_t jlo = (uint32_t)j & ((1u << r) - 1), jhi = (uint32_t)j >> r;
-                uint32_t e = spread((uint32_t)t | (jhi << C::LOGT), pe, r) | (jlo << pe);
+                const uint32_t tt = swap_thread_bits((uint32_t)t, pass_swaps(pe, r, C::LOGT));
+                uint32_t e = spread(tt | (jhi << C::LOGT), pe, r) | (jlo << pe);
                 if (e >= (uint32_t)C::E || seen[e]++) return false;
             }
     }
@@ -512,7 +513,7 @@ int nttemu_hmul_tensor(void* plan, uint32_t sched, const uint64_t* a, const uint
     PlanDev d;
     d.fwd = p->h.fwd.data();
     d.inv = p->h.inv.data();
-    d.lc = p->h.consts.data();
+    d.lc = p->h.consts_mont.data();   // Montgomery products (see capi)
     d.status = &p->status;
     d.n_moduli = p->h.n_moduli;
     d.check = 0;
@@ -629,7 +630,7 @@ int nttemu_inverse_mul(void* plan, uint32_t sched, const uint64_t* a, const uint
     PlanDev d;
     d.fwd = p->h.fwd.data();
     d.inv = p->h.inv.data();
-    d.lc = p->h.consts.data();
+    d.lc = p->h.consts_mont.data();   // Montgomery products (see capi)
     d.status = &p->status;
     d.n_moduli = p->h.n_moduli;
     d.check = 0;

@@ -141,6 +141,17 @@ NTT_HD void gs_butterfly_scaled(uint64_t& X, uint64_t& Y, uint64_t ninv, uint64_
 // underestimates floor(x / q) by at most 2, so r = x - q3 q < 3q (Handbook of
 // Applied Cryptography, Alg. 14.42).  The lazy form returns r in [0, 3q); the
 // exact form subtracts q up to twice.
+// Montgomery product (R = 2^64) of a, b < q < 2^62 with qn = -q^-1 mod 2^64:
+// m = (a b mod R) qn mod R makes a b + m q divisible by R, and
+// t = (a b + m q) / R < q^2 / R + q < 2q is congruent to a b R^-1 mod q.
+// The low words of a b and m q sum to 0 mod R, so their carry is 1 exactly
+// when the low word of a b is nonzero.
+NTT_HD uint64_t mont_mul(uint64_t a, uint64_t b, uint64_t q, uint64_t qn) {
+    const uint64_t lo = a * b, hi = mulhi64(a, b);
+    const uint64_t m = lo * qn;
+    return hi + mulhi64(m, q) + (lo != 0 ? 1u : 0u);
+}
+
 NTT_HD uint64_t barrett_mulmod_lazy(uint64_t a, uint64_t b, uint64_t q, uint64_t mu, uint32_t k) {
     uint64_t lo = a * b;
     uint64_t hi = mulhi64(a, b);

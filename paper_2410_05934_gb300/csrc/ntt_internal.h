@@ -27,6 +27,7 @@ struct PlanHost {
     std::vector<uint64_t> moduli, psi;
     std::vector<TwPair> fwd, inv;      // [n_moduli][N]
     std::vector<LimbConst> consts;     // [n_moduli]
+    std::vector<LimbConst> consts_mont;   // the same with the last-stage scale times 2^64
     std::vector<TwPair> otf_fwd, otf_inv;   // NTT_FLAG_OTF_TWIDDLES: [n_moduli][otf_entries(log2n)]
     std::vector<Tw32> fwd32, inv32;    // NTT_FLAG_WORD32 plans: 32-bit tables
     std::vector<LimbConst32> consts32;
@@ -61,6 +62,7 @@ struct ntt_plan_s {
     nttgb::TwPair* d_fwd = nullptr;
     nttgb::TwPair* d_inv = nullptr;
     nttgb::LimbConst* d_consts = nullptr;
+    nttgb::LimbConst* d_consts_mont = nullptr;
     int* d_status = nullptr;
     nttgb::Tw32* d_fwd32 = nullptr;
     nttgb::Tw32* d_inv32 = nullptr;

@@ -60,6 +60,8 @@ struct LimbConst {
     uint64_t rs_inv, rs_inv_p;  // q_last^-1 mod q and its Shoup form (Rescale; 0 for the last limb)
     uint32_t bits;              // bit length of q
     uint32_t red_m;             // floor(2^(32 + red_sh) / q), red_sh = max(bits - 25, 0): reduce_65q
+    uint64_t qn;                // -q^-1 mod 2^64: Montgomery products of the fused operators, whose
+                                // inverse runs on a copy of the constants with ninv, w1ninv times 2^64
 };
 
 // Modulus classes: 0 = any q < 2^62 (exact Shoup quotient, Harvey bounds),
@@ -422,20 +424,17 @@ NTT_HD void load_direct(TileRegs<C>& st, const TileArgs& a, const TileLoc& L, in
                 load_pair(a0 + step + off, u0, u1);
                 load_pair(b0 + off, v0, v1);
             }
-            uint64_t r0, r1;
-            if (C::MC == 1) {   // lazily reduced: [0, 3q), or a sum folded into [0, 4q)
-                r0 = barrett_mulmod_lazy(x0, y0, lc.q, lc.mu, lc.bits);
-                r1 = barrett_mulmod_lazy(x1, y1, lc.q, lc.mu, lc.bits);
-                if (k == 1) {
-                    r0 = csub(r0 + barrett_mulmod_lazy(u0, v0, lc.q, lc.mu, lc.bits), lc.two_q);
-                    r1 = csub(r1 + barrett_mulmod_lazy(u1, v1, lc.q, lc.mu, lc.bits), lc.two_q);
-                }
-            } else {
-                r0 = barrett_mulmod(x0, y0, lc.q, lc.mu, lc.bits);
-                r1 = barrett_mulmod(x1, y1, lc.q, lc.mu, lc.bits);
-                if (k == 1) {
-                    r0 = csub(r0 + barrett_mulmod(u0, v0, lc.q, lc.mu, lc.bits), lc.q);
-                    r1 = csub(r1 + barrett_mulmod(u1, v1, lc.q, lc.mu, lc.bits), lc.q);
+            // Montgomery products (x y 2^-64 in [0, 2q)); the inverse's last
+            // stage multiplies by 2^64 again.  A sum of two stays below 4q,
+            // the small-modulus class's input bound; the exact class folds it.
+            uint64_t r0 = mont_mul(x0, y0, lc.q, lc.qn);
+            uint64_t r1 = mont_mul(x1, y1, lc.q, lc.qn);
+            if (k == 1) {
+                r0 += mont_mul(u0, v0, lc.q, lc.qn);
+                r1 += mont_mul(u1, v1, lc.q, lc.qn);
+                if (C::MC != 1) {
+                    r0 = csub(r0, lc.two_q);
+                    r1 = csub(r1, lc.two_q);
                 }
             }
             st.x[2 * i] = r0;
@@ -475,11 +474,10 @@ NTT_HD void load_direct(TileRegs<C>& st, const TileArgs& a, const TileLoc& L, in
             uint64_t x0, x1, y0, y1;
             load_pair(x + off, x0, x1);
             load_pair(y + off, y0, y1);
-            // lazily reduced: the GS stages take [0, 4q) in the small-modulus class, [0, 2q) otherwise
-            const uint64_t p0 = barrett_mulmod_lazy(x0, y0, lc.q, lc.mu, lc.bits);
-            const uint64_t p1 = barrett_mulmod_lazy(x1, y1, lc.q, lc.mu, lc.bits);
-            st.x[2 * i] = C::MC == 1 ? p0 : csub(p0, lc.q);
-            st.x[2 * i + 1] = C::MC == 1 ? p1 : csub(p1, lc.q);
+            // Montgomery products x y 2^-64 in [0, 2q), inside every class's
+            // GS input bound; the inverse's last stage multiplies by 2^64 again
+            st.x[2 * i] = mont_mul(x0, y0, lc.q, lc.qn);
+            st.x[2 * i + 1] = mont_mul(x1, y1, lc.q, lc.qn);
         }
         return;
     }
@@ -600,6 +598,54 @@ NTT_HD void otf_twiddle(const TwPair* otf, uint32_t k, TwPair& lo, TwPair& hi) {
     hi = load_tw(otf, (1u << LO) + (e >> LO));
 }
 
+// Thread-bit exchanges of a pass.  Thread bit i of a pass with lowest e-bit
+// PE and r stages sits at e-bit i (i < PE) or i + r.  The 16 lanes of a
+// half-warp differ in thread bits 0..3, and swz folds e-bit k onto bank pair
+// k mod 4 of a 64-bit word, so those four bits must land on e-bits of
+// distinct residues mod 4 for a conflict-free access.  Where they do not,
+// a lane bit is exchanged with a higher thread bit of a missing residue
+// (any bijection of the threads is valid: each pass reads and writes through
+// shared memory).  Up to four exchanges (i | j << 4 per byte, 0 = none).
+NTT_HD constexpr uint32_t pass_swaps(int pe, int r, int logt) {
+    int pos[32] = {};
+    for (int i = 0; i < logt; ++i) pos[i] = i < pe ? i : i + r;
+    uint32_t packed = 0, used = 0;
+    int ns = 0;
+    const int lim = logt < 4 ? logt : 4;
+    for (int i = 0; i < lim; ++i) {
+        if (used & (1u << (pos[i] & 3))) {
+            for (int j = 4; j < logt; ++j) {
+                bool ok = !(used & (1u << (pos[j] & 3)));
+                for (int k = i + 1; k < lim; ++k) ok = ok && (pos[j] & 3) != (pos[k] & 3);
+                if (ok) {
+                    const int tmp = pos[i];
+                    pos[i] = pos[j];
+                    pos[j] = tmp;
+                    packed |= (uint32_t)(i | (j << 4)) << (8 * ns);
+                    ++ns;
+                    break;
+                }
+            }
+        }
+        used |= 1u << (pos[i] & 3);
+    }
+    return packed;
+}
+
+// t with the recorded exchanges applied (last first, so thread bit i ends at
+// the e-bit chosen for it)
+NTT_HD constexpr uint32_t swap_thread_bits(uint32_t t, uint32_t packed) {
+    int n = 0;
+    while (n < 4 && ((packed >> (8 * n)) & 0xffu)) ++n;
+    for (int s = n - 1; s >= 0; --s) {
+        const uint32_t p = (packed >> (8 * s)) & 0xffu;
+        const uint32_t i = p & 15u, j = p >> 4;
+        const uint32_t d = ((t >> i) ^ (t >> j)) & 1u;
+        t ^= (d << i) | (d << j);
+    }
+    return t;
+}
+
 // ---- passes: one fused group of r stages in registers ----
 template <class C, int P>
 struct PassGeom {
@@ -609,9 +655,14 @@ struct PassGeom {
     static constexpr int PE = C::LOGP + C::S1 - S_LO - r;   // e-bit of the pass's lowest bit
     static constexpr int G = C::R >> r;                     // independent groups per thread
     static constexpr int GS = 1 << r;                       // elements per group
-    // e of register j, minus the thread's contribution spread(t)
+    static constexpr uint32_t SWAPS = pass_swaps(PE, r, C::LOGT);
+    // e of register j, minus the thread's contribution et(t)
     static NTT_HD constexpr uint32_t ej(int j) {
         return spread(((uint32_t)j >> r) << C::LOGT, PE, r) | (((uint32_t)j & (GS - 1)) << PE);
+    }
+    // the thread's contribution to its elements' e in this pass
+    static NTT_HD constexpr uint32_t et(uint32_t t) {
+        return spread(SWAPS ? swap_thread_bits(t, SWAPS) : t, PE, r);
     }
 };
 
@@ -619,7 +670,7 @@ template <class C, int P>
 NTT_HD void pass_read(TileRegs<C>& st, const TileLoc& L, int t, const uint64_t* sm) {
     if (!L.valid) return;
     using Gm = PassGeom<C, P>;
-    const uint32_t b = swz(spread((uint32_t)t, Gm::PE, Gm::r));
+    const uint32_t b = swz(Gm::et((uint32_t)t));
 #pragma unroll
     for (int j = 0; j < C::R; ++j) {
         const uint32_t addr = b ^ swz(Gm::ej(j));
@@ -632,7 +683,7 @@ template <class C, int P>
 NTT_HD void pass_write(const TileRegs<C>& st, const TileLoc& L, int t, uint64_t* sm) {
     if (!L.valid) return;
     using Gm = PassGeom<C, P>;
-    const uint32_t b = swz(spread((uint32_t)t, Gm::PE, Gm::r));
+    const uint32_t b = swz(Gm::et((uint32_t)t));
 #pragma unroll
     for (int j = 0; j < C::R; ++j) {
         const uint32_t addr = b ^ swz(Gm::ej(j));
@@ -651,7 +702,7 @@ NTT_HD void pass_compute(TileRegs<C>& st, const TileArgs& a, const TileLoc& L, i
     const TwPair* otf = C::MODE == 3 ? a.otf + (uint64_t)L.limb * otf_entries(C::LOGN) : nullptr;
     // row-local index bits above the pass: (g >> (LOGN - S_LO)) = hi part | pre_t | pre(gi)
     constexpr int SH = C::LOGN - S_LO;
-    const uint32_t pre_t = place<C>(spread((uint32_t)t, Gm::PE, r)) >> SH;
+    const uint32_t pre_t = place<C>(Gm::et((uint32_t)t)) >> SH;
     const uint32_t hi_part = L.hi << (S_LO - C::S0);
 #pragma unroll
     for (int gi = 0; gi < Gm::G; ++gi) {

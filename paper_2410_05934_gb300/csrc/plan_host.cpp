@@ -206,6 +206,11 @@ int build_plan_host(PlanHost& h, uint32_t log2n, const uint64_t* moduli, uint32_
         c.ninv_p = shoup_of(c.ninv, q);
         c.w1ninv = mul_mod(v[1].w, c.ninv, q);
         c.w1ninv_p = shoup_of(c.w1ninv, q);
+        {
+            uint64_t inv = q;                      // q^-1 mod 2^64 by Newton: each step doubles the correct bits
+            for (int it = 0; it < 6; ++it) inv *= 2 - q * inv;
+            c.qn = 0 - inv;
+        }
         c.bits = bit_length(q);
         c.mu = (uint64_t)(((u128)1 << (2 * c.bits)) / q);
         {
@@ -217,6 +222,15 @@ int build_plan_host(PlanHost& h, uint32_t log2n, const uint64_t* moduli, uint32_
             c.rs_inv = ql ? pow_mod(ql, q - 2, q) : 0;
             c.rs_inv_p = shoup_of(c.rs_inv, q);
         }
+    }
+    // the inverse after Montgomery products: last-stage scale N^-1 2^64
+    h.consts_mont = h.consts;
+    for (LimbConst& c : h.consts_mont) {
+        const uint64_t r = (uint64_t)(((u128)1 << 64) % c.q);
+        c.ninv = mul_mod(c.ninv, r, c.q);
+        c.ninv_p = shoup_of(c.ninv, c.q);
+        c.w1ninv = mul_mod(c.w1ninv, r, c.q);
+        c.w1ninv_p = shoup_of(c.w1ninv, c.q);
     }
     if (flags & NTT_FLAG_OTF_TWIDDLES) {
         // per limb: psi^(+-lo), lo < 2^LO, then psi^(+-hi 2^LO); table entry
