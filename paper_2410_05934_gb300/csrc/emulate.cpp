@@ -210,7 +210,9 @@ static int emu_kernel(const PlanDev& p, const uint64_t* in, uint64_t* out, uint6
 
 template <int LOGN, int LOGT, int LOGRP, int TPC, int PIPE, bool INV>
 static int emu_s1(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t rb, uint64_t nr) {
-    if (p.mc == 1)
+    if (INV && p.mc == 2)     // class 2 differs from class 1 only in the inverse (as the launcher)
+        return emu_kernel<TileCfg<LOGN, 0, LOGN, 0, LOGT, LOGRP, TPC, INV, INV ? 2 : 1, PIPE>>(p, in, out, rb, nr);
+    if (p.mc >= 1)
         return emu_kernel<TileCfg<LOGN, 0, LOGN, 0, LOGT, LOGRP, TPC, INV, 1, PIPE>>(p, in, out, rb, nr);
     return emu_kernel<TileCfg<LOGN, 0, LOGN, 0, LOGT, LOGRP, TPC, INV, 0, PIPE>>(p, in, out, rb, nr);
 }
@@ -234,7 +236,9 @@ static int emu_s2_mc(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64
 template <int LOGN, int SPLIT, int LOGP, int LOGTA, int LOGRPA, int TPCA, int LOGTB, int LOGRPB,
           int TPCB, int PIPE, bool INV>
 static int emu_s2(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t rb, uint64_t nr) {
-    if (p.mc == 1)
+    if (INV && p.mc == 2)
+        return emu_s2_mc<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE, INV, INV ? 2 : 1>(p, in, out, rb, nr);
+    if (p.mc >= 1)
         return emu_s2_mc<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE, INV, 1>(p, in, out, rb, nr);
     return emu_s2_mc<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE, INV, 0>(p, in, out, rb, nr);
 }

@@ -126,6 +126,40 @@ NTT_HD uint64_t reduce_65q(uint64_t x, uint32_t m, uint32_t k, uint64_t q) {
     return csub(x - (uint64_t)qe * q, q);
 }
 
+// Modulus class 2 (q < 2^50): the inverse's GS butterflies skip the
+// conditional subtraction of the sum.  Before the k-th stage of a kernel
+// every value is below B_k = 2^k 4q, so with c = B_k
+//   X + Y < B_(k+1),   X - Y + c in (0, 2 B_k),   (X - Y + c) w in [0, 4q)
+// and a kernel of at most 11 stages stays below 2^13 q < 2^63.
+NTT_HD void gs_butterfly_lazy(uint64_t& X, uint64_t& Y, uint64_t w, uint64_t wp, uint64_t q, uint64_t c) {
+    const uint64_t s = X + Y;
+    Y = shoup_mul_approx(X - Y + c, w, wp, q);
+    X = s;
+}
+
+NTT_HD void gs_butterfly_scaled_lazy(uint64_t& X, uint64_t& Y, uint64_t ninv, uint64_t ninv_p, uint64_t wn,
+                                     uint64_t wn_p, uint64_t q, uint64_t c) {
+    const uint64_t s = X + Y, d = X - Y + c;
+    X = shoup_mul_approx(s, ninv, ninv_p, q);
+    Y = shoup_mul_approx(d, wn, wn_p, q);
+}
+
+// x < 2^(k + 14) (k the bit length of q) to [0, 3q): with sh = max(k - 18, 0),
+// t = floor(x / 2^sh) < 2^32 and m = floor(2^(32 + sh) / q), Qe = floor(t m / 2^32)
+// is short of floor(x / q) by less than t / 2^32 + 2^sh / q + 1 < 2 + 2^-17.
+// Ends a class-2 inverse kernel that is not the last (its values are below
+// 2^(A + 2) q for A <= 11 stages), inside the next kernel's input bound 4q.
+NTT_HD uint64_t reduce_lazy(uint64_t x, uint32_t m, uint32_t k, uint64_t q) {
+    const uint32_t sh = k > 18 ? k - 18 : 0;
+    const uint32_t t = (uint32_t)(x >> sh);
+#if defined(__CUDA_ARCH__)
+    const uint32_t qe = __umulhi(t, m);
+#else
+    const uint32_t qe = (uint32_t)(((uint64_t)t * m) >> 32);
+#endif
+    return x - (uint64_t)qe * q;
+}
+
 // Last GS stage with the N^-1 scaling folded in:
 //   X' = (X + Y) N^-1,  Y' = (X - Y) w N^-1;   in [0, 2q) -> out [0, 2q).
 NTT_HD void gs_butterfly_scaled(uint64_t& X, uint64_t& Y, uint64_t ninv, uint64_t ninv_p,

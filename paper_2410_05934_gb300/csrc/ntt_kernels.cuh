@@ -278,7 +278,11 @@ template <int LOGN, int LOGT, int LOGRP, int TPC, int PIPE, bool INV>
 int launch_s1(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t row_begin,
               uint64_t n_rows, void* stream, uint32_t* launches) {
     int rc;
-    if (p.mc == 1)
+    // class 2 differs from class 1 only in the inverse: the forward runs the class-1 kernels
+    if (INV && p.mc == 2)
+        rc = launch_tile_kernel<TileCfg<LOGN, 0, LOGN, 0, LOGT, LOGRP, TPC, INV, INV ? 2 : 1, PIPE>>(
+            p, in, out, row_begin, n_rows, (cudaStream_t)stream);
+    else if (p.mc >= 1)
         rc = launch_tile_kernel<TileCfg<LOGN, 0, LOGN, 0, LOGT, LOGRP, TPC, INV, 1, PIPE>>(
             p, in, out, row_begin, n_rows, (cudaStream_t)stream);
     else
@@ -310,7 +314,10 @@ template <int LOGN, int SPLIT, int LOGP, int LOGTA, int LOGRPA, int TPCA, int LO
 int launch_s2(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t row_begin,
               uint64_t n_rows, void* stream, uint32_t* launches) {
     cudaStream_t st = (cudaStream_t)stream;
-    int rc = p.mc == 1
+    // class 2 differs from class 1 only in the inverse: the forward runs the class-1 kernels
+    int rc = (INV && p.mc == 2)
+        ? launch_s2_mc<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE, INV, INV ? 2 : 1>(p, in, out, row_begin, n_rows, st)
+        : p.mc >= 1
         ? launch_s2_mc<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE, INV, 1>(p, in, out, row_begin, n_rows, st)
         : launch_s2_mc<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE, INV, 0>(p, in, out, row_begin, n_rows, st);
     if (rc == NTT_OK && launches) *launches += 2;

@@ -14,7 +14,7 @@ struct PlanDev {
     int* status;
     uint32_t n_moduli;
     uint32_t check;
-    uint32_t mc;        // modulus class: 1 when every modulus is below 2^57
+    uint32_t mc;        // modulus class: 1 when every modulus is below 2^57, 2 below 2^50
     uint32_t src_mode;  // 1: the inverse's first kernel computes the CKKS tensor product;
                         // 2: the forward transform is the Rescale by aux_q (TileArgs);
                         // 3: the inverse's first kernel multiplies two rows pointwise

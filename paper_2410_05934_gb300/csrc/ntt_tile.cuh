@@ -62,12 +62,18 @@ struct LimbConst {
     uint32_t red_m;             // floor(2^(32 + red_sh) / q), red_sh = max(bits - 25, 0): reduce_65q
     uint64_t qn;                // -q^-1 mod 2^64: Montgomery products of the fused operators, whose
                                 // inverse runs on a copy of the constants with ninv, w1ninv times 2^64
+    uint32_t red2_m;            // floor(2^(32 + max(bits - 18, 0)) / q): reduce_lazy
+    uint32_t pad_;
 };
 
 // Modulus classes: 0 = any q < 2^62 (exact Shoup quotient, Harvey bounds),
 // 1 = q < 2^57 (approximate quotient, 4q-wide lazy bounds, no conditional
 // subtraction in the forward transform).
 #define NTT_SMALL_MODULUS_BITS 57
+// 2 = q < 2^50: as class 1, and the inverse's kernels of at most 11 stages
+// skip the conditional subtraction of the GS sum (values grow at most 2x per
+// stage), ending a kernel that is not the last with one reduce_lazy.
+#define NTT_LAZY_MODULUS_BITS 50
 
 #ifndef NTT_MUL_MAX_MAPPED
 #define NTT_MUL_MAX_MAPPED 32     // polynomials of one ntt_inverse_mul call with index maps
@@ -187,6 +193,8 @@ struct TileCfg {
     static constexpr int MC = MC_;
     static constexpr int MODE = MODE_;
     static constexpr bool PIPE = MODE_ == 1;
+    // class-2 inverse kernels run their GS stages without subtractions
+    static constexpr bool LAZY_GS = MC_ == 2 && INV_ && S1_ - S0_ <= 11;
     static constexpr int A = S1 - S0;
     static constexpr int LOGLO = LOGN - S1;
     static constexpr int LOGE = A + LOGP;
@@ -432,7 +440,7 @@ NTT_HD void load_direct(TileRegs<C>& st, const TileArgs& a, const TileLoc& L, in
             if (k == 1) {
                 r0 += mont_mul(u0, v0, lc.q, lc.qn);
                 r1 += mont_mul(u1, v1, lc.q, lc.qn);
-                if (C::MC != 1) {
+                if (C::MC == 0) {
                     r0 = csub(r0, lc.two_q);
                     r1 = csub(r1, lc.two_q);
                 }
@@ -730,13 +738,13 @@ NTT_HD void pass_compute(TileRegs<C>& st, const TileArgs& a, const TileLoc& L, i
                         // the butterfly's product supplies the second
                         TwPair w_lo;
                         otf_twiddle<C>(otf, k0 + off, w_lo, w);
-                        x[jl + d] = C::MC == 1 ? shoup_mul_approx(x[jl + d], w_lo.w, w_lo.wp, lc.q)
+                        x[jl + d] = C::MC >= 1 ? shoup_mul_approx(x[jl + d], w_lo.w, w_lo.wp, lc.q)
                                                : shoup_mul(x[jl + d], w_lo.w, w_lo.wp, lc.q);
                     } else {
                         NTT_GMEM_CHECK(k0 + off, 1u << C::LOGN);
                         w = load_tw(tw, k0 + off);
                     }
-                    if (C::MC == 1)
+                    if (C::MC >= 1)
                         ct_butterfly_small(x[jl], x[jl + d], w.w, w.wp, lc.q, lc.four_q);
                     else
                         ct_butterfly(x[jl], x[jl + d], w.w, w.wp, lc.q, lc.two_q);
@@ -754,7 +762,10 @@ NTT_HD void pass_compute(TileRegs<C>& st, const TileArgs& a, const TileLoc& L, i
                 for (int jl = 0; jl < GS; ++jl) {
                     if (jl & d) continue;
                     if (s == 0) {
-                        if (C::MC == 1)
+                        if (C::LAZY_GS)
+                            gs_butterfly_scaled_lazy(x[jl], x[jl + d], lc.ninv, lc.ninv_p, lc.w1ninv,
+                                                     lc.w1ninv_p, lc.q, lc.four_q << (C::S1 - 1));
+                        else if (C::MC >= 1)
                             gs_butterfly_scaled_small(x[jl], x[jl + d], lc.ninv, lc.ninv_p, lc.w1ninv,
                                                       lc.w1ninv_p, lc.q, lc.four_q);
                         else
@@ -772,12 +783,14 @@ NTT_HD void pass_compute(TileRegs<C>& st, const TileArgs& a, const TileLoc& L, i
                             NTT_GMEM_CHECK(k0 + off, 1u << C::LOGN);
                             w = load_tw(tw, k0 + off);
                         }
-                        if (C::MC == 1)
+                        if (C::LAZY_GS)     // the kernel's (S1 - 1 - s)-th stage: values below 4q 2^(S1 - 1 - s)
+                            gs_butterfly_lazy(x[jl], x[jl + d], w.w, w.wp, lc.q, lc.four_q << (C::S1 - 1 - s));
+                        else if (C::MC >= 1)
                             gs_butterfly_small(x[jl], x[jl + d], w.w, w.wp, lc.q, lc.four_q);
                         else
                             gs_butterfly(x[jl], x[jl + d], w.w, w.wp, lc.q, lc.two_q);
                         if (C::MODE == 3)   // the difference times the second factor: still [0, 2q) / [0, 4q)
-                            x[jl + d] = C::MC == 1 ? shoup_mul_approx(x[jl + d], w_hi.w, w_hi.wp, lc.q)
+                            x[jl + d] = C::MC >= 1 ? shoup_mul_approx(x[jl + d], w_hi.w, w_hi.wp, lc.q)
                                                    : shoup_mul(x[jl + d], w_hi.w, w_hi.wp, lc.q);
                     }
                 }
@@ -810,12 +823,17 @@ NTT_HD void store_tile(const TileArgs& a, const TileLoc& L, int t, const uint64_
             x = sm[b ^ c];
             y = sm[(b ^ c) ^ 1u];
         }
+        if (C::LAZY_GS && !C::LAST) {      // [0, 2^(A + 2) q) -> [0, 3q), the next kernel's input bound
+            const LimbConst& lc = a.lc[L.limb];
+            x = reduce_lazy(x, lc.red2_m, lc.bits, q);
+            y = reduce_lazy(y, lc.red2_m, lc.bits, q);
+        }
         if (C::LAST) {
-            if (C::MC == 1 && !C::INV) {  // [0, 65q) -> [0, q)
+            if (C::MC >= 1 && !C::INV) {  // [0, 65q) -> [0, q)
                 const LimbConst& lc = a.lc[L.limb];
                 x = reduce_65q(x, lc.red_m, lc.bits, q);
                 y = reduce_65q(y, lc.red_m, lc.bits, q);
-            } else if (C::MC == 1 || !C::INV) {  // [0, 4q) -> [0, q)
+            } else if (C::MC >= 1 || !C::INV) {  // [0, 4q) -> [0, q)
                 x = csub(csub(x, two_q), q);
                 y = csub(csub(y, two_q), q);
             } else {        // [0, 2q) -> [0, q)

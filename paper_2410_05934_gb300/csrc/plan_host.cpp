@@ -157,9 +157,11 @@ int build_plan_host(PlanHost& h, uint32_t log2n, const uint64_t* moduli, uint32_
     h.fwd.resize((size_t)n_moduli * n);
     h.inv.resize((size_t)n_moduli * n);
     h.consts.resize(n_moduli);
-    h.mc = 1;
-    for (uint32_t l = 0; l < n_moduli; ++l)
+    h.mc = 2;
+    for (uint32_t l = 0; l < n_moduli; ++l) {
         if (moduli[l] >= (1ull << NTT_SMALL_MODULUS_BITS)) h.mc = 0;
+        else if (moduli[l] >= (1ull << NTT_LAZY_MODULUS_BITS) && h.mc == 2) h.mc = 1;
+    }
     std::vector<uint64_t> pw(n), pwi(n);
     std::vector<uint32_t> rev(n);
     for (uint64_t k = 0; k < n; ++k) rev[k] = brv((uint32_t)k, log2n);
@@ -213,6 +215,7 @@ int build_plan_host(PlanHost& h, uint32_t log2n, const uint64_t* moduli, uint32_
         }
         c.bits = bit_length(q);
         c.mu = (uint64_t)(((u128)1 << (2 * c.bits)) / q);
+        c.red2_m = (uint32_t)(((u128)1 << (32 + (c.bits > 18 ? c.bits - 18 : 0))) / q);
         {
             const uint32_t sh = c.bits > 25 ? c.bits - 25 : 0;
             c.red_m = (uint32_t)(((u128)1 << (32 + sh)) / q);

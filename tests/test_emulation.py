@@ -8,18 +8,31 @@ from paper_2410_05934_gb300 import workloads as W
 import emu
 
 
+def _primes_below(bits, log2n, count):
+    """The largest `count` primes below 2^bits that are 1 mod 2^(log2n + 1)."""
+    from oracle import oracle as O
+    step = 1 << (log2n + 1)
+    q, out = ((1 << bits) - 1) // step * step + 1, []
+    while len(out) < count:
+        if O.is_prime(q):
+            out.append(q)
+        q -= step
+    return out
+
+
 def _moduli(log2n, cls="big"):
-    """big: 59/62-bit moduli (exact-quotient class); small: 50-bit (approximate class)."""
-    if log2n <= 10 and cls == "big":
-        return [W.Q62_N1024, W.Q59_N1024]
+    """big: 59..62-bit moduli (exact-quotient class 0); mid: 55-bit (class 1,
+    approximate quotients); small: 50-bit (class 2, also lazy inverse sums)."""
+    if cls == "big":
+        return [W.Q62_N1024, W.Q59_N1024] if log2n <= 10 else _primes_below(62, log2n, 2)
+    if cls == "mid":
+        return _primes_below(55, max(log2n, 16), 2)
     return [W.POOL50[0], W.POOL50[7]]
 
 
-@pytest.mark.parametrize("cls", ["big", "small"])
+@pytest.mark.parametrize("cls", ["big", "mid", "small"])
 @pytest.mark.parametrize("log2n", range(1, 17))
 def test_every_schedule_matches_oracle(oracle, log2n, cls):
-    if cls == "big" and log2n > 10:
-        pytest.skip("no 59/62-bit prime is 1 mod 2N beyond N = 1024")
     n = 1 << log2n
     mods = _moduli(log2n, cls)
     batch = 2
