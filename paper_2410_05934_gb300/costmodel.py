@@ -6,7 +6,7 @@ every candidate schedule of a shape from (log2 N, limbs, batch, modulus
 bits); the schedule with the smallest prediction is chosen.  It is trained on
 timings the autotuner measures, on the GPU, by the library's own forward,
 backward and Adam kernels (C ABI ``ntt_mlp_*``); exhaustive autotuning stays
-the fallback for shapes in the timing DB and the judge of the model's regret.
+the fallback for shapes in the timing DB and the yardstick of the model's regret.
 
 Features (all in [0, 1] over the supported range):
   (log2 N - 10) / 6,  log2(limbs) / 6,  log2(batch) / 12,  (bits - 50) / 12
