@@ -21,12 +21,12 @@ def _primes_below(bits, log2n, count):
 
 
 def _moduli(log2n, cls="big"):
-    """big: 59..62-bit moduli (exact-quotient class 0); mid: 55-bit (class 1,
+    """big: 59..62-bit moduli (exact-quotient class 0); mid: the largest below 2^57 (class 1,
     approximate quotients); small: 50-bit (class 2, also lazy inverse sums)."""
     if cls == "big":
         return [W.Q62_N1024, W.Q59_N1024] if log2n <= 10 else _primes_below(62, log2n, 2)
     if cls == "mid":
-        return _primes_below(55, max(log2n, 16), 2)
+        return _primes_below(57, max(log2n, 16), 2)
     return [W.POOL50[0], W.POOL50[7]]
 
 
@@ -519,3 +519,30 @@ def test_products_at_the_largest_residues(log2n):
                         for _ in range(8)]).astype(np.uint32)
         want = O.transform_rows(prod, [mods[k % 2] for k in range(8)], inverse=True, idx=idx)
         assert np.array_equal(got[np.arange(8)[:, None], idx], want)
+
+
+@pytest.mark.parametrize("log2n", [12, 13, 16])
+@pytest.mark.parametrize("cls", ["big", "mid", "small"])
+def test_largest_residues_every_schedule(oracle, log2n, cls):
+    """Inputs q - 1 (and q - 1 alternating with 0) drive every lazy bound to
+    its largest value; with the largest primes of each modulus class every
+    schedule must still give the oracle's outputs and round trip."""
+    n = 1 << log2n
+    mods = _moduli(log2n, cls)
+    x = np.zeros((4, n), dtype=np.uint64)
+    x[0, :] = mods[0] - 1
+    x[1, :] = mods[1] - 1
+    x[2, ::2] = mods[0] - 1
+    x[3, 1::2] = mods[1] - 1
+    per_row = [mods[r % 2] for r in range(4)]
+    rng = np.random.default_rng(log2n)
+    idx = np.stack([np.concatenate([[0, 1, n - 1], rng.integers(0, n, 9)]) for _ in per_row]).astype(np.uint32)
+    r = np.arange(4)[:, None]
+    want = oracle.transform_rows(x, per_row, idx=idx)
+    want_inv = oracle.transform_rows(x, per_row, inverse=True, idx=idx)
+    plan = emu.EmuPlan(log2n, mods, 2)
+    for s in range(emu.schedule_count(log2n)):
+        fwd = plan.transform(x, s)
+        assert np.array_equal(fwd[r, idx], want), s
+        assert np.array_equal(plan.transform(fwd, s, inverse=True), x), s
+        assert np.array_equal(plan.transform(x, s, inverse=True)[r, idx], want_inv), s

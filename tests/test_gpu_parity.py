@@ -31,12 +31,12 @@ def _primes_below(bits, log2n, count):
 
 
 def _moduli(log2n, cls="big"):
-    """big: 59..62-bit moduli (exact-quotient class 0); mid: 55-bit (class 1,
+    """big: 59..62-bit moduli (exact-quotient class 0); mid: the largest below 2^57 (class 1,
     approximate quotients); small: 50-bit (class 2, also lazy inverse sums)."""
     if cls == "big":
         return [W.Q62_N1024, W.Q59_N1024] if log2n <= 10 else _primes_below(62, log2n, 2)
     if cls == "mid":
-        return _primes_below(55, 16, 2)
+        return _primes_below(57, 16, 2)
     return [W.POOL50[0], W.POOL50[7]]
 
 
