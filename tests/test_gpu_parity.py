@@ -474,3 +474,33 @@ def test_otf_twiddle_plans(oracle, log2n):
     for log2n_, flags in [(9, ntt.NTT_FLAG_OTF_TWIDDLES), (12, ntt.NTT_FLAG_OTF_TWIDDLES | ntt.NTT_FLAG_NATURAL_ORDER)]:
         with pytest.raises(ntt.NttError):
             ntt.Plan(log2n_, [W.POOL50[0]], 1, flags=flags)
+
+
+@pytest.mark.parametrize("log2n", [12, 13, 16])
+@pytest.mark.parametrize("cls", ["big", "mid", "small"])
+def test_largest_residues_every_schedule(oracle, log2n, cls):
+    """Inputs q - 1 (and q - 1 alternating with 0) with the largest primes of
+    each modulus class drive every lazy bound to its largest value."""
+    n = 1 << log2n
+    mods = _moduli(log2n, cls)
+    x = np.zeros((4, n), dtype=np.uint64)
+    x[0, :] = mods[0] - 1
+    x[1, :] = mods[1] - 1
+    x[2, ::2] = mods[0] - 1
+    x[3, 1::2] = mods[1] - 1
+    per_row = [mods[r % 2] for r in range(4)]
+    idx = _sample_idx(n, 4, 9, log2n)
+    r = np.arange(4)[:, None]
+    want = oracle.transform_rows(x, per_row, idx=idx)
+    want_inv = oracle.transform_rows(x, per_row, inverse=True, idx=idx)
+    plan = ntt.Plan(log2n, mods, 2)
+    dx = to_dev(x)
+    for s in range(ntt.schedule_count(log2n)):
+        plan.schedule = s
+        fwd, back, inv = torch.empty_like(dx), torch.empty_like(dx), torch.empty_like(dx)
+        plan.forward(dx, fwd)
+        assert np.array_equal(to_host(fwd)[r, idx], want), s
+        plan.inverse(fwd, back)
+        assert torch.equal(back, dx), s
+        plan.inverse(dx, inv)
+        assert np.array_equal(to_host(inv)[r, idx], want_inv), s
