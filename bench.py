@@ -123,6 +123,26 @@ class ClockSampler:
 
 # ---------------------------------------------------------- CPU baseline --
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
 def oracle_sample(seconds_target, nthreads=None):
     """Times the C oracle (O(N^2) definitions) on a bounded sample of the
     workload: forward outputs and inverse outputs of rows of the same batch.
@@ -231,7 +251,7 @@ def run_reference(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "log2n": LOG2N, "limbs": LIMBS, "polys": POLYS},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "cpu": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -469,7 +489,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, desc, dt = oracle_sample(args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": desc, "seconds": dt}
+                                "sample": desc, "seconds": dt, "cpu": cpu_model()}
         v2, cores2, dt2 = radix2_sample()
         line["cpu_radix2"] = {"value": v2, "unit": UNIT, "cores": cores2,
                               "kind": "plain radix-2 O(N log N) transforms, Shoup twiddles (oracle/ntt_radix2.c)",
@@ -1117,6 +1137,15 @@ def run_cost_model(args):
     import torch
     torch.cuda.set_device(dist_env()[2])
     model, rep = CM.train_and_evaluate(steps=4000)
+    # what the model replaces: exhaustive autotuning of a shape (every candidate
+    # schedule timed, as the sweep does), on three held-out-sized shapes
+    import tempfile
+    from paper_2410_05934_gb300 import tune as T
+    shapes = [(16, 24, 4, 50), (14, 8, 32, 50), (10, 1, 3780, 62)]
+    with tempfile.TemporaryDirectory() as tmp:
+        t0 = time.perf_counter()
+        T.sweep(shapes, db=os.path.join(tmp, "t.jsonl"), reps=5, skip_done=False)
+        exhaustive_ms = 1e3 * (time.perf_counter() - t0) / len(shapes)
     line = {"metric": "schedule regret vs exhaustive autotuning (mean over held-out shapes)",
             "value": rep["mlp"]["mean"], "unit": "fraction", "n_gpus": 1, "steps": rep["train"]["train_steps"],
             "warmup": 0, "ms_per_step": 1e3 * rep["train"]["train_seconds"] / rep["train"]["train_steps"],
@@ -1125,7 +1154,9 @@ def run_cost_model(args):
             "config": {"workload": "cost_model", "mlp": "4-64-64-12 ReLU, FP32, Adam, cosine lr",
                        "train_shapes": rep["train"]["train_shapes"], "heldout_shapes": rep["mlp"]["n"]},
             "regret": {"mlp": rep["mlp"], "sm_rule": rep["sm_rule"], "default": rep["default"]},
-            "decision_us": rep["decision_us"], "train_seconds_gpu": rep["train"]["train_seconds"]}
+            "decision_us": rep["decision_us"], "train_seconds_gpu": rep["train"]["train_seconds"],
+            "exhaustive_tuning_ms_per_shape": exhaustive_ms,
+            "exhaustive_shapes": ["N=2^%d limbs=%d batch=%d %d-bit" % sh for sh in shapes]}
     print(json.dumps(line))
     return 0
 
