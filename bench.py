@@ -51,7 +51,7 @@ def parse():
                     help="mixed batches: requests of at least 2^k coefficients run their own learned schedule")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "mixed_batch", "tfhe_blind_rotation", "plain_n1024", "cost_model",
-                             "serving", "hmul_fused", "mixed_small", "tfhe_cmux", "ckks_bconv", "otf_twiddles",
+                             "serving", "hmul_fused", "mixed_small", "tfhe_cmux", "ckks_bconv", "otf_twiddles", "n_sweep",
                              "ckks_rescale", "natural_order", "word32"],
                     help="the line the driver records is the default (CKKS-HMUL-shaped) workload")
     return ap.parse_args()
@@ -1062,6 +1062,70 @@ def run_otf_twiddles(args):
     return 0
 
 
+def run_n_sweep(args):
+    """Forward + inverse throughput for every N from 2^10 to 2^16 on a batch of
+    2^25 coefficients (8 limbs of the 50-bit pool, 256 MB per buffer, larger
+    than L2), each N on its default schedule; roofline fraction against the
+    in-run butterfly probe.  One JSON line, the per-N results under "sizes"."""
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2410_05934_gb300 import build as B
+    B.build_product()
+    import paper_2410_05934_gb300 as ntt
+    from paper_2410_05934_gb300 import _native
+    from paper_2410_05934_gb300 import workloads as W
+    L_ = _native.load()
+    stream = torch.cuda.current_stream()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mods = W.POOL50[:8]
+    total = 1 << 25
+    peak = _probe(torch, L_, mods[0], 2, sms, stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    g = torch.Generator(device="cuda")
+    g.manual_seed(W.DEFAULT_SEED + rank)
+    x = torch.randint(0, 1 << 49, (total,), dtype=torch.int64, device="cuda", generator=g)   # < every q
+    y = torch.empty_like(x)
+    sizes, all_ms, launches = [], [], 0
+    for log2n in range(10, 17):
+        n = 1 << log2n
+        batch = total // (n * len(mods))
+        plan = ntt.Plan(log2n, mods, batch)
+
+        def step(p=plan):
+            p.forward(x, y)
+            k = p.last_launches()
+            p.inverse(y, y)
+            return k + p.last_launches()
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        ms, k = _events_loop(torch, stream, args.steps, step, flush)
+        launches += k
+        t = sum(ms) * 1e-3 / args.steps
+        bfly = 2 * (total // 2) * log2n
+        sizes.append({"log2n": log2n, "rows": batch * len(mods), "schedule": plan.schedule,
+                      "ms_per_step": 1e3 * t, "coeffs_per_s": 2 * total / t,
+                      "frac": bfly / t / peak})
+        all_ms.append(t)
+        plan.close()
+    t_all = sum(all_ms)
+    line = {"metric": "NTT coeffs/s (coefficient-transforms per second)", "value": 2 * total * len(sizes) / t_all,
+            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_all, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64", "data": "synthetic", "gpu_launches": launches,
+            "config": {"workload": "n_sweep", "coefficients_per_size": total, "limbs": len(mods),
+                       "step": "forward + inverse of 2^25 coefficients at each N = 2^10 .. 2^16",
+                       "l2": "inputs (256 MB) > L2; flushed before every step"},
+            "roofline": {"bound": "alu", "peak": peak / 1e9, "unit": "Gbutterfly/s",
+                         "frac": min(sz["frac"] for sz in sizes), "traffic": None,
+                         "peak_source": "in-run butterfly probe (kind 2); frac is the smallest over N"},
+            "sizes": sizes}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def run_word32(args):
     """The TFHE blind-rotation-shaped batch (3780 forward + 1260 inverse rows
     at N = 1024) with a 30-bit prime on 32-bit words (NTT_FLAG_WORD32),
@@ -1205,6 +1269,8 @@ def main():
         return run_tfhe_cmux(args)
     if args.workload == "otf_twiddles":
         return run_otf_twiddles(args)
+    if args.workload == "n_sweep":
+        return run_n_sweep(args)
     if args.workload == "ckks_bconv":
         return run_ckks_bconv(args)
     if args.workload == "ckks_rescale":
