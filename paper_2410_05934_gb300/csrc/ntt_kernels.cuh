@@ -116,10 +116,22 @@ __device__ __forceinline__ void run_passes(TileRegs<C>& st, const TileArgs& a, c
     }
 }
 
+// Programmatic dependent launch: the direct-form kernels are launched with
+// programmatic stream serialization, so the next kernel on the stream may be
+// scheduled once every CTA of this one has started (its CTAs then fill the
+// SMs this grid's last wave leaves idle); griddepcontrol.wait holds a kernel
+// until the previous grid has completed and its writes are visible, before
+// it touches global data.  Without the launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_begin() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // ---- direct form: one CTA = TPC tiles, loaded with 16-byte loads ----
 template <class C>
 __global__ void __launch_bounds__(C::THREADS) k_ntt_tile(TileArgs a) {
     extern __shared__ __align__(16) uint64_t smem[];
+    pdl_begin();
     const int tid = threadIdx.x;
     const int tin = tid >> C::LOGT;
     const int t = tid & (C::T - 1);
@@ -269,7 +281,17 @@ int launch_tile_kernel(const PlanDev& p, const uint64_t* in, uint64_t* out, uint
             cudaFuncSetAttribute(k_ntt_tile<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_BYTES) !=
                 cudaSuccess)
             return NTT_ERR_CUDA;
-        k_ntt_tile<C><<<(unsigned)groups, C::THREADS, C::SMEM_BYTES, st>>>(a);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)groups);
+        cfg.blockDim = dim3(C::THREADS);
+        cfg.dynamicSmemBytes = C::SMEM_BYTES;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (cudaLaunchKernelEx(&cfg, k_ntt_tile<C>, a) != cudaSuccess) return NTT_ERR_CUDA;
     }
     return cudaPeekAtLastError() == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
 }
