@@ -18,6 +18,7 @@ __global__ void __launch_bounds__(CmuxCfg<LOGN, MC>::THREADS, CmuxCfg<LOGN, MC>:
     using F = typename K::F;
     using I = typename K::I;
     extern __shared__ __align__(16) uint64_t smem[];
+    pdl_begin();     // consecutive CMux steps: launched early, reading only after the previous step
     const int s = threadIdx.x >> K::LOGT;
     const int t = threadIdx.x & (K::T - 1);
     uint64_t* sm = smem + (size_t)s * K::N;
@@ -68,8 +69,17 @@ static int launch_cmux(const CmuxArgs& c, const TileArgs& af, const TileArgs& ai
     // enough CTAs for several waves; each walks ciphertexts ct, ct + grid, ...
     const uint64_t cap = (uint64_t)std::max(1, sms) * (uint64_t)std::max(1, per_sm) * 16u;
     const unsigned grid = (unsigned)std::min<uint64_t>(c.n_ct, cap);
-    k_tfhe_cmux<LOGN, MC><<<grid, K::THREADS, K::SMEM_BYTES, st>>>(c, af, ai);
-    return cudaPeekAtLastError() == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(K::THREADS);
+    cfg.dynamicSmemBytes = K::SMEM_BYTES;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_tfhe_cmux<LOGN, MC>, c, af, ai) == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
 }
 
 // Shared argument checks of both entry points; fills c (not in/rot/out) and
