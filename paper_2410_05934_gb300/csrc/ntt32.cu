@@ -25,6 +25,7 @@ __device__ __forceinline__ void run_passes32(Regs32<C>& st, const Args32& a, con
 template <class C>
 __global__ void __launch_bounds__(C::THREADS) k_ntt32(Args32 a) {
     extern __shared__ __align__(16) uint32_t smem32[];
+    pdl_begin();
     const int tin = threadIdx.x >> C::LOGT;
     const int t = threadIdx.x & (C::T - 1);
     const Loc32 L = locate32<C>(a, blockIdx.x, tin);
@@ -42,8 +43,17 @@ static int launch32_n(const Args32& a, cudaStream_t st) {
     const uint64_t ctas = ((uint64_t)a.n_rows + C::TPC - 1) / C::TPC;
     if (ctas == 0) return NTT_OK;
     if (ctas > 0x7fffffffull) return NTT_ERR_ARG;
-    k_ntt32<C><<<(unsigned)ctas, C::THREADS, sizeof(uint32_t) * C::E * C::TPC, st>>>(a);
-    return cudaPeekAtLastError() == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
+    cudaLaunchConfig_t cfg = {};       // programmatic dependent launch, as the 64-bit tile kernels
+    cfg.gridDim = dim3((unsigned)ctas);
+    cfg.blockDim = dim3(C::THREADS);
+    cfg.dynamicSmemBytes = sizeof(uint32_t) * C::E * C::TPC;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_ntt32<C>, a) == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
 }
 
 #define NTT32_CASE(LOGN) \
