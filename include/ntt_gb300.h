@@ -22,7 +22,12 @@
  *  - Device pointers are caller-owned CUDA device memory, 16-byte aligned.
  *    Calls are asynchronous on the given stream (a cudaStream_t passed as
  *    void*, NULL = legacy default stream).  Launch errors are returned at
- *    once; errors detected inside kernels are read with ntt_status().
+ *    once; errors detected inside kernels are read with ntt_status().  The
+ *    transform and CMux kernels are launched with programmatic stream
+ *    serialization: a kernel may be scheduled while the previous kernel of
+ *    the stream finishes, but reads nothing before that kernel has completed
+ *    and its writes are visible, so stream order holds as for plain launches
+ *    (and a caller's own launches, without that attribute, wait as usual).
  *  - Inputs must be canonical (< q of their row); with NTT_FLAG_CHECK the
  *    kernels verify this and report NTT_ERR_RANGE through ntt_status().
  *  - Data layout: [batch][n_moduli][N] uint64, row r = b * n_moduli + l uses
