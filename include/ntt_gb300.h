@@ -254,6 +254,31 @@ int ntt_bench_butterflies(uint64_t q, uint32_t kind, uint32_t blocks, uint32_t t
                           uint32_t iters, uint64_t* d_sink, void* cuda_stream);
 
 /*
+ * Test aid for the bounded device-side waits.  The paper has no counterpart:
+ * its kernels synchronise with barriers that have no time limit, while every
+ * wait of this library on an mbarrier (the pipelined transform form) gives
+ * up after a fixed number of rounds, records NTT_ERR_TIMEOUT and returns, so
+ * that a lost copy leaves the context usable.  This call makes that path
+ * observable without any fault.
+ * Launches one CTA of 32 threads that arms an mbarrier for 16 bytes and
+ * waits on it with the same bounded wait, for at most `spin_limit` try_wait
+ * rounds (1 .. NTT_DEBUG_SPIN_LIMIT_MAX; each round suspends the warp for a
+ * hardware-chosen interval).
+ *  - deliver != 0: one 16-byte bulk copy of the plan's first forward twiddle
+ *    pair {w, w'} completes the barrier; the pair is written to d_out
+ *    (2 uint64, caller-owned device memory, 16-byte aligned; may be NULL).
+ *  - deliver == 0: no copy is issued, the wait runs out, and the kernel
+ *    records NTT_ERR_TIMEOUT in the plan's status word (read and cleared by
+ *    ntt_status).  Nothing is in flight when the CTA returns.
+ * Errors: NTT_ERR_ARG for a NULL, host-only or 32-bit-word plan, a spin limit
+ * out of range or a misaligned d_out; NTT_ERR_CUDA if the launch fails.
+ * Asynchronous on cuda_stream.
+ */
+#define NTT_DEBUG_SPIN_LIMIT_MAX (1u << 22)
+int ntt_debug_bounded_wait(ntt_plan_t plan, uint32_t deliver, uint32_t spin_limit, uint64_t* d_out,
+                           void* cuda_stream);
+
+/*
  * Uneven mixed batches (Sec. IV-A's batching of many independent transforms
  * into one launch, applied to whole requests): many requests of different N,
  * limb count, polynomial count and direction run in ONE persistent kernel

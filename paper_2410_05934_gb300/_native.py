@@ -55,6 +55,7 @@ SIGNATURES = [
     ("ntt_status", i32, [vp, vp]),
     ("ntt_plan_last_launches", i32, [vp, U32P]),
     ("ntt_bench_butterflies", i32, [u64, u32, u32, u32, u32, vp, vp]),
+    ("ntt_debug_bounded_wait", i32, [vp, u32, u32, vp, vp]),
     ("ntt_batch_plan", i32, [ctypes.POINTER(vp), REQP, u32, U64P, u32, u32]),
     ("ntt_batch_update", i32, [vp, REQP, u32, vp]),
     ("ntt_batch_execute", i32, [vp, vp]),

@@ -560,6 +560,15 @@ int ntt_plan_last_launches(ntt_plan_t plan, uint32_t* launches) {
     return NTT_OK;
 }
 
+int ntt_debug_bounded_wait(ntt_plan_t plan, uint32_t deliver, uint32_t spin_limit, uint64_t* d_out,
+                           void* cuda_stream) {
+    if (!plan || spin_limit == 0 || spin_limit > NTT_DEBUG_SPIN_LIMIT_MAX) return NTT_ERR_ARG;
+    int rc = check_device(plan);
+    if (rc) return rc;
+    if (!plan->d_fwd || (d_out && !aligned16(d_out))) return NTT_ERR_ARG;
+    return launch_debug_bounded_wait(plan->d_fwd, deliver, spin_limit, plan->d_status, d_out, cuda_stream);
+}
+
 int ntt_bench_butterflies(uint64_t q, uint32_t kind, uint32_t blocks, uint32_t threads,
                           uint32_t iters, uint64_t* d_sink, void* cuda_stream) {
     if (q < 3 || q >= (1ull << NTT_MAX_MODULUS_BITS) || kind > 5 ||

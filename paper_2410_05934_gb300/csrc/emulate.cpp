@@ -745,6 +745,46 @@ int nttemu_reduce_65q(void* plan, uint32_t limb, const uint64_t* x, uint64_t* ou
     return NTT_OK;
 }
 
+// The bounded-wait test kernel of ntt_debug_bounded_wait on a host model of
+// its mbarrier: one expected arrival that announces 16 transaction bytes; the
+// phase completes once the arrival has happened and the announced bytes have
+// all been delivered.  With `deliver` the 16-byte copy of the plan's first
+// forward twiddle pair lands before the wait; without, nothing delivers, the
+// wait gives up after `spin_limit` rounds and the status records the timeout.
+int nttemu_debug_bounded_wait(void* plan, uint32_t deliver, uint32_t spin_limit, uint64_t* out) {
+    EmuPlan* p = static_cast<EmuPlan*>(plan);
+    if (!p || spin_limit == 0 || spin_limit > NTT_DEBUG_SPIN_LIMIT_MAX || p->h.fwd.empty()) return NTT_ERR_ARG;
+    struct {
+        uint32_t arrivals_left;
+        int64_t tx;
+        uint32_t phase;
+    } bar{1, 0, 0};
+    auto settle = [&]() {
+        if (bar.arrivals_left == 0 && bar.tx == 0) bar.phase ^= 1u;
+    };
+    uint64_t buf[2] = {0, 0};
+    bar.tx += 16;             // arrive.expect_tx(16)
+    bar.arrivals_left -= 1;
+    settle();
+    if (deliver) {            // the bulk copy completes its bytes
+        buf[0] = p->h.fwd[0].w;
+        buf[1] = p->h.fwd[0].wp;
+        bar.tx -= 16;
+        settle();
+    }
+    bool ok = false;
+    for (uint32_t i = 0; i < spin_limit && !ok; ++i) ok = bar.phase != 0;   // try_wait.parity 0
+    if (!ok) {
+        if (p->status == 0) p->status = NTT_STATUS_TIMEOUT;
+        return NTT_OK;
+    }
+    if (out) {
+        out[0] = buf[0];
+        out[1] = buf[1];
+    }
+    return NTT_OK;
+}
+
 int nttemu_status(void* plan) {
     EmuPlan* p = static_cast<EmuPlan*>(plan);
     int s = p->status;

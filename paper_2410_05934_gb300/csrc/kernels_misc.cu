@@ -6,6 +6,7 @@
 #include <algorithm>
 
 #include "ntt_gb300.h"
+#include "ntt_kernels.cuh"
 #include "ntt_launch.h"
 #include "ntt32.cuh"
 
@@ -171,6 +172,46 @@ int launch_bench_bfly(uint64_t q, uint32_t kind, uint32_t blocks, uint32_t threa
         case 3: k_bench_bfly<3><<<blocks, threads, 0, st>>>(q, w, wp, iters, sink); break;
         default: k_bench_bfly<4><<<blocks, threads, 0, st>>>(q, w, wp, iters, sink); break;
     }
+    return cudaPeekAtLastError() == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
+}
+
+// Test aid for the bounded waits: one CTA arms an mbarrier for 16 bytes and
+// waits on it with the transform kernels' bounded wait.  With `deliver` one
+// bulk copy of 16 bytes completes it; without, nothing ever arrives, the wait
+// runs out after `limit` rounds and the status word records the timeout.
+// Nothing is in flight when the CTA leaves: the only copy is issued when
+// `deliver` is set, and then the wait ends by its completion (or, if even that
+// copy were lost, after the bound, a copy that never writes).
+__global__ void __launch_bounds__(32) k_debug_bounded_wait(const uint64_t* src, uint32_t deliver, uint32_t limit,
+                                                          int* status, uint64_t* out) {
+    __shared__ __align__(16) uint64_t buf[2];
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        buf[0] = buf[1] = 0;
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&bar, 16);
+        if (deliver) bulk_load(buf, src, 16, &bar);
+    }
+    const bool ok = mbar_wait_bounded(&bar, 0, limit);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) record_status(status, NTT_STATUS_TIMEOUT);
+        return;
+    }
+    if (threadIdx.x == 0 && out) {
+        out[0] = buf[0];
+        out[1] = buf[1];
+    }
+}
+
+int launch_debug_bounded_wait(const void* src, uint32_t deliver, uint32_t limit, int* status, uint64_t* out,
+                              void* stream) {
+    k_debug_bounded_wait<<<1, 32, 0, (cudaStream_t)stream>>>(static_cast<const uint64_t*>(src), deliver, limit,
+                                                            status, out);
     return cudaPeekAtLastError() == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
 }
 

@@ -44,8 +44,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // Bounded wait: each try_wait suspends for a hardware-chosen interval, so
 // the iteration limit bounds the total time; false means it ran out.
 #define NTT_MBAR_SPIN_LIMIT (1u << 22)
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (uint32_t i = 0; i < NTT_MBAR_SPIN_LIMIT; ++i)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  uint32_t limit = NTT_MBAR_SPIN_LIMIT) {
+    for (uint32_t i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -199,9 +200,16 @@ __global__ void __launch_bounds__(C::THREADS) k_ntt_tile_pipe(TileArgs a, uint64
         const bool ok = mbar_wait_bounded(&bars[b], (parity >> b) & 1u);
         parity ^= 1u << b;
         if (__syncthreads_or(!ok)) {
-            // a copy never completed: report, wait (bounded) for the other
-            // buffer's copies in flight, and leave
+            // A copy of buffer b did not complete within the bound.  Report it,
+            // then wait once more (bounded) on BOTH buffers before leaving: on
+            // b, whose late copy may still be writing, and on b ^ 1, whose
+            // copies for the next group were issued above.  A CTA must not
+            // exit while a bulk copy may still write its shared memory (the
+            // next CTA on the SM could own those bytes by then); a copy that
+            // is still pending after a second full bound is taken as lost,
+            // i.e. one that never writes.
             if (tid == 0) record_status(a.status, NTT_STATUS_TIMEOUT);
+            (void)mbar_wait_bounded(&bars[b], ((parity >> b) & 1u) ^ 1u);   // the phase waited on above
             if (gn < groups) (void)mbar_wait_bounded(&bars[b ^ 1], (parity >> (b ^ 1)) & 1u);
             return;
         }

@@ -69,6 +69,12 @@ int launch_bitrev_rows(const uint64_t* in, uint64_t* out, uint64_t row_begin, ui
 int launch_bench_bfly(uint64_t q, uint32_t kind, uint32_t blocks, uint32_t threads, uint32_t iters,
                       uint64_t* sink, void* stream);
 
+// one CTA waiting, bounded, on an mbarrier that only a 16-byte copy from src
+// completes (issued when deliver != 0); records NTT_STATUS_TIMEOUT when the
+// wait runs out
+int launch_debug_bounded_wait(const void* src, uint32_t deliver, uint32_t limit, int* status, uint64_t* out,
+                              void* stream);
+
 struct SchedEntry {
     uint32_t log2n;
     uint32_t kernels;

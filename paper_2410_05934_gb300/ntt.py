@@ -141,6 +141,15 @@ class Plan:
         """Synchronises the stream; returns and clears the device status word."""
         return load().ntt_status(self._h, _stream_handle(stream))
 
+    def debug_bounded_wait(self, deliver, spin_limit, out=None, stream=None):
+        """ntt_debug_bounded_wait: one CTA waits (bounded) on an mbarrier that a
+        16-byte copy completes only when `deliver`; otherwise the wait runs out
+        and the status word records NTT_ERR_TIMEOUT.  `out` (2 uint64 on the
+        device, optional) receives the copied pair."""
+        ptr = None if out is None else _ptr(out, 2, "out")
+        check(load().ntt_debug_bounded_wait(self._h, 1 if deliver else 0, spin_limit, ptr, _stream_handle(stream)),
+              "ntt_debug_bounded_wait")
+
     # -- compute --
     def forward(self, x, out=None, stream=None):
         out = x if out is None else out

@@ -22,6 +22,8 @@ def lib():
         L.nttemu_transform.restype = i32
         L.nttemu_pointwise.argtypes = [vp, U64P, U64P, U64P, u64]
         L.nttemu_status.argtypes = [vp]
+        L.nttemu_debug_bounded_wait.argtypes = [vp, u32, u32, U64P]
+        L.nttemu_debug_bounded_wait.restype = i32
         L.nttemu_batch_transform.argtypes = [vp, i32, U64P, U64P]
         L.nttemu_batch_transform.restype = i32
         L.nttemu_hmul_tensor.argtypes = [vp, u32, U64P, U64P, U64P]
@@ -172,6 +174,11 @@ class EmuPlan:
 
     def status(self):
         return lib().nttemu_status(self.h)
+
+    def debug_bounded_wait(self, deliver, spin_limit):
+        out = np.zeros(2, dtype=np.uint64)
+        rc = lib().nttemu_debug_bounded_wait(self.h, 1 if deliver else 0, spin_limit, _p(out))
+        return rc, out
 
 
 def bconv(x, Q, P):

@@ -504,3 +504,25 @@ def test_largest_residues_every_schedule(oracle, log2n, cls):
         assert torch.equal(back, dx), s
         plan.inverse(dx, inv)
         assert np.array_equal(to_host(inv)[r, idx], want_inv), s
+
+
+def test_word32_back_to_back_in_place(oracle):
+    """In-place 32-bit transforms issued back to back with no host
+    synchronisation (each launch may start while the previous finishes):
+    forward, inverse, forward again equals the oracle's forward; one more
+    inverse gives the input back."""
+    q = Q30[0]
+    x = W.rows_uniform(37, 10, [q] * 2048, 1024)
+    p = ntt.Plan(10, [q], 2048, flags=ntt.NTT_FLAG_WORD32)
+    d = _to_dev32(x)
+    ref_in = d.clone()
+    torch.cuda.synchronize()
+    p.forward(d)
+    p.inverse(d)
+    p.forward(d)
+    got = _to_host32(d)
+    rows = np.array([0, 5, 1024, 2047])
+    assert np.array_equal(got[rows], oracle.transform_rows(x[rows], [q] * 4))
+    p.inverse(d)
+    assert torch.equal(d, ref_in)
+    assert p.status() == 0

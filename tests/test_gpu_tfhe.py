@@ -132,3 +132,28 @@ def test_full_size_cmux_step_as_benchmarked():
         idx = sorted(set([0, 1023] + rng.integers(0, 1024, 6).tolist()))
         assert np.array_equal(got[c][:, idx], TO.cmux_rotate(w["acc"][c], int(w["rot"][0][c]), w["key"][0], q,
                                                              log2_base, levels, key_coef=kc, idx=idx)), c
+
+
+def test_back_to_back_cmux_steps_match_the_oracle_chain():
+    """Consecutive in-place CMux launches with nothing between them on the
+    stream, as in a blind rotation: every key and rotation tensor is prepared
+    first, then six steps are issued with no host synchronisation, so each
+    launch may be scheduled while the previous one finishes (programmatic
+    dependent launch) and must still read only its finished output.  600
+    ciphertexts give more than one wave of CTAs per launch."""
+    q, log2n, levels, log2_base, steps = W.Q62_N1024, 10, 3, 8, 6
+    w = W.tfhe_cmux(seed=21, n_ct=600, log2n=log2n, q=q, levels=levels, steps=steps)
+    plan = ntt.Plan(log2n, [q])
+    keys = [plan.tfhe_key_prepare(to_dev(w["key"][s]), levels) for s in range(steps)]
+    rots = [_rot_dev(w["rot"][s]) for s in range(steps)]
+    x = to_dev(w["acc"])
+    torch.cuda.synchronize()
+    for s in range(steps):
+        plan.tfhe_cmux_rotate(x, rots[s], keys[s], levels, log2_base)
+    got = to_host(x)
+    assert plan.status() == 0
+    for c in (0, 599):
+        ref = w["acc"][c].copy()
+        for s in range(steps):
+            ref = TO.cmux_rotate(ref, int(w["rot"][s][c]), w["key"][s], q, log2_base, levels)
+        assert np.array_equal(got[c], ref), c

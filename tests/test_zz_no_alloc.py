@@ -72,3 +72,28 @@ def test_static_entry_point_rejects_too_many_requests():
     reqs = _requests([p] * n, [x] * n, [x] * n, [0] * n)
     assert L.ntt_batch_execute_static(reqs, n, None) == -1
     assert L.ntt_batch_execute_static(reqs, 0, None) == -1
+
+
+def test_static_entry_point_allocates_no_device_memory():
+    """The property the entry point exists for: once its per-device set-up has
+    run (the first call), further calls leave the device's free memory and
+    torch's allocated bytes exactly as they were."""
+    L = _native.load()
+    stream = torch.cuda.current_stream()
+    plans, ins = [], []
+    for k, (log2n, limbs, polys) in enumerate(SHAPES):
+        plans.append(ntt.Plan(log2n, W.POOL50[:limbs], polys))
+        ins.append(_dev(W.request_rows(43, k, log2n, limbs, polys)))
+    outs = [torch.empty_like(x) for x in ins]
+    reqs = _requests(plans, ins, outs, [0, 1, 1, 0])
+    h = ctypes.c_void_p(stream.cuda_stream)
+    assert L.ntt_batch_execute_static(reqs, len(plans), h) == 0     # set-up, kernel module loaded
+    torch.cuda.synchronize()
+    free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    for _ in range(5):
+        assert L.ntt_batch_execute_static(reqs, len(plans), h) == 0
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == alloc0
+    for p in plans:
+        assert p.status() == 0
