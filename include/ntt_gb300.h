@@ -35,6 +35,11 @@
  *  - A plan owns its twiddle tables (device memory) and is immutable after
  *    creation except for its schedule and status word; do not destroy a plan
  *    while work using it is in flight or while another thread uses it.
+ *  - Plans of N >= 2^13 also own a small work area (2 + rows uint32): the
+ *    control words of the fused two-phase schedules, which run a transform's
+ *    column and row kernels as one persistent launch with a work queue.
+ *    Transforms with one plan must not overlap in time: issue them on one
+ *    stream, or order streams with events, or give each stream its own plan.
  */
 #ifndef NTT_GB300_H
 #define NTT_GB300_H

@@ -58,6 +58,7 @@ __device__ __forceinline__ void batch_phase(TileArgs a, uint64_t n_rows, uint64_
         TileRegs<C> st;
         load_direct<C>(st, a, L, t, sm);
         write_pairs_swizzled<C>(st, L, t, sm);
+        async_wait_all();
         __syncthreads();
         run_passes<C, 0>(st, a, L, t, sm);
         store_tile<C>(a, L, t, sm);

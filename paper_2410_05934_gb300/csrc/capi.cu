@@ -74,9 +74,10 @@ static void sched_describe(int i, char* buf, size_t len) {
         const int fa = form_col(s.pipe), fb = form_row(s.pipe);
         char form[48];
         if (fa == fb)
-            snprintf(form, sizeof form, "%s", form_name(fa));
+            snprintf(form, sizeof form, "%s%s", form_fused(s.pipe) ? " fused" : "", form_name(fa));
         else
-            snprintf(form, sizeof form, " col%s row%s", fa ? form_name(fa) : " direct", form_name(fb));
+            snprintf(form, sizeof form, "%s col%s row%s", form_fused(s.pipe) ? " fused" : "",
+                     fa ? form_name(fa) : " direct", form_name(fb));
         snprintf(buf, len,
                  "2k%s split %d+%d: col tile 2^%dx%d (%d thr x %d coef, <=%d/pass, %d/CTA); "
                  "row tile 2^%d (%d thr x %d coef, <=%d/pass, %d/CTA)",
@@ -116,6 +117,8 @@ static PlanDev plan_dev(const ntt_plan_s* p) {
     d.aux_q = 0;
     d.nat = 0;
     d.has_map = 0;
+    d.fused_ctl = p->d_fused;
+    d.fused_rows = p->fused_rows;
     return d;
 }
 
@@ -215,6 +218,8 @@ static void free_device(ntt_plan_s* p) {
     if (p->d_fwd32) cudaFree(p->d_fwd32);
     if (p->d_inv32) cudaFree(p->d_inv32);
     if (p->d_consts32) cudaFree(p->d_consts32);
+    if (p->d_fused) cudaFree(p->d_fused);
+    p->d_fused = nullptr;
     if (p->d_otf_fwd) cudaFree(p->d_otf_fwd);
     if (p->d_otf_inv) cudaFree(p->d_otf_inv);
     p->d_otf_fwd = p->d_otf_inv = nullptr;
@@ -293,6 +298,14 @@ int ntt_plan(ntt_plan_t* out, uint32_t log2n, const uint64_t* moduli, uint32_t n
                  cudaMalloc(&p->d_otf_inv, otf_bytes) == cudaSuccess &&
                  cudaMemcpy(p->d_otf_fwd, p->h.otf_fwd.data(), otf_bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
                  cudaMemcpy(p->d_otf_inv, p->h.otf_inv.data(), otf_bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+        }
+        if (ok && log2n >= 13) {
+            // control words of the fused two-phase form: queue, leave count, one
+            // counter per row (zero between launches)
+            const size_t words = NTT_FUSED_CTL_WORDS + (size_t)p->h.rows;
+            ok = cudaMalloc(&p->d_fused, words * sizeof(uint32_t)) == cudaSuccess &&
+                 cudaMemset(p->d_fused, 0, words * sizeof(uint32_t)) == cudaSuccess;
+            p->fused_rows = p->h.rows;
         }
         if (!ok) {
             free_device(p);
