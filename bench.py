@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: skip the per-N sweep, mixed batch, TFHE batch and cost-model keys")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--schedule", type=int, default=None)
@@ -259,6 +261,85 @@ def run_reference(args):
 
 # --------------------------------------------------------------- GPU arm --
 
+def flush_l2(torch, flush, sink, s):
+    """Evicts L2 between timed steps: writes a buffer larger than L2, then
+    reads it back, so that the lines the flush leaves behind are clean and the
+    timed step does not pay for writing the flush buffer back to HBM."""
+    flush.fill_(s)
+    sink.copy_(flush.sum(dtype=torch.int64).view(1))
+
+
+def probe_rate(torch, L, q, kind, sms, stream, reps=4, iters=4000):
+    """Best of `reps` runs of the in-run integer-pipe probe (operations/s)."""
+    sink = torch.empty(sms * 8 * 256, dtype=torch.int64, device="cuda")
+    best = 0.0
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc = L.ntt_bench_butterflies(q, kind, sms * 8, 256, iters, sink.data_ptr(), stream.cuda_stream)
+        assert rc == 0, rc
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = max(best, sms * 8 * 256 * iters * 8 / (e0.elapsed_time(e1) * 1e-3))
+    return best
+
+
+def committed_profile(name, stamp):
+    """A committed ncu summary (profiles/<name>.json) when it was taken on
+    these kernel sources, else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", name + ".json")) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    return d if d.get("kernel_stamp") == stamp else None
+
+
+def metric_extras(torch, ntt, W, L, stream, sms, peak_fwd, flush, sink, hybrid_log2):
+    """The other halves of the metric, measured in the same run: coefficients/s
+    and roofline fraction for every N from 2^10 to 2^16, the 200-request mixed
+    batch against plain per-request launches (with the ceiling the plain arm
+    leaves: its time over the probe-rate time of the same butterflies), the
+    TFHE-shaped batch, and the cost model's regret.  A few seconds each."""
+    t0 = time.perf_counter()
+    fl = lambda k: flush_l2(torch, flush, sink, k)
+    out = {}
+    sizes, _, total = measure_n_sweep(torch, ntt, W, stream, 3, 2, fl, W.DEFAULT_SEED)
+    out["n_sweep"] = {
+        "how": "forward + inverse of 2^%d coefficients (8 limbs of 50-bit primes) per N, default schedule, L2 "
+               "flushed; frac against the forward probe" % (total.bit_length() - 1),
+        "sizes": [{"log2n": z["log2n"], "rows": z["rows"], "schedule": z["schedule"], "ms": z["ms_per_step"],
+                   "coeffs_per_s": z["coeffs_per_s"], "frac": z["butterflies_per_s"] / peak_fwd} for z in sizes]}
+    spec = W.mixed_requests(seed=W.DEFAULT_SEED)
+    res, coef, bfly, n_sched = measure_mixed(torch, ntt, W, stream, 3, 1, hybrid_log2, spec, W.DEFAULT_SEED)
+    ms = {k: sum(v[0]) / len(v[0]) for k, v in res.items()}
+    ideal_ms = bfly / peak_fwd * 1e3
+    out["mixed_batch"] = {
+        "requests": len(spec), "coefficients": coef, "scheduled_requests": n_sched, "ms": ms,
+        "speedup_vs_plain": ms["plain_per_request"] / ms["batched"],
+        "persistent_only_vs_plain": ms["plain_per_request"] / ms["persistent_only"],
+        "frac": {k: ideal_ms / v for k, v in ms.items()},
+        "ceiling_vs_plain": ms["plain_per_request"] / ideal_ms,
+        "how": "forward transforms of 200 uneven requests (inputs %.1f GB > L2); frac = probe-rate time of all "
+               "butterflies / measured time; ceiling_vs_plain = the largest speedup any form could show over the "
+               "plain arm" % (coef * 8 / 1e9)}
+    res, coef, bfly, q = measure_tfhe_batch(torch, ntt, W, stream, 5, 2, fl)
+    peak0 = probe_rate(torch, L, q, 0, sms, stream, reps=2)
+    ms = {k: sum(v[0]) / len(v[0]) for k, v in res.items()}
+    out["tfhe_batch"] = {
+        "ms": ms, "speedup_vs_plain": ms["plain_per_request"] / ms["batched"],
+        "persistent_only_vs_plain": ms["plain_per_request"] / ms["persistent_only"],
+        "frac": {k: bfly / peak0 * 1e3 / v for k, v in ms.items()},
+        "how": "3780 forward + 1260 inverse rows at N = 1024, 62-bit prime, L2 flushed; frac against the "
+               "exact-class forward probe (kind 0)"}
+    try:
+        out["cost_model"] = cost_model_summary()
+    except Exception as e:   # the committed model or DB is missing or does not match the schedule lists
+        out["cost_model"] = {"unavailable": "%s: %s" % (type(e).__name__, e)}
+    out["extras_seconds"] = time.perf_counter() - t0
+    return out
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_env()
@@ -289,47 +370,43 @@ def run_ours(args):
     A = torch.empty_like(x)
     P = torch.empty_like(x)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    flush_sink = torch.empty(1, dtype=torch.int64, device=dev)
     pairs = [(0, 0), (0, 1), (1, 0), (1, 1)]
     A_POLY, B_POLY = [i for i, _ in pairs], [2 + j for _, j in pairs]
 
-    fwd_ev = []
+    fwd_ev, inv_ev = [], []
 
     def step(x_in, record=False):
         launches = 0
         if record:
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             e0.record(stream)
         plan.forward(x_in, A)
         launches += plan.last_launches()
         if record:
             e1.record(stream)
-            fwd_ev.append((e0, e1))
         # the 4 cross products a_i (.) b_j, formed in the inverse's first kernel
         plan.inverse_mul(A, A, P, a_poly=A_POLY, b_poly=B_POLY)
         launches += plan.last_launches()
+        if record:
+            e2.record(stream)
+            fwd_ev.append((e0, e1))
+            inv_ev.append((e1, e2))
         return launches
 
-    # ---- integer-pipe probe: the "alu" roofline denominator ----
+    # ---- integer-pipe probes: the "alu" roofline denominators ----
+    # the butterflies of the plan's modulus class (moduli below 2^57: the
+    # approximate-quotient forward, kind 2; below 2^50 the inverse's lazy GS
+    # butterfly, kind 7; else the exact-quotient kinds 0 and 1) and the
+    # Montgomery product formed inside the inverse (kind 6)
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
-    sink = torch.empty(sms * 8 * 256, dtype=torch.int64, device=dev)
     L = _native.load()
-    probe_iters = 4000
-    probe_best = 0.0
-    for _ in range(4):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        # the butterfly of the plan's modulus class: moduli below 2^57 use the
-        # small-modulus class (kind 2), others the exact-quotient class (kind 0)
-        probe_kind = 2 if max(mods) < (1 << 57) else 0
-        rc = L.ntt_bench_butterflies(mods[0], probe_kind, sms * 8, 256, probe_iters, sink.data_ptr(),
-                                     stream.cuda_stream)
-        assert rc == 0, rc
-        e1.record(stream)
-        torch.cuda.synchronize()
-        bfly = sms * 8 * 256 * probe_iters * 8
-        probe_best = max(probe_best, bfly / (e0.elapsed_time(e1) * 1e-3))
+    probe_kind = 2 if max(mods) < (1 << 57) else 0
+    inv_kind = 7 if max(mods) < (1 << 50) else (3 if max(mods) < (1 << 57) else 1)
+    probe_best = probe_rate(torch, L, mods[0], probe_kind, sms, stream)
+    probe_inv = probe_rate(torch, L, mods[0], inv_kind, sms, stream)
+    probe_mont = probe_rate(torch, L, mods[0], 6, sms, stream)
 
     # ---- warm-up ----
     for _ in range(max(3, args.warmup)):
@@ -347,7 +424,7 @@ def run_ours(args):
     launches = 0
     wall0 = time.perf_counter()
     for s in range(args.steps):
-        flush.fill_(s)
+        flush_l2(torch, flush, flush_sink, s)
         starts[s].record(stream)
         launches += step(x, record=True)
         ends[s].record(stream)
@@ -357,6 +434,7 @@ def run_ours(args):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     fwd_ms = [a.elapsed_time(b) for a, b in fwd_ev]
+    inv_ms = [a.elapsed_time(b) for a, b in inv_ev]
     t_total = shard.max_over_ranks(sum(step_ms) * 1e-3)
     coeffs_step = 2 * rows * n
     value = world * args.steps * coeffs_step / t_total
@@ -448,7 +526,13 @@ def run_ours(args):
             traffic = t.get("fwd_bytes_per_transform")
     except (OSError, ValueError):
         pass
-    clock_mhz = (clk or {}).get("sm_mhz")
+    # the inverse with its products: ideal time = its GS butterflies at the
+    # inverse probe's rate + its Montgomery products at the product probe's rate
+    inv_s = statistics.mean(inv_ms) * 1e-3
+    bfly_inv = rows * (n // 2) * LOG2N
+    prods = rows * n
+    inv_ideal_s = bfly_inv / probe_inv + prods / probe_mont
+    pipes = committed_profile("butterfly_probe_pipes", B.kernel_stamp())
     roofline = {
         "bound": "alu",
         "kernel": "ntt_forward (%s)" % ntt.schedule_name(LOG2N, plan.schedule),
@@ -456,12 +540,21 @@ def run_ours(args):
         "frac": achieved_bfly / probe_best,
         "peak_source": "in-run probe: %d SMs x 8 CTAs x 256 thr x 8 independent forward butterflies "
                        "with the kernels' arithmetic for these moduli (probe kind %d)" % (sms, probe_kind),
-        "imad_slots_per_butterfly": (sms * 64 * (clock_mhz or 2070.0) * 1e6) / probe_best,
+        "probe_pipes": pipes and pipes.get("summary"),
         "traffic": traffic,
         "hbm": {"achieved": bytes_fwd / fwd_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
                 "frac": bytes_fwd / fwd_s / 1e9 / hbm_peak, "peak_source": hbm_src,
                 "algorithmic_bytes": bytes_fwd},
         "fwd_ms": statistics.mean(fwd_ms),
+        "inverse": {
+            "kernel": "ntt_inverse_mul (%s): 96 Montgomery cross products formed in its first kernel, then the "
+                      "inverse of the 96 product rows" % ntt.schedule_name(LOG2N, plan.schedule),
+            "achieved": bfly_inv / inv_s / 1e9, "unit": "Gbutterfly/s",
+            "frac": inv_ideal_s / inv_s,
+            "peak": probe_inv / 1e9, "peak_products": probe_mont / 1e9,
+            "peak_source": "in-run probes: inverse butterfly (kind %d) and Montgomery product (kind 6); frac = "
+                           "(butterflies / butterfly peak + products / product peak) / measured time" % inv_kind,
+            "butterflies": bfly_inv, "products": prods, "inv_ms": statistics.mean(inv_ms)},
     }
 
     line = {
@@ -473,7 +566,8 @@ def run_ours(args):
                    "step": "NTT(96 rows) -> 4 cross products x 24 limbs formed inside the INTT's first kernel "
                            "-> INTT(96 rows)",
                    "schedule": plan.schedule,
-                   "l2": "flushed before every timed step (512 MiB write, outside the step events)",
+                   "l2": "flushed before every timed step, outside the step events: 512 MiB written, then read "
+                         "back so that the evicted L2 holds clean lines",
                    "timing": "CUDA events per step on the launching stream, summed; max over ranks",
                    "wall_s_timed_loop": wall},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x.numel() * 8),
@@ -486,6 +580,9 @@ def run_ours(args):
         "clocks": clk,
         "roofline": roofline,
     }
+    if world == 1 and not args.no_extras:
+        line.update(metric_extras(torch, ntt, W, L, stream, sms, probe_best, flush, flush_sink,
+                                  args.hybrid_min_log2_coef))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, desc, dt = oracle_sample(args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -533,6 +630,139 @@ def _probe(torch, L, q, kind, sms, stream):
     return best
 
 
+def measure_mixed(torch, ntt, W, stream, steps, warmup, hybrid_log2, spec, seed):
+    """Times one uneven request list four ways: the batched form (one CUDA
+    graph: the persistent kernel beside the requests that fill the GPU by
+    themselves, each on its learned schedule on a concurrent branch), the
+    persistent kernel alone, plain per-request launches on each N's default
+    schedule, and plain launches on learned schedules.  Returns per-arm
+    (per-step ms, launches) and the list's coefficient and butterfly counts."""
+    from paper_2410_05934_gb300.costmodel import choose_schedule, schedule_requests
+    reqs, coef, bfly = [], 0, 0
+    for i, (log2n, limbs, polys) in enumerate(spec):
+        x = W.request_rows_torch(seed, i, log2n, limbs, polys)
+        reqs.append(dict(log2n=log2n, n_moduli=limbs, n_polys=polys, moduli_offset=0, inverse=0,
+                         **{"in": x, "out": torch.empty_like(x)}))
+        coef += x.numel()
+        bfly += x.shape[0] * (x.shape[1] // 2) * log2n
+    sreqs = schedule_requests(reqs, W.POOL50, hybrid_log2)
+    batch = ntt.Batch(sreqs, W.POOL50, flags=ntt.NTT_BATCH_GRAPH)
+    persistent = ntt.Batch(reqs, W.POOL50, flags=ntt.NTT_BATCH_GRAPH)
+    learned = [choose_schedule(r["log2n"], r["n_moduli"], r["n_polys"], 50)[0] for r in reqs]
+    arms = [("batched", lambda: (batch.execute(), batch.info()["last_launches"])[1]),
+            ("persistent_only", lambda: (persistent.execute(), 1)[1]),
+            ("plain_per_request", lambda: (persistent.execute_plain(), persistent.info()["last_launches"])[1]),
+            ("plain_learned_schedule",
+             lambda: (persistent.execute_plain(learned), persistent.info()["last_launches"])[1])]
+    for _ in range(max(1, warmup)):
+        for _, fn in arms:
+            fn()
+    torch.cuda.synchronize()
+    res = {name: _events_loop(torch, stream, steps, fn, None) for name, fn in arms}
+    n_sched = sum(1 for r in sreqs if r["schedule"])
+    batch.close()
+    persistent.close()
+    return res, coef, bfly, n_sched
+
+
+def measure_tfhe_batch(torch, ntt, W, stream, steps, warmup, flush_fn):
+    """The TFHE blind-rotation-shaped batch (3780 forward + 1260 inverse rows,
+    N = 1024, 62-bit prime) three ways: one CUDA graph with both requests on
+    their learned schedules on concurrent branches, one persistent launch,
+    and the two plain launches."""
+    from paper_2410_05934_gb300.costmodel import schedule_requests
+    w = W.tfhe_blind_rotation()
+    q = w["moduli"][0]
+    xf, xi = to_dev_np(torch, w["fwd"]), to_dev_np(torch, w["inv"])
+    reqs = [dict(log2n=10, n_moduli=1, n_polys=xf.shape[0], inverse=0, **{"in": xf, "out": torch.empty_like(xf)}),
+            dict(log2n=10, n_moduli=1, n_polys=xi.shape[0], inverse=1, **{"in": xi, "out": torch.empty_like(xi)})]
+    batch = ntt.Batch(schedule_requests(reqs, [q], 21), [q], flags=ntt.NTT_BATCH_GRAPH)
+    persistent = ntt.Batch(reqs, [q], flags=ntt.NTT_BATCH_GRAPH)
+    arms = [("batched", lambda: (batch.execute(), batch.info()["last_launches"])[1]),
+            ("persistent_only", lambda: (persistent.execute(), 1)[1]),
+            ("plain_per_request", lambda: (batch.execute_plain(), 2)[1])]
+    for _ in range(max(1, warmup)):
+        for _, fn in arms:
+            fn()
+    torch.cuda.synchronize()
+    res = {}
+    for name, fn in arms:
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        launches = 0
+        for k in range(steps):
+            flush_fn(k)
+            starts[k].record(stream)
+            launches += fn()
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        res[name] = ([a.elapsed_time(b) for a, b in zip(starts, ends)], launches)
+    coef = xf.numel() + xi.numel()
+    bfly = (xf.shape[0] + xi.shape[0]) * 512 * 10
+    batch.close()
+    persistent.close()
+    return res, coef, bfly, q
+
+
+def measure_n_sweep(torch, ntt, W, stream, steps, warmup, flush_fn, seed, log2ns=range(10, 17)):
+    """Forward + inverse of 2^25 coefficients (8 limbs of the 50-bit pool,
+    256 MB per buffer, larger than L2) at each N on its default schedule."""
+    mods = W.POOL50[:8]
+    total = 1 << 25
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    x = torch.randint(0, 1 << 49, (total,), dtype=torch.int64, device="cuda", generator=g)   # < every q
+    y = torch.empty_like(x)
+    sizes, launches = [], 0
+    for log2n in log2ns:
+        n = 1 << log2n
+        batch = total // (n * len(mods))
+        plan = ntt.Plan(log2n, mods, batch)
+
+        def step(p=plan):
+            p.forward(x, y)
+            k = p.last_launches()
+            p.inverse(y, y)
+            return k + p.last_launches()
+        for _ in range(max(1, warmup)):
+            step()
+        torch.cuda.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        for k in range(steps):
+            flush_fn(k)
+            starts[k].record(stream)
+            launches += step()
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        t = sum(a.elapsed_time(b) for a, b in zip(starts, ends)) * 1e-3 / steps
+        sizes.append({"log2n": log2n, "rows": batch * len(mods), "schedule": plan.schedule,
+                      "ms_per_step": 1e3 * t, "coeffs_per_s": 2 * total / t,
+                      "butterflies_per_s": 2 * (total // 2) * log2n / t})
+        plan.close()
+    del x, y
+    return sizes, launches, total
+
+
+def cost_model_summary():
+    """Regret of the committed cost model on its held-out shapes of the
+    committed timing DB (mean, p90, max), beside the paper's SM-count rule and
+    the built-in default; decision time per shape."""
+    from paper_2410_05934_gb300 import costmodel as CM
+    from paper_2410_05934_gb300 import tune as T
+    model = CM.CostModel.load()
+    recs = T.load_db(CM.DEFAULT_DB, current=True)
+    X, Tt, M, keys, times = CM.dataset(recs)
+    _, ho = CM.split_heldout(keys, model.meta.get("heldout", 100), model.meta.get("split_seed", 7))
+    rep = CM.evaluate(model, [keys[i] for i in ho], [times[i] for i in ho])
+    stale = sorted(int(n) for n, sig in (model.meta.get("sigs") or {}).items() if sig != T.schedule_signature(int(n)))
+    return {"mlp": rep["mlp"], "sm_rule_mean": rep["sm_rule"]["mean"], "default_mean": rep["default"]["mean"],
+            "decision_us": rep["decision_us"], "heldout_shapes": len(ho), "db_records": len(recs),
+            "model_stale_for_log2n": stale,
+            "how": "committed model (trained on the GPU by the library's MLP kernels) on the held-out shapes of "
+                   "the committed GB300 timing DB"}
+
+
 def run_other(args):
     """Lines for the mixed batch, the TFHE-shaped batch and the plain N=1024
     workload (same schema; the default line is the default workload)."""
@@ -559,53 +789,23 @@ def run_other(args):
             spec = W.mixed_requests(seed=W.DEFAULT_SEED + rank, n_requests=2000, max_limbs=4, max_polys=4,
                                     log2ns=(10, 11), weights=(0.7, 0.3))
             dist_note = "2000 requests, N in {2^10, 2^11} (.7/.3), limbs U{1..4}, polys U{1..4}, forward"
-        reqs, coef, bfly = [], 0, 0
-        for i, (log2n, limbs, polys) in enumerate(spec):
-            x = W.request_rows_torch(W.DEFAULT_SEED + rank, i, log2n, limbs, polys)
-            reqs.append(dict(log2n=log2n, n_moduli=limbs, n_polys=polys, moduli_offset=0, inverse=0,
-                             **{"in": x, "out": torch.empty_like(x)}))
-            coef += x.numel()
-            bfly += x.shape[0] * (x.shape[1] // 2) * log2n
-        from paper_2410_05934_gb300.costmodel import choose_schedule, schedule_requests
-        # the batched + learned-schedule form: requests that fill the GPU by
-        # themselves run their chosen schedule on a second graph branch, the
-        # rest are work items of the persistent kernel
-        sreqs = schedule_requests(reqs, W.POOL50, args.hybrid_min_log2_coef)
-        batch = ntt.Batch(sreqs, W.POOL50, flags=ntt.NTT_BATCH_GRAPH)
-        persistent = ntt.Batch(reqs, W.POOL50, flags=ntt.NTT_BATCH_GRAPH)
-        learned = [choose_schedule(r["log2n"], r["n_moduli"], r["n_polys"], 50)[0] for r in reqs]
-        flush_t = None                      # ~9 GB of inputs: far larger than L2
-        q_probe = W.POOL50[0]
-        kind = 2
-        for _ in range(max(3, args.warmup)):
-            batch.execute()
-            persistent.execute()
-            persistent.execute_plain()
-            persistent.execute_plain(learned)
-        torch.cuda.synchronize()
+        q_probe, kind = W.POOL50[0], 2
         clocks.start()
-        ms, launches = _events_loop(torch, stream, args.steps,
-                                    lambda: (batch.execute(), batch.info()["last_launches"])[1], flush_t)
+        res, coef, bfly, n_sched = measure_mixed(torch, ntt, W, stream, args.steps, max(3, args.warmup),
+                                                 args.hybrid_min_log2_coef, spec, W.DEFAULT_SEED + rank)
         clk = clocks.stop()
-        ms_pers, _ = _events_loop(torch, stream, args.steps, lambda: (persistent.execute(), 1)[1], flush_t)
-        ms_plain, launches_plain = _events_loop(
-            torch, stream, args.steps, lambda: (persistent.execute_plain(), persistent.info()["last_launches"])[1],
-            flush_t)
-        ms_learned, _ = _events_loop(torch, stream, args.steps,
-                                     lambda: (persistent.execute_plain(learned), 1)[1], flush_t)
-        n_sched = sum(1 for r in sreqs if r["schedule"])
-        extra["persistent_only"] = {
-            "value": coef * args.steps / (sum(ms_pers) * 1e-3), "ms_per_step": sum(ms_pers) / args.steps,
-            "how": "every request as work items of the one persistent kernel (one launch under a CUDA graph)"}
-        extra["plain_per_request"] = {
-            "value": coef * args.steps / (sum(ms_plain) * 1e-3), "ms_per_step": sum(ms_plain) / args.steps,
-            "launches_per_step": launches_plain // args.steps,
-            "how": "one launch sequence per request, default schedule of its N, same tables"}
-        extra["plain_learned_schedule"] = {
-            "value": coef * args.steps / (sum(ms_learned) * 1e-3), "ms_per_step": sum(ms_learned) / args.steps,
-            "how": "one launch sequence per request, schedule from the autotuner DB / cost model"}
-        extra["speedup_vs_plain"] = sum(ms_plain) / sum(ms)
-        extra["speedup_vs_plain_learned"] = sum(ms_learned) / sum(ms)
+        ms, launches = res["batched"]
+        for name, how in (("persistent_only", "every request as work items of the one persistent kernel (one "
+                                               "launch under a CUDA graph)"),
+                          ("plain_per_request", "one launch sequence per request, default schedule of its N, "
+                                                "same tables"),
+                          ("plain_learned_schedule", "one launch sequence per request, schedule from the "
+                                                     "autotuner DB / cost model")):
+            m, k = res[name]
+            extra[name] = {"value": coef * args.steps / (sum(m) * 1e-3), "ms_per_step": sum(m) / args.steps,
+                           "launches_per_step": k // args.steps, "how": how}
+        extra["speedup_vs_plain"] = sum(res["plain_per_request"][0]) / sum(ms)
+        extra["speedup_vs_plain_learned"] = sum(res["plain_learned_schedule"][0]) / sum(ms)
         config = {"workload": args.workload, "requests": len(spec), "coefficients": coef,
                   "distribution": dist_note,
                   "batched": ("one CUDA graph: persistent kernel over %d requests || %d requests of >= 2^%d "
@@ -615,37 +815,20 @@ def run_other(args):
                   else "inputs (%.0f MB) fit L2: timed warm" % (coef * 8 / 1e6)}
         unit_coef = coef
     elif args.workload == "tfhe_blind_rotation":
-        w = W.tfhe_blind_rotation()
-        q = w["moduli"][0]
-        xf, xi = to_dev_np(torch, w["fwd"]), to_dev_np(torch, w["inv"])
-        reqs = [dict(log2n=10, n_moduli=1, n_polys=xf.shape[0], inverse=0, **{"in": xf, "out": torch.empty_like(xf)}),
-                dict(log2n=10, n_moduli=1, n_polys=xi.shape[0], inverse=1, **{"in": xi, "out": torch.empty_like(xi)})]
-        from paper_2410_05934_gb300.costmodel import schedule_requests
-        # one graph launch: both requests on their learned schedules on two
-        # concurrent branches; beside it the one-kernel persistent form
-        batch = ntt.Batch(schedule_requests(reqs, [q], 21), [q], flags=ntt.NTT_BATCH_GRAPH)
-        persistent = ntt.Batch(reqs, [q], flags=ntt.NTT_BATCH_GRAPH)
-        coef = xf.numel() + xi.numel()
-        bfly = (xf.shape[0] + xi.shape[0]) * 512 * 10
-        q_probe, kind = q, 0
-        for _ in range(max(3, args.warmup)):
-            batch.execute()
-            persistent.execute()
-            batch.execute_plain()
-        torch.cuda.synchronize()
+        sink = torch.empty(1, dtype=torch.int64, device="cuda")
         clocks.start()
-        ms, launches = _events_loop(torch, stream, args.steps,
-                                    lambda: (batch.execute(), batch.info()["last_launches"])[1], flush)
+        res, coef, bfly, q_probe = measure_tfhe_batch(torch, ntt, W, stream, args.steps, max(3, args.warmup),
+                                                      lambda k: flush_l2(torch, flush, sink, k))
         clk = clocks.stop()
-        ms_pers, _ = _events_loop(torch, stream, args.steps, lambda: (persistent.execute(), 1)[1], flush)
-        ms_plain, _ = _events_loop(torch, stream, args.steps, lambda: (batch.execute_plain(), 2)[1], flush)
-        extra["plain_per_request"] = {"value": coef * args.steps / (sum(ms_plain) * 1e-3),
-                                      "ms_per_step": sum(ms_plain) / args.steps,
+        kind = 0
+        ms, launches = res["batched"]
+        extra["plain_per_request"] = {"value": coef * args.steps / (sum(res["plain_per_request"][0]) * 1e-3),
+                                      "ms_per_step": sum(res["plain_per_request"][0]) / args.steps,
                                       "how": "forward launch + inverse launch, default schedule"}
-        extra["persistent_only"] = {"value": coef * args.steps / (sum(ms_pers) * 1e-3),
-                                    "ms_per_step": sum(ms_pers) / args.steps,
+        extra["persistent_only"] = {"value": coef * args.steps / (sum(res["persistent_only"][0]) * 1e-3),
+                                    "ms_per_step": sum(res["persistent_only"][0]) / args.steps,
                                     "how": "both requests as work items of one persistent kernel launch"}
-        extra["speedup_vs_plain"] = sum(ms_plain) / sum(ms)
+        extra["speedup_vs_plain"] = sum(res["plain_per_request"][0]) / sum(ms)
         config = {"workload": "tfhe_blind_rotation", "log2n": 10, "modulus_bits": 62,
                   "rows": "3780 forward (signed digits) + 1260 inverse",
                   "batched": "one CUDA graph launch: the two requests on their learned schedules, concurrent branches",
@@ -1078,37 +1261,15 @@ def run_n_sweep(args):
     L_ = _native.load()
     stream = torch.cuda.current_stream()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    mods = W.POOL50[:8]
-    total = 1 << 25
-    peak = _probe(torch, L_, mods[0], 2, sms, stream)
+    peak = _probe(torch, L_, W.POOL50[0], 2, sms, stream)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
-    g = torch.Generator(device="cuda")
-    g.manual_seed(W.DEFAULT_SEED + rank)
-    x = torch.randint(0, 1 << 49, (total,), dtype=torch.int64, device="cuda", generator=g)   # < every q
-    y = torch.empty_like(x)
-    sizes, all_ms, launches = [], [], 0
-    for log2n in range(10, 17):
-        n = 1 << log2n
-        batch = total // (n * len(mods))
-        plan = ntt.Plan(log2n, mods, batch)
-
-        def step(p=plan):
-            p.forward(x, y)
-            k = p.last_launches()
-            p.inverse(y, y)
-            return k + p.last_launches()
-        for _ in range(max(3, args.warmup)):
-            step()
-        torch.cuda.synchronize()
-        ms, k = _events_loop(torch, stream, args.steps, step, flush)
-        launches += k
-        t = sum(ms) * 1e-3 / args.steps
-        bfly = 2 * (total // 2) * log2n
-        sizes.append({"log2n": log2n, "rows": batch * len(mods), "schedule": plan.schedule,
-                      "ms_per_step": 1e3 * t, "coeffs_per_s": 2 * total / t,
-                      "frac": bfly / t / peak})
-        all_ms.append(t)
-        plan.close()
+    sink = torch.empty(1, dtype=torch.int64, device="cuda")
+    sizes, launches, total = measure_n_sweep(torch, ntt, W, stream, args.steps, max(3, args.warmup),
+                                             lambda k: flush_l2(torch, flush, sink, k), W.DEFAULT_SEED + rank)
+    mods = W.POOL50[:8]
+    for sz in sizes:
+        sz["frac"] = sz["butterflies_per_s"] / peak
+    all_ms = [sz["ms_per_step"] * 1e-3 for sz in sizes]
     t_all = sum(all_ms)
     line = {"metric": "NTT coeffs/s (coefficient-transforms per second)", "value": 2 * total * len(sizes) / t_all,
             "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -1200,7 +1361,7 @@ def run_cost_model(args):
     from paper_2410_05934_gb300 import costmodel as CM
     import torch
     torch.cuda.set_device(dist_env()[2])
-    model, rep = CM.train_and_evaluate(steps=4000)
+    model, rep = CM.train_and_evaluate(steps=16000)
     # what the model replaces: exhaustive autotuning of a shape (every candidate
     # schedule timed, as the sweep does), on three held-out-sized shapes
     import tempfile

@@ -35,11 +35,6 @@
  *  - A plan owns its twiddle tables (device memory) and is immutable after
  *    creation except for its schedule and status word; do not destroy a plan
  *    while work using it is in flight or while another thread uses it.
- *  - Plans of N >= 2^13 also own a small work area (2 + rows uint32): the
- *    control words of the fused two-phase schedules, which run a transform's
- *    column and row kernels as one persistent launch with a work queue.
- *    Transforms with one plan must not overlap in time: issue them on one
- *    stream, or order streams with events, or give each stream its own plan.
  */
 #ifndef NTT_GB300_H
 #define NTT_GB300_H
@@ -250,7 +245,10 @@ int ntt_plan_last_launches(ntt_plan_t plan, uint32_t* launches);
  * butterflies of the small-modulus class, q < 2^57; kind 4: a 64 x 64 ->
  * 128-bit multiply-accumulate, the inner step of ntt_bconv, counted as one
  * operation; kind 5: the 32-bit forward butterfly of NTT_FLAG_WORD32 plans,
- * q < 2^30).  Total operations = blocks * threads * iters * 8; time it with
+ * q < 2^30; kind 6: a Montgomery product (R = 2^64, odd q < 2^62), the
+ * pointwise product formed inside ntt_inverse_mul and ntt_hmul_tensor;
+ * kind 7: the inverse butterfly of moduli below 2^50, whose sum is not
+ * reduced).  Total operations = blocks * threads * iters * 8; time it with
  * events on `cuda_stream`.
  * d_sink (blocks * threads uint64, caller-owned) only defeats dead-code
  * elimination.  Not part of the paper: a measurement aid.

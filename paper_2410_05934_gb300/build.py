@@ -58,7 +58,7 @@ def _stamp(kind, flags):
 
 TILE_KERNEL_SOURCES = ["ntt_arith.cuh", "ntt_tile.cuh", "ntt_kernels.cuh", "ntt_schedules.h",
                        "kernels_small.cu", "kernels_mid.cu", "kernels_large.cu", "kernels_huge.cu",
-                       "kernels_otf.cu"]
+                       "kernels_otf.cu", "kernels_misc.cu"]
 
 
 def kernel_stamp():

@@ -300,7 +300,7 @@ def load_db_default():
     return load_db(DEFAULT_DB, current=True)
 
 
-def train_and_evaluate(db=DEFAULT_DB, n_heldout=100, steps=4000, lr=3e-3, seed=0, split_seed=7):
+def train_and_evaluate(db=DEFAULT_DB, n_heldout=100, steps=16000, lr=3e-3, seed=0, split_seed=7):
     from .tune import load_db, schedule_signature
     recs = load_db(db, current=True)
     X, T, M, keys, times = dataset(recs)
@@ -321,7 +321,7 @@ def main():
     ap = argparse.ArgumentParser(description="train the schedule cost model on the GPU and report regret")
     ap.add_argument("--db", default=DEFAULT_DB)
     ap.add_argument("--out", default=DEFAULT_PARAMS)
-    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--steps", type=int, default=16000)
     ap.add_argument("--heldout", type=int, default=100)
     args = ap.parse_args()
     model, report = train_and_evaluate(args.db, args.heldout, args.steps)

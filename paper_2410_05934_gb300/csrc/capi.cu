@@ -74,10 +74,9 @@ static void sched_describe(int i, char* buf, size_t len) {
         const int fa = form_col(s.pipe), fb = form_row(s.pipe);
         char form[48];
         if (fa == fb)
-            snprintf(form, sizeof form, "%s%s", form_fused(s.pipe) ? " fused" : "", form_name(fa));
+            snprintf(form, sizeof form, "%s", form_name(fa));
         else
-            snprintf(form, sizeof form, "%s col%s row%s", form_fused(s.pipe) ? " fused" : "",
-                     fa ? form_name(fa) : " direct", form_name(fb));
+            snprintf(form, sizeof form, " col%s row%s", fa ? form_name(fa) : " direct", form_name(fb));
         snprintf(buf, len,
                  "2k%s split %d+%d: col tile 2^%dx%d (%d thr x %d coef, <=%d/pass, %d/CTA); "
                  "row tile 2^%d (%d thr x %d coef, <=%d/pass, %d/CTA)",
@@ -86,19 +85,19 @@ static void sched_describe(int i, char* buf, size_t len) {
     }
 }
 
-// Default choice before any tuning: the schedule measured fastest on GB300
-// for typical batches of each N (timing sweep of the autotuner); small
-// batches of N <= 2^12 prefer the persistent pipelined form, which keeps
-// every SM busy with fewer CTAs.
+// Default choice before any tuning: per N and batch size, the schedule that
+// won most often in the GB300 timing sweep of the autotuner (1100 random
+// shapes, every candidate timed): small batches prefer short per-row tiles
+// and the two-kernel split only pays once there are enough rows.
 uint32_t default_schedule(uint32_t log2n, uint64_t rows) {
     switch (log2n) {
-        case 10: return rows < 256 ? 1u : 7u;    // pipelined / read-only twiddles, 128 thr x 8 coef
-        case 11: return rows < 256 ? 1u : 5u;    // pipelined / read-only twiddles, 256 thr x 8 coef
-        case 12: return rows < 256 ? 1u : 5u;    // pipelined / read-only twiddles, 512 thr x 8 coef
-        case 13: return 5u;                      // column + row kernels (6 + 7), rows read-only twiddles
-        case 14: return 6u;                      // column + row kernels (7 + 7), rows read-only twiddles
-        case 15: return 6u;                      // column + row kernels (7 + 8), rows read-only twiddles
-        case 16: return 5u;                      // column + row kernels (7 + 9), rows read-only twiddles
+        case 10: return rows < 64 ? 6u : (rows < 256 ? 0u : 7u);      // 256 thr x 4 / 128 thr x 8 / read-only
+        case 11: return rows < 128 ? 0u : 5u;                         // staged twiddles / read-only twiddles
+        case 12: return rows < 64 ? 0u : 5u;
+        case 13: return rows < 64 ? 3u : (rows < 1024 ? 4u : 5u);     // column + row kernels (6 + 7)
+        case 14: return rows < 64 ? 4u : (rows < 256 ? 5u : 6u);      // column + row kernels (7 + 7)
+        case 15: return rows < 4 ? 3u : (rows < 16 ? 6u : (rows < 64 ? 5u : 6u));
+        case 16: return rows < 4 ? 6u : (rows < 16 ? 5u : (rows < 64 ? 1u : 5u));
         default: return 0u;
     }
 }
@@ -117,8 +116,6 @@ static PlanDev plan_dev(const ntt_plan_s* p) {
     d.aux_q = 0;
     d.nat = 0;
     d.has_map = 0;
-    d.fused_ctl = p->d_fused;
-    d.fused_rows = p->fused_rows;
     return d;
 }
 
@@ -218,8 +215,6 @@ static void free_device(ntt_plan_s* p) {
     if (p->d_fwd32) cudaFree(p->d_fwd32);
     if (p->d_inv32) cudaFree(p->d_inv32);
     if (p->d_consts32) cudaFree(p->d_consts32);
-    if (p->d_fused) cudaFree(p->d_fused);
-    p->d_fused = nullptr;
     if (p->d_otf_fwd) cudaFree(p->d_otf_fwd);
     if (p->d_otf_inv) cudaFree(p->d_otf_inv);
     p->d_otf_fwd = p->d_otf_inv = nullptr;
@@ -298,14 +293,6 @@ int ntt_plan(ntt_plan_t* out, uint32_t log2n, const uint64_t* moduli, uint32_t n
                  cudaMalloc(&p->d_otf_inv, otf_bytes) == cudaSuccess &&
                  cudaMemcpy(p->d_otf_fwd, p->h.otf_fwd.data(), otf_bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
                  cudaMemcpy(p->d_otf_inv, p->h.otf_inv.data(), otf_bytes, cudaMemcpyHostToDevice) == cudaSuccess;
-        }
-        if (ok && log2n >= 13) {
-            // control words of the fused two-phase form: queue, leave count, one
-            // counter per row (zero between launches)
-            const size_t words = NTT_FUSED_CTL_WORDS + (size_t)p->h.rows;
-            ok = cudaMalloc(&p->d_fused, words * sizeof(uint32_t)) == cudaSuccess &&
-                 cudaMemset(p->d_fused, 0, words * sizeof(uint32_t)) == cudaSuccess;
-            p->fused_rows = p->h.rows;
         }
         if (!ok) {
             free_device(p);
@@ -584,8 +571,9 @@ int ntt_debug_bounded_wait(ntt_plan_t plan, uint32_t deliver, uint32_t spin_limi
 
 int ntt_bench_butterflies(uint64_t q, uint32_t kind, uint32_t blocks, uint32_t threads,
                           uint32_t iters, uint64_t* d_sink, void* cuda_stream) {
-    if (q < 3 || q >= (1ull << NTT_MAX_MODULUS_BITS) || kind > 5 ||
+    if (q < 3 || q >= (1ull << NTT_MAX_MODULUS_BITS) || kind > 7 || (kind == 6 && (q & 1) == 0) ||
         ((kind == 2 || kind == 3) && q >= (1ull << NTT_SMALL_MODULUS_BITS)) ||
+        (kind == 7 && q >= (1ull << NTT_LAZY_MODULUS_BITS)) ||
         (kind == 5 && q >= (1ull << NTT_WORD32_MAX_MODULUS_BITS)) || blocks == 0 || threads == 0 ||
         threads > 256 || !d_sink)
         return NTT_ERR_ARG;

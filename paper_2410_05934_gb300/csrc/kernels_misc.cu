@@ -75,6 +75,8 @@ __global__ void __launch_bounds__(256) k_bench_bfly(uint64_t q, uint64_t w0, uin
             else if (KIND == 1) gs_butterfly(X[i], Y[i], w, wp, q, two_q);
             else if (KIND == 2) ct_butterfly_small(X[i], Y[i], w, wp, q, 2 * two_q);
             else if (KIND == 3) gs_butterfly_small(X[i], Y[i], w, wp, q, 2 * two_q);
+            else if (KIND == 6) X[i] = mont_mul(X[i], Y[i], q, wp);   // wp carries -q^-1 mod 2^64
+            else if (KIND == 7) gs_butterfly_lazy(X[i], Y[i], w, wp, q, 8 * two_q);
             else {   // 64 x 64 -> 128-bit multiply-accumulate (the inner step of the basis conversion)
                 const uint64_t lo = X[i] * w;
                 Y[i] += lo;
@@ -170,6 +172,13 @@ int launch_bench_bfly(uint64_t q, uint32_t kind, uint32_t blocks, uint32_t threa
         case 1: k_bench_bfly<1><<<blocks, threads, 0, st>>>(q, w, wp, iters, sink); break;
         case 2: k_bench_bfly<2><<<blocks, threads, 0, st>>>(q, w, wp, iters, sink); break;
         case 3: k_bench_bfly<3><<<blocks, threads, 0, st>>>(q, w, wp, iters, sink); break;
+        case 6: {   // Montgomery products: the second operand stays fixed below q, the first below 2q
+            uint64_t inv = q;   // q^-1 mod 2^64 by Newton's iteration (q odd): 3 correct bits, doubled 5 times
+            for (int i = 0; i < 5; ++i) inv *= 2 - q * inv;
+            k_bench_bfly<6><<<blocks, threads, 0, st>>>(q, w, 0 - inv, iters, sink);
+            break;
+        }
+        case 7: k_bench_bfly<7><<<blocks, threads, 0, st>>>(q, w, wp, iters, sink); break;
         default: k_bench_bfly<4><<<blocks, threads, 0, st>>>(q, w, wp, iters, sink); break;
     }
     return cudaPeekAtLastError() == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;

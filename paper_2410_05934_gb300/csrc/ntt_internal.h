@@ -69,8 +69,6 @@ struct ntt_plan_s {
     nttgb::LimbConst32* d_consts32 = nullptr;
     nttgb::TwPair* d_otf_fwd = nullptr;
     nttgb::TwPair* d_otf_inv = nullptr;
-    uint32_t* d_fused = nullptr;      // control words of fused two-phase transforms (log2n >= 13)
-    uint64_t fused_rows = 0;
     uint32_t schedule = 0;
     uint32_t last_launches = 0;
 };

@@ -147,124 +147,6 @@ __global__ void __launch_bounds__(C::THREADS) k_ntt_tile(TileArgs a) {
     store_tile<C>(a, L, t, sm);
 }
 
-// ---- fused two-phase transform: one persistent launch for both kernels ----
-// A two-kernel schedule's column and row kernels run as the two phases of
-// one launch.  Work items are the tile groups of the first phase (all rows),
-// then those of the second; CTAs take them from an atomic queue.  A second-
-// phase item reads a row that first-phase items of the same row write, so
-// it waits (bounded) until the row's first-phase count is complete; every
-// such producer was taken from the queue earlier by a CTA that is running
-// and never waits itself, so the wait always ends.  The second phase starts
-// on the first finished rows while the first phase's last items still run:
-// no SM idles at the boundary between the two kernels.
-//
-// Control words (plan-owned, zero between launches): ctl[0] the queue,
-// ctl[1] the count of CTAs that have left, ctl[2 + r] the finished
-// first-phase groups of row r of the launch.  The last CTA to leave zeroes
-// them all, so no reset is launched; launches with one plan must therefore
-// not overlap (they are stream-ordered on one stream).
-#define NTT_FUSED_SPIN_LIMIT (1u << 24)
-#ifndef NTT_FUSED_MIN_CTAS
-#define NTT_FUSED_MIN_CTAS 7      // resident CTAs per SM the register budget must allow
-#endif
-
-struct FusedCtl {
-    uint32_t* ctl;
-    uint64_t n1, n2;          // groups of the first and second phase
-    uint32_t per_row1;        // first-phase groups per row
-    uint32_t log_groups2_per_row;
-};
-
-__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void red_release_gpu_add(uint32_t* p, uint32_t v) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// one tile group of config C (the body of the direct-form kernel)
-template <class C, bool CG>
-__device__ __forceinline__ void tile_group(const TileArgs& a, uint64_t g, uint64_t* smem) {
-    const int tid = threadIdx.x;
-    const int tin = tid >> C::LOGT;
-    const int t = tid & (C::T - 1);
-    const TileLoc L = locate_in_group<C>(a, g, tin);
-    uint64_t* sm = smem + (size_t)tin * C::TILE_WORDS;
-    TileRegs<C> st;
-    load_direct<C, CG>(st, a, L, t, sm);
-    write_input_tile<C>(st, a, L, t, sm);
-    async_wait_all();
-    __syncthreads();
-    run_passes<C, 0>(st, a, L, t, sm);
-    store_tile<C>(a, L, t, sm);
-}
-
-template <class C1, class C2>
-__global__ void __launch_bounds__(C1::THREADS, NTT_FUSED_MIN_CTAS) k_ntt_fused(TileArgs a1, TileArgs a2, FusedCtl f) {
-    static_assert(C1::THREADS == C2::THREADS, "both phases run in the same CTA shape");
-    extern __shared__ __align__(16) uint64_t smem[];
-    __shared__ uint32_t s_item;
-    __shared__ int s_abort;
-    pdl_begin();
-    const int tid = threadIdx.x;
-    const uint64_t total = f.n1 + f.n2;
-    if (tid == 0) s_abort = 0;
-    for (;;) {
-        if (tid == 0) s_item = atomicAdd(&f.ctl[0], 1u);
-        __syncthreads();
-        const uint64_t item = s_item;
-        if (item >= total || s_abort) break;
-        if (item < f.n1) {
-            tile_group<C1, false>(a1, item, smem);
-            __syncthreads();   // the CTA's stores of the group precede the release below
-            if (tid == 0) {
-                const uint64_t row = (item * C1::TPC) >> C1::LOGTPR;
-                red_release_gpu_add(&f.ctl[NTT_FUSED_CTL_WORDS + row], 1u);
-            }
-        } else {
-            const uint64_t g = item - f.n1;
-            const uint64_t row = g >> f.log_groups2_per_row;
-            if (tid == 0) {
-                const uint32_t* done = &f.ctl[NTT_FUSED_CTL_WORDS + row];
-                uint32_t spins = 0;
-                while (ld_acquire_gpu(done) < f.per_row1) {
-                    if (++spins == NTT_FUSED_SPIN_LIMIT) {
-                        record_status(a2.status, NTT_STATUS_TIMEOUT);
-                        s_abort = 1;
-                        break;
-                    }
-                    __nanosleep(64);
-                }
-            }
-            __syncthreads();
-            if (s_abort) break;
-            tile_group<C2, true>(a2, g, smem);
-        }
-        __syncthreads();   // s_item and the shared buffers are reused by the next item
-    }
-    // leave; the last CTA out zeroes the control words for the next launch
-    // (every other CTA has made its last queue and row-count update before
-    // its own count of leaving)
-    __shared__ int s_last;
-    if (tid == 0) {
-        __threadfence();
-        s_last = atomicAdd(&f.ctl[1], 1u) == gridDim.x - 1;
-        if (s_last) __threadfence();
-    }
-    __syncthreads();
-    if (s_last) {
-        const uint64_t rows = f.n1 / f.per_row1;
-        for (uint64_t r = tid; r < rows; r += blockDim.x) f.ctl[NTT_FUSED_CTL_WORDS + r] = 0;
-        if (tid == 0) {
-            f.ctl[0] = 0;
-            f.ctl[1] = 0;
-        }
-    }
-}
-
 // Issues the bulk copies of tile group g into buffer `buf` (all threads take
 // part; thread 0 arms the barrier with the byte count).
 template <class C>
@@ -441,103 +323,12 @@ int launch_s1(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t row_
     return rc;
 }
 
-// tile arguments of config C (shared by the plain and the fused launches)
-template <class C>
-TileArgs tile_args(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t row_begin, uint64_t n_rows) {
-    TileArgs a;
-    a.in = in;
-    a.out = out;
-    a.tw = C::INV ? p.inv : p.fwd;
-    a.lc = p.lc;
-    a.status = p.status;
-    a.row_begin = row_begin;
-    a.n_tiles = n_rows << C::LOGTPR;
-    a.n_moduli = p.n_moduli;
-    a.check = p.check;
-    a.fast32 = (row_begin + n_rows < (1ull << 32) && a.n_tiles < (1ull << 32)) ? 1u : 0u;
-    a.mod_magic = fdiv_magic(a.n_moduli);
-    a.src_mode = p.src_mode;
-    a.in_b = p.in_b;
-    a.aux_q = p.aux_q;
-    a.nat = p.nat;
-    a.has_map = p.has_map;
-    for (int i = 0; i < NTT_MUL_MAX_MAPPED; ++i) {
-        a.a_map[i] = p.a_map[i];
-        a.b_map[i] = p.b_map[i];
-    }
-    a.otf = C::INV ? p.otf_inv : p.otf_fwd;
-    return a;
-}
-
-// Both kernels of a transform as one persistent launch: C1 runs first (the
-// column config of a forward, the row config of an inverse).
-template <class C1, class C2>
-int launch_fused(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t row_begin, uint64_t n_rows,
-                 cudaStream_t st) {
-    static_assert(!C1::PIPE && !C2::PIPE, "the fused form runs the direct phases");
-    static_assert(((1 << C1::LOGTPR) % C1::TPC) == 0 && ((1 << C2::LOGTPR) % C2::TPC) == 0,
-                  "a tile group lies in one row");
-    if (C1::MODE == 3 || C2::MODE == 3) {
-        if (!(C1::INV ? p.otf_inv : p.otf_fwd)) return NTT_ERR_ARG;
-    }
-    const TileArgs a1 = tile_args<C1>(p, in, out, row_begin, n_rows);
-    const TileArgs a2 = tile_args<C2>(p, in, out, row_begin, n_rows);
-    FusedCtl f;
-    f.ctl = p.fused_ctl;
-    f.per_row1 = (uint32_t)((1u << C1::LOGTPR) / C1::TPC);
-    f.n1 = n_rows * f.per_row1;
-    const uint32_t per_row2 = (uint32_t)((1u << C2::LOGTPR) / C2::TPC);
-    f.log_groups2_per_row = floor_log2(per_row2);
-    f.n2 = n_rows * per_row2;
-    if (f.n1 == 0) return NTT_OK;
-    constexpr size_t smem = C1::SMEM_BYTES > C2::SMEM_BYTES ? C1::SMEM_BYTES : C2::SMEM_BYTES;
-    static int cached[64] = {0};   // resident CTAs of the whole GPU, per device
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return NTT_ERR_CUDA;
-    if (dev < 0 || dev >= 64) dev = 0;
-    if (!cached[dev]) {
-        if (smem > 48 * 1024 &&
-            cudaFuncSetAttribute(k_ntt_fused<C1, C2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                cudaSuccess)
-            return NTT_ERR_CUDA;
-        int n = 0, sms = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ntt_fused<C1, C2>, C1::THREADS, smem) !=
-                cudaSuccess ||
-            n < 1)
-            n = 1;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cached[dev] = n * (sms > 0 ? sms : 1);
-    }
-    uint64_t grid = (uint64_t)cached[dev];
-    if (grid > f.n1 + f.n2) grid = f.n1 + f.n2;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(C1::THREADS);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    if (cudaLaunchKernelEx(&cfg, k_ntt_fused<C1, C2>, a1, a2, f) != cudaSuccess) return NTT_ERR_CUDA;
-    return cudaPeekAtLastError() == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
-}
-
 template <int LOGN, int SPLIT, int LOGP, int LOGTA, int LOGRPA, int TPCA, int LOGTB, int LOGRPB,
           int TPCB, int PIPE, bool INV, int MC>
 int launch_s2_mc(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t row_begin,
                  uint64_t n_rows, cudaStream_t st) {
     using CA = TileCfg<LOGN, 0, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, INV, MC, form_col(PIPE)>;
     using CB = TileCfg<LOGN, SPLIT, LOGN, 0, LOGTB, LOGRPB, TPCB, INV, MC, form_row(PIPE)>;
-    if constexpr (form_fused(PIPE)) {
-        if (p.fused_ctl && n_rows <= p.fused_rows) {
-            if constexpr (!INV)
-                return launch_fused<CA, CB>(p, in, out, row_begin, n_rows, st);
-            else
-                return launch_fused<CB, CA>(p, in, out, row_begin, n_rows, st);
-        }
-    }
     int rc;
     if (!INV) {
         rc = launch_tile_kernel<CA>(p, in, out, row_begin, n_rows, st);
@@ -560,8 +351,7 @@ int launch_s2(const PlanDev& p, const uint64_t* in, uint64_t* out, uint64_t row_
         : p.mc >= 1
         ? launch_s2_mc<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE, INV, 1>(p, in, out, row_begin, n_rows, st)
         : launch_s2_mc<LOGN, SPLIT, LOGP, LOGTA, LOGRPA, TPCA, LOGTB, LOGRPB, TPCB, PIPE, INV, 0>(p, in, out, row_begin, n_rows, st);
-    const bool fused = form_fused(PIPE) && p.fused_ctl && n_rows <= p.fused_rows && n_rows > 0;
-    if (rc == NTT_OK && launches) *launches += fused ? 1 : 2;
+    if (rc == NTT_OK && launches) *launches += 2;
     return rc;
 }
 

@@ -6,9 +6,6 @@
 
 namespace nttgb {
 
-// control words of a fused two-phase launch ahead of its per-row counters
-#define NTT_FUSED_CTL_WORDS 2
-
 // Device-side view of a plan (host pointers when used by the emulation).
 struct PlanDev {
     const TwPair* fwd;
@@ -28,10 +25,6 @@ struct PlanDev {
     uint8_t a_map[NTT_MUL_MAX_MAPPED], b_map[NTT_MUL_MAX_MAPPED];
     const TwPair* otf_fwd = nullptr;   // on-the-fly twiddle tables (form 3 kernels)
     const TwPair* otf_inv = nullptr;
-    // control words of the fused two-phase form (2 + fused_rows uint32, zero
-    // between launches); null: fused schedules run as two launches
-    uint32_t* fused_ctl = nullptr;
-    uint64_t fused_rows = 0;
 };
 
 // Transforms rows [row_begin, row_begin + n_rows) of the layout that starts

@@ -19,9 +19,7 @@
 //       in shared memory.  An S2 entry may give its row kernel another form:
 //       PIPE = A | B << 2 with B != 0 runs the column kernel in form A and
 //       the row kernel in form B (8 = column direct, rows read-only); below
-//       4 both kernels use PIPE.  Bit 16 (NTT_FORM_FUSED) runs the two
-//       kernels as the two phases of one persistent launch with a work queue
-//       (both configs need the same CTA size).
+//       4 both kernels use PIPE.
 //
 // The lists are split by N so that the kernel translation units can be
 // compiled in parallel; NTT_SCHEDULES_ALL keeps the table order (which is
@@ -50,15 +48,15 @@
 #define NTT_SCHEDULES_LARGE(S1, S2)                                                   \
     S1(13, 9, 4, 1, 0) S1(13, 8, 5, 1, 0) S1(13, 10, 3, 1, 0)                     \
     S2(13, 6, 4, 6, 4, 1, 5, 3, 4, 0) S2(13, 6, 4, 6, 4, 1, 5, 3, 4, 2)           \
-    S2(13, 6, 4, 6, 4, 1, 5, 3, 4, 8) S2(13, 6, 4, 6, 4, 2, 5, 3, 4, 24)          \
+    S2(13, 6, 4, 6, 4, 1, 5, 3, 4, 8)                                             \
     S1(14, 10, 4, 1, 0) S1(14, 9, 5, 1, 0)                                        \
     S2(14, 7, 4, 7, 4, 1, 4, 4, 8, 1) S2(14, 7, 4, 7, 4, 1, 4, 3, 8, 0)           \
     S2(14, 7, 4, 7, 4, 1, 5, 2, 4, 0) S2(14, 7, 4, 7, 4, 1, 4, 3, 8, 2)           \
-    S2(14, 7, 4, 7, 4, 1, 4, 3, 8, 8) S2(14, 7, 4, 7, 4, 1, 4, 3, 8, 24)          \
+    S2(14, 7, 4, 7, 4, 1, 4, 3, 8, 8)                                             \
     S2(15, 7, 4, 7, 4, 1, 4, 4, 8, 1) S2(15, 7, 4, 6, 5, 1, 3, 5, 16, 0)          \
     S2(15, 5, 4, 4, 5, 4, 5, 5, 4, 0) S2(15, 7, 4, 8, 3, 1, 5, 3, 8, 0)           \
     S2(15, 7, 4, 7, 4, 1, 5, 3, 4, 0) S2(15, 7, 4, 7, 4, 1, 5, 3, 4, 2)           \
-    S2(15, 7, 4, 7, 4, 1, 5, 3, 4, 8) S2(15, 7, 4, 7, 4, 1, 5, 3, 4, 24)
+    S2(15, 7, 4, 7, 4, 1, 5, 3, 4, 8)
 
 #define NTT_SCHEDULES_HUGE(S1, S2)                                                    \
     S2(16, 8, 4, 8, 4, 1, 5, 3, 4, 0) S2(16, 7, 4, 7, 4, 1, 6, 3, 2, 2)           \
@@ -66,7 +64,7 @@
     S2(16, 8, 4, 8, 4, 1, 6, 2, 2, 0) S2(16, 7, 4, 7, 4, 1, 6, 3, 2, 8)           \
     S2(16, 7, 4, 7, 4, 1, 6, 3, 2, 0) S2(16, 8, 4, 8, 4, 1, 5, 3, 4, 2)           \
     S2(16, 7, 4, 7, 4, 1, 5, 3, 4, 8) S2(16, 7, 4, 7, 4, 1, 5, 4, 4, 8)           \
-    S2(16, 7, 4, 7, 4, 1, 5, 3, 2, 8) S2(16, 7, 4, 7, 4, 1, 6, 3, 2, 24)
+    S2(16, 7, 4, 7, 4, 1, 5, 3, 2, 8)
 
 #define NTT_SCHEDULES_ALL(S1, S2)                                           \
     NTT_SCHEDULES_SMALL(S1, S2) NTT_SCHEDULES_MID(S1, S2) NTT_SCHEDULES_LARGE(S1, S2) \

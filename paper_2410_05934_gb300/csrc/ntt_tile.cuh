@@ -183,11 +183,6 @@ NTT_HD constexpr uint32_t spread(uint32_t x, int pe, int r) {
 // the row kernel form B.
 constexpr int form_col(int f) { return f & 3; }
 constexpr int form_row(int f) { return f < 4 ? f : (f >> 2) & 3; }
-// Bit 16 of a two-kernel entry's form: run both kernels as the two phases of
-// one persistent launch (k_ntt_fused); the low bits then give the column and
-// row forms as A | B << 2 (neither pipelined).
-#define NTT_FORM_FUSED 16
-constexpr bool form_fused(int f) { return (f & NTT_FORM_FUSED) != 0; }
 
 template <int LOGN_, int S0_, int S1_, int LOGP_, int LOGT_, int LOGRP_, int TPC_, bool INV_,
           int MC_ = 0, int MODE_ = 0>
@@ -362,19 +357,6 @@ NTT_HD void load_pair(const uint64_t* p, uint64_t& x, uint64_t& y) {
 #endif
 }
 
-// load_pair through L2 only (ld.global.cg): for data another CTA of the same
-// launch wrote, so that no line this SM's L1 may hold is used
-NTT_HD void load_pair_cg(const uint64_t* p, uint64_t& x, uint64_t& y) {
-#if defined(__CUDA_ARCH__)
-    const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2*>(p));
-    x = v.x;
-    y = v.y;
-#else
-    x = p[0];
-    y = p[1];
-#endif
-}
-
 NTT_HD void store_pair(uint64_t* p, uint64_t x, uint64_t y) {
 #if defined(__CUDA_ARCH__)
     *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(x, y);
@@ -429,10 +411,7 @@ struct TileRegs {
 // ---- load (direct form): global -> registers, 16-byte coalesced pairs ----
 // Thread t holds the pairs e = 2 (t + i T) = 2t ^ 2iT (disjoint bits), so
 // g(e) = (gbase | place(2t)) + place(2iT) with a compile-time second term.
-// CG: the tile's data (when this is not the transform's first kernel) were
-// written earlier in the same launch by other CTAs (fused transform): read
-// them through L2 only.
-template <class C, bool CG = false>
+template <class C>
 NTT_HD void load_direct(TileRegs<C>& st, const TileArgs& a, const TileLoc& L, int t, uint64_t* sm) {
     if (!L.valid) return;
     if (C::TWS && L.tw_off == 0) {
@@ -538,10 +517,7 @@ NTT_HD void load_direct(TileRegs<C>& st, const TileArgs& a, const TileLoc& L, in
     for (int i = 0; i < C::R / 2; ++i) {
         const uint32_t off = place<C>(2u * (uint32_t)i * C::T);
         NTT_GMEM_CHECK(gt + off + 1, 1u << C::LOGN);
-        if (CG && !C::FIRST)
-            load_pair_cg(src + off, st.x[2 * i], st.x[2 * i + 1]);
-        else
-            load_pair(src + off, st.x[2 * i], st.x[2 * i + 1]);
+        load_pair(src + off, st.x[2 * i], st.x[2 * i + 1]);
         if (C::FIRST) bad |= st.x[2 * i] >= q || st.x[2 * i + 1] >= q;
     }
     if (C::FIRST && a.check && bad) record_status(a.status, NTT_STATUS_RANGE);

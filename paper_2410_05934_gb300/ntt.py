@@ -64,8 +64,7 @@ def schedule_params(log2n, sched_id):
     form_col = v[1] & 3
     form_row = v[1] if v[1] < 4 else (v[1] >> 2) & 3
     d = {"kernels": v[0], "form": v[1], "pipelined": form_col == 1 or form_row == 1,
-         "staged_twiddles": form_col != 2 and form_row != 2, "log2n": v[2],
-         "fused": v[0] == 2 and bool(v[1] & 16)}
+         "staged_twiddles": form_col != 2 and form_row != 2, "log2n": v[2]}
     if v[0] == 1:
         d.update(logt=v[3], logrp=v[4], tpc=v[5])
     else:

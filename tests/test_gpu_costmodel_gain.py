@@ -21,7 +21,7 @@ from paper_2410_05934_gb300 import costmodel as CM  # noqa: E402
 
 
 def test_trained_model_gains_over_rule_and_default():
-    model, report = CM.train_and_evaluate(steps=3000)
+    model, report = CM.train_and_evaluate(steps=16000)
     mlp, rule, default = report["mlp"], report["sm_rule"], report["default"]
     assert mlp["n"] == 100
     assert mlp["mean"] <= 0.10                     # regret target vs exhaustive tuning
@@ -41,3 +41,26 @@ def test_plan_auto_schedule():
     p = ntt.Plan(16, W.POOL50[:24], 4, schedule="auto")
     assert p.schedule_source in ("autotuner", "cost_model")
     assert 0 <= p.schedule < ntt.schedule_count(16)
+
+
+def test_regret_on_fresh_timings_of_heldout_shapes():
+    """Grades the committed model on the GPU it runs on: every candidate
+    schedule of 8 held-out shapes (spread over their sizes) is timed again
+    here with the autotuner's own timing (median of 5, L2 flushed for shapes
+    below 256 MB), and the model's choice is compared with the fastest."""
+    import os
+    import tempfile
+    from paper_2410_05934_gb300 import tune as T
+    model = CM.CostModel.load()
+    _, _, _, keys, _ = CM.dataset(CM.load_db_default())
+    _, ho = CM.split_heldout(keys, model.meta.get("heldout", 100), model.meta.get("split_seed", 7))
+    held = sorted((keys[i] for i in ho), key=lambda k: (k[1] * k[2]) << k[0])
+    picks = [held[round(j * (len(held) - 1) / 7)] for j in range(8)]
+    with tempfile.TemporaryDirectory() as tmp:
+        db = os.path.join(tmp, "fresh.jsonl")
+        T.sweep(picks, db=db, reps=5, skip_done=False)
+        fresh = T.load_db(db, current=True)
+    _, _, _, fkeys, ftimes = CM.dataset(fresh)
+    assert sorted(fkeys) == sorted(set(picks))
+    regrets = [CM.regret(t, model.choose(*k)) for k, t in zip(fkeys, ftimes)]
+    assert float(np.mean(regrets)) <= 0.10, regrets
