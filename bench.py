@@ -317,6 +317,7 @@ def metric_extras(torch, ntt, W, L, stream, sms, peak_fwd, flush, sink, hybrid_l
     out["mixed_batch"] = {
         "requests": len(spec), "coefficients": coef, "scheduled_requests": n_sched, "ms": ms,
         "speedup_vs_plain": ms["plain_per_request"] / ms["batched"],
+        "grouped_vs_plain": ms["plain_per_request"] / ms["grouped"],
         "persistent_only_vs_plain": ms["plain_per_request"] / ms["persistent_only"],
         "frac": {k: ideal_ms / v for k, v in ms.items()},
         "ceiling_vs_plain": ms["plain_per_request"] / ideal_ms,
@@ -328,6 +329,7 @@ def metric_extras(torch, ntt, W, L, stream, sms, peak_fwd, flush, sink, hybrid_l
     ms = {k: sum(v[0]) / len(v[0]) for k, v in res.items()}
     out["tfhe_batch"] = {
         "ms": ms, "speedup_vs_plain": ms["plain_per_request"] / ms["batched"],
+        "grouped_vs_plain": ms["plain_per_request"] / ms["grouped"],
         "persistent_only_vs_plain": ms["plain_per_request"] / ms["persistent_only"],
         "frac": {k: bfly / peak0 * 1e3 / v for k, v in ms.items()},
         "how": "3780 forward + 1260 inverse rows at N = 1024, 62-bit prime, L2 flushed; frac against the "
@@ -648,8 +650,10 @@ def measure_mixed(torch, ntt, W, stream, steps, warmup, hybrid_log2, spec, seed)
     sreqs = schedule_requests(reqs, W.POOL50, hybrid_log2)
     batch = ntt.Batch(sreqs, W.POOL50, flags=ntt.NTT_BATCH_GRAPH)
     persistent = ntt.Batch(reqs, W.POOL50, flags=ntt.NTT_BATCH_GRAPH)
+    grouped = ntt.Batch(reqs, W.POOL50, flags=ntt.NTT_BATCH_GRAPH | ntt.NTT_BATCH_GROUPED)
     learned = [choose_schedule(r["log2n"], r["n_moduli"], r["n_polys"], 50)[0] for r in reqs]
     arms = [("batched", lambda: (batch.execute(), batch.info()["last_launches"])[1]),
+            ("grouped", lambda: (grouped.execute(), grouped.info()["last_launches"])[1]),
             ("persistent_only", lambda: (persistent.execute(), 1)[1]),
             ("plain_per_request", lambda: (persistent.execute_plain(), persistent.info()["last_launches"])[1]),
             ("plain_learned_schedule",
@@ -662,6 +666,7 @@ def measure_mixed(torch, ntt, W, stream, steps, warmup, hybrid_log2, spec, seed)
     n_sched = sum(1 for r in sreqs if r["schedule"])
     batch.close()
     persistent.close()
+    grouped.close()
     return res, coef, bfly, n_sched
 
 
@@ -678,7 +683,9 @@ def measure_tfhe_batch(torch, ntt, W, stream, steps, warmup, flush_fn):
             dict(log2n=10, n_moduli=1, n_polys=xi.shape[0], inverse=1, **{"in": xi, "out": torch.empty_like(xi)})]
     batch = ntt.Batch(schedule_requests(reqs, [q], 21), [q], flags=ntt.NTT_BATCH_GRAPH)
     persistent = ntt.Batch(reqs, [q], flags=ntt.NTT_BATCH_GRAPH)
+    grouped = ntt.Batch(reqs, [q], flags=ntt.NTT_BATCH_GRAPH | ntt.NTT_BATCH_GROUPED)
     arms = [("batched", lambda: (batch.execute(), batch.info()["last_launches"])[1]),
+            ("grouped", lambda: (grouped.execute(), grouped.info()["last_launches"])[1]),
             ("persistent_only", lambda: (persistent.execute(), 1)[1]),
             ("plain_per_request", lambda: (batch.execute_plain(), 2)[1])]
     for _ in range(max(1, warmup)):
@@ -701,6 +708,7 @@ def measure_tfhe_batch(torch, ntt, W, stream, steps, warmup, flush_fn):
     bfly = (xf.shape[0] + xi.shape[0]) * 512 * 10
     batch.close()
     persistent.close()
+    grouped.close()
     return res, coef, bfly, q
 
 

@@ -313,11 +313,19 @@ int ntt_debug_bounded_wait(ntt_plan_t plan, uint32_t deliver, uint32_t spin_limi
  * execution, since their pointers are kernel arguments.  ntt_batch_execute_plain is the comparison arm: one launch sequence
  * per request on the same tables (schedules[i] per request, or the default
  * schedule of its N when schedules is NULL).
+ * NTT_BATCH_GROUPED replaces the persistent kernel by grouped launches: the
+ * unscheduled requests of one N, forward and inverse alike, are segments of
+ * one grid per kernel phase of that N's configuration (one launch for N <=
+ * 2^12, two above), CTA b working on the segment whose range of tile groups
+ * holds b; the grids of different N go to the branches (N group k on branch
+ * k mod 4 after the scheduled requests) so that their last waves overlap.
+ * The same tables, pointers and results as the persistent form.
  * Errors: ARG, NOT_PRIME, NOT_NTT_FRIENDLY, MODULUS_TOO_LARGE, ALIGN,
  * UNSUPPORTED (log2n below NTT_BATCH_MIN_LOG2N), NOMEM, CUDA.
  */
 #define NTT_BATCH_MIN_LOG2N 10
 #define NTT_BATCH_GRAPH 1u
+#define NTT_BATCH_GROUPED 4u
 
 typedef struct {
     uint32_t log2n;

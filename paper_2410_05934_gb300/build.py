@@ -31,7 +31,8 @@ CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-Wall", "-Wno-unused-function",
 
 PRODUCT_SOURCES = ["capi.cu", "kernels_small.cu", "kernels_mid.cu", "kernels_large.cu", "kernels_huge.cu",
                    "kernels_otf.cu",
-                   "kernels_misc.cu", "batch.cu", "costmodel.cu", "tfhe.cu", "rns.cu", "ntt32.cu", "plan_host.cpp"]
+                   "kernels_misc.cu", "batch.cu", "grouped.cu", "costmodel.cu", "tfhe.cu", "rns.cu", "ntt32.cu",
+                   "plan_host.cpp"]
 EMU_SOURCES = ["plan_host.cpp", "emulate.cpp"]
 
 

@@ -322,6 +322,15 @@ struct ntt_batch_s {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     cudaStream_t graph_stream = nullptr;
+    // NTT_BATCH_GROUPED: one group per N of the unscheduled requests
+    struct Group {
+        uint32_t log2n = 0, mc = 0, phases = 0, n_segs = 0;
+        std::vector<uint32_t> reqs;                 // request indices, in order
+        std::vector<nttgb::GroupSeg> hsegs[2];      // per phase
+        nttgb::GroupSeg* d_segs[2] = {nullptr, nullptr};
+        uint64_t grid[2] = {0, 0};
+    };
+    std::vector<Group> groups;
 };
 
 namespace nttgb {
@@ -345,6 +354,9 @@ static void batch_free(ntt_batch_s* b) {
         if (t.d_inv) cudaFree(t.d_inv);
         if (t.d_lc) cudaFree(t.d_lc);
     }
+    for (auto& g : b->groups)
+        for (auto* d : g.d_segs)
+            if (d) cudaFree(d);
     if (b->d_reqs) cudaFree(b->d_reqs);
     if (b->d_items) cudaFree(b->d_items);
     if (b->d_counter) cudaFree(b->d_counter);
@@ -371,6 +383,38 @@ static int validate_reqs(const ntt_request_t* reqs, uint32_t n, uint32_t pool_le
     return NTT_OK;
 }
 
+// The segments of group g's requests for every phase of its configuration:
+// tile counts of that phase's config over each request's rows, consecutive
+// ranges of CTAs.
+static void batch_fill_segments(ntt_batch_s* b, ntt_batch_s::Group& g) {
+    for (uint32_t p = 0; p < g.phases; ++p) {
+        g.hsegs[p].resize(g.reqs.size());
+        uint64_t begin = 0;
+        for (size_t k = 0; k < g.reqs.size(); ++k) {
+            const uint32_t i = g.reqs[k];
+            const ntt_request_t& r = b->reqs[i];
+            const BatchReq& d = b->hreqs[i];
+            uint32_t ltpr = 0, tpc = 1;
+            grouped_geometry(r.log2n, (int)p, r.inverse != 0, &ltpr, &tpc);
+            const uint64_t rows = (uint64_t)r.n_polys * r.n_moduli;
+            GroupSeg& sg = g.hsegs[p][k];
+            sg.in = r.in;
+            sg.out = r.out;
+            sg.tw = r.inverse ? d.tw_inv : d.tw_fwd;
+            sg.lc = d.lc;
+            sg.n_tiles = rows << ltpr;
+            sg.group_begin = begin;
+            sg.mod_magic = fdiv_magic(r.n_moduli);
+            sg.n_moduli = r.n_moduli;
+            sg.inverse = r.inverse;
+            sg.fast32 = (rows < (1ull << 32) && sg.n_tiles < (1ull << 32)) ? 1u : 0u;
+            sg.pad = 0;
+            begin += (sg.n_tiles + tpc - 1) / tpc;
+        }
+        g.grid[p] = begin;
+    }
+}
+
 }  // namespace nttgb
 
 using namespace nttgb;
@@ -382,7 +426,7 @@ int ntt_batch_plan(ntt_batch_t* out, const ntt_request_t* reqs, uint32_t n_reqs,
     if (!out) return NTT_ERR_ARG;
     *out = nullptr;
     if (!moduli_pool || pool_len == 0) return NTT_ERR_ARG;
-    if (flags & ~(NTT_BATCH_GRAPH | NTT_FLAG_CHECK)) return NTT_ERR_ARG;
+    if (flags & ~(NTT_BATCH_GRAPH | NTT_FLAG_CHECK | NTT_BATCH_GROUPED)) return NTT_ERR_ARG;
     int rc = validate_reqs(reqs, n_reqs, pool_len);
     if (rc) return rc;
     ntt_batch_s* b = new (std::nothrow) ntt_batch_s();
@@ -411,6 +455,18 @@ int ntt_batch_plan(ntt_batch_t* out, const ntt_request_t* reqs, uint32_t n_reqs,
             b->coefficients += rows << r.log2n;
             if (r.schedule) {
                 b->scheduled.push_back(i);
+                continue;
+            }
+            if (flags & NTT_BATCH_GROUPED) {
+                auto it = std::find_if(b->groups.begin(), b->groups.end(),
+                                       [&](const ntt_batch_s::Group& g) { return g.log2n == r.log2n; });
+                if (it == b->groups.end()) {
+                    b->groups.emplace_back();
+                    it = b->groups.end() - 1;
+                    it->log2n = r.log2n;
+                    it->phases = (uint32_t)grouped_phases(r.log2n);
+                }
+                it->reqs.push_back(i);
                 continue;
             }
             const uint32_t per = rows_per_item(r.log2n);
@@ -472,8 +528,23 @@ int ntt_batch_plan(ntt_batch_t* out, const ntt_request_t* reqs, uint32_t n_reqs,
                          cudaMemcpyHostToDevice) == cudaSuccess) &&
              cudaMemset(b->d_status, 0, sizeof(int)) == cudaSuccess;
     }
-    if (ok && !b->scheduled.empty()) {
-        b->n_branches = (uint32_t)std::min<size_t>(NTT_BATCH_BRANCHES, b->scheduled.size());
+    if (ok && !b->groups.empty()) {
+        // largest N first; segments of every phase, uploaded once
+        std::sort(b->groups.begin(), b->groups.end(),
+                  [](const ntt_batch_s::Group& x, const ntt_batch_s::Group& y) { return x.log2n > y.log2n; });
+        for (auto& g : b->groups) {
+            g.mc = b->tables[g.log2n].host.mc;
+            g.n_segs = (uint32_t)g.reqs.size();
+            batch_fill_segments(b, g);
+            for (uint32_t p = 0; ok && p < g.phases; ++p)
+                ok = cudaMalloc(&g.d_segs[p], sizeof(GroupSeg) * g.n_segs) == cudaSuccess &&
+                     cudaMemcpy(g.d_segs[p], g.hsegs[p].data(), sizeof(GroupSeg) * g.n_segs,
+                                cudaMemcpyHostToDevice) == cudaSuccess;
+        }
+    }
+    const size_t branch_users = b->scheduled.size() + (b->groups.size() > 1 ? b->groups.size() : 0);
+    if (ok && branch_users) {
+        b->n_branches = (uint32_t)std::min<size_t>(NTT_BATCH_BRANCHES, branch_users);
         ok = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess;
         for (uint32_t k = 0; ok && k < b->n_branches; ++k)
             ok = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking) == cudaSuccess &&
@@ -515,6 +586,14 @@ int ntt_batch_update(ntt_batch_t b, const ntt_request_t* reqs, uint32_t n_reqs, 
     }
     // the scheduled requests' pointers are kernel arguments of the captured graph
     if (!b->scheduled.empty()) batch_drop_graph(b);
+    // grouped segments hold the pointers in device memory: refresh them in stream order
+    for (auto& g : b->groups) {
+        batch_fill_segments(b, g);
+        for (uint32_t p = 0; p < g.phases; ++p)
+            if (cudaMemcpyAsync(g.d_segs[p], g.hsegs[p].data(), sizeof(GroupSeg) * g.n_segs, cudaMemcpyHostToDevice,
+                                (cudaStream_t)cuda_stream) != cudaSuccess)
+                return NTT_ERR_CUDA;
+    }
     // pageable source: the runtime stages it before returning, so hreqs may change afterwards
     return cudaMemcpyAsync(b->d_reqs, b->hreqs.data(), sizeof(BatchReq) * n_reqs, cudaMemcpyHostToDevice,
                            (cudaStream_t)cuda_stream) == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
@@ -564,6 +643,26 @@ static int batch_enqueue(ntt_batch_t b, cudaStream_t st, uint32_t* launches) {
             int rc = batch_launch_request(b, i, b->reqs[i].schedule - 1, b->side[k % b->n_branches], launches);
             if (rc) return rc;
         }
+    }
+    // grouped grids: one N per branch after the scheduled requests (or on the
+    // caller's stream when there is a single N)
+    const bool group_branches = b->groups.size() > 1;
+    if (group_branches && b->scheduled.empty()) {
+        if (cudaEventRecord(b->ev_fork, st) != cudaSuccess) return NTT_ERR_CUDA;
+        for (uint32_t k = 0; k < b->n_branches; ++k)
+            if (cudaStreamWaitEvent(b->side[k], b->ev_fork, 0) != cudaSuccess) return NTT_ERR_CUDA;
+    }
+    for (size_t j = 0; j < b->groups.size(); ++j) {
+        const auto& g = b->groups[j];
+        cudaStream_t gs = group_branches ? b->side[(b->scheduled.size() + j) % b->n_branches] : st;
+        for (uint32_t p = 0; p < g.phases; ++p) {
+            int rc = launch_grouped(g.log2n, g.mc, (int)p, g.d_segs[p], g.n_segs, g.grid[p], b->d_status, b->check,
+                                    gs);
+            if (rc) return rc;
+            ++*launches;
+        }
+    }
+    if (!b->scheduled.empty() || group_branches) {
         for (uint32_t k = 0; k < b->n_branches; ++k)
             if (cudaEventRecord(b->ev_join[k], b->side[k]) != cudaSuccess) return NTT_ERR_CUDA;
     }
@@ -582,8 +681,9 @@ static int batch_enqueue(ntt_batch_t b, cudaStream_t st, uint32_t* launches) {
         if (cudaPeekAtLastError() != cudaSuccess) return NTT_ERR_CUDA;
         ++*launches;
     }
-    for (uint32_t k = 0; k < b->n_branches; ++k)
-        if (cudaStreamWaitEvent(st, b->ev_join[k], 0) != cudaSuccess) return NTT_ERR_CUDA;
+    if (!b->scheduled.empty() || group_branches)
+        for (uint32_t k = 0; k < b->n_branches; ++k)
+            if (cudaStreamWaitEvent(st, b->ev_join[k], 0) != cudaSuccess) return NTT_ERR_CUDA;
     return NTT_OK;
 }
 

@@ -5,7 +5,9 @@
 // y < 2^64,  Q = floor(y w' / 2^64)  and  r = y w - Q q  satisfy
 // r = y w mod q  or  r = y w mod q + q, i.e. r in [0, 2q).  (y w/q - y w'/2^64
 // lies in [0, 1), so Q is floor(y w / q) or one less.)  Only the low 64 bits
-// of y w and Q q are needed because r < 2q < 2^64.
+// of y w and Q q are needed because r < 2q < 2^64.  The kernels estimate Q
+// from three of the four 32 x 32-bit partial products (shoup_mul_approx) and
+// fix the range with at most one subtraction where a bound needs it.
 //
 // Butterflies keep values lazily reduced (Harvey's bounds), which q < 2^62
 // makes safe in 64-bit words:
@@ -33,18 +35,13 @@ NTT_HD uint64_t mulhi64(uint64_t a, uint64_t b) {
 #endif
 }
 
-// y * w mod q lazily: result in [0, 2q) for any y < 2^64 (w < q, wp its Shoup form).
-NTT_HD uint64_t shoup_mul(uint64_t y, uint64_t w, uint64_t wp, uint64_t q) {
-    uint64_t Q = mulhi64(y, wp);
-    return y * w - Q * q;
-}
-
 // Shoup product with a three-partial-product quotient: with y = yh 2^32 + yl
 // and w' = wh 2^32 + wl,  Q~ = yh wh + floor(yh wl / 2^32) + floor(yl wh / 2^32)
 // drops three fractional parts (each < 1) of y w' / 2^64, so
 // floor(y w' / 2^64) - Q~ is in {0, 1, 2} and floor(y w / q) - Q~ in {0..3}:
 // the result y w - Q~ q is y w mod q plus 0..3 q, i.e. in [0, 4q), for any
-// y < 2^64.  Used when 4q-wide lazy bounds fit (moduli below 2^57).
+// y < 2^64.  The butterflies of moduli below 2^57 use it as it is (4q-wide
+// lazy bounds fit); shoup_mul adds one conditional subtraction for the rest.
 //
 // On the GPU the product is written with 32-bit multiplies of the integer
 // multiply pipe, which binds the transforms: two high halves and one
@@ -97,6 +94,16 @@ NTT_HD uint64_t shoup_mul_approx(uint64_t y, uint64_t w, uint64_t wp, uint64_t q
 
 // x in [0, 2m) -> [0, m)
 NTT_HD uint64_t csub(uint64_t x, uint64_t m) { return x >= m ? x - m : x; }
+
+// y * w mod q lazily: result in [0, 2q) for any y < 2^64 (w < q, wp its
+// Shoup form), for every q < 2^62.  The three-partial-product quotient
+// leaves y w mod q + {0..3} q, which is below 4q < 2^64, and one conditional
+// subtraction of 2q brings it into [0, 2q).  That costs two integer adds
+// where the exact quotient floor(y w' / 2^64) costs four more multiplies on
+// the integer multiply pipe, which is the one that binds.
+NTT_HD uint64_t shoup_mul(uint64_t y, uint64_t w, uint64_t wp, uint64_t q) {
+    return csub(shoup_mul_approx(y, w, wp, q), 2 * q);
+}
 
 // Cooley-Tukey butterfly, Harvey-lazy.  In/out in [0, 4q).
 NTT_HD void ct_butterfly(uint64_t& X, uint64_t& Y, uint64_t w, uint64_t wp, uint64_t q,

@@ -129,14 +129,13 @@ __device__ __forceinline__ void pdl_begin() {
 }
 
 // ---- direct form: one CTA = TPC tiles, loaded with 16-byte loads ----
+// tile group g of config C (the CTA's whole work in the direct form)
 template <class C>
-__global__ void __launch_bounds__(C::THREADS) k_ntt_tile(TileArgs a) {
-    extern __shared__ __align__(16) uint64_t smem[];
-    pdl_begin();
+__device__ __forceinline__ void tile_group(const TileArgs& a, uint64_t g, uint64_t* smem) {
     const int tid = threadIdx.x;
     const int tin = tid >> C::LOGT;
     const int t = tid & (C::T - 1);
-    const TileLoc L = locate_in_group<C>(a, blockIdx.x, tin);
+    const TileLoc L = locate_in_group<C>(a, g, tin);
     uint64_t* sm = smem + (size_t)tin * C::TILE_WORDS;
     TileRegs<C> st;
     load_direct<C>(st, a, L, t, sm);
@@ -145,6 +144,13 @@ __global__ void __launch_bounds__(C::THREADS) k_ntt_tile(TileArgs a) {
     __syncthreads();
     run_passes<C, 0>(st, a, L, t, sm);
     store_tile<C>(a, L, t, sm);
+}
+
+template <class C>
+__global__ void __launch_bounds__(C::THREADS) k_ntt_tile(TileArgs a) {
+    extern __shared__ __align__(16) uint64_t smem[];
+    pdl_begin();
+    tile_group<C>(a, blockIdx.x, smem);
 }
 
 // Issues the bulk copies of tile group g into buffer `buf` (all threads take

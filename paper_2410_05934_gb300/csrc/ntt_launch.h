@@ -66,6 +66,25 @@ int launch_pointwise32(const Plan32Dev& p, uint32_t log2n, const uint32_t* a, co
 int launch_bitrev_rows(const uint64_t* in, uint64_t* out, uint64_t row_begin, uint64_t n_rows, uint32_t log2n,
                        void* stream, uint32_t* launches);
 
+// ---- grouped launches (batch.cu / grouped.cu) ----
+// One request's segment of a grouped grid for one kernel phase.
+struct GroupSeg {
+    const uint64_t* in;
+    uint64_t* out;
+    const TwPair* tw;          // the request's forward or inverse tables
+    const LimbConst* lc;
+    uint64_t n_tiles;          // tiles of this phase's configuration over the request's rows
+    uint64_t group_begin;      // first CTA of the segment in the grid
+    uint64_t mod_magic;        // fdiv_magic(n_moduli)
+    uint32_t n_moduli, inverse, fast32, pad;
+};
+// kernel phases of N's grouped configuration (0: N not covered)
+int grouped_phases(uint32_t log2n);
+// log2 tiles per row and tiles per CTA of one phase and direction
+int grouped_geometry(uint32_t log2n, int phase, bool inverse, uint32_t* log_tiles_per_row, uint32_t* tpc);
+int launch_grouped(uint32_t log2n, uint32_t mc, int phase, const GroupSeg* d_segs, uint32_t n_segs, uint64_t grid,
+                   int* status, uint32_t check, void* stream);
+
 int launch_bench_bfly(uint64_t q, uint32_t kind, uint32_t blocks, uint32_t threads, uint32_t iters,
                       uint64_t* sink, void* stream);
 

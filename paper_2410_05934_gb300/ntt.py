@@ -252,6 +252,7 @@ class Plan:
 
 
 NTT_BATCH_GRAPH = 1
+NTT_BATCH_GROUPED = 4
 
 
 class Batch:

@@ -185,3 +185,83 @@ def test_full_mixed_batch_as_benchmarked(oracle):
         got = to_host(sreqs[i]["out"][pick])
         assert np.array_equal(got[np.arange(len(pick))[:, None], idx], ref), (i, log2n, limbs, polys)
         sreqs[i]["in"] = sreqs[i]["out"] = None       # free as we go
+
+
+@pytest.mark.parametrize("flags", [ntt.NTT_BATCH_GROUPED, ntt.NTT_BATCH_GROUPED | ntt.NTT_BATCH_GRAPH])
+def test_grouped_batch_matches_oracle(oracle, flags):
+    """Grouped launches: the requests of one N (both directions) are segments
+    of one grid per kernel phase; every N from 2^10 to 2^16."""
+    reqs, hosts = _make(5)
+    b = ntt.Batch(reqs, W.POOL50, flags=flags)
+    b.execute()
+    torch.cuda.synchronize()
+    phases = {10: 1, 11: 1, 12: 1, 13: 2, 14: 2, 15: 2, 16: 2}
+    assert b.info()["last_launches"] == sum(phases[n] for n in {s[0] for s in SHAPES})
+    assert b.info()["items"] == 0                      # no persistent-kernel work items
+    _check(oracle, reqs, hosts)
+    assert b.status() == 0
+
+
+def test_grouped_replay_after_pointer_update_in_place(oracle):
+    reqs, hosts = _make(6, in_place=True)
+    saved = [r["in"].clone() for r in reqs]
+    b = ntt.Batch(reqs, W.POOL50, flags=ntt.NTT_BATCH_GROUPED | ntt.NTT_BATCH_GRAPH)
+    b.execute()
+    torch.cuda.synchronize()
+    _check(oracle, reqs, hosts)
+    # new buffers with the original inputs, same shapes: the replay uses them
+    for r, s in zip(reqs, saved):
+        r["in"] = s.clone()
+        r["out"] = torch.empty_like(s)
+    b.update(reqs)
+    b.execute()
+    torch.cuda.synchronize()
+    _check(oracle, reqs, hosts)
+    assert b.status() == 0
+
+
+def test_grouped_tfhe_batch_is_one_launch(oracle):
+    """The TFHE blind-rotation-shaped batch (3780 forward + 1260 inverse rows
+    at N = 1024, 62-bit prime) as one grouped launch."""
+    w = W.tfhe_blind_rotation()
+    q = w["moduli"][0]
+    xf, xi = to_dev(w["fwd"]), to_dev(w["inv"])
+    reqs = [dict(log2n=10, n_moduli=1, n_polys=xf.shape[0], moduli_offset=0, inverse=0,
+                 **{"in": xf, "out": torch.empty_like(xf)}),
+            dict(log2n=10, n_moduli=1, n_polys=xi.shape[0], moduli_offset=0, inverse=1,
+                 **{"in": xi, "out": torch.empty_like(xi)})]
+    b = ntt.Batch(reqs, [q], flags=ntt.NTT_BATCH_GROUPED | ntt.NTT_BATCH_GRAPH)
+    b.execute()
+    torch.cuda.synchronize()
+    assert b.info()["last_launches"] == 1 and b.status() == 0
+    for r, x, inv in ((reqs[0], w["fwd"], False), (reqs[1], w["inv"], True)):
+        rows = np.array([0, 1, x.shape[0] // 2, x.shape[0] - 1])
+        got = to_host(r["out"])[rows]
+        assert np.array_equal(got, oracle.transform_rows(x[rows], [q] * len(rows), inverse=inv))
+
+
+def test_full_mixed_batch_grouped(oracle):
+    """The 200-request mixed batch at full size through grouped launches (one
+    grid per N and phase, the four N on concurrent branches); sampled rows and
+    outputs of every request."""
+    spec = W.mixed_requests(seed=W.DEFAULT_SEED)
+    reqs = []
+    for i, (log2n, limbs, polys) in enumerate(spec):
+        x = W.request_rows_torch(W.DEFAULT_SEED, i, log2n, limbs, polys)
+        reqs.append(dict(log2n=log2n, n_moduli=limbs, n_polys=polys, moduli_offset=0, inverse=0,
+                         **{"in": x, "out": torch.empty_like(x)}))
+    b = ntt.Batch(reqs, W.POOL50, flags=ntt.NTT_BATCH_GROUPED | ntt.NTT_BATCH_GRAPH)
+    b.execute()
+    b.execute()
+    torch.cuda.synchronize()
+    assert b.status() == 0
+    rng = np.random.default_rng(201)
+    for i, (log2n, limbs, polys) in enumerate(spec):
+        n, rows = 1 << log2n, limbs * polys
+        pick = sorted(set([0, rows - 1] + rng.integers(0, rows, 1).tolist()))
+        x = np.stack([W.uniform_mod(W.DEFAULT_SEED, 1000 + i, n, W.POOL50[r % limbs], start=r * n) for r in pick])
+        idx = np.stack([np.concatenate([[0, n - 1], rng.integers(0, n, 4)]) for _ in pick]).astype(np.uint32)
+        ref = oracle.transform_rows(x, [W.POOL50[r % limbs] for r in pick], idx=idx)
+        got = to_host(reqs[i]["out"][pick])
+        assert np.array_equal(got[np.arange(len(pick))[:, None], idx], ref), (i, log2n, limbs, polys)
+        reqs[i]["in"] = reqs[i]["out"] = None
