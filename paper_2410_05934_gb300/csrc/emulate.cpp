@@ -296,8 +296,35 @@ static void emu_passes32(std::vector<Regs32<C>>& st, const Args32& a, const std:
     }
 }
 
+// The N = 1024 kernel: four rows (warps) per CTA, every phase for all 128
+// threads before the next (the kernel's __syncwarp points).
+template <bool INV>
+static int emu_ntt32_w1024(const Args32& a) {
+    const uint32_t ctas = (a.n_rows + 3) / 4;
+    std::vector<uint32_t> sm(4 * 1024, 0xdeadbeefu);
+    std::vector<Row1024> r(128);
+    for (uint32_t cta = 0; cta < ctas; ++cta) {
+        Loc32 L[4];
+        for (int w = 0; w < 4; ++w) L[w] = locate1024(a, cta, w);
+        auto each = [&](auto&& phase) {
+            for (int tid = 0; tid < 128; ++tid) phase(r[tid], L[tid >> 5], tid & 31, sm.data() + (tid >> 5) * 1024);
+        };
+        if (!INV) {
+            each([&](Row1024& x, const Loc32& l, int t, uint32_t* s) { w1024_fwd_a(x, a, l, t, s); });
+            each([&](Row1024& x, const Loc32& l, int t, uint32_t* s) { w1024_fwd_b(x, a, l, t, s); });
+            each([&](Row1024&, const Loc32& l, int t, uint32_t* s) { w1024_store(a, l, t, s); });
+        } else {
+            each([&](Row1024&, const Loc32& l, int t, uint32_t* s) { w1024_inv_a(a, l, t, s); });
+            each([&](Row1024& x, const Loc32& l, int t, uint32_t* s) { w1024_inv_b(x, a, l, t, s); });
+            each([&](Row1024& x, const Loc32& l, int t, uint32_t* s) { w1024_inv_c(x, a, l, t, s); });
+        }
+    }
+    return NTT_OK;
+}
+
 template <int LOGN, bool INV>
 static int emu_ntt32(const Args32& a) {
+    if constexpr (LOGN == 10) return emu_ntt32_w1024<INV>(a);
     using C = typename Cfg32Sel<LOGN, INV>::C;
     if (!verify_cfg<C>()) return NTT_ERR_UNSUPPORTED;
     const uint32_t ctas = (a.n_rows + C::TPC - 1) / C::TPC;

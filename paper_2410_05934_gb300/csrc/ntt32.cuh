@@ -78,6 +78,24 @@ NTT_HD Tw32 load_tw32(const Tw32* tw, uint32_t k) {
 #endif
 }
 
+// Shared-memory slot of tile element e for 32-bit words: 32 four-byte banks,
+// so the higher 5-bit groups of e are XOR-folded into its low 5 bits (the
+// 64-bit tiles fold 4-bit groups onto 16 eight-byte bank pairs).  A bijection,
+// linear over GF(2), and swz32(e + 1) = swz32(e) ^ 1 for even e.
+NTT_HD constexpr uint32_t swz32(uint32_t e) { return e ^ (((e >> 5) ^ (e >> 10)) & 31u); }
+
+// The thread layout of pass P with the lane-bit exchanges that make its
+// accesses conflict-free: the 5 lane bits land on e-bits of distinct
+// residues mod 5.
+template <class C, int P>
+struct Pass32Geom {
+    using Gm = PassGeom<C, P>;
+    static constexpr uint64_t SWAPS = pass_swaps_g(Gm::PE, Gm::r, C::LOGT, 5);
+    static NTT_HD constexpr uint32_t et(uint32_t t) {
+        return spread(SWAPS ? swap_thread_bits_g(t, SWAPS) : t, Gm::PE, Gm::r);
+    }
+};
+
 // one whole row per tile: C = TileCfg<LOGN, 0, LOGN, 0, LOGT, 3, TPC, INV, 1, 2> for the geometry
 template <class C>
 struct Regs32 {
@@ -123,10 +141,10 @@ NTT_HD void load32(Regs32<C>& st, const Args32& a, const Loc32& L, int t, uint32
         bad |= st.x[2 * i] >= q || st.x[2 * i + 1] >= q;
     }
     if (a.check && bad) record_status(a.status, NTT_STATUS_RANGE);
-    const uint32_t b = swz(2u * (uint32_t)t);
+    const uint32_t b = swz32(2u * (uint32_t)t);
 #pragma unroll
     for (int i = 0; i < C::R / 2; ++i) {
-        const uint32_t c = swz(2u * (uint32_t)i * C::T);
+        const uint32_t c = swz32(2u * (uint32_t)i * C::T);
         NTT_SMEM_CHECK(b ^ c, C::E);
         sm[b ^ c] = st.x[2 * i];
         sm[(b ^ c) ^ 1u] = st.x[2 * i + 1];
@@ -138,18 +156,20 @@ template <class C, int P>
 NTT_HD void pass32(Regs32<C>& st, const Args32& a, const Loc32& L, int t, uint32_t* sm) {
     if (!L.valid) return;
     using Gm = PassGeom<C, P>;
+    using G32 = Pass32Geom<C, P>;
     constexpr int S_LO = Gm::S_LO, r = Gm::r, GS = Gm::GS;
-    const uint32_t b = swz(spread((uint32_t)t, Gm::PE, Gm::r));
+    const uint32_t et = G32::et((uint32_t)t);
+    const uint32_t b = swz32(et);
 #pragma unroll
     for (int j = 0; j < C::R; ++j) {
-        const uint32_t addr = b ^ swz(Gm::ej(j));
+        const uint32_t addr = b ^ swz32(Gm::ej(j));
         NTT_SMEM_CHECK(addr, C::E);
         st.x[j] = sm[addr];
     }
     const LimbConst32 lc = a.lc[L.limb];
     const Tw32* tw = a.tw + ((uint64_t)L.limb << C::LOGN);
     constexpr int SH = C::LOGN - S_LO;
-    const uint32_t pre_t = place<C>(spread((uint32_t)t, Gm::PE, r)) >> SH;
+    const uint32_t pre_t = place<C>(et) >> SH;
 #pragma unroll
     for (int gi = 0; gi < Gm::G; ++gi) {
         const uint32_t pre = pre_t | (place<C>(Gm::ej(gi * GS)) >> SH);
@@ -190,7 +210,7 @@ NTT_HD void pass32(Regs32<C>& st, const Args32& a, const Loc32& L, int t, uint32
     }
 #pragma unroll
     for (int j = 0; j < C::R; ++j) {
-        const uint32_t addr = b ^ swz(Gm::ej(j));
+        const uint32_t addr = b ^ swz32(Gm::ej(j));
         sm[addr] = st.x[j];
     }
 }
@@ -201,10 +221,10 @@ NTT_HD void store32(const Args32& a, const Loc32& L, int t, const uint32_t* sm) 
     if (!L.valid) return;
     uint32_t* dst = a.out + ((uint64_t)L.row << C::LOGN);
     const uint32_t q = a.lc[L.limb].q, two_q = a.lc[L.limb].two_q;
-    const uint32_t b = swz(2u * (uint32_t)t);
+    const uint32_t b = swz32(2u * (uint32_t)t);
 #pragma unroll
     for (int i = 0; i < C::R / 2; ++i) {
-        const uint32_t c = swz(2u * (uint32_t)i * C::T);
+        const uint32_t c = swz32(2u * (uint32_t)i * C::T);
         uint32_t x = sm[b ^ c], y = sm[(b ^ c) ^ 1u];
         if (!C::INV) {          // [0, 4q) -> [0, q)
             x = csub32(csub32(x, two_q), q);
@@ -230,12 +250,175 @@ NTT_HD uint32_t mulmod32(uint32_t x, uint32_t y, const LimbConst32& c) {
     return csub32((uint32_t)(p - mulhi64(p, c.mu) * c.q), c.q);
 }
 
+// ---- N = 1024: one warp per row, two passes of five stages ----
+// Lane t holds 32 coefficients.  Layout A: x[j] = element t + 32 j (lane bits
+// = e-bits 0..4, registers = e-bits 5..9), which a coalesced load or store
+// of consecutive words gives directly; stages 0..4 pair registers j and
+// j + 2^(4 - s), with twiddle 2^s + (j >> (5 - s)) shared by all lanes.
+// Layout B: x[j] = element 32 t + j (registers = e-bits 0..4); stages 5..9
+// pair j and j + 2^(9 - s) with twiddle 2^s + t 2^(s - 5) + (j >> (10 - s)).
+// The plan stores the N = 1024 tables with each stage s >= 5 transposed,
+// entry 2^s + t 2^(s - 5) + i at 2^s + 32 i + t, so the 32 lanes' twiddles
+// of one load are consecutive words.  The two layouts meet in shared
+// memory through slot(e) = e ^ ((e >> 5) & 31): both the lanes of a layout-A
+// access (e-bits 0..4 = t) and of a layout-B access (e = 32 t + j) hit 32
+// distinct banks.  Only the row's own warp touches the row's words, so
+// __syncwarp orders the exchanges.
+NTT_HD constexpr uint32_t slot1024(uint32_t e) { return e ^ ((e >> 5) & 31u); }
+NTT_HD constexpr uint32_t tw1024_pos(uint32_t s, uint32_t t, uint32_t i) { return (1u << s) + 32u * i + t; }
+
+// table position of canonical entry k of a N = 1024 table (the transpose above)
+NTT_HD constexpr uint32_t tw1024_perm(uint32_t k) {
+    uint32_t s = 0;
+    while ((2u << s) <= k) ++s;
+    if (s < 5) return k;
+    const uint32_t o = k - (1u << s), per = 1u << (s - 5);
+    return tw1024_pos(s, o / per, o % per);
+}
+
+struct Row1024 {
+    uint32_t x[32];
+};
+
+// row of warp w of CTA cta (four rows per CTA)
+NTT_HD Loc32 locate1024(const Args32& a, uint32_t cta, int w) {
+    Loc32 L;
+    const uint32_t r = cta * 4u + (uint32_t)w;
+    L.valid = r < a.n_rows;
+    L.row = a.row_begin + (L.valid ? r : 0u);
+    const uint32_t rq = a.n_moduli == 1 ? L.row : fdiv32(L.row, a.mod_magic, a.n_moduli);
+    L.limb = a.n_moduli == 1 ? 0u : L.row - rq * a.n_moduli;
+    return L;
+}
+
+// forward, phase 1: coalesced load (layout A), stages 0..4, into shared memory
+NTT_HD void w1024_fwd_a(Row1024& r, const Args32& a, const Loc32& L, int t, uint32_t* sm) {
+    if (!L.valid) return;
+    const uint32_t* src = a.in + ((uint64_t)L.row << 10);
+    const LimbConst32 lc = a.lc[L.limb];
+    const Tw32* tw = a.tw + ((uint64_t)L.limb << 10);
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        NTT_GMEM_CHECK(t + 32 * j, 1024);
+        r.x[j] = src[t + 32 * j];
+        bad |= r.x[j] >= lc.q;
+    }
+    if (a.check && bad) record_status(a.status, NTT_STATUS_RANGE);
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int d = 16 >> s;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            if (j & d) continue;
+            ct32(r.x[j], r.x[j + d], load_tw32(tw, (1u << s) + ((uint32_t)j >> (5 - s))), lc.q, lc.two_q);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        NTT_SMEM_CHECK(slot1024(t + 32 * j), 1024);
+        sm[slot1024(t + 32 * j)] = r.x[j];
+    }
+}
+
+// forward, phase 2: layout B from shared memory, stages 5..9, canonical,
+// back to shared memory in place (each lane rewrites only the words it read)
+NTT_HD void w1024_fwd_b(Row1024& r, const Args32& a, const Loc32& L, int t, uint32_t* sm) {
+    if (!L.valid) return;
+    const LimbConst32 lc = a.lc[L.limb];
+    const Tw32* tw = a.tw + ((uint64_t)L.limb << 10);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) r.x[j] = sm[slot1024(32 * t + j)];
+#pragma unroll
+    for (int s = 5; s < 10; ++s) {
+        const int d = 1 << (9 - s);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            if (j & d) continue;
+            NTT_GMEM_CHECK(tw1024_pos(s, t, (uint32_t)j >> (10 - s)), 1024);
+            ct32(r.x[j], r.x[j + d], load_tw32(tw, tw1024_pos(s, t, (uint32_t)j >> (10 - s))), lc.q, lc.two_q);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) sm[slot1024(32 * t + j)] = csub32(csub32(r.x[j], lc.two_q), lc.q);
+}
+
+// store phase (both directions' forward output / the inverse's input
+// transpose): shared memory in layout A -> consecutive words of the row
+NTT_HD void w1024_store(const Args32& a, const Loc32& L, int t, const uint32_t* sm) {
+    if (!L.valid) return;
+    uint32_t* dst = a.out + ((uint64_t)L.row << 10);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) dst[t + 32 * j] = sm[slot1024(t + 32 * j)];
+}
+
+// inverse, phase 1: coalesced load into shared memory (layout A positions)
+NTT_HD void w1024_inv_a(const Args32& a, const Loc32& L, int t, uint32_t* sm) {
+    if (!L.valid) return;
+    const uint32_t* src = a.in + ((uint64_t)L.row << 10);
+    const uint32_t q = a.lc[L.limb].q;
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const uint32_t v = src[t + 32 * j];
+        bad |= v >= q;
+        sm[slot1024(t + 32 * j)] = v;
+    }
+    if (a.check && bad) record_status(a.status, NTT_STATUS_RANGE);
+}
+
+// inverse, phase 2: layout B, GS stages 9..5, back in place
+NTT_HD void w1024_inv_b(Row1024& r, const Args32& a, const Loc32& L, int t, uint32_t* sm) {
+    if (!L.valid) return;
+    const LimbConst32 lc = a.lc[L.limb];
+    const Tw32* tw = a.tw + ((uint64_t)L.limb << 10);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) r.x[j] = sm[slot1024(32 * t + j)];
+#pragma unroll
+    for (int s = 9; s >= 5; --s) {
+        const int d = 1 << (9 - s);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            if (j & d) continue;
+            gs32(r.x[j], r.x[j + d], load_tw32(tw, tw1024_pos(s, t, (uint32_t)j >> (10 - s))), lc.q, lc.two_q);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) sm[slot1024(32 * t + j)] = r.x[j];
+}
+
+// inverse, phase 3: layout A, GS stages 4..0 (stage 0 with N^-1), canonical, coalesced store
+NTT_HD void w1024_inv_c(Row1024& r, const Args32& a, const Loc32& L, int t, const uint32_t* sm) {
+    if (!L.valid) return;
+    const LimbConst32 lc = a.lc[L.limb];
+    const Tw32* tw = a.tw + ((uint64_t)L.limb << 10);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) r.x[j] = sm[slot1024(t + 32 * j)];
+#pragma unroll
+    for (int s = 4; s >= 0; --s) {
+        const int d = 16 >> s;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            if (j & d) continue;
+            if (s == 0)
+                gs32_scaled(r.x[j], r.x[j + d], lc);
+            else
+                gs32(r.x[j], r.x[j + d], load_tw32(tw, (1u << s) + ((uint32_t)j >> (5 - s))), lc.q, lc.two_q);
+        }
+    }
+    uint32_t* dst = a.out + ((uint64_t)L.row << 10);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) dst[t + 32 * j] = csub32(r.x[j], lc.q);
+}
+
 // the 32-bit configuration of a ring size: 8 coefficients per thread (or the
-// whole row for N <= 8), passes of up to 3 stages, 256-thread CTAs
+// whole row for N <= 8), passes of up to 3 stages, 128-thread CTAs (one row
+// per CTA at N = 1024, so that a batch of a few hundred rows still spreads
+// over every SM)
 template <int LOGN, bool INV>
 struct Cfg32Sel {
     static constexpr int LOGT = LOGN > 3 ? LOGN - 3 : 0;
-    static constexpr int TPC = (256 >> LOGT) > 0 ? (256 >> LOGT) : 1;
+    static constexpr int TPC = (128 >> LOGT) > 0 ? (128 >> LOGT) : 1;
     using C = TileCfg<LOGN, 0, LOGN, 0, LOGT, 3, TPC, INV, 1, 2>;
 };
 

@@ -676,6 +676,49 @@ NTT_HD constexpr uint32_t swap_thread_bits(uint32_t t, uint32_t packed) {
     return t;
 }
 
+// The same exchange search for G bank-index bits (a word's bank is the XOR of
+// its e-bits' residues mod G after a G-bit fold, and 2^G lanes access at
+// once): G = 5 for 32-bit words, whose 32 lanes of a warp hit the 32 banks.
+// Up to 8 exchanges (i | j << 4 per byte).
+NTT_HD constexpr uint64_t pass_swaps_g(int pe, int r, int logt, int g) {
+    int pos[32] = {};
+    for (int i = 0; i < logt; ++i) pos[i] = i < pe ? i : i + r;
+    uint64_t packed = 0;
+    uint32_t used = 0;
+    int ns = 0;
+    const int lim = logt < g ? logt : g;
+    for (int i = 0; i < lim; ++i) {
+        if (used & (1u << (pos[i] % g))) {
+            for (int j = g; j < logt; ++j) {
+                bool ok = !(used & (1u << (pos[j] % g)));
+                for (int k = i + 1; k < lim; ++k) ok = ok && (pos[j] % g) != (pos[k] % g);
+                if (ok) {
+                    const int tmp = pos[i];
+                    pos[i] = pos[j];
+                    pos[j] = tmp;
+                    packed |= (uint64_t)(i | (j << 4)) << (8 * ns);
+                    ++ns;
+                    break;
+                }
+            }
+        }
+        used |= 1u << (pos[i] % g);
+    }
+    return packed;
+}
+
+NTT_HD constexpr uint32_t swap_thread_bits_g(uint32_t t, uint64_t packed) {
+    int n = 0;
+    while (n < 8 && ((packed >> (8 * n)) & 0xffu)) ++n;
+    for (int s = n - 1; s >= 0; --s) {
+        const uint32_t p = (uint32_t)(packed >> (8 * s)) & 0xffu;
+        const uint32_t i = p & 15u, j = p >> 4;
+        const uint32_t d = ((t >> i) ^ (t >> j)) & 1u;
+        t ^= (d << i) | (d << j);
+    }
+    return t;
+}
+
 // ---- passes: one fused group of r stages in registers ----
 template <class C, int P>
 struct PassGeom {

@@ -258,8 +258,11 @@ int build_plan_host(PlanHost& h, uint32_t log2n, const uint64_t* moduli, uint32_
         h.inv32.resize(h.inv.size());
         for (size_t k = 0; k < h.fwd.size(); ++k) {
             const uint64_t q = moduli[k >> log2n];
-            h.fwd32[k] = Tw32{(uint32_t)h.fwd[k].w, sp32(h.fwd[k].w, q)};
-            h.inv32[k] = Tw32{(uint32_t)h.inv[k].w, sp32(h.inv[k].w, q)};
+            // N = 1024 tables are stored with each stage >= 5 transposed (the
+            // one-warp-per-row kernel's order, tw1024_perm)
+            const size_t pos = log2n == 10 ? ((k >> 10) << 10) + tw1024_perm((uint32_t)(k & 1023)) : k;
+            h.fwd32[pos] = Tw32{(uint32_t)h.fwd[k].w, sp32(h.fwd[k].w, q)};
+            h.inv32[pos] = Tw32{(uint32_t)h.inv[k].w, sp32(h.inv[k].w, q)};
         }
         h.consts32.resize(n_moduli);
         for (uint32_t l = 0; l < n_moduli; ++l) {
