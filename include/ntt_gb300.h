@@ -130,6 +130,21 @@ int ntt_forward(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, void* cu
 int ntt_inverse(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, void* cuda_stream);
 
 /*
+ * Both directions of one step at once (Sec. IV-A batches the independent
+ * transforms of one iteration into one launch; config: the 3780 digit NTTs
+ * and 1260 accumulator INTTs of a blind-rotation step): the forward of
+ * fwd_plan's rows d_fwd_in -> d_fwd_out and the inverse of inv_plan's rows
+ * d_inv_in -> d_inv_out, with the same results as ntt_forward followed by
+ * ntt_inverse.  The two transforms run concurrently, in one launch for
+ * 32-bit-word plans at N = 1024, otherwise one after the other on the stream.
+ * Both plans must have the same N and word size.  Each transform may work in
+ * place, but no buffer of one transform may overlap a buffer of the other
+ * (NTT_ERR_ARG).  Layout, alignment and ownership as ntt_forward.
+ */
+int ntt_forward_inverse(ntt_plan_t fwd_plan, const uint64_t* d_fwd_in, uint64_t* d_fwd_out,
+                        ntt_plan_t inv_plan, const uint64_t* d_inv_in, uint64_t* d_inv_out, void* cuda_stream);
+
+/*
  * Row-range variants: transform rows [row_begin, row_begin + n_rows) of the
  * plan's layout; d_in / d_out point at the FIRST ROW OF THE PLAN (row 0), so
  * a multi-device caller can give each device a disjoint range of one buffer

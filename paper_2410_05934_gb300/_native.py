@@ -40,6 +40,7 @@ SIGNATURES = [
     ("ntt_plan_shape", i32, [vp, U32P, U32P, U32P, U64P]),
     ("ntt_forward", i32, [vp, vp, vp, vp]),
     ("ntt_inverse", i32, [vp, vp, vp, vp]),
+    ("ntt_forward_inverse", i32, [vp, vp, vp, vp, vp, vp, vp]),
     ("ntt_forward_rows", i32, [vp, vp, vp, u64, u64, vp]),
     ("ntt_inverse_rows", i32, [vp, vp, vp, u64, u64, vp]),
     ("poly_mul_pointwise", i32, [vp, vp, vp, vp, u32, vp]),

@@ -339,6 +339,36 @@ int ntt_inverse(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, void* cu
     return transform(plan, true, d_in, d_out, 0, plan ? plan->h.rows : 0, cuda_stream);
 }
 
+int ntt_forward_inverse(ntt_plan_t fwd_plan, const uint64_t* d_fwd_in, uint64_t* d_fwd_out,
+                        ntt_plan_t inv_plan, const uint64_t* d_inv_in, uint64_t* d_inv_out, void* cuda_stream) {
+    if (!fwd_plan || !inv_plan || !d_fwd_in || !d_fwd_out || !d_inv_in || !d_inv_out) return NTT_ERR_ARG;
+    if (fwd_plan->h.log2n != inv_plan->h.log2n || word32(fwd_plan) != word32(inv_plan)) return NTT_ERR_ARG;
+    const uint64_t word = word32(fwd_plan) ? 4 : 8;
+    const uint64_t fb = (fwd_plan->h.rows << fwd_plan->h.log2n) * word, ib = (inv_plan->h.rows << inv_plan->h.log2n) * word;
+    auto overlap = [](const void* a, uint64_t na, const void* b, uint64_t nb) {
+        const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+        return na && nb && x < y + nb && y < x + na;
+    };
+    if (overlap(d_fwd_in, fb, d_inv_in, ib) || overlap(d_fwd_in, fb, d_inv_out, ib) ||
+        overlap(d_fwd_out, fb, d_inv_in, ib) || overlap(d_fwd_out, fb, d_inv_out, ib))
+        return NTT_ERR_ARG;
+    if (!word32(fwd_plan)) {
+        const int rc = transform(fwd_plan, false, d_fwd_in, d_fwd_out, 0, fwd_plan->h.rows, cuda_stream);
+        return rc ? rc : transform(inv_plan, true, d_inv_in, d_inv_out, 0, inv_plan->h.rows, cuda_stream);
+    }
+    if (!aligned16(d_fwd_in) || !aligned16(d_fwd_out) || !aligned16(d_inv_in) || !aligned16(d_inv_out))
+        return NTT_ERR_ALIGN;
+    int rc = check_device(fwd_plan);
+    if (!rc) rc = check_device(inv_plan);
+    if (rc) return rc;
+    fwd_plan->last_launches = 0;
+    inv_plan->last_launches = 0;
+    return launch_ntt32_fwd_inv(plan32_dev(fwd_plan), reinterpret_cast<const uint32_t*>(d_fwd_in),
+                                reinterpret_cast<uint32_t*>(d_fwd_out), fwd_plan->h.rows, plan32_dev(inv_plan),
+                                reinterpret_cast<const uint32_t*>(d_inv_in), reinterpret_cast<uint32_t*>(d_inv_out),
+                                inv_plan->h.rows, fwd_plan->h.log2n, cuda_stream, &fwd_plan->last_launches);
+}
+
 int ntt_forward_rows(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, uint64_t row_begin,
                      uint64_t n_rows, void* cuda_stream) {
     return transform(plan, false, d_in, d_out, row_begin, n_rows, cuda_stream);

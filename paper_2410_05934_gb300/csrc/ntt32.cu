@@ -66,6 +66,34 @@ __global__ void __launch_bounds__(128, INV ? 6 : 8) k_ntt32_w1024(Args32 a) {
     }
 }
 
+// N = 1024, both directions in one grid: CTAs [0, ctas_i) run the inverse
+// rows of ai, the others the forward rows of af (the two are independent,
+// e.g. the accumulator INTTs and digit NTTs of one step of a blind
+// rotation).  One launch fills the SMs with both row sets at once, where
+// two launches leave the second one's rows waiting for the first one's tail.
+__global__ void __launch_bounds__(128, 8) k_ntt32_w1024_fi(Args32 af, Args32 ai, uint32_t ctas_i) {
+    __shared__ __align__(16) uint32_t sm_rows[4 * 1024];
+    pdl_begin();
+    const int w = threadIdx.x >> 5, t = threadIdx.x & 31;
+    uint32_t* sm = sm_rows + w * 1024;
+    Row1024 r;
+    if (blockIdx.x >= ctas_i) {
+        const Loc32 L = locate1024(af, blockIdx.x - ctas_i, w);
+        w1024_fwd_a(r, af, L, t, sm);
+        __syncwarp();
+        w1024_fwd_b(r, af, L, t, sm);
+        __syncwarp();
+        w1024_store(af, L, t, sm);
+    } else {
+        const Loc32 L = locate1024(ai, blockIdx.x, w);
+        w1024_inv_a(ai, L, t, sm);
+        __syncwarp();
+        w1024_inv_b(r, ai, L, t, sm);
+        __syncwarp();
+        w1024_inv_c(r, ai, L, t, sm);
+    }
+}
+
 template <bool INV>
 static int launch32_w1024(const Args32& a, cudaStream_t st) {
     const uint64_t ctas = ((uint64_t)a.n_rows + 3) / 4;
@@ -128,6 +156,48 @@ int launch_ntt32(const Plan32Dev& p, bool inverse, const uint32_t* in, uint32_t*
         case 10: return inverse ? launch32_w1024<true>(a, st) : launch32_w1024<false>(a, st);
         default: return NTT_ERR_UNSUPPORTED;
     }
+}
+
+static Args32 args32(const Plan32Dev& p, bool inverse, const uint32_t* in, uint32_t* out, uint64_t n_rows) {
+    Args32 a;
+    a.in = in;
+    a.out = out;
+    a.tw = inverse ? p.inv : p.fwd;
+    a.lc = p.lc;
+    a.status = p.status;
+    a.row_begin = 0;
+    a.n_rows = (uint32_t)n_rows;
+    a.n_moduli = p.n_moduli;
+    a.check = p.check;
+    a.mod_magic = fdiv_magic(p.n_moduli);
+    return a;
+}
+
+int launch_ntt32_fwd_inv(const Plan32Dev& pf, const uint32_t* fin, uint32_t* fout, uint64_t f_rows,
+                         const Plan32Dev& pi, const uint32_t* iin, uint32_t* iout, uint64_t i_rows, uint32_t log2n,
+                         void* stream, uint32_t* launches) {
+    if (f_rows > 0xffffffffull || i_rows > 0xffffffffull) return NTT_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (log2n != 10 || f_rows == 0 || i_rows == 0) {     // the two transforms in stream order
+        int rc = launch_ntt32(pf, false, fin, fout, 0, f_rows, log2n, stream, launches);
+        return rc ? rc : launch_ntt32(pi, true, iin, iout, 0, i_rows, log2n, stream, launches);
+    }
+    const Args32 af = args32(pf, false, fin, fout, f_rows), ai = args32(pi, true, iin, iout, i_rows);
+    const uint64_t ctas_i = (i_rows + 3) / 4, ctas = ctas_i + (f_rows + 3) / 4;
+    if (ctas > 0x7fffffffull) return NTT_ERR_ARG;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)ctas);
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, k_ntt32_w1024_fi, af, ai, (uint32_t)ctas_i) != cudaSuccess) return NTT_ERR_CUDA;
+    if (launches) ++*launches;
+    return NTT_OK;
 }
 
 __global__ void k_pointwise32(const uint32_t* __restrict__ a, const uint32_t* __restrict__ b, uint32_t* c,

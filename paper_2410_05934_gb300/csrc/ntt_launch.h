@@ -59,6 +59,11 @@ struct Plan32Dev {
 };
 int launch_ntt32(const Plan32Dev& p, bool inverse, const uint32_t* in, uint32_t* out, uint64_t row_begin,
                  uint64_t n_rows, uint32_t log2n, void* stream, uint32_t* launches);
+// the forward rows of pf and the inverse rows of pi (independent buffers):
+// one grid at N = 1024, else the two transforms in stream order
+int launch_ntt32_fwd_inv(const Plan32Dev& pf, const uint32_t* fin, uint32_t* fout, uint64_t f_rows,
+                         const Plan32Dev& pi, const uint32_t* iin, uint32_t* iout, uint64_t i_rows, uint32_t log2n,
+                         void* stream, uint32_t* launches);
 int launch_pointwise32(const Plan32Dev& p, uint32_t log2n, const uint32_t* a, const uint32_t* b, uint32_t* c,
                        uint64_t n_rows, void* stream, uint32_t* launches);
 

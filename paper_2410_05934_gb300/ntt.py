@@ -355,6 +355,20 @@ class BConv:
 
 
 # C-ABI names as plain functions
+def forward_inverse(fwd_plan, x_fwd, x_inv, inv_plan, out_fwd=None, out_inv=None, stream=None):
+    """ntt_forward_inverse: the forward transform of fwd_plan's rows and the
+    inverse of inv_plan's rows, issued together (one launch for 32-bit words
+    at N = 1024).  The two transforms' buffers must not overlap."""
+    out_fwd = x_fwd if out_fwd is None else out_fwd
+    out_inv = x_inv if out_inv is None else out_inv
+    nf, ni = fwd_plan.rows * fwd_plan.n, inv_plan.rows * inv_plan.n
+    check(load().ntt_forward_inverse(fwd_plan.handle, _ptr(x_fwd, nf, "fwd in", fwd_plan.word),
+                                     _ptr(out_fwd, nf, "fwd out", fwd_plan.word), inv_plan.handle,
+                                     _ptr(x_inv, ni, "inv in", inv_plan.word), _ptr(out_inv, ni, "inv out", inv_plan.word),
+                                     _stream_handle(stream)), "ntt_forward_inverse")
+    return out_fwd, out_inv
+
+
 def ntt_plan(log2n, moduli, batch=1, flags=0):
     return Plan(log2n, moduli, batch, flags)
 

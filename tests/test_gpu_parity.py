@@ -526,3 +526,55 @@ def test_word32_back_to_back_in_place(oracle):
     p.inverse(d)
     assert torch.equal(d, ref_in)
     assert p.status() == 0
+
+
+def test_forward_inverse_word32_tfhe_batch(oracle):
+    """ntt_forward_inverse on the blind-rotation shape with 32-bit words (3780
+    digit rows forward, 1260 rows inverse, one launch) equals the oracle's
+    forward and inverse definitions on sampled rows and the separate calls
+    on every row; issued twice in a row in place, with no host
+    synchronisation in between."""
+    q = Q30[0]
+    xf = W.signed_digits_mod(W.DEFAULT_SEED, 3, 3780 * 1024, q).reshape(3780, 1024)
+    xi = W.uniform_mod(W.DEFAULT_SEED, 4, 1260 * 1024, q).reshape(1260, 1024)
+    pf = ntt.Plan(10, [q], 3780, flags=ntt.NTT_FLAG_WORD32)
+    pi = ntt.Plan(10, [q], 1260, flags=ntt.NTT_FLAG_WORD32)
+    df, di = _to_dev32(xf), _to_dev32(xi)
+    of, oi = torch.empty_like(df), torch.empty_like(di)
+    ntt.forward_inverse(pf, df, di, pi, of, oi)
+    assert pf.last_launches() == 1
+    rf, ri = np.array([0, 1, 2000, 3779]), np.array([0, 7, 1259])
+    assert np.array_equal(_to_host32(of)[rf], oracle.transform_rows(xf[rf], [q] * 4))
+    assert np.array_equal(_to_host32(oi)[ri], oracle.transform_rows(xi[ri], [q] * 3, inverse=True))
+    sf, si = torch.empty_like(df), torch.empty_like(di)
+    pf.forward(df, sf)
+    pi.inverse(di, si)
+    assert torch.equal(of, sf) and torch.equal(oi, si)
+    # twice in place, back to back: forward twice and inverse twice
+    ntt.forward_inverse(pf, of, oi, pi)
+    pf.forward(sf)
+    pi.inverse(si)
+    assert torch.equal(of, sf) and torch.equal(oi, si)
+    assert pf.status() == 0 and pi.status() == 0
+
+
+def test_forward_inverse_rules_and_64_bit(oracle):
+    """64-bit plans run the two transforms in stream order with the same
+    results; overlapping buffers of the two transforms, different N and
+    mixed word sizes are argument errors."""
+    q = W.Q62_N1024
+    x = W.rows_uniform(43, 10, [q] * 6, 1024)
+    pf, pi = ntt.Plan(10, [q], 4), ntt.Plan(10, [q], 2)
+    d = to_dev(x)
+    f, i = torch.empty_like(d[:4]), torch.empty_like(d[4:])
+    ntt.forward_inverse(pf, d[:4].contiguous(), d[4:].contiguous(), pi, f, i)
+    assert np.array_equal(to_host(f), oracle.transform_rows(x[:4], [q] * 4))
+    assert np.array_equal(to_host(i), oracle.transform_rows(x[4:], [q] * 2, inverse=True))
+    with pytest.raises(ntt.NttError):
+        ntt.forward_inverse(pf, d[:4], d[2:4], pi)                 # inverse rows inside the forward's buffer
+    with pytest.raises(ntt.NttError):
+        ntt.forward_inverse(pf, f, i, ntt.Plan(11, [_prime_62(11)], 1),
+                            out_inv=torch.empty((1, 2048), dtype=torch.int64, device="cuda"))
+    p32 = ntt.Plan(10, [Q30[0]], 2, flags=ntt.NTT_FLAG_WORD32)
+    with pytest.raises(ntt.NttError):
+        ntt.forward_inverse(pf, f, torch.zeros((2, 1024), dtype=torch.int32, device="cuda"), p32)
