@@ -194,8 +194,10 @@ int ntt_inverse_mul(ntt_plan_t plan, const uint64_t* d_a, const uint32_t* a_poly
  *   d_out   [n_polys][L-1][N] NTT domain; must not overlap d_in or d_work
  *   d_work  [n_polys][N] caller-owned scratch (the last limb's coefficients)
  *   n_polys 0 = the plan's batch; at most the plan's batch
- * The plan needs L >= 2 and a last modulus distinct from the others.  One
- * strided copy and two or three kernel launches on cuda_stream.
+ * The plan needs L >= 2 and a last modulus distinct from the others.  The
+ * INTT reads the last limb's rows of d_in in place (on the default schedule
+ * for n_polys rows) and the forward runs on the plan's schedule: two to four
+ * kernel launches on cuda_stream.
  * Errors: ARG, ALIGN, UNSUPPORTED, CUDA.
  */
 int ntt_rescale(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, uint64_t* d_work, uint32_t n_polys,

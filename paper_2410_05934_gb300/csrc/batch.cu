@@ -162,6 +162,7 @@ __global__ void __launch_bounds__(NTT_BATCH_THREADS, BatchOcc<MC, NMAX>::ctas)
         a.aux_q = 0;
         a.nat = 0;
         a.has_map = 0;
+        a.in_skip = 0;
         if (rq.inverse)
             batch_dispatch<true, MC, NMAX>(a, rq, it.n_rows, smem);
         else
@@ -254,6 +255,7 @@ __global__ void __launch_bounds__(NTT_BATCH_THREADS, NTT_BATCH_MIN_CTAS)
         a.aux_q = 0;
         a.nat = 0;
         a.has_map = 0;
+        a.in_skip = 0;
         if (sr.inverse)
             batch_dispatch<true, MC, 16>(a, rq, n_rows, smem);
         else

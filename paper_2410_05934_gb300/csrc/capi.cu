@@ -468,16 +468,14 @@ int ntt_rescale(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, uint64_t
     int rc = check_device(plan);
     if (rc) return rc;
     plan->last_launches = 0;
-    cudaStream_t st = (cudaStream_t)cuda_stream;
     const uint32_t log2n = plan->h.log2n;
     const size_t n = (size_t)1 << log2n;
-    // 1. the dropped limb's rows (every L-th row) into the work buffer
-    if (cudaMemcpy2DAsync(d_work, n * sizeof(uint64_t), d_in + (size_t)(L - 1) * n, (size_t)L * n * sizeof(uint64_t),
-                          n * sizeof(uint64_t), n_polys, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-        return NTT_ERR_CUDA;
-    // 2. back to coefficients under the dropped modulus (the plan's schedule)
+    // 1. the dropped limb's rows (every L-th row of d_in, read in place by the
+    //    first kernel) back to coefficients under the dropped modulus, into
+    //    the work buffer, on the default schedule for that many rows
+    const int inv_idx = sched_index(log2n, default_schedule(log2n, n_polys));
     int idx = sched_index(log2n, plan->schedule);
-    if (idx < 0) return NTT_ERR_UNSUPPORTED;
+    if (idx < 0 || inv_idx < 0) return NTT_ERR_UNSUPPORTED;
     PlanDev last = plan_dev(plan);
     last.fwd = plan->d_fwd + (size_t)(L - 1) * n;
     last.inv = plan->d_inv + (size_t)(L - 1) * n;
@@ -485,9 +483,11 @@ int ntt_rescale(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, uint64_t
     last.n_moduli = 1;
     last.check = 0;
     last.mc = plan->h.consts[L - 1].q < (1ull << NTT_SMALL_MODULUS_BITS) ? 1u : 0u;
-    rc = g_table[idx].inv(last, d_work, d_work, 0, n_polys, cuda_stream, &plan->last_launches);
+    last.in_skip = L - 1;
+    rc = g_table[inv_idx].inv(last, d_in + (size_t)(L - 1) * n, d_work, 0, n_polys, cuda_stream,
+                              &plan->last_launches);
     if (rc) return rc;
-    // 3. forward transform of c = (h - [w + h]) mod q_i with the Rescale
+    // 2. forward transform of c = (h - [w + h]) mod q_i with the Rescale
     //    epilogue, over the n_polys x (L - 1) output rows (direct-form first kernel)
     auto forward_first_pipelined = [](int k) { return (g_params[k].kind == 1 ? g_params[k].pipe
                                                                           : form_col(g_params[k].pipe)) == 1; };

@@ -124,6 +124,7 @@ static TileArgs emu_args(const PlanDev& p, const uint64_t* in, uint64_t* out, ui
         a.b_map[i] = p.b_map[i];
     }
     a.otf = C::INV ? p.otf_inv : p.otf_fwd;
+    a.in_skip = p.in_skip;
     return a;
 }
 
@@ -296,30 +297,61 @@ static void emu_passes32(std::vector<Regs32<C>>& st, const Args32& a, const std:
     }
 }
 
-// The N = 1024 kernel: four rows (warps) per CTA, every phase for all 128
-// threads before the next (the kernel's __syncwarp points).
-template <bool INV>
-static int emu_ntt32_w1024(const Args32& a) {
-    const uint32_t ctas = (a.n_rows + 3) / 4;
-    std::vector<uint32_t> sm(4 * 1024, 0xdeadbeefu);
+// The N = 1024 kernel: persistent CTAs of four warps walking their row lists
+// with two landing buffers per warp (a small pseudo-grid of 3 CTAs, so that
+// warps take several rows and the buffers rotate), every phase for all 128
+// threads before the next (the kernel's __syncwarp points); the 16-byte
+// copies of a prefetch land at once, where the kernel's would land by the
+// wait two rows later.
+static int emu_w1024_rows(const Args32& af, const Args32& ai, uint64_t f_rows, uint64_t i_rows) {
+    const uint32_t quads_i = (uint32_t)((i_rows + 3) / 4), quads = quads_i + (uint32_t)((f_rows + 3) / 4);
+    const uint32_t grid = quads < 3 ? quads : 3;
     std::vector<Row1024> r(128);
-    for (uint32_t cta = 0; cta < ctas; ++cta) {
-        Loc32 L[4];
-        for (int w = 0; w < 4; ++w) L[w] = locate1024(a, cta, w);
-        auto each = [&](auto&& phase) {
-            for (int tid = 0; tid < 128; ++tid) phase(r[tid], L[tid >> 5], tid & 31, sm.data() + (tid >> 5) * 1024);
-        };
-        if (!INV) {
-            each([&](Row1024& x, const Loc32& l, int t, uint32_t* s) { w1024_fwd_a(x, a, l, t, s); });
-            each([&](Row1024& x, const Loc32& l, int t, uint32_t* s) { w1024_fwd_b(x, a, l, t, s); });
-            each([&](Row1024&, const Loc32& l, int t, uint32_t* s) { w1024_store(a, l, t, s); });
-        } else {
-            each([&](Row1024&, const Loc32& l, int t, uint32_t* s) { w1024_inv_a(a, l, t, s); });
-            each([&](Row1024& x, const Loc32& l, int t, uint32_t* s) { w1024_inv_b(x, a, l, t, s); });
-            each([&](Row1024& x, const Loc32& l, int t, uint32_t* s) { w1024_inv_c(x, a, l, t, s); });
+    for (uint32_t cta = 0; cta < grid; ++cta) {
+        std::vector<uint32_t> sm(4 * 3 * 1024, 0xdeadbeefu);
+        auto land = [&](int w, uint32_t k) { return sm.data() + w * 3072 + (k & 1) * 1024; };
+        auto work = [&](int w) { return sm.data() + w * 3072 + 2048; };
+        W1024Pick cur[4], nxt[4], after[4];
+        for (int w = 0; w < 4; ++w) {
+            cur[w] = w1024_pick(af, ai, quads_i, quads, cta, grid, 0, w);
+            nxt[w] = w1024_pick(af, ai, quads_i, quads, cta, grid, 1, w);
+        }
+        for (int tid = 0; tid < 128; ++tid) {
+            const int w = tid >> 5, t = tid & 31;
+            w1024_prefetch(cur[w].inv ? ai : af, cur[w].L, t, land(w, 0));
+            w1024_prefetch(nxt[w].inv ? ai : af, nxt[w].L, t, land(w, 1));
+        }
+        for (uint32_t k = 0; cur[0].live; ++k) {
+            for (int w = 0; w < 4; ++w) after[w] = w1024_pick(af, ai, quads_i, quads, cta, grid, k + 2, w);
+            auto each = [&](auto&& phase) {
+                for (int tid = 0; tid < 128; ++tid) phase(r[tid], tid >> 5, tid & 31);
+            };
+            const bool inv = cur[0].inv;     // one quad per CTA and step: the same direction in every warp
+            const Args32& a = inv ? ai : af;
+            if (!inv) {
+                each([&](Row1024& x, int w, int t) { w1024_fwd_a_land(x, a, cur[w].L, t, land(w, k)); });
+                each([&](Row1024&, int w, int t) { w1024_prefetch(after[w].inv ? ai : af, after[w].L, t, land(w, k)); });
+                each([&](Row1024& x, int w, int t) { w1024_write_a(x, cur[w].L, t, work(w)); });
+                each([&](Row1024& x, int w, int t) { w1024_fwd_b(x, a, cur[w].L, t, work(w)); });
+                each([&](Row1024&, int w, int t) { w1024_store(a, cur[w].L, t, work(w)); });
+            } else {
+                each([&](Row1024&, int w, int t) { w1024_inv_a_land(a, cur[w].L, t, land(w, k), work(w)); });
+                each([&](Row1024&, int w, int t) { w1024_prefetch(after[w].inv ? ai : af, after[w].L, t, land(w, k)); });
+                each([&](Row1024& x, int w, int t) { w1024_inv_b(x, a, cur[w].L, t, work(w)); });
+                each([&](Row1024& x, int w, int t) { w1024_inv_c(x, a, cur[w].L, t, work(w)); });
+            }
+            for (int w = 0; w < 4; ++w) {
+                cur[w] = nxt[w];
+                nxt[w] = after[w];
+            }
         }
     }
     return NTT_OK;
+}
+
+template <bool INV>
+static int emu_ntt32_w1024(const Args32& a) {
+    return INV ? emu_w1024_rows(a, a, 0, a.n_rows) : emu_w1024_rows(a, a, a.n_rows, 0);
 }
 
 template <int LOGN, bool INV>
@@ -641,6 +673,33 @@ int nttemu_transform32(void* plan, int inverse, const uint32_t* in, uint32_t* ou
 #undef NTT_EMU32_CASE
 }
 
+// ntt_forward_inverse of two N = 1024 32-bit-word plans: one pseudo-grid
+// over the inverse rows of iplan and the forward rows of fplan
+int nttemu_forward_inverse32(void* fplan, const uint32_t* fin, uint32_t* fout, void* iplan, const uint32_t* iin,
+                             uint32_t* iout) {
+    EmuPlan* pf = static_cast<EmuPlan*>(fplan);
+    EmuPlan* pi = static_cast<EmuPlan*>(iplan);
+    if (!pf || !pi || !fin || !fout || !iin || !iout) return NTT_ERR_ARG;
+    if (!(pf->h.flags & NTT_FLAG_WORD32) || !(pi->h.flags & NTT_FLAG_WORD32) || pf->h.log2n != 10 ||
+        pi->h.log2n != 10)
+        return NTT_ERR_ARG;
+    auto args = [](EmuPlan* p, bool inverse, const uint32_t* in, uint32_t* out) {
+        Args32 a;
+        a.in = in;
+        a.out = out;
+        a.tw = inverse ? p->h.inv32.data() : p->h.fwd32.data();
+        a.lc = p->h.consts32.data();
+        a.status = &p->status;
+        a.row_begin = 0;
+        a.n_rows = (uint32_t)p->h.rows;
+        a.n_moduli = p->h.n_moduli;
+        a.check = (p->h.flags & NTT_FLAG_CHECK) ? 1u : 0u;
+        a.mod_magic = fdiv_magic(p->h.n_moduli);
+        return a;
+    };
+    return emu_w1024_rows(args(pf, false, fin, fout), args(pi, true, iin, iout), pf->h.rows, pi->h.rows);
+}
+
 int nttemu_pointwise32(void* plan, const uint32_t* x, const uint32_t* y, uint32_t* c, uint64_t n_rows) {
     EmuPlan* p = static_cast<EmuPlan*>(plan);
     if (!p || !(p->h.flags & NTT_FLAG_WORD32) || n_rows > p->h.rows) return NTT_ERR_ARG;
@@ -694,7 +753,6 @@ int nttemu_rescale(void* plan, uint32_t sched, const uint64_t* in, uint64_t* out
     const EmuEntry* e = emu_find(p->h.log2n, sched);
     if (!e) return NTT_ERR_ARG;
     const size_t n = (size_t)1 << p->h.log2n;
-    for (uint32_t k = 0; k < n_polys; ++k) memcpy(work + k * n, in + ((size_t)k * L + L - 1) * n, n * sizeof(uint64_t));
     PlanDev last;
     last.fwd = p->h.fwd.data() + (size_t)(L - 1) * n;
     last.inv = p->h.inv.data() + (size_t)(L - 1) * n;
@@ -708,9 +766,11 @@ int nttemu_rescale(void* plan, uint32_t sched, const uint64_t* in, uint64_t* out
     last.aux_q = 0;
     last.nat = 0;
     last.has_map = 0;
-    int rc = e->inv(last, work, work, 0, n_polys);
+    last.in_skip = L - 1;       // the dropped limb's rows, read in place
+    int rc = e->inv(last, in + (size_t)(L - 1) * n, work, 0, n_polys);
     if (rc) return rc;
     PlanDev d = last;
+    d.in_skip = 0;
     d.fwd = p->h.fwd.data();
     d.inv = p->h.inv.data();
     d.lc = p->h.consts.data();

@@ -67,6 +67,7 @@ __global__ void __launch_bounds__(CF::THREADS) k_ntt_grouped(const GroupSeg* __r
     a.nat = 0;
     a.has_map = 0;
     a.otf = nullptr;
+    a.in_skip = 0;
     if (sg.inverse)
         tile_group<CI>(a, b - sg.group_begin, smem);
     else

@@ -37,78 +37,90 @@ __global__ void __launch_bounds__(C::THREADS) k_ntt32(Args32 a) {
     store32<C>(a, L, t, sm);
 }
 
-// N = 1024: one warp per row, four rows per CTA (see ntt32.cuh)
-template <bool INV>
-// Registers for 8 resident CTAs per SM in the forward (64 per thread: a
-// batch of a few thousand rows is about one wave, so more warps per SM is
-// what hides the latency; 14 % faster than the unbounded 72), while the
-// inverse gets room instead (it spills below 72 registers, and its batch of a
-// thousand rows is well under one wave).
-__global__ void __launch_bounds__(128, INV ? 6 : 8) k_ntt32_w1024(Args32 a) {
-    __shared__ __align__(16) uint32_t sm_rows[4 * 1024];
+// N = 1024: persistent CTAs of four warps, each warp walking its list of
+// rows with the next rows' loads in flight (see ntt32.cuh); inverse rows of
+// ai (quads [0, quads_i)) and forward rows of af in one grid.  Shared
+// memory per warp: two landing buffers and the work buffer (12 KiB).
+#define NTT_W1024_SMEM (4 * 3 * 1024 * sizeof(uint32_t))
+#ifndef NTT_W1024_CTAS_PER_SM
+#define NTT_W1024_CTAS_PER_SM 3     // resident CTAs per SM the grid is sized for
+#endif
+__global__ void __launch_bounds__(128, NTT_W1024_CTAS_PER_SM) k_ntt32_w1024(Args32 af, Args32 ai, uint32_t quads_i,
+                                                                         uint32_t quads) {
+    extern __shared__ __align__(16) uint32_t sm_w1024[];
     pdl_begin();
     const int w = threadIdx.x >> 5, t = threadIdx.x & 31;
-    const Loc32 L = locate1024(a, blockIdx.x, w);
-    uint32_t* sm = sm_rows + w * 1024;
+    uint32_t* land[2] = {sm_w1024 + w * 3072, sm_w1024 + w * 3072 + 1024};
+    uint32_t* work = sm_w1024 + w * 3072 + 2048;
+    const uint32_t grid = gridDim.x, cta = blockIdx.x;
+    W1024Pick cur = w1024_pick(af, ai, quads_i, quads, cta, grid, 0, w);
+    W1024Pick nxt = w1024_pick(af, ai, quads_i, quads, cta, grid, 1, w);
+    w1024_prefetch(cur.inv ? ai : af, cur.L, t, land[0]);
+    async_commit();
+    w1024_prefetch(nxt.inv ? ai : af, nxt.L, t, land[1]);
+    async_commit();
     Row1024 r;
-    if (!INV) {
-        w1024_fwd_a(r, a, L, t, sm);
+    for (uint32_t k = 0; cur.live; ++k) {
+        uint32_t* ld = land[k & 1];
+        async_wait_prev();          // row k has landed (row k + 1 may be in flight)
         __syncwarp();
-        w1024_fwd_b(r, a, L, t, sm);
-        __syncwarp();
-        w1024_store(a, L, t, sm);
-    } else {
-        w1024_inv_a(a, L, t, sm);
-        __syncwarp();
-        w1024_inv_b(r, a, L, t, sm);
-        __syncwarp();
-        w1024_inv_c(r, a, L, t, sm);
+        const W1024Pick after = w1024_pick(af, ai, quads_i, quads, cta, grid, k + 2, w);
+        if (!cur.inv) {
+            w1024_fwd_a_land(r, af, cur.L, t, ld);
+            __syncwarp();           // every lane has read the landing buffer: refill it
+            w1024_prefetch(after.inv ? ai : af, after.L, t, ld);
+            async_commit();
+            w1024_write_a(r, cur.L, t, work);
+            __syncwarp();
+            w1024_fwd_b(r, af, cur.L, t, work);
+            __syncwarp();
+            w1024_store(af, cur.L, t, work);
+        } else {
+            w1024_inv_a_land(ai, cur.L, t, ld, work);
+            __syncwarp();
+            w1024_prefetch(after.inv ? ai : af, after.L, t, ld);
+            async_commit();
+            w1024_inv_b(r, ai, cur.L, t, work);
+            __syncwarp();
+            w1024_inv_c(r, ai, cur.L, t, work);
+        }
+        __syncwarp();               // the work buffer is free for the next row
+        cur = nxt;
+        nxt = after;
     }
+    async_wait_all();
 }
 
-// N = 1024, both directions in one grid: CTAs [0, ctas_i) run the inverse
-// rows of ai, the others the forward rows of af (the two are independent,
-// e.g. the accumulator INTTs and digit NTTs of one step of a blind
-// rotation).  One launch fills the SMs with both row sets at once, where
-// two launches leave the second one's rows waiting for the first one's tail.
-__global__ void __launch_bounds__(128, 8) k_ntt32_w1024_fi(Args32 af, Args32 ai, uint32_t ctas_i) {
-    __shared__ __align__(16) uint32_t sm_rows[4 * 1024];
-    pdl_begin();
-    const int w = threadIdx.x >> 5, t = threadIdx.x & 31;
-    uint32_t* sm = sm_rows + w * 1024;
-    Row1024 r;
-    if (blockIdx.x >= ctas_i) {
-        const Loc32 L = locate1024(af, blockIdx.x - ctas_i, w);
-        w1024_fwd_a(r, af, L, t, sm);
-        __syncwarp();
-        w1024_fwd_b(r, af, L, t, sm);
-        __syncwarp();
-        w1024_store(af, L, t, sm);
-    } else {
-        const Loc32 L = locate1024(ai, blockIdx.x, w);
-        w1024_inv_a(ai, L, t, sm);
-        __syncwarp();
-        w1024_inv_b(r, ai, L, t, sm);
-        __syncwarp();
-        w1024_inv_c(r, ai, L, t, sm);
-    }
-}
-
-template <bool INV>
-static int launch32_w1024(const Args32& a, cudaStream_t st) {
-    const uint64_t ctas = ((uint64_t)a.n_rows + 3) / 4;
-    if (ctas == 0) return NTT_OK;
+static int launch32_w1024_rows(const Args32& af, const Args32& ai, uint64_t f_rows, uint64_t i_rows, cudaStream_t st) {
+    const uint64_t quads_i = (i_rows + 3) / 4, quads = quads_i + (f_rows + 3) / 4;
+    if (quads == 0) return NTT_OK;
+    if (quads > 0x7fffffffull) return NTT_ERR_ARG;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return NTT_ERR_CUDA;
+    uint64_t ctas = (uint64_t)(sms > 0 ? sms : 1) * NTT_W1024_CTAS_PER_SM;
+    if (ctas > quads) ctas = quads;
+    if (cudaFuncSetAttribute(k_ntt32_w1024, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NTT_W1024_SMEM) !=
+        cudaSuccess)
+        return NTT_ERR_CUDA;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)ctas);
     cfg.blockDim = dim3(128);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = NTT_W1024_SMEM;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_ntt32_w1024<INV>, a) == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
+    return cudaLaunchKernelEx(&cfg, k_ntt32_w1024, af, ai, (uint32_t)quads_i, (uint32_t)quads) == cudaSuccess
+               ? NTT_OK
+               : NTT_ERR_CUDA;
+}
+
+template <bool INV>
+static int launch32_w1024(const Args32& a, cudaStream_t st) {
+    return INV ? launch32_w1024_rows(a, a, 0, a.n_rows, st) : launch32_w1024_rows(a, a, a.n_rows, 0, st);
 }
 
 template <int LOGN, bool INV>
@@ -183,21 +195,9 @@ int launch_ntt32_fwd_inv(const Plan32Dev& pf, const uint32_t* fin, uint32_t* fou
         return rc ? rc : launch_ntt32(pi, true, iin, iout, 0, i_rows, log2n, stream, launches);
     }
     const Args32 af = args32(pf, false, fin, fout, f_rows), ai = args32(pi, true, iin, iout, i_rows);
-    const uint64_t ctas_i = (i_rows + 3) / 4, ctas = ctas_i + (f_rows + 3) / 4;
-    if (ctas > 0x7fffffffull) return NTT_ERR_ARG;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)ctas);
-    cfg.blockDim = dim3(128);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    if (cudaLaunchKernelEx(&cfg, k_ntt32_w1024_fi, af, ai, (uint32_t)ctas_i) != cudaSuccess) return NTT_ERR_CUDA;
-    if (launches) ++*launches;
-    return NTT_OK;
+    const int rc = launch32_w1024_rows(af, ai, f_rows, i_rows, st);
+    if (rc == NTT_OK && launches) ++*launches;
+    return rc;
 }
 
 __global__ void k_pointwise32(const uint32_t* __restrict__ a, const uint32_t* __restrict__ b, uint32_t* c,

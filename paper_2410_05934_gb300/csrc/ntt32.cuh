@@ -291,36 +291,6 @@ NTT_HD Loc32 locate1024(const Args32& a, uint32_t cta, int w) {
     return L;
 }
 
-// forward, phase 1: coalesced load (layout A), stages 0..4, into shared memory
-NTT_HD void w1024_fwd_a(Row1024& r, const Args32& a, const Loc32& L, int t, uint32_t* sm) {
-    if (!L.valid) return;
-    const uint32_t* src = a.in + ((uint64_t)L.row << 10);
-    const LimbConst32 lc = a.lc[L.limb];
-    const Tw32* tw = a.tw + ((uint64_t)L.limb << 10);
-    bool bad = false;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        NTT_GMEM_CHECK(t + 32 * j, 1024);
-        r.x[j] = src[t + 32 * j];
-        bad |= r.x[j] >= lc.q;
-    }
-    if (a.check && bad) record_status(a.status, NTT_STATUS_RANGE);
-#pragma unroll
-    for (int s = 0; s < 5; ++s) {
-        const int d = 16 >> s;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            if (j & d) continue;
-            ct32(r.x[j], r.x[j + d], load_tw32(tw, (1u << s) + ((uint32_t)j >> (5 - s))), lc.q, lc.two_q);
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        NTT_SMEM_CHECK(slot1024(t + 32 * j), 1024);
-        sm[slot1024(t + 32 * j)] = r.x[j];
-    }
-}
-
 // forward, phase 2: layout B from shared memory, stages 5..9, canonical,
 // back to shared memory in place (each lane rewrites only the words it read)
 NTT_HD void w1024_fwd_b(Row1024& r, const Args32& a, const Loc32& L, int t, uint32_t* sm) {
@@ -350,21 +320,6 @@ NTT_HD void w1024_store(const Args32& a, const Loc32& L, int t, const uint32_t* 
     uint32_t* dst = a.out + ((uint64_t)L.row << 10);
 #pragma unroll
     for (int j = 0; j < 32; ++j) dst[t + 32 * j] = sm[slot1024(t + 32 * j)];
-}
-
-// inverse, phase 1: coalesced load into shared memory (layout A positions)
-NTT_HD void w1024_inv_a(const Args32& a, const Loc32& L, int t, uint32_t* sm) {
-    if (!L.valid) return;
-    const uint32_t* src = a.in + ((uint64_t)L.row << 10);
-    const uint32_t q = a.lc[L.limb].q;
-    bool bad = false;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        const uint32_t v = src[t + 32 * j];
-        bad |= v >= q;
-        sm[slot1024(t + 32 * j)] = v;
-    }
-    if (a.check && bad) record_status(a.status, NTT_STATUS_RANGE);
 }
 
 // inverse, phase 2: layout B, GS stages 9..5, back in place
@@ -409,6 +364,111 @@ NTT_HD void w1024_inv_c(Row1024& r, const Args32& a, const Loc32& L, int t, cons
     uint32_t* dst = a.out + ((uint64_t)L.row << 10);
 #pragma unroll
     for (int j = 0; j < 32; ++j) dst[t + 32 * j] = csub32(r.x[j], lc.q);
+}
+
+// ---- N = 1024, persistent warps with the next rows' loads in flight ----
+// A warp walks a list of rows (forward or inverse, one per quad of the
+// combined row space).  Row k lands in landing buffer k mod 2 in natural
+// order through 16-byte cp.async copies issued two rows ahead; the compute
+// phases then read it from shared memory, so the loads of the next row
+// overlap the butterflies of this one.  Layout A reads of the natural order
+// (word t + 32 j, lane t) hit 32 distinct banks.  The warp's work buffer
+// holds the slot layout of the phases above.
+
+NTT_HD void async_commit() {
+#if defined(__CUDA_ARCH__)
+    asm volatile("cp.async.commit_group;" ::: "memory");
+#endif
+}
+
+// waits until at most one committed group of this thread is pending
+NTT_HD void async_wait_prev() {
+#if defined(__CUDA_ARCH__)
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+#endif
+}
+
+// row L of a (1024 words) -> landing buffer, lane t copying words
+// 4 (t + 32 i) .. 4 (t + 32 i) + 3 (512 contiguous bytes per copy round)
+NTT_HD void w1024_prefetch(const Args32& a, const Loc32& L, int t, uint32_t* land) {
+    if (!L.valid) return;
+    const uint32_t* src = a.in + ((uint64_t)L.row << 10);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const uint32_t w = 4u * ((uint32_t)t + 32u * (uint32_t)i);
+        NTT_GMEM_CHECK(w + 3, 1024);
+        NTT_SMEM_CHECK(w + 3, 1024);
+        async_copy16(land + w, src + w);
+    }
+}
+
+// forward, phase 1 from the landing buffer: layout A, range check, stages 0..4
+NTT_HD void w1024_fwd_a_land(Row1024& r, const Args32& a, const Loc32& L, int t, const uint32_t* land) {
+    if (!L.valid) return;
+    const LimbConst32 lc = a.lc[L.limb];
+    const Tw32* tw = a.tw + ((uint64_t)L.limb << 10);
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        NTT_SMEM_CHECK(t + 32 * j, 1024);
+        r.x[j] = land[t + 32 * j];
+        bad |= r.x[j] >= lc.q;
+    }
+    if (a.check && bad) record_status(a.status, NTT_STATUS_RANGE);
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int d = 16 >> s;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            if (j & d) continue;
+            ct32(r.x[j], r.x[j + d], load_tw32(tw, (1u << s) + ((uint32_t)j >> (5 - s))), lc.q, lc.two_q);
+        }
+    }
+}
+
+// layout A registers -> the work buffer's slot layout
+NTT_HD void w1024_write_a(const Row1024& r, const Loc32& L, int t, uint32_t* work) {
+    if (!L.valid) return;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        NTT_SMEM_CHECK(slot1024(t + 32 * j), 1024);
+        work[slot1024(t + 32 * j)] = r.x[j];
+    }
+}
+
+// inverse, phase 1 from the landing buffer: range check, natural -> slot layout
+NTT_HD void w1024_inv_a_land(const Args32& a, const Loc32& L, int t, const uint32_t* land, uint32_t* work) {
+    if (!L.valid) return;
+    const uint32_t q = a.lc[L.limb].q;
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        NTT_SMEM_CHECK(t + 32 * j, 1024);
+        const uint32_t v = land[t + 32 * j];
+        bad |= v >= q;
+        work[slot1024(t + 32 * j)] = v;
+    }
+    if (a.check && bad) record_status(a.status, NTT_STATUS_RANGE);
+}
+
+// The row list of warp w of CTA `cta` in a grid of `grid` CTAs: its k-th row
+// is row w of quad cta + k grid of the combined space (quads [0, quads_i)
+// inverse rows of ai, the rest forward rows of af).
+struct W1024Pick {
+    bool live;      // the quad exists
+    bool inv;
+    Loc32 L;
+};
+NTT_HD W1024Pick w1024_pick(const Args32& af, const Args32& ai, uint32_t quads_i, uint32_t quads, uint32_t cta,
+                            uint32_t grid, uint32_t k, int w) {
+    W1024Pick p;
+    const uint64_t qd = (uint64_t)cta + (uint64_t)k * grid;
+    p.live = qd < quads;
+    p.inv = qd < quads_i;
+    const uint32_t qq = p.live ? (uint32_t)qd : 0u;
+    p.L = p.inv ? locate1024(ai, qq, w) : locate1024(af, qq - quads_i, w);
+    p.L.valid = p.L.valid && p.live;
+    return p;
 }
 
 // the 32-bit configuration of a ring size: 8 coefficients per thread (or the

@@ -312,6 +312,7 @@ int launch_tile_kernel(const PlanDev& p, const uint64_t* in, uint64_t* out, uint
         a.b_map[i] = p.b_map[i];
     }
     a.otf = C::INV ? p.otf_inv : p.otf_fwd;
+    a.in_skip = p.in_skip;
     if (C::MODE == 3 && !a.otf) return NTT_ERR_ARG;
     if (C::PIPE && C::FIRST && p.src_mode) return NTT_ERR_UNSUPPORTED;  // direct form only
     const uint64_t groups = (a.n_tiles + C::TPC - 1) / C::TPC;

@@ -25,6 +25,7 @@ struct PlanDev {
     uint8_t a_map[NTT_MUL_MAX_MAPPED], b_map[NTT_MUL_MAX_MAPPED];
     const TwPair* otf_fwd = nullptr;   // on-the-fly twiddle tables (form 3 kernels)
     const TwPair* otf_inv = nullptr;
+    uint32_t in_skip = 0;              // TileArgs.in_skip of the first kernel
 };
 
 // Transforms rows [row_begin, row_begin + n_rows) of the layout that starts

@@ -115,6 +115,10 @@ struct TileArgs {
     // on-the-fly twiddles (MODE 3): per limb otf_entries(LOGN) pairs, first
     // psi^(+-lo) for lo < 2^otf_lo_bits, then psi^(+-hi 2^otf_lo_bits)
     const TwPair* otf;
+    // rows of `in` skipped between two input rows of the first kernel (source
+    // mode 0): row r reads in + r (1 + in_skip) N, e.g. every L-th row of a
+    // multi-limb layout; the other kernels and `out` stay contiguous
+    uint32_t in_skip;
 };
 
 // on-the-fly twiddle tables of a ring of 2^logn: e = hi 2^lo_bits + lo
@@ -511,7 +515,8 @@ NTT_HD void load_direct(TileRegs<C>& st, const TileArgs& a, const TileLoc& L, in
         }
         return;
     }
-    const uint64_t* src = (C::FIRST ? a.in : a.out) + (L.row << C::LOGN) + gt;
+    const uint64_t* src =
+        (C::FIRST ? a.in + ((L.row * (1ull + a.in_skip)) << C::LOGN) : a.out + (L.row << C::LOGN)) + gt;
     bool bad = false;
 #pragma unroll
     for (int i = 0; i < C::R / 2; ++i) {
@@ -933,7 +938,8 @@ template <class C>
 NTT_HD CopyDesc tile_copy(const TileArgs& a, const TileLoc& L, int c) {
     CopyDesc d;
     if (c < C::RUNS) {
-        const uint64_t* src = (C::FIRST ? a.in : a.out) + (L.row << C::LOGN);
+        const uint64_t* src =
+            C::FIRST ? a.in + ((L.row * (1ull + a.in_skip)) << C::LOGN) : a.out + (L.row << C::LOGN);
         d.src = src + (L.gbase | ((uint32_t)c << C::LOGLO));
         d.dst_word = (uint32_t)c << C::LOGP;
         d.bytes = C::RUN_BYTES;

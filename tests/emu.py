@@ -40,6 +40,8 @@ def lib():
         L.nttemu_inverse_mul.restype = i32
         L.nttemu_transform32.argtypes = [vp, i32, U32P, U32P, u64, u64]
         L.nttemu_transform32.restype = i32
+        L.nttemu_forward_inverse32.argtypes = [vp, U32P, U32P, vp, U32P, U32P]
+        L.nttemu_forward_inverse32.restype = i32
         L.nttemu_pointwise32.argtypes = [vp, U32P, U32P, U32P, u64]
         L.nttemu_pointwise32.restype = i32
         L.nttemu_reduce_65q.argtypes = [vp, u32, U64P, U64P, u64]
@@ -145,6 +147,18 @@ class EmuPlan:
         if rc:
             raise ValueError("nttemu_transform32 failed: %d" % rc)
         return out
+
+    def forward_inverse32(self, xf, inv_plan, xi):
+        """ntt_forward_inverse of this plan's rows (forward) and inv_plan's (inverse), N = 1024."""
+        U32P = ctypes.POINTER(ctypes.c_uint32)
+        xf = np.ascontiguousarray(xf, dtype=np.uint32)
+        xi = np.ascontiguousarray(xi, dtype=np.uint32)
+        of, oi = np.zeros_like(xf), np.zeros_like(xi)
+        rc = lib().nttemu_forward_inverse32(self.h, xf.ctypes.data_as(U32P), of.ctypes.data_as(U32P), inv_plan.h,
+                                            xi.ctypes.data_as(U32P), oi.ctypes.data_as(U32P))
+        if rc:
+            raise ValueError("nttemu_forward_inverse32 failed: %d" % rc)
+        return of, oi
 
     def pointwise32(self, a, b):
         U32P = ctypes.POINTER(ctypes.c_uint32)

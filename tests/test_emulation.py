@@ -546,3 +546,26 @@ def test_largest_residues_every_schedule(oracle, log2n, cls):
         assert np.array_equal(fwd[r, idx], want), s
         assert np.array_equal(plan.transform(fwd, s, inverse=True), x), s
         assert np.array_equal(plan.transform(x, s, inverse=True)[r, idx], want_inv), s
+
+
+def test_word32_n1024_row_lists_and_forward_inverse():
+    """N = 1024 on 32-bit words: the persistent kernel's warps walk lists of
+    several rows with two landing buffers (partial last quads included), in
+    one direction and with forward and inverse rows in one grid
+    (ntt_forward_inverse), against the oracle's definitions."""
+    from oracle import oracle as O
+    mods = Q30[:2]
+    rng = np.random.default_rng(1024)
+    xf = np.array([rng.integers(0, mods[r % 2], 1024, dtype=np.uint64) for r in range(30)])
+    xi = np.array([rng.integers(0, mods[r % 2], 1024, dtype=np.uint64) for r in range(14)])
+    pf, pi = emu.EmuPlan(10, mods, 15, flags=8), emu.EmuPlan(10, mods, 7, flags=8)
+    want_f = O.transform_rows(xf, [mods[r % 2] for r in range(30)])
+    want_i = O.transform_rows(xi, [mods[r % 2] for r in range(14)], inverse=True)
+    assert np.array_equal(pf.transform32(xf.astype(np.uint32)).astype(np.uint64), want_f)
+    assert np.array_equal(pi.transform32(xi.astype(np.uint32), inverse=True).astype(np.uint64), want_i)
+    of, oi = pf.forward_inverse32(xf, pi, xi)
+    assert np.array_equal(of.astype(np.uint64), want_f)
+    assert np.array_equal(oi.astype(np.uint64), want_i)
+    part = pf.transform32(xf.astype(np.uint32), row_begin=5, n_rows=19)
+    assert not part[:5].any() and not part[24:].any() and np.array_equal(part[5:24].astype(np.uint64), want_f[5:24])
+    assert pf.status() == 0 and pi.status() == 0
