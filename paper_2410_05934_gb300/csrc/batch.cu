@@ -5,9 +5,9 @@
 // idea is applied to whole transform requests: requests of different N,
 // limb counts, polynomial counts and directions become (request, row range)
 // work items, sorted largest first, and one persistent kernel with a fixed
-// 256-thread CTA pulls them from an atomic queue.  Every N in [2^10, 2^16]
-// has a 256-thread tile configuration: one tile kernel's phases for
-// N <= 2^13, and for N >= 2^14 the column phase then the row phase of a
+// 128-thread CTA pulls them from an atomic queue.  Every N in [2^10, 2^16]
+// has a 128-thread tile configuration: one tile kernel's phases for
+// N <= 2^11, and for N >= 2^12 the column phase then the row phase of a
 // row inside the same CTA (the intermediate goes through the output buffer;
 // __syncthreads orders the CTA's global writes before its reads).
 #include <cuda_runtime.h>
@@ -41,14 +41,14 @@ struct BatchItem {
     uint64_t row_begin;
 };
 
-#define NTT_BATCH_THREADS 256
+#define NTT_BATCH_THREADS 128
 #define NTT_BATCH_BRANCHES 4     // concurrent graph branches for the scheduled requests
 static constexpr size_t kBatchSmemBound = 18 * 1024;
 
 // One phase (stage range) of a config over rows [a.row_begin, +n_rows).
 template <class C>
 __device__ __forceinline__ void batch_phase(TileArgs a, uint64_t n_rows, uint64_t* smem) {
-    static_assert(C::THREADS == NTT_BATCH_THREADS, "batch configs use 256-thread CTAs");
+    static_assert(C::THREADS == NTT_BATCH_THREADS, "batch configs use 128-thread CTAs");
     static_assert(C::SMEM_BYTES <= kBatchSmemBound, "batch configs fit the kernel's shared memory");
     a.n_tiles = n_rows << C::LOGTPR;
     const int tin = threadIdx.x >> C::LOGT, t = threadIdx.x & (C::T - 1);
@@ -120,15 +120,14 @@ __device__ __forceinline__ void batch_dispatch(const TileArgs& a, const BatchReq
 
 // Largest shared-memory footprint among the batch configurations (18 KiB).
 static constexpr size_t kBatchSmem = kBatchSmemBound;
-#define NTT_BATCH_MIN_CTAS 3
 // kernel variants: all N (NMAX 16), or short polynomials only (NMAX 11)
 #define NTT_BATCH_SHORT_NMAX 11
-// CTAs per SM the register budget is set for: the exact-quotient class
-// (q >= 2^57) needs more registers per butterfly than the small-modulus class
+// CTAs per SM the register budget is set for (the standalone column kernels'
+// 72 registers): the exact-quotient class (q >= 2^57) needs more registers
+// per butterfly than the small-modulus class
 template <int MC, int NMAX>
 struct BatchOcc {
-    static constexpr int ctas = MC ? (NMAX <= NTT_BATCH_SHORT_NMAX ? 4 : NTT_BATCH_MIN_CTAS)
-                                   : (NMAX <= NTT_BATCH_SHORT_NMAX ? 3 : 2);
+    static constexpr int ctas = MC ? 6 : 5;
 };
 
 template <int MC, int NMAX>
@@ -210,7 +209,7 @@ static_assert(256 + sizeof(StaticReq) * NTT_STATIC_MAX_REQUESTS <= NTT_STATIC_SC
 static __device__ __align__(256) unsigned char g_ntt_static_scratch[NTT_STATIC_SCRATCH_BYTES];
 
 template <int MC>
-__global__ void __launch_bounds__(NTT_BATCH_THREADS, NTT_BATCH_MIN_CTAS)
+__global__ void __launch_bounds__(NTT_BATCH_THREADS, BatchOcc<MC, 16>::ctas)
     k_ntt_batch_static(const StaticReq* __restrict__ reqs, uint32_t n_reqs, uint32_t n_items,
                        uint32_t* counter) {
     extern __shared__ __align__(16) uint64_t smem[];
