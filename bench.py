@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "mixed_batch", "tfhe_blind_rotation", "plain_n1024", "cost_model",
                              "serving", "hmul_fused", "mixed_small", "tfhe_cmux", "ckks_bconv", "otf_twiddles", "n_sweep",
-                             "ckks_rescale", "natural_order", "word32"],
+                             "ckks_rescale", "natural_order", "word32", "probe_pipes"],
                     help="the line the driver records is the default (CKKS-HMUL-shaped) workload")
     return ap.parse_args()
 
@@ -1431,6 +1431,46 @@ def run_serving(args):
     return 0
 
 
+def run_probe_pipes(args):
+    """The workload of the integer-pipe counter capture (profiles/butterfly_probe_pipes.md):
+    one launch of each butterfly probe kind (2, 7, 6, 3 with a 50-bit prime, 0 with a 62-bit
+    one; SMs x 8 CTAs x 256 threads x 400 iterations x 8 operations), then one forward and one
+    ntt_inverse_mul of 16 rows (4 polynomials x 4 limbs of 50-bit primes) at N = 2^16 on the
+    plan's default schedule.  Prints a JSON line with the timings; meant to run under ncu."""
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2410_05934_gb300 import build as B
+    B.build_product()
+    import paper_2410_05934_gb300 as ntt
+    from paper_2410_05934_gb300 import _native
+    from paper_2410_05934_gb300 import workloads as W
+    L_ = _native.load()
+    stream = torch.cuda.current_stream()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    sink = torch.empty(sms * 8 * 256, dtype=torch.int64, device="cuda")
+    out = {}
+    for kind in (2, 7, 6, 3, 0):
+        q = W.Q62_N1024 if kind == 0 else W.POOL50[0]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        assert L_.ntt_bench_butterflies(q, kind, sms * 8, 256, 400, sink.data_ptr(), stream.cuda_stream) == 0
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out["probe_%d_ms" % kind] = e0.elapsed_time(e1)
+    mods = W.POOL50[:4]
+    x = to_dev_np(torch, W.rows_uniform(3, 16, [m for _ in range(4) for m in mods], 1 << 16))
+    A, P = torch.empty_like(x), torch.empty_like(x)
+    plan = ntt.Plan(16, mods, 4)
+    plan.forward(x, A)
+    plan.inverse_mul(A, A, P, a_poly=[0, 0, 1, 1], b_poly=[2, 3, 2, 3])
+    torch.cuda.synchronize()
+    out.update(workload="probe_pipes", schedule=plan.schedule)
+    if rank == 0:
+        print(json.dumps(out))
+    return 0
+
+
 def to_dev_np(torch, x):
     return torch.from_numpy(np.ascontiguousarray(x).view(np.int64)).cuda()
 
@@ -1457,6 +1497,8 @@ def main():
         return run_natural_order(args)
     if args.workload == "word32":
         return run_word32(args)
+    if args.workload == "probe_pipes":
+        return run_probe_pipes(args)
     if args.workload != WORKLOAD:
         return run_other(args)
     return run_ours(args)
