@@ -265,8 +265,12 @@ int ntt_plan_last_launches(ntt_plan_t plan, uint32_t* launches);
  * q < 2^30; kind 6: a Montgomery product (R = 2^64, odd q < 2^62), the
  * pointwise product formed inside ntt_inverse_mul and ntt_hmul_tensor;
  * kind 7: the inverse butterfly of moduli below 2^50, whose sum is not
- * reduced).  Total operations = blocks * threads * iters * 8; time it with
- * events on `cuda_stream`.
+ * reduced; kind 8: the 32-bit forward butterfly with its conditional
+ * subtraction as compare and select, which a loop of independent
+ * butterflies runs faster than kind 5's subtract-and-minimum form, while the
+ * transform kernels are faster with the latter: the higher of kinds 5 and 8
+ * is the 32-bit roofline denominator).  Total operations = blocks * threads
+ * * iters * 8; time it with events on `cuda_stream`.
  * d_sink (blocks * threads uint64, caller-owned) only defeats dead-code
  * elimination.  Not part of the paper: a measurement aid.
  */

@@ -601,12 +601,13 @@ int ntt_debug_bounded_wait(ntt_plan_t plan, uint32_t deliver, uint32_t spin_limi
 
 int ntt_bench_butterflies(uint64_t q, uint32_t kind, uint32_t blocks, uint32_t threads,
                           uint32_t iters, uint64_t* d_sink, void* cuda_stream) {
-    if (q < 3 || q >= (1ull << NTT_MAX_MODULUS_BITS) || kind > 7 || (kind == 6 && (q & 1) == 0) ||
+    if (q < 3 || q >= (1ull << NTT_MAX_MODULUS_BITS) || kind > 8 || (kind == 6 && (q & 1) == 0) ||
         ((kind == 2 || kind == 3) && q >= (1ull << NTT_SMALL_MODULUS_BITS)) ||
         (kind == 7 && q >= (1ull << NTT_LAZY_MODULUS_BITS)) ||
-        (kind == 5 && q >= (1ull << NTT_WORD32_MAX_MODULUS_BITS)) || blocks == 0 || threads == 0 ||
-        threads > 256 || !d_sink)
+        ((kind == 5 || kind == 8) && q >= (1ull << NTT_WORD32_MAX_MODULUS_BITS)) || blocks == 0 ||
+        threads == 0 || threads > 256 || !d_sink)
         return NTT_ERR_ARG;
+    if (kind == 8) return launch_bench_bfly32_cmp(q, blocks, threads, iters, d_sink, cuda_stream);
     return launch_bench_bfly(q, kind, blocks, threads, iters, d_sink, cuda_stream);
 }
 

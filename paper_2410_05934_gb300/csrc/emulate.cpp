@@ -303,10 +303,17 @@ static void emu_passes32(std::vector<Regs32<C>>& st, const Args32& a, const std:
 // threads before the next (the kernel's __syncwarp points); the 16-byte
 // copies of a prefetch land at once, where the kernel's would land by the
 // wait two rows later.
-static int emu_w1024_rows(const Args32& af, const Args32& ai, uint64_t f_rows, uint64_t i_rows) {
+template <bool SMTW>
+static int emu_w1024_rows_t(const Args32& af, const Args32& ai, uint64_t f_rows, uint64_t i_rows) {
     const uint32_t quads_i = (uint32_t)((i_rows + 3) / 4), quads = quads_i + (uint32_t)((f_rows + 3) / 4);
     const uint32_t grid = quads < 3 ? quads : 3;
     std::vector<Row1024> r(128);
+    // the CTA's shared-memory copies of the two tables (single modulus)
+    std::vector<Tw32> tf(SMTW ? 1024 : 0), ti(SMTW ? 1024 : 0);
+    if (SMTW) {
+        memcpy(tf.data(), af.tw, 1024 * sizeof(Tw32));
+        memcpy(ti.data(), ai.tw, 1024 * sizeof(Tw32));
+    }
     for (uint32_t cta = 0; cta < grid; ++cta) {
         std::vector<uint32_t> sm(4 * 3 * 1024, 0xdeadbeefu);
         auto land = [&](int w, uint32_t k) { return sm.data() + w * 3072 + (k & 1) * 1024; };
@@ -329,16 +336,16 @@ static int emu_w1024_rows(const Args32& af, const Args32& ai, uint64_t f_rows, u
             const bool inv = cur[0].inv;     // one quad per CTA and step: the same direction in every warp
             const Args32& a = inv ? ai : af;
             if (!inv) {
-                each([&](Row1024& x, int w, int t) { w1024_fwd_a_land(x, a, cur[w].L, t, land(w, k)); });
+                each([&](Row1024& x, int w, int t) { w1024_fwd_a_land<SMTW>(x, a, cur[w].L, t, land(w, k), tf.data()); });
                 each([&](Row1024&, int w, int t) { w1024_prefetch(after[w].inv ? ai : af, after[w].L, t, land(w, k)); });
                 each([&](Row1024& x, int w, int t) { w1024_write_a(x, cur[w].L, t, work(w)); });
-                each([&](Row1024& x, int w, int t) { w1024_fwd_b(x, a, cur[w].L, t, work(w)); });
+                each([&](Row1024& x, int w, int t) { w1024_fwd_b<SMTW>(x, a, cur[w].L, t, work(w), tf.data()); });
                 each([&](Row1024&, int w, int t) { w1024_store(a, cur[w].L, t, work(w)); });
             } else {
                 each([&](Row1024&, int w, int t) { w1024_inv_a_land(a, cur[w].L, t, land(w, k), work(w)); });
                 each([&](Row1024&, int w, int t) { w1024_prefetch(after[w].inv ? ai : af, after[w].L, t, land(w, k)); });
-                each([&](Row1024& x, int w, int t) { w1024_inv_b(x, a, cur[w].L, t, work(w)); });
-                each([&](Row1024& x, int w, int t) { w1024_inv_c(x, a, cur[w].L, t, work(w)); });
+                each([&](Row1024& x, int w, int t) { w1024_inv_b<SMTW>(x, a, cur[w].L, t, work(w), ti.data()); });
+                each([&](Row1024& x, int w, int t) { w1024_inv_c<SMTW>(x, a, cur[w].L, t, work(w), ti.data()); });
             }
             for (int w = 0; w < 4; ++w) {
                 cur[w] = nxt[w];
@@ -347,6 +354,11 @@ static int emu_w1024_rows(const Args32& af, const Args32& ai, uint64_t f_rows, u
         }
     }
     return NTT_OK;
+}
+
+static int emu_w1024_rows(const Args32& af, const Args32& ai, uint64_t f_rows, uint64_t i_rows) {
+    if (af.n_moduli == 1 && ai.n_moduli == 1) return emu_w1024_rows_t<true>(af, ai, f_rows, i_rows);
+    return emu_w1024_rows_t<false>(af, ai, f_rows, i_rows);
 }
 
 template <bool INV>

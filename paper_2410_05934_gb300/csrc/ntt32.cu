@@ -40,11 +40,15 @@ __global__ void __launch_bounds__(C::THREADS) k_ntt32(Args32 a) {
 // N = 1024: persistent CTAs of four warps, each warp walking its list of
 // rows with the next rows' loads in flight (see ntt32.cuh); inverse rows of
 // ai (quads [0, quads_i)) and forward rows of af in one grid.  Shared
-// memory per warp: two landing buffers and the work buffer (12 KiB).
+// memory per warp: two landing buffers and the work buffer (12 KiB); with a
+// single modulus (SMTW) the CTA also holds both twiddle tables (2 x 8 KiB),
+// copied once, so the butterflies read them from shared memory.
 #define NTT_W1024_SMEM (4 * 3 * 1024 * sizeof(uint32_t))
+#define NTT_W1024_TW_SMEM (2 * 1024 * sizeof(Tw32))
 #ifndef NTT_W1024_CTAS_PER_SM
 #define NTT_W1024_CTAS_PER_SM 3     // resident CTAs per SM the grid is sized for
 #endif
+template <bool SMTW>
 __global__ void __launch_bounds__(128, NTT_W1024_CTAS_PER_SM) k_ntt32_w1024(Args32 af, Args32 ai, uint32_t quads_i,
                                                                          uint32_t quads) {
     extern __shared__ __align__(16) uint32_t sm_w1024[];
@@ -52,13 +56,26 @@ __global__ void __launch_bounds__(128, NTT_W1024_CTAS_PER_SM) k_ntt32_w1024(Args
     const int w = threadIdx.x >> 5, t = threadIdx.x & 31;
     uint32_t* land[2] = {sm_w1024 + w * 3072, sm_w1024 + w * 3072 + 1024};
     uint32_t* work = sm_w1024 + w * 3072 + 2048;
+    Tw32* tws_f = reinterpret_cast<Tw32*>(sm_w1024 + 4 * 3072);
+    Tw32* tws_i = tws_f + 1024;
     const uint32_t grid = gridDim.x, cta = blockIdx.x;
+    if (SMTW) {     // both tables of the single modulus, 16 bytes per copy
+        for (uint32_t i = threadIdx.x; i < 512; i += 128) {
+            async_copy16(tws_f + 2 * i, af.tw + 2 * i);
+            async_copy16(tws_i + 2 * i, ai.tw + 2 * i);
+        }
+        async_commit();
+    }
     W1024Pick cur = w1024_pick(af, ai, quads_i, quads, cta, grid, 0, w);
     W1024Pick nxt = w1024_pick(af, ai, quads_i, quads, cta, grid, 1, w);
     w1024_prefetch(cur.inv ? ai : af, cur.L, t, land[0]);
     async_commit();
     w1024_prefetch(nxt.inv ? ai : af, nxt.L, t, land[1]);
     async_commit();
+    if (SMTW) {     // the tables' group (the two row groups may stay in flight)
+        asm volatile("cp.async.wait_group 2;" ::: "memory");
+        __syncthreads();
+    }
     Row1024 r;
     for (uint32_t k = 0; cur.live; ++k) {
         uint32_t* ld = land[k & 1];
@@ -66,13 +83,13 @@ __global__ void __launch_bounds__(128, NTT_W1024_CTAS_PER_SM) k_ntt32_w1024(Args
         __syncwarp();
         const W1024Pick after = w1024_pick(af, ai, quads_i, quads, cta, grid, k + 2, w);
         if (!cur.inv) {
-            w1024_fwd_a_land(r, af, cur.L, t, ld);
+            w1024_fwd_a_land<SMTW>(r, af, cur.L, t, ld, tws_f);
             __syncwarp();           // every lane has read the landing buffer: refill it
             w1024_prefetch(after.inv ? ai : af, after.L, t, ld);
             async_commit();
             w1024_write_a(r, cur.L, t, work);
             __syncwarp();
-            w1024_fwd_b(r, af, cur.L, t, work);
+            w1024_fwd_b<SMTW>(r, af, cur.L, t, work, tws_f);
             __syncwarp();
             w1024_store(af, cur.L, t, work);
         } else {
@@ -80,9 +97,9 @@ __global__ void __launch_bounds__(128, NTT_W1024_CTAS_PER_SM) k_ntt32_w1024(Args
             __syncwarp();
             w1024_prefetch(after.inv ? ai : af, after.L, t, ld);
             async_commit();
-            w1024_inv_b(r, ai, cur.L, t, work);
+            w1024_inv_b<SMTW>(r, ai, cur.L, t, work, tws_i);
             __syncwarp();
-            w1024_inv_c(r, ai, cur.L, t, work);
+            w1024_inv_c<SMTW>(r, ai, cur.L, t, work, tws_i);
         }
         __syncwarp();               // the work buffer is free for the next row
         cur = nxt;
@@ -100,22 +117,23 @@ static int launch32_w1024_rows(const Args32& af, const Args32& ai, uint64_t f_ro
         return NTT_ERR_CUDA;
     uint64_t ctas = (uint64_t)(sms > 0 ? sms : 1) * NTT_W1024_CTAS_PER_SM;
     if (ctas > quads) ctas = quads;
-    if (cudaFuncSetAttribute(k_ntt32_w1024, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NTT_W1024_SMEM) !=
-        cudaSuccess)
+    const bool smtw = af.n_moduli == 1 && ai.n_moduli == 1;
+    const auto kernel = smtw ? k_ntt32_w1024<true> : k_ntt32_w1024<false>;
+    const size_t smem = NTT_W1024_SMEM + (smtw ? NTT_W1024_TW_SMEM : 0);
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return NTT_ERR_CUDA;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)ctas);
     cfg.blockDim = dim3(128);
-    cfg.dynamicSmemBytes = NTT_W1024_SMEM;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_ntt32_w1024, af, ai, (uint32_t)quads_i, (uint32_t)quads) == cudaSuccess
-               ? NTT_OK
-               : NTT_ERR_CUDA;
+    return cudaLaunchKernelEx(&cfg, kernel, af, ai, (uint32_t)quads_i, (uint32_t)quads) == cudaSuccess ? NTT_OK
+                                                                                                   : NTT_ERR_CUDA;
 }
 
 template <bool INV>
@@ -198,6 +216,42 @@ int launch_ntt32_fwd_inv(const Plan32Dev& pf, const uint32_t* fin, uint32_t* fou
     const int rc = launch32_w1024_rows(af, ai, f_rows, i_rows, st);
     if (rc == NTT_OK && launches) ++*launches;
     return rc;
+}
+
+// Probe kind 8: 32-bit Harvey CT butterflies as in k_bench_bfly32 (kind 5),
+// with the conditional subtraction written as compare and select
+__global__ void __launch_bounds__(256) k_bench_bfly32_cmp(uint32_t q, uint32_t w, uint32_t wp, uint32_t iters,
+                                                          uint64_t* sink) {
+    constexpr int P = 8;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t X[P], Y[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        X[i] = (uint32_t)((tid * 7919u + (uint64_t)i * 104729u) % q);
+        Y[i] = (uint32_t)((tid * 31u + (uint64_t)i * 17u) % q);
+    }
+    const uint32_t two_q = 2 * q;
+    for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            const uint32_t x = X[i] >= two_q ? X[i] - two_q : X[i];
+            const uint32_t t = shoup32(Y[i], w, wp, q);
+            X[i] = x + t;
+            Y[i] = x - t + two_q;
+        }
+    }
+    uint32_t acc = 0;
+#pragma unroll
+    for (int i = 0; i < P; ++i) acc ^= X[i] ^ Y[i];
+    if (acc == 0x5eed5eedu) sink[tid] = acc;   // practically never taken
+}
+
+int launch_bench_bfly32_cmp(uint64_t q, uint32_t blocks, uint32_t threads, uint32_t iters, uint64_t* sink,
+                            void* stream) {
+    const uint32_t w = (uint32_t)(q / 3);
+    const uint32_t wp = (uint32_t)(((uint64_t)w << 32) / q);
+    k_bench_bfly32_cmp<<<blocks, threads, 0, (cudaStream_t)stream>>>((uint32_t)q, w, wp, iters, sink);
+    return cudaPeekAtLastError() == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
 }
 
 __global__ void k_pointwise32(const uint32_t* __restrict__ a, const uint32_t* __restrict__ b, uint32_t* c,

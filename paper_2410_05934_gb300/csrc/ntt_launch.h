@@ -65,6 +65,9 @@ int launch_ntt32(const Plan32Dev& p, bool inverse, const uint32_t* in, uint32_t*
 int launch_ntt32_fwd_inv(const Plan32Dev& pf, const uint32_t* fin, uint32_t* fout, uint64_t f_rows,
                          const Plan32Dev& pi, const uint32_t* iin, uint32_t* iout, uint64_t i_rows, uint32_t log2n,
                          void* stream, uint32_t* launches);
+// the 32-bit butterfly probe with compare-and-select conditional subtractions (kind 8)
+int launch_bench_bfly32_cmp(uint64_t q, uint32_t blocks, uint32_t threads, uint32_t iters, uint64_t* sink,
+                            void* stream);
 int launch_pointwise32(const Plan32Dev& p, uint32_t log2n, const uint32_t* a, const uint32_t* b, uint32_t* c,
                        uint64_t n_rows, void* stream, uint32_t* launches);
 

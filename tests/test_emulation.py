@@ -548,17 +548,20 @@ def test_largest_residues_every_schedule(oracle, log2n, cls):
         assert np.array_equal(plan.transform(x, s, inverse=True)[r, idx], want_inv), s
 
 
-def test_word32_n1024_row_lists_and_forward_inverse():
+@pytest.mark.parametrize("n_mod", [2, 1])
+def test_word32_n1024_row_lists_and_forward_inverse(n_mod):
     """N = 1024 on 32-bit words: the persistent kernel's warps walk lists of
     several rows with two landing buffers (partial last quads included), in
     one direction and with forward and inverse rows in one grid
-    (ntt_forward_inverse), against the oracle's definitions."""
+    (ntt_forward_inverse), against the oracle's definitions; with one
+    modulus the twiddles come from the CTA's shared-memory copy."""
     from oracle import oracle as O
-    mods = Q30[:2]
+    mods = (Q30 * 2)[:2] if n_mod == 2 else [Q30[0]] * 2
     rng = np.random.default_rng(1024)
     xf = np.array([rng.integers(0, mods[r % 2], 1024, dtype=np.uint64) for r in range(30)])
     xi = np.array([rng.integers(0, mods[r % 2], 1024, dtype=np.uint64) for r in range(14)])
-    pf, pi = emu.EmuPlan(10, mods, 15, flags=8), emu.EmuPlan(10, mods, 7, flags=8)
+    pf = emu.EmuPlan(10, mods[:n_mod], 30 // n_mod, flags=8)
+    pi = emu.EmuPlan(10, mods[:n_mod], 14 // n_mod, flags=8)
     want_f = O.transform_rows(xf, [mods[r % 2] for r in range(30)])
     want_i = O.transform_rows(xi, [mods[r % 2] for r in range(14)], inverse=True)
     assert np.array_equal(pf.transform32(xf.astype(np.uint32)).astype(np.uint64), want_f)
