@@ -126,11 +126,8 @@ static constexpr size_t kBatchSmem = kBatchSmemBound;
 // 72 registers): the exact-quotient class (q >= 2^57) needs more registers
 // per butterfly than the small-modulus class
 template <int MC, int NMAX>
-#ifndef NTT_BATCH_SHORT_CTAS
-#define NTT_BATCH_SHORT_CTAS 0
-#endif
 struct BatchOcc {
-    static constexpr int ctas = (NTT_BATCH_SHORT_CTAS && NMAX <= NTT_BATCH_SHORT_NMAX) ? NTT_BATCH_SHORT_CTAS : (MC ? 6 : 5);
+    static constexpr int ctas = MC ? 6 : 5;
 };
 
 template <int MC, int NMAX>
@@ -179,10 +176,7 @@ static const void* batch_kernel(uint32_t mc, uint32_t short_only) {
 
 // rows per work item: one tile group of the batch configuration (two rows at
 // N = 2^10, one row above), so that the queue's last wave is short
-#ifndef NTT_BATCH_ROWS_N1024
-#define NTT_BATCH_ROWS_N1024 2u
-#endif
-static uint32_t rows_per_item(uint32_t log2n) { return log2n <= 10 ? NTT_BATCH_ROWS_N1024 : 1u; }
+static uint32_t rows_per_item(uint32_t log2n) { return log2n <= 10 ? 2u : 1u; }
 
 struct NTableSet {
     PlanHost host;              // pool prefix tables of one N
