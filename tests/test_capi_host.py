@@ -103,6 +103,25 @@ def test_compute_on_host_only_plan_is_rejected(ntt):
     assert L.ntt_forward(p.handle, None, addr, None) == -1
 
 
+def test_forward_inverse_argument_rules_on_the_host(ntt):
+    """ntt_forward_inverse rejects null plans and pointers, plans of different
+    N or word size, and overlapping buffers of the two transforms before any
+    device work (host-only plans reach no launch either)."""
+    from paper_2410_05934_gb300 import _native
+    L = _native.load()
+    f = ntt.Plan(10, [W.Q59_N1024], 2, flags=ntt.NTT_FLAG_HOST_ONLY)
+    i = ntt.Plan(10, [W.Q59_N1024], 1, flags=ntt.NTT_FLAG_HOST_ONLY)
+    i11 = ntt.Plan(11, [4611686018427322369], 1, flags=ntt.NTT_FLAG_HOST_ONLY)   # a 62-bit prime = 1 mod 2^12
+    buf = ctypes.create_string_buffer(8 * 4096 + 16)
+    a = (ctypes.addressof(buf) + 15) & ~15
+    b = a + 8 * 2048                              # after the forward's 2 rows
+    assert L.ntt_forward_inverse(None, a, a, i.handle, b, b, None) == -1
+    assert L.ntt_forward_inverse(f.handle, None, a, i.handle, b, b, None) == -1
+    assert L.ntt_forward_inverse(f.handle, a, a, i11.handle, b, b, None) == -1      # different N
+    assert L.ntt_forward_inverse(f.handle, a, a, i.handle, a + 8 * 1024, b, None) == -1   # overlap
+    assert L.ntt_forward_inverse(f.handle, a, a, i.handle, b, b, None) == -1        # host-only plans
+
+
 def test_twiddle_tables_and_shoup_companions(ntt, oracle):
     """Host tables of a plan (emulation library exposes none, so check through
     the emulator's transforms and directly through the oracle's root): every
