@@ -330,6 +330,7 @@ def metric_extras(torch, ntt, W, L, stream, sms, peak_fwd, flush, sink, hybrid_l
     out["tfhe_batch"] = {
         "ms": ms, "speedup_vs_plain": ms["plain_per_request"] / ms["batched"],
         "grouped_vs_plain": ms["plain_per_request"] / ms["grouped"],
+        "forward_inverse_vs_plain": ms["plain_per_request"] / ms["forward_inverse"],
         "persistent_only_vs_plain": ms["plain_per_request"] / ms["persistent_only"],
         "frac": {k: bfly / peak0 * 1e3 / v for k, v in ms.items()},
         "how": "3780 forward + 1260 inverse rows at N = 1024, 62-bit prime, L2 flushed; frac against the "
@@ -684,8 +685,11 @@ def measure_tfhe_batch(torch, ntt, W, stream, steps, warmup, flush_fn):
     batch = ntt.Batch(schedule_requests(reqs, [q], 21), [q], flags=ntt.NTT_BATCH_GRAPH)
     persistent = ntt.Batch(reqs, [q], flags=ntt.NTT_BATCH_GRAPH)
     grouped = ntt.Batch(reqs, [q], flags=ntt.NTT_BATCH_GRAPH | ntt.NTT_BATCH_GROUPED)
+    pf, pi = ntt.Plan(10, [q], xf.shape[0]), ntt.Plan(10, [q], xi.shape[0])
+    of, oi = torch.empty_like(xf), torch.empty_like(xi)
     arms = [("batched", lambda: (batch.execute(), batch.info()["last_launches"])[1]),
             ("grouped", lambda: (grouped.execute(), grouped.info()["last_launches"])[1]),
+            ("forward_inverse", lambda: (ntt.forward_inverse(pf, xf, xi, pi, of, oi), pf.last_launches())[1]),
             ("persistent_only", lambda: (persistent.execute(), 1)[1]),
             ("plain_per_request", lambda: (batch.execute_plain(), 2)[1])]
     for _ in range(max(1, warmup)):
@@ -836,7 +840,14 @@ def run_other(args):
         extra["persistent_only"] = {"value": coef * args.steps / (sum(res["persistent_only"][0]) * 1e-3),
                                     "ms_per_step": sum(res["persistent_only"][0]) / args.steps,
                                     "how": "both requests as work items of one persistent kernel launch"}
+        extra["forward_inverse"] = {"value": coef * args.steps / (sum(res["forward_inverse"][0]) * 1e-3),
+                                    "ms_per_step": sum(res["forward_inverse"][0]) / args.steps,
+                                    "how": "one ntt_forward_inverse call: both row sets in one grid"}
+        extra["grouped"] = {"value": coef * args.steps / (sum(res["grouped"][0]) * 1e-3),
+                            "ms_per_step": sum(res["grouped"][0]) / args.steps,
+                            "how": "ntt_batch_execute with NTT_BATCH_GROUPED: one grid per kernel phase"}
         extra["speedup_vs_plain"] = sum(res["plain_per_request"][0]) / sum(ms)
+        extra["forward_inverse_vs_plain"] = sum(res["plain_per_request"][0]) / sum(res["forward_inverse"][0])
         config = {"workload": "tfhe_blind_rotation", "log2n": 10, "modulus_bits": 62,
                   "rows": "3780 forward (signed digits) + 1260 inverse",
                   "batched": "one CUDA graph launch: the two requests on their learned schedules, concurrent branches",

@@ -135,9 +135,14 @@ int ntt_inverse(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, void* cu
  * and 1260 accumulator INTTs of a blind-rotation step): the forward of
  * fwd_plan's rows d_fwd_in -> d_fwd_out and the inverse of inv_plan's rows
  * d_inv_in -> d_inv_out, with the same results as ntt_forward followed by
- * ntt_inverse.  The two transforms run concurrently, in one launch for
- * 32-bit-word plans at N = 1024, otherwise one after the other on the stream.
- * Both plans must have the same N and word size.  Each transform may work in
+ * ntt_inverse.  The two transforms run concurrently: in one launch for
+ * 32-bit-word plans at N = 1024; for 64-bit plans of one modulus class in
+ * one grid per kernel phase (one launch for N <= 2^12, two above) on the
+ * N's grouped configuration (the one of NTT_BATCH_GROUPED, not the plans'
+ * schedules); otherwise (natural-order or on-the-fly-twiddle plans, 32-bit
+ * words at other N, different classes) one after the other on the stream.
+ * Errors found in the kernels go to each plan's own status word.  Both
+ * plans must have the same N and word size.  Each transform may work in
  * place, but no buffer of one transform may overlap a buffer of the other
  * (NTT_ERR_ARG).  Layout, alignment and ownership as ntt_forward.
  */

@@ -353,6 +353,52 @@ int ntt_forward_inverse(ntt_plan_t fwd_plan, const uint64_t* d_fwd_in, uint64_t*
         overlap(d_fwd_out, fb, d_inv_in, ib) || overlap(d_fwd_out, fb, d_inv_out, ib))
         return NTT_ERR_ARG;
     if (!word32(fwd_plan)) {
+        // one grid per kernel phase with N's grouped configuration, when both
+        // plans are bit-reversed, table-twiddle plans of one modulus class
+        const uint32_t log2n = fwd_plan->h.log2n;
+        const int phases = grouped_phases(log2n);
+        if (phases > 0 && fwd_plan->h.mc == inv_plan->h.mc && !natural(fwd_plan) && !natural(inv_plan) &&
+            !otf(fwd_plan) && !otf(inv_plan)) {
+            if (!aligned16(d_fwd_in) || !aligned16(d_fwd_out) || !aligned16(d_inv_in) || !aligned16(d_inv_out))
+                return NTT_ERR_ALIGN;
+            int rc = check_device(fwd_plan);
+            if (!rc) rc = check_device(inv_plan);
+            if (rc) return rc;
+            fwd_plan->last_launches = 0;
+            inv_plan->last_launches = 0;
+            int* status[2] = {fwd_plan->d_status, inv_plan->d_status};
+            const uint32_t check[2] = {(fwd_plan->h.flags & NTT_FLAG_CHECK) ? 1u : 0u,
+                                       (inv_plan->h.flags & NTT_FLAG_CHECK) ? 1u : 0u};
+            for (int ph = 0; ph < phases; ++ph) {
+                GroupSeg seg[2];
+                uint64_t groups[2];
+                for (int k = 0; k < 2; ++k) {     // 0: forward, 1: inverse
+                    const ntt_plan_s* p = k ? inv_plan : fwd_plan;
+                    uint32_t ltpr = 0, tpc = 1;
+                    rc = grouped_geometry(log2n, ph, k == 1, &ltpr, &tpc);
+                    if (rc) return rc;
+                    GroupSeg& g = seg[k];
+                    g.in = ph == 0 ? (k ? d_inv_in : d_fwd_in) : (k ? d_inv_out : d_fwd_out);
+                    g.out = k ? d_inv_out : d_fwd_out;
+                    g.tw = k ? p->d_inv : p->d_fwd;
+                    g.lc = p->d_consts;
+                    g.n_tiles = p->h.rows << ltpr;
+                    g.n_moduli = p->h.n_moduli;
+                    g.inverse = (uint32_t)k;
+                    g.fast32 = (p->h.rows < (1ull << 32) && g.n_tiles < (1ull << 32)) ? 1u : 0u;
+                    g.mod_magic = fdiv_magic(p->h.n_moduli);
+                    g.pad = 0;
+                    groups[k] = (g.n_tiles + tpc - 1) / tpc;
+                }
+                seg[1].group_begin = 0;
+                seg[0].group_begin = groups[1];     // the inverse rows' CTAs first
+                rc = launch_pair(log2n, fwd_plan->h.mc, ph, seg[0], seg[1], groups[0] + groups[1], status, check,
+                                 cuda_stream);
+                if (rc) return rc;
+                ++fwd_plan->last_launches;
+            }
+            return NTT_OK;
+        }
         const int rc = transform(fwd_plan, false, d_fwd_in, d_fwd_out, 0, fwd_plan->h.rows, cuda_stream);
         return rc ? rc : transform(inv_plan, true, d_inv_in, d_inv_out, 0, inv_plan->h.rows, cuda_stream);
     }

@@ -93,6 +93,11 @@ int grouped_phases(uint32_t log2n);
 int grouped_geometry(uint32_t log2n, int phase, bool inverse, uint32_t* log_tiles_per_row, uint32_t* tpc);
 int launch_grouped(uint32_t log2n, uint32_t mc, int phase, const GroupSeg* d_segs, uint32_t n_segs, uint64_t grid,
                    int* status, uint32_t check, void* stream);
+// phase `phase` of one forward and one inverse segment of N in one grid, the
+// segments passed by value (the inverse's CTAs first: sf.group_begin is
+// their count); status / check: {forward plan's, inverse plan's}
+int launch_pair(uint32_t log2n, uint32_t mc, int phase, const GroupSeg& sf, const GroupSeg& si, uint64_t grid,
+                int* const* status, const uint32_t* check, void* stream);
 
 int launch_bench_bfly(uint64_t q, uint32_t kind, uint32_t blocks, uint32_t threads, uint32_t iters,
                       uint64_t* sink, void* stream);

@@ -559,17 +559,20 @@ def test_forward_inverse_word32_tfhe_batch(oracle):
 
 
 def test_forward_inverse_rules_and_64_bit(oracle):
-    """64-bit plans run the two transforms in stream order with the same
-    results; overlapping buffers of the two transforms, different N and
-    mixed word sizes are argument errors."""
+    """64-bit plans of one modulus class run both transforms in one grid
+    (one launch at N = 1024) with the oracle's results; overlapping buffers
+    of the two transforms, different N and mixed word sizes are argument
+    errors."""
     q = W.Q62_N1024
     x = W.rows_uniform(43, 10, [q] * 6, 1024)
     pf, pi = ntt.Plan(10, [q], 4), ntt.Plan(10, [q], 2)
     d = to_dev(x)
     f, i = torch.empty_like(d[:4]), torch.empty_like(d[4:])
     ntt.forward_inverse(pf, d[:4].contiguous(), d[4:].contiguous(), pi, f, i)
+    assert pf.last_launches() == 1
     assert np.array_equal(to_host(f), oracle.transform_rows(x[:4], [q] * 4))
     assert np.array_equal(to_host(i), oracle.transform_rows(x[4:], [q] * 2, inverse=True))
+    assert pf.status() == 0 and pi.status() == 0
     with pytest.raises(ntt.NttError):
         ntt.forward_inverse(pf, d[:4], d[2:4], pi)                 # inverse rows inside the forward's buffer
     with pytest.raises(ntt.NttError):
@@ -578,3 +581,36 @@ def test_forward_inverse_rules_and_64_bit(oracle):
     p32 = ntt.Plan(10, [Q30[0]], 2, flags=ntt.NTT_FLAG_WORD32)
     with pytest.raises(ntt.NttError):
         ntt.forward_inverse(pf, f, torch.zeros((2, 1024), dtype=torch.int32, device="cuda"), p32)
+
+
+@pytest.mark.parametrize("log2n", [12, 13, 16])
+def test_forward_inverse_64_bit_two_phases_and_fallback(oracle, log2n):
+    """64-bit ntt_forward_inverse at larger N (one grid per kernel phase: two
+    launches from 2^13 up) on multi-limb plans with different row counts,
+    against the separate calls and sampled oracle outputs; plans of
+    different modulus classes fall back to the two calls in stream order."""
+    n = 1 << log2n
+    mods = [W.POOL50[0], W.POOL50[5]]
+    xf = W.rows_uniform(51, log2n, mods * 3, n)       # 3 polys x 2 limbs
+    xi = W.rows_uniform(52, log2n, mods * 2, n)       # 2 polys x 2 limbs
+    pf, pi = ntt.Plan(log2n, mods, 3), ntt.Plan(log2n, mods, 2)
+    df, di = to_dev(xf), to_dev(xi)
+    of, oi = torch.empty_like(df), torch.empty_like(di)
+    ntt.forward_inverse(pf, df, di, pi, of, oi)
+    assert pf.last_launches() == (1 if log2n <= 12 else 2)
+    sf, si = torch.empty_like(df), torch.empty_like(di)
+    pf.forward(df, sf)
+    pi.inverse(di, si)
+    assert torch.equal(of, sf) and torch.equal(oi, si)
+    idx = np.array([[0, 1, n // 2, n - 1]] * 2, dtype=np.uint32)
+    assert np.array_equal(to_host(of)[[0, 5]][:, [0, 1, n // 2, n - 1]],
+                          oracle.transform_rows(xf[[0, 5]], [mods[0], mods[1]], idx=idx))
+    q62 = _prime_62(log2n)
+    p62 = ntt.Plan(log2n, [q62], 2)
+    x62 = W.rows_uniform(53, log2n, [q62] * 2, n)
+    d62, o62 = to_dev(x62), torch.empty((2, n), dtype=torch.int64, device="cuda")
+    ntt.forward_inverse(p62, d62, di, pi, o62, oi)     # class 0 forward, class 2 inverse
+    assert torch.equal(oi, si)
+    p62.forward(d62, sf[:2])
+    assert torch.equal(o62, sf[:2])
+    assert pf.status() == 0 and pi.status() == 0 and p62.status() == 0
