@@ -37,30 +37,38 @@ __global__ void __launch_bounds__(C::THREADS) k_ntt32(Args32 a) {
     store32<C>(a, L, t, sm);
 }
 
-// N = 1024: persistent CTAs of four warps, each warp walking its list of
-// rows with the next rows' loads in flight (see ntt32.cuh); inverse rows of
-// ai (quads [0, quads_i)) and forward rows of af in one grid.  Shared
-// memory per warp: two landing buffers and the work buffer (12 KiB); with a
-// single modulus (SMTW) the CTA also holds both twiddle tables (2 x 8 KiB),
-// copied once, so the butterflies read them from shared memory.
-#define NTT_W1024_SMEM (4 * 3 * 1024 * sizeof(uint32_t))
-#define NTT_W1024_TW_SMEM (2 * 1024 * sizeof(Tw32))
+// N = 1024: persistent CTAs of NTT_W1024_WARPS warps, each warp walking its
+// list of rows with the next rows' loads in flight (see ntt32.cuh); inverse
+// rows of ai (quads [0, quads_i)) and forward rows of af in one grid.  Every
+// four warps of a CTA take one quad of rows per step (a CTA of 4 m warps
+// counts as m consecutive quad walkers).  Shared memory per warp: two
+// landing buffers and the work buffer (12 KiB); with a single modulus (SMTW)
+// the CTA also holds both twiddle tables (2 x 8 KiB), copied once, so the
+// butterflies read them from shared memory.
+#ifndef NTT_W1024_WARPS
+#define NTT_W1024_WARPS 4           // warps per CTA, a multiple of 4
+#endif
 #ifndef NTT_W1024_CTAS_PER_SM
 #define NTT_W1024_CTAS_PER_SM 3     // resident CTAs per SM the grid is sized for
 #endif
+static_assert(NTT_W1024_WARPS % 4 == 0 && NTT_W1024_WARPS <= 16, "quads of warps");
+#define NTT_W1024_SMEM (NTT_W1024_WARPS * 3 * 1024 * sizeof(uint32_t))
+#define NTT_W1024_TW_SMEM (2 * 1024 * sizeof(Tw32))
 template <bool SMTW>
-__global__ void __launch_bounds__(128, NTT_W1024_CTAS_PER_SM) k_ntt32_w1024(Args32 af, Args32 ai, uint32_t quads_i,
-                                                                         uint32_t quads) {
+__global__ void __launch_bounds__(32 * NTT_W1024_WARPS, NTT_W1024_CTAS_PER_SM)
+    k_ntt32_w1024(Args32 af, Args32 ai, uint32_t quads_i, uint32_t quads) {
     extern __shared__ __align__(16) uint32_t sm_w1024[];
     pdl_begin();
-    const int w = threadIdx.x >> 5, t = threadIdx.x & 31;
-    uint32_t* land[2] = {sm_w1024 + w * 3072, sm_w1024 + w * 3072 + 1024};
-    uint32_t* work = sm_w1024 + w * 3072 + 2048;
-    Tw32* tws_f = reinterpret_cast<Tw32*>(sm_w1024 + 4 * 3072);
+    constexpr uint32_t SUB = NTT_W1024_WARPS / 4;      // quad walkers per CTA
+    const int wc = threadIdx.x >> 5, t = threadIdx.x & 31;
+    const int w = wc & 3;
+    uint32_t* const land0 = sm_w1024 + wc * 3072;      // landing buffers at +0 and +1024
+    uint32_t* work = sm_w1024 + wc * 3072 + 2048;
+    Tw32* tws_f = reinterpret_cast<Tw32*>(sm_w1024 + NTT_W1024_WARPS * 3072);
     Tw32* tws_i = tws_f + 1024;
-    const uint32_t grid = gridDim.x, cta = blockIdx.x;
+    const uint32_t grid = gridDim.x * SUB, cta = blockIdx.x * SUB + (uint32_t)(wc >> 2);
     if (SMTW) {     // both tables of the single modulus, 16 bytes per copy
-        for (uint32_t i = threadIdx.x; i < 512; i += 128) {
+        for (uint32_t i = threadIdx.x; i < 512; i += 32 * NTT_W1024_WARPS) {
             async_copy16(tws_f + 2 * i, af.tw + 2 * i);
             async_copy16(tws_i + 2 * i, ai.tw + 2 * i);
         }
@@ -68,9 +76,9 @@ __global__ void __launch_bounds__(128, NTT_W1024_CTAS_PER_SM) k_ntt32_w1024(Args
     }
     W1024Pick cur = w1024_pick(af, ai, quads_i, quads, cta, grid, 0, w);
     W1024Pick nxt = w1024_pick(af, ai, quads_i, quads, cta, grid, 1, w);
-    w1024_prefetch(cur.inv ? ai : af, cur.L, t, land[0]);
+    w1024_prefetch(cur.inv ? ai : af, cur.L, t, land0);
     async_commit();
-    w1024_prefetch(nxt.inv ? ai : af, nxt.L, t, land[1]);
+    w1024_prefetch(nxt.inv ? ai : af, nxt.L, t, land0 + 1024);
     async_commit();
     if (SMTW) {     // the tables' group (the two row groups may stay in flight)
         asm volatile("cp.async.wait_group 2;" ::: "memory");
@@ -78,7 +86,7 @@ __global__ void __launch_bounds__(128, NTT_W1024_CTAS_PER_SM) k_ntt32_w1024(Args
     }
     Row1024 r;
     for (uint32_t k = 0; cur.live; ++k) {
-        uint32_t* ld = land[k & 1];
+        uint32_t* ld = land0 + ((k & 1u) << 10);
         async_wait_prev();          // row k has landed (row k + 1 may be in flight)
         __syncwarp();
         const W1024Pick after = w1024_pick(af, ai, quads_i, quads, cta, grid, k + 2, w);
@@ -116,7 +124,8 @@ static int launch32_w1024_rows(const Args32& af, const Args32& ai, uint64_t f_ro
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return NTT_ERR_CUDA;
     uint64_t ctas = (uint64_t)(sms > 0 ? sms : 1) * NTT_W1024_CTAS_PER_SM;
-    if (ctas > quads) ctas = quads;
+    const uint64_t need = (quads + NTT_W1024_WARPS / 4 - 1) / (NTT_W1024_WARPS / 4);
+    if (ctas > need) ctas = need;
     const bool smtw = af.n_moduli == 1 && ai.n_moduli == 1;
     const auto kernel = smtw ? k_ntt32_w1024<true> : k_ntt32_w1024<false>;
     const size_t smem = NTT_W1024_SMEM + (smtw ? NTT_W1024_TW_SMEM : 0);
@@ -124,7 +133,7 @@ static int launch32_w1024_rows(const Args32& af, const Args32& ai, uint64_t f_ro
         return NTT_ERR_CUDA;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)ctas);
-    cfg.blockDim = dim3(128);
+    cfg.blockDim = dim3(32 * NTT_W1024_WARPS);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
