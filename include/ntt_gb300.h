@@ -125,6 +125,16 @@ int ntt_plan_shape(ntt_plan_t plan, uint32_t* log2n, uint32_t* n_moduli, uint32_
  * the rows (one more kernel launch).  The fused operators (ntt_hmul_tensor,
  * ntt_rescale, tfhe_*, ntt_batch_execute_static) take bit-reversed plans only
  * and return NTT_ERR_UNSUPPORTED for natural-order ones.
+ * Row split: on a two-kernel schedule, a call of 64-bit words over 3 * 2^20
+ * to 2^26 coefficients (ntt_forward / ntt_inverse / their _rows forms on
+ * bit-reversed table-twiddle plans, ntt_inverse_mul, ntt_hmul_tensor and the
+ * forward of ntt_rescale) issues the first half of its rows on cuda_stream
+ * and the second half on a side stream the plan owns, forked from and
+ * joined back to cuda_stream through events: the call keeps stream order
+ * (work queued after it on cuda_stream sees both halves) and is valid under
+ * CUDA graph capture, where it records a fork and a join.  Host threads that
+ * share one plan are serialised while they enqueue such a call, and their
+ * second halves run in order on the plan's side stream.
  */
 int ntt_forward(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, void* cuda_stream);
 int ntt_inverse(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, void* cuda_stream);

@@ -163,6 +163,40 @@ static const OtfEntry* otf_entry(uint32_t log2n) {
     return nullptr;
 }
 
+// Two-kernel schedules end each of their kernels with a partly filled wave,
+// which for batches of a few million coefficients is a visible share of the
+// transform.  Such batches are issued as two halves of their rows: the first
+// on the caller's stream, the second on the plan's side stream, forked from
+// and joined back to the caller's stream through events (so the call keeps
+// stream order, also under graph capture).  The first half's second kernel
+// then runs beside the second half's first kernel and fills its tail.
+#ifndef NTT_SPLIT_MIN_COEFFS
+#define NTT_SPLIT_MIN_COEFFS (3ull << 20)
+#endif
+#ifndef NTT_SPLIT_MAX_COEFFS
+#define NTT_SPLIT_MAX_COEFFS (1ull << 26)
+#endif
+static int launch_rows(ntt_plan_s* p, int idx, LaunchFn fn, const PlanDev& d, const uint64_t* in, uint64_t* out,
+                       uint64_t row_begin, uint64_t n_rows, void* stream) {
+    const uint64_t coeffs = n_rows << p->h.log2n;
+    if (!p->side || g_params[idx].kind != 2 || n_rows < 2 || coeffs < NTT_SPLIT_MIN_COEFFS ||
+        coeffs > NTT_SPLIT_MAX_COEFFS)
+        return fn(d, in, out, row_begin, n_rows, stream, &p->last_launches);
+    std::lock_guard<std::mutex> lock(p->split_mu);
+    cudaStream_t st = (cudaStream_t)stream, side = (cudaStream_t)p->side;
+    const cudaEvent_t fork = (cudaEvent_t)p->ev_fork, join = (cudaEvent_t)p->ev_join;
+    if (cudaEventRecord(fork, st) != cudaSuccess || cudaStreamWaitEvent(side, fork, 0) != cudaSuccess)
+        return NTT_ERR_CUDA;
+    const uint64_t h = n_rows / 2;
+    int rc = fn(d, in, out, row_begin, h, stream, &p->last_launches);
+    if (rc == NTT_OK) rc = fn(d, in, out, row_begin + h, n_rows - h, p->side, &p->last_launches);
+    // joined even after a failed launch, so the caller's stream never runs
+    // ahead of work already queued on the side stream
+    if (cudaEventRecord(join, side) != cudaSuccess || cudaStreamWaitEvent(st, join, 0) != cudaSuccess)
+        return NTT_ERR_CUDA;
+    return rc;
+}
+
 static int transform(ntt_plan_t plan, bool inverse, const uint64_t* in, uint64_t* out,
                      uint64_t row_begin, uint64_t n_rows, void* stream) {
     if (!plan || !in || !out) return NTT_ERR_ARG;
@@ -188,7 +222,7 @@ static int transform(ntt_plan_t plan, bool inverse, const uint64_t* in, uint64_t
     }
     const SchedEntry& e = g_table[idx];
     const LaunchFn fn = inverse ? e.inv : e.fwd;
-    if (!natural(plan)) return fn(d, in, out, row_begin, n_rows, stream, &plan->last_launches);
+    if (!natural(plan)) return launch_rows(plan, idx, fn, d, in, out, row_begin, n_rows, stream);
     // natural order: a one-kernel schedule holds whole rows and permutes in
     // shared memory; two-kernel schedules add a bit-reversal pass over HBM
     if (g_params[idx].kind == 1) {
@@ -223,6 +257,10 @@ static void free_device(ntt_plan_s* p) {
     p->d_status = nullptr;
     p->d_fwd32 = p->d_inv32 = nullptr;
     p->d_consts32 = nullptr;
+    if (p->ev_fork) cudaEventDestroy((cudaEvent_t)p->ev_fork);
+    if (p->ev_join) cudaEventDestroy((cudaEvent_t)p->ev_join);
+    if (p->side) cudaStreamDestroy((cudaStream_t)p->side);     // released once its work has finished
+    p->ev_fork = p->ev_join = p->side = nullptr;
 }
 
 
@@ -293,6 +331,16 @@ int ntt_plan(ntt_plan_t* out, uint32_t log2n, const uint64_t* moduli, uint32_t n
                  cudaMalloc(&p->d_otf_inv, otf_bytes) == cudaSuccess &&
                  cudaMemcpy(p->d_otf_fwd, p->h.otf_fwd.data(), otf_bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
                  cudaMemcpy(p->d_otf_inv, p->h.otf_inv.data(), otf_bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+        }
+        if (ok) {
+            cudaStream_t side = nullptr;
+            cudaEvent_t fork = nullptr, join = nullptr;
+            ok = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) == cudaSuccess;
+            p->side = side;
+            ok = ok && cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess;
+            p->ev_fork = fork;
+            ok = ok && cudaEventCreateWithFlags(&join, cudaEventDisableTiming) == cudaSuccess;
+            p->ev_join = join;
         }
         if (!ok) {
             free_device(p);
@@ -454,7 +502,7 @@ int ntt_hmul_tensor(ntt_plan_t plan, const uint64_t* d_a, const uint64_t* d_b, u
     d.src_mode = 1;
     d.in_b = d_b;
     d.lc = plan->d_consts_mont;     // Montgomery products: the last stage scales by N^-1 2^64
-    return g_table[idx].inv(d, d_a, d_out, 0, 3ull * plan->h.n_moduli, cuda_stream, &plan->last_launches);
+    return launch_rows(plan, idx, g_table[idx].inv, d, d_a, d_out, 0, 3ull * plan->h.n_moduli, cuda_stream);
 }
 
 int ntt_inverse_mul(ntt_plan_t plan, const uint64_t* d_a, const uint32_t* a_poly, uint32_t a_polys,
@@ -497,7 +545,7 @@ int ntt_inverse_mul(ntt_plan_t plan, const uint64_t* d_a, const uint32_t* a_poly
     d.src_mode = 3;
     d.in_b = d_b;
     d.lc = plan->d_consts_mont;     // Montgomery products: the last stage scales by N^-1 2^64
-    return g_table[idx].inv(d, d_a, d_out, 0, plan->h.rows, cuda_stream, &plan->last_launches);
+    return launch_rows(plan, idx, g_table[idx].inv, d, d_a, d_out, 0, plan->h.rows, cuda_stream);
 }
 
 int ntt_rescale(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, uint64_t* d_work, uint32_t n_polys,
@@ -557,7 +605,7 @@ int ntt_rescale(ntt_plan_t plan, const uint64_t* d_in, uint64_t* d_out, uint64_t
     d.src_mode = 2;
     d.in_b = d_in;
     d.aux_q = plan->h.moduli[L - 1];
-    return g_table[idx].fwd(d, d_work, d_out, 0, (uint64_t)n_polys * (L - 1), cuda_stream, &plan->last_launches);
+    return launch_rows(plan, idx, g_table[idx].fwd, d, d_work, d_out, 0, (uint64_t)n_polys * (L - 1), cuda_stream);
 }
 
 int poly_mul_pointwise(ntt_plan_t plan, const uint64_t* d_a, const uint64_t* d_b, uint64_t* d_c,

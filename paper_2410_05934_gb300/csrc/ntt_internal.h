@@ -2,6 +2,7 @@
 // the kernel launchers and the host emulation.  Not part of the public ABI.
 #pragma once
 #include <stdint.h>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -71,4 +72,12 @@ struct ntt_plan_s {
     nttgb::TwPair* d_otf_inv = nullptr;
     uint32_t schedule = 0;
     uint32_t last_launches = 0;
+    // the two-stream row split of two-kernel schedules (device plans of
+    // 64-bit words): a non-blocking side stream and its fork / join events
+    // (cudaStream_t / cudaEvent_t), and the lock that keeps one call's
+    // record / wait pairs together when several host threads share the plan
+    void* side = nullptr;
+    void* ev_fork = nullptr;
+    void* ev_join = nullptr;
+    std::mutex split_mu;
 };

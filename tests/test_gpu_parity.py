@@ -614,3 +614,56 @@ def test_forward_inverse_64_bit_two_phases_and_fallback(oracle, log2n):
     p62.forward(d62, sf[:2])
     assert torch.equal(o62, sf[:2])
     assert pf.status() == 0 and pi.status() == 0 and p62.status() == 0
+
+
+@pytest.mark.gpu
+def test_two_stream_row_split_parity_and_graph_capture(oracle):
+    """A two-kernel batch inside the split window (N = 2^16, 48 rows: 3.1 M
+    coefficients) runs as two row halves on the caller's stream and the
+    plan's side stream: sampled outputs against the oracle, equality with
+    row ranges below the window (issued unsplit), the inverse round trip,
+    the fused-product inverse against pointwise + inverse, and the same
+    transform captured in a CUDA graph and replayed."""
+    log2n, n = 16, 1 << 16
+    mods = [W.POOL50[i] for i in (0, 3, 7, 11)]
+    polys = 12
+    x = W.rows_uniform(61, log2n, mods * polys, n)
+    plan = ntt.Plan(log2n, mods, polys)
+    d = to_dev(x)
+    out = torch.empty_like(d)
+    plan.forward(d, out)
+    assert plan.last_launches() == 4          # two halves x two kernels
+    rows = [0, 5, 23, 24, 25, 47]
+    idx = _sample_idx(n, len(rows), 6, 62)
+    got = to_host(out)[rows][np.arange(len(rows))[:, None], idx]
+    assert np.array_equal(got, oracle.transform_rows(x[rows], [mods[r % 4] for r in rows], idx=idx))
+    parts = torch.empty_like(d)
+    for r0 in range(0, 48, 12):               # 12 rows: 0.79 M coefficients, below the window
+        plan.forward_rows(d, parts, r0, 12)
+        assert plan.last_launches() == 2
+    assert torch.equal(parts, out)
+    back = torch.empty_like(d)
+    plan.inverse(out, back)
+    assert plan.last_launches() == 4 and torch.equal(back, d)
+    b = to_dev(W.rows_uniform(63, log2n, mods * polys, n))
+    fused = torch.empty_like(d)
+    plan.inverse_mul(out, b, fused)
+    prod = torch.empty_like(d)
+    plan.pointwise(out, b, prod)
+    ref = torch.empty_like(d)
+    plan.inverse(prod, ref)
+    assert torch.equal(fused, ref)
+    g_out = torch.zeros_like(d)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        plan.forward(d, g_out)                # warm-up outside the capture
+    torch.cuda.current_stream().wait_stream(side)
+    g_out.zero_()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        plan.forward(d, g_out)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(g_out, out)
+    assert plan.status() == 0
